@@ -1,0 +1,310 @@
+"""Benchmark of the VIE hot path on one GB300 (or N replicas under torchrun).
+
+Workload (one "step"): the 2D heterogeneous 128x128 medium (16384 unknowns,
+sigma_t = 1 + 4 seeded Gaussian bumps, sigma_s = 0.9 sigma_t, bilinear
+sigma_t, tau by a 64-step march, FP32 kernel tiles), Gaussian source at the
+centre: phi = A f, then FP64 GMRES(64) to 1e-6 relative residual, every
+Arnoldi step one on-the-fly operator apply.  The medium's handle (sigma_t
+staging, self-cell diagonal) is built once before timing; inputs sit in HBM.
+
+value  = pairs evaluated per second over the whole job (n_apply * N^2 per
+         step, summed over ranks) in Gpair/s.
+e2e    = the same through the C ABI from host buffers: vie_create from host
+         sigma_t/sigma_s, vie_solve_gmres with host f and host U (copies
+         inside), vie_destroy; per step.
+roofline: the pair kernel, FP32-pipe bound; algorithmic work 13 S + 12
+         FP32 lane operations per pair, peak = SMs x 128 lanes x max clock.
+cpu_baseline: the FP64 oracle's matrix-free apply on a bounded sample of
+         target rows of the same medium, on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import vie_synth as V  # noqa: E402
+
+METRIC = "VIE matvec Gpair/s; GMRES solve ms to 1e-6 rel. residual, plain vs chosen"
+UNIT = "Gpair/s"
+WORKLOAD = "2D heterogeneous 128x128, sigma_t = 1 + 4 seeded bumps, sigma_s = 0.9 sigma_t, S=64 march"
+S_STEPS = 64
+RTOL = 1e-6
+# Pair-kernel traffic per launch from the ncu capture of this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
+# the current kernel.
+PAIR_KERNEL_DRAM_BYTES = None
+
+
+def ops_per_pair(S: int) -> int:
+    """FP32 lane operations the method needs per off-diagonal pair (2D):
+    per march step 2 position FMAs, 2 floor/fraction ops, 2 weight ops,
+    6 for the three lerps and 1 accumulate (13), plus about 12 for r, tau,
+    the kernel weight and the product with the source."""
+    return 13 * S + 12
+
+
+def medium(rank: int):
+    return V.heterogeneous_2d(n=128, seed=V.seed_for(2, rank))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def cpu_baseline_sample(m, seconds: float = 12.0) -> dict:
+    """The oracle's apply on a bounded sample of target rows (host cores)."""
+    import oracle as O
+    g = m.f
+    diag = O.selfcells(2, m.sigma_t)
+    rows = np.arange(0, m.N, 997)[:8]
+    t0 = time.perf_counter()
+    O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows, diag=diag)
+    dt = time.perf_counter() - t0
+    count = int(max(8, min(m.N, len(rows) * seconds / max(dt, 1e-3))))
+    rows = np.linspace(0, m.N - 1, count).astype(np.int64)
+    t0 = time.perf_counter()
+    O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows, diag=diag)
+    dt = time.perf_counter() - t0
+    return {"value": len(rows) * m.N / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(rows)} target rows x {m.N} sources of the 128x128 medium, "
+                      f"S={S_STEPS}, FP64 matrix-free apply ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    m = medium(0)
+    diag = O.selfcells(2, m.sigma_t)
+    per_step_rows = 24
+    stride = m.N // per_step_rows
+    times = []
+    for it in range(args.warmup + args.steps):
+        rows = (np.arange(per_step_rows) * stride + it) % m.N
+        t0 = time.perf_counter()
+        O.apply(2, m.sigma_t, m.sigma_s, m.f, rows=rows, diag=diag)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step_rows * m.N * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; oracle apply on 24 target rows per step",
+                   "l2": "not applicable (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{per_step_rows} target rows x {m.N} sources per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1610_00835_gb300 as P
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    P.load()
+    m = medium(rank)
+    N = m.N
+    h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS, device=local)
+    f_dev = torch.as_tensor(m.f, dtype=torch.float64, device=f"cuda:{local}")
+    U = torch.empty(N, dtype=torch.float64, device=f"cuda:{local}")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        P.vie_solve_gmres(h, f_dev, U, rtol=RTOL)
+    torch.cuda.synchronize()
+    launches0 = P.vie_kernel_launches()
+    step_ms, reps = [], []
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            barrier()
+            start.record(stream)
+            rep = P.vie_solve_gmres(h, f_dev, U, rtol=RTOL, time_apply=True)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(start.elapsed_time(stop))
+            reps.append(rep)
+    launches = P.vie_kernel_launches() - launches0
+    total_ms = sum(step_ms)
+    pairs = sum(r["n_apply"] for r in reps) * float(N) * N
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        p = torch.tensor([pairs], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        pairs = float(p.item())
+    value = pairs / (total_ms * 1e-3) / 1e9
+
+    # roofline of the pair kernel, from the per-launch CUDA events of the timed steps
+    n_apply = sum(r["n_apply"] for r in reps)
+    kern_ms = sum(r["t_apply_kernel_ms"] for r in reps) / n_apply
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    clocks = clk.summary()
+    max_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak = sms * 128 * max_mhz * 1e6 / 1e12                     # Tops/s at max clock
+    ops = ops_per_pair(S_STEPS) * float(N) * (N - 1)             # per launch
+    achieved = ops / (kern_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES,
+                "kernel": "k_pairs_f32<2,smem,S=64>", "kernel_ms": kern_ms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max clock)"}
+    if clocks["sm_mhz"]:
+        roofline["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the C ABI from host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    U_host = np.zeros(N)
+    t_e2e = []
+    for _ in range(e2e_steps):
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        he = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS, device=local)
+        rep_e = P.vie_solve_gmres(he, m.f, U_host, rtol=RTOL)
+        P.vie_destroy(he)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_pairs = rep_e["n_apply"] * float(N) * N * e2e_steps
+    e2e = {"value": e2e_pairs / sum(t_e2e) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": N * 8}
+
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline_sample(m) if world == 1 else None
+        last = reps[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 tiles / f64 krylov",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "S": S_STEPS, "rtol": RTOL,
+                       "solver": "plain: FP64 GMRES(64), on-the-fly FP32 operator",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "solve": {"iters": last["iters"], "n_apply": last["n_apply"],
+                      "relres": last["relres"], "solve_ms_plain": total_ms / args.steps,
+                      "apply_ms": sum(r["t_apply_ms"] for r in reps) / n_apply},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    P.vie_destroy(h)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

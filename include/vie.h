@@ -1,0 +1,185 @@
+/*
+ * vie.h -- C ABI of the GB300 (sm_103a) volume-integral-equation library.
+ *
+ * The library implements the hot path of the two-step method of Ren, Zhang
+ * & Zhong for the radiative transfer equation in isotropic media
+ * (arXiv 1610.00835):
+ *
+ *   * the operator of Section 2, Eqs. EQ:Operator K and EQ:Kernel,
+ *       (K g)(x) = int K(x,y) g(y) dy,
+ *       K(x,y)   = sigma_s(y) exp(-tau(x,y)) / (|S^{d-1}| |x-y|^{d-1}),
+ *     with tau(x,y) the line integral of sigma_t along the segment x -> y,
+ *     discretised by piecewise-constant collocation on a uniform grid
+ *     (Section 3.1) with approach M-iii of Section 3.2 (off-diagonal entries
+ *     |T_k| K(x_j, x_k), the self cell integrated explicitly);
+ *   * GMRES for (I - K) U = phi, phi = K(sigma_s^{-1} f) (Eq. EQ:ERT Intgrl
+ *     FMM; Algorithm 1, S.2);
+ *   * the scattering-free sweep that recovers Phi(x, v) from U
+ *     (Algorithm 1, S.3; Eq. EQ:ERT Intgrl).
+ *
+ * Conventions shared by every entry point:
+ *   - Domain (0,1)^d, d = 2 or 3, n cells per side, h = 1/n, N = n^d cells,
+ *     cell centres x_j = (i + 1/2) h, linear index j = ix + n*iy (+ n^2*iz),
+ *     x fastest (Section 3.1, uniform grid).
+ *   - sigma_t is interpolated between cell centres bilinearly (2D) or
+ *     trilinearly (3D), clamped to the hull of the centres.
+ *   - tau is the S-step midpoint march
+ *       tau = (r/S) sum_{i=0}^{S-1} sigma_t~(x + (i+1/2)/S (y - x)),
+ *     or sigma_t r for homogeneous media (Eq. EQ:Kernel Cons).
+ *   - A_jk = h^d exp(-tau_jk) / (|S^{d-1}| r_jk^{d-1}) for j != k and the
+ *     self-cell integral d_j = int_{T_j} e^{-sigma_t,j |z|} / (|S^{d-1}|
+ *     |z|^{d-1}) dz for j == k; K_jk = A_jk sigma_s,k.  |S^1| = 2 pi,
+ *     |S^2| = 4 pi.
+ *   - Every call returns a vie_status; on failure vie_last_error() gives a
+ *     message (thread-local).  No C++ exception crosses this boundary.
+ *   - Vectors (g, y, f, U, Phi) may be host or device pointers; the library
+ *     detects which.  Device pointers stay owned by the caller and work is
+ *     queued on the caller's stream (asynchronous unless stated).  Host
+ *     pointers are copied through library-owned device buffers and the call
+ *     returns after the copy back (synchronous).
+ *   - The handle owns all device memory it allocates; vie_destroy frees it.
+ *     A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VIE_OK = 0,
+  VIE_ERR_INVALID_ARG = 1,  /* bad size, pointer, option or coefficient   */
+  VIE_ERR_CUDA = 2,         /* a CUDA runtime call failed                 */
+  VIE_ERR_OOM = 3,          /* device allocation failed                   */
+  VIE_ERR_NOT_CONVERGED = 4,/* GMRES hit maxit; U and the report are valid */
+  VIE_ERR_TIMEOUT = 5,      /* a device-side bounded wait gave up         */
+  VIE_ERR_NONFINITE = 6,    /* NaN or Inf in an input or a residual       */
+  VIE_ERR_UNSUPPORTED = 7   /* option combination not built               */
+} vie_status;
+
+/* Uniform grid on the unit square (dim 2) or cube (dim 3), n cells per side.
+ * Section 3.1 (uniform grid, centroid collocation points). */
+typedef struct {
+  int dim; /* 2 or 3                       */
+  int n;   /* cells per side, 1 <= n <= 4096 (2D), 1 <= n <= 256 (3D) */
+} vie_grid;
+
+enum { VIE_TAU_MARCH = 0, VIE_TAU_CLOSED = 1 };
+enum { VIE_PREC_FP32 = 0, VIE_PREC_FP64 = 1 };
+
+typedef struct {
+  int steps;     /* S, midpoint-march steps for tau (>= 1; 64 by default)   */
+  int tau_mode;  /* VIE_TAU_MARCH, or VIE_TAU_CLOSED (needs constant sigma_t) */
+  int precision; /* VIE_PREC_FP32: FP32 kernel tiles, FP64 sums across tiles;
+                    VIE_PREC_FP64: every pair in FP64                        */
+  int device;    /* CUDA device ordinal                                     */
+} vie_opts;
+
+/* Default options: S = 64, march, FP32 tiles, device 0. */
+void vie_default_opts(vie_opts *o);
+
+typedef struct vie_handle vie_handle;
+
+/* Create an operator for one medium (Section 3.1-3.2).
+ *   g        : grid.
+ *   sigma_t  : host FP64 [N], total attenuation mu at the cell centres, >= 0.
+ *   sigma_s  : host FP64 [N], scattering coefficient mu_s, >= 0.
+ *   o        : options (NULL: defaults).
+ * Both arrays are copied; the caller keeps ownership.  The self-cell
+ * diagonal d_j is computed on the device here (FP64 Gauss-Legendre).
+ * Errors: INVALID_ARG (sizes, negative coefficient, non-constant sigma_t
+ * with VIE_TAU_CLOSED), NONFINITE, OOM, CUDA. */
+vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t,
+                      const double *sigma_s, const vie_opts *o);
+
+/* Free every device buffer of the handle (after synchronising its device).
+ * NULL is accepted. */
+vie_status vie_destroy(vie_handle *h);
+
+typedef enum {
+  VIE_OP_K_SIGMA_S = 0, /* y = K g,        K_jk = A_jk sigma_s,k           */
+  VIE_OP_I_MINUS_K = 1, /* y = g - K g     (Eq. EQ: LINEAR SYSTEM)          */
+  VIE_OP_A_RAW = 2      /* y = A g         (phi = A f, Eq. EQ:ERT Intgrl FMM) */
+} vie_op;
+
+/* Apply the discrete operator (Section 3.2, Eq. EQ: DISCRETIZED; Section 3.3:
+ * "the main computational cost ... the evaluations of K U").
+ *   g, y   : FP64 [nrhs][N] (RHS r at offset r*N), host or device; g and y
+ *            must not overlap.
+ *   nrhs   : >= 1.
+ *   stream : cudaStream_t (NULL: legacy default stream).
+ * Errors: INVALID_ARG, CUDA. */
+vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int nrhs,
+                     void *stream);
+
+typedef struct {
+  double rtol;  /* stop when ||phi - (I-K)U||_2 / ||phi||_2 <= rtol (FP64)   */
+  int restart;  /* m, Krylov dimension per cycle (1..256; 64 by default)    */
+  int maxit;    /* total Arnoldi steps allowed (default 1000)               */
+  int zero_x0;  /* 1: ignore U on entry and start from U = 0               */
+  int rhs_is_phi; /* 1: f already holds phi; 0: phi = A f is formed here     */
+  int time_apply; /* 1: record CUDA events around every operator apply      */
+} vie_gmres_opts;
+
+void vie_default_gmres_opts(vie_gmres_opts *o);
+
+typedef struct {
+  int iters;           /* Arnoldi steps taken                                 */
+  int restarts;        /* completed restart cycles                            */
+  int converged;       /* 1 if relres <= rtol                                 */
+  int n_apply;         /* operator applications (including phi and residuals) */
+  double relres;       /* final true relative residual, FP64                  */
+  double relres_est;   /* last Givens residual estimate                       */
+  double t_total_ms;   /* host wall time of the call                          */
+  double t_apply_ms;   /* summed CUDA-event time of the applies (time_apply)  */
+  double t_apply_kernel_ms; /* of that, the pair kernel alone (time_apply)     */
+} vie_report;
+
+/* Solve (I - K) U = phi by restarted GMRES(m) in FP64 (Algorithm 1, S.2;
+ * Section 5: GMRES).  Arnoldi with classical Gram-Schmidt applied twice,
+ * Givens rotations and the triangular solve run on the device in FP64; the
+ * operator is applied with the handle's precision; convergence is judged
+ * on the FP64 true residual.
+ *   f      : FP64 [N] source f (or phi if rhs_is_phi), host or device.
+ *   U      : FP64 [N] initial guess on entry (unless zero_x0), solution on exit.
+ *   rep    : may be NULL.
+ * The call synchronises the stream once per Arnoldi step (residual test).
+ * Returns NOT_CONVERGED (U and rep valid) when maxit is reached. */
+vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U,
+                           const vie_gmres_opts *o, vie_report *rep, void *stream);
+
+/* Step two (Algorithm 1, S.3): Q = sigma_s U + f, then for every direction
+ * v_m and cell x_j the backward characteristic of Eq. EQ:ERT Intgrl,
+ *   Phi(x_j, v_m) = int_0^L exp(-int_0^l sigma_t(x_j - l' v_m) dl') Q(x_j - l v_m) dl,
+ * L the distance to the boundary along -v_m.  The ray is cut into
+ * ceil(2 n L - 1e-6) equal steps (each <= h/2, decided in FP64); on each
+ * step sigma_t and Q (interpolated like sigma_t) are frozen at the step
+ * midpoint and the step is integrated exactly.
+ *   U, f : FP64 [N], host or device.
+ *   dirs : FP32 [M][dim] unit vectors, host or device.
+ *   Phi  : FP32 [M][N], host or device.
+ * Errors: INVALID_ARG, CUDA. */
+vie_status ert_sweep(vie_handle *h, const double *U, const double *f, const float *dirs,
+                     int M, float *Phi, void *stream);
+
+/* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
+vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *vie_last_error(void);
+
+/* Library version string. */
+const char *vie_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles, all devices); a diagnostic for benchmarks. */
+unsigned long long vie_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H */

@@ -1,0 +1,639 @@
+// C ABI of the VIE library: handle management, operator apply, the FP64
+// GMRES driver (Algorithm 1, S.2) and the step-two sweep (Algorithm 1, S.3).
+// Everything numeric runs in the kernels of k_apply.cu, k_krylov.cu and
+// k_sweep.cu; this file validates arguments, owns device memory, stages host
+// buffers and sequences launches on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+vie_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+}
+
+static vie_status invalid(const std::string &msg) {
+  set_error(msg);
+  return VIE_ERR_INVALID_ARG;
+}
+
+// Select the handle's device for the duration of a call, then restore the
+// caller's current device.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static vie_status dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return VIE_OK;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  return VIE_OK;
+}
+
+template <typename T>
+static void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+// A growable device buffer.
+template <typename T>
+struct DBuf {
+  T *ptr = nullptr;
+  size_t count = 0;
+  vie_status reserve(size_t want) {
+    if (want <= count) return VIE_OK;
+    dfree(ptr);
+    count = 0;
+    vie_status s = dalloc(&ptr, want);
+    if (s == VIE_OK) count = want;
+    return s;
+  }
+  void release() {
+    dfree(ptr);
+    count = 0;
+  }
+};
+
+// Events around one operator apply: [0] start, [1] before the pair kernel,
+// [2] after it, [3] end.
+struct ApplyEvents {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool pending = false;
+};
+
+}  // namespace vie
+
+using namespace vie;
+
+struct vie_handle {
+  int device = 0;
+  int dim = 2, n = 1, P = 2;
+  long N = 1;
+  vie_opts opts{};
+  double *sig_t = nullptr, *sig_s = nullptr;  // FP64 [N]
+  float *sig32 = nullptr;                     // padded FP32 lattice
+  double *sig64 = nullptr;                    // padded FP64 lattice
+  double *diag = nullptr;                     // self-cell d_j [N]
+  Medium med{};
+  PairPlan plan{};
+  void *src = nullptr;                        // per-source values [N]
+  double *partial = nullptr;                  // [plan.splits][N]
+  DBuf<double> stage_a, stage_b, stage_c;     // host-pointer staging
+  DBuf<float> stage_f1, stage_f2;
+  float *qpad = nullptr;                      // sweep source lattice
+  // GMRES workspace
+  int gm_m = 0;
+  double *V = nullptr, *phi = nullptr, *r = nullptr, *w = nullptr, *H = nullptr;
+  double *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr, *hcol = nullptr;
+  double *htmp = nullptr, *part = nullptr, *scal = nullptr;
+  double *h_pinned = nullptr;                 // host-pinned scalars / gv seed
+  // apply timing
+  std::vector<ApplyEvents> events;
+  size_t ev_next = 0;
+  double t_apply_ms = 0.0, t_kernel_ms = 0.0;
+  int n_apply = 0;
+};
+
+namespace {
+
+void free_gmres(vie_handle *h) {
+  dfree(h->V);
+  dfree(h->phi);
+  dfree(h->r);
+  dfree(h->w);
+  dfree(h->H);
+  dfree(h->cs);
+  dfree(h->sn);
+  dfree(h->gv);
+  dfree(h->yv);
+  dfree(h->hcol);
+  dfree(h->htmp);
+  dfree(h->part);
+  dfree(h->scal);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  h->h_pinned = nullptr;
+  h->gm_m = 0;
+}
+
+void free_all(vie_handle *h) {
+  dfree(h->sig_t);
+  dfree(h->sig_s);
+  dfree(h->sig32);
+  dfree(h->sig64);
+  dfree(h->diag);
+  if (h->src) cudaFree(h->src);
+  h->src = nullptr;
+  dfree(h->partial);
+  h->stage_a.release();
+  h->stage_b.release();
+  h->stage_c.release();
+  h->stage_f1.release();
+  h->stage_f2.release();
+  dfree(h->qpad);
+  free_gmres(h);
+  for (auto &ev : h->events)
+    for (auto &e : ev.e)
+      if (e) cudaEventDestroy(e);
+  h->events.clear();
+}
+
+vie_status ensure_gmres(vie_handle *h, int m) {
+  if (h->gm_m >= m) return VIE_OK;
+  free_gmres(h);
+  const long N = h->N;
+  const int blocks = dot_blocks(N);
+  vie_status s;
+  if ((s = dalloc(&h->V, (size_t)(m + 1) * N)) != VIE_OK) return s;
+  if ((s = dalloc(&h->phi, N)) != VIE_OK) return s;
+  if ((s = dalloc(&h->r, N)) != VIE_OK) return s;
+  if ((s = dalloc(&h->w, N)) != VIE_OK) return s;
+  if ((s = dalloc(&h->H, (size_t)(m + 1) * m)) != VIE_OK) return s;
+  if ((s = dalloc(&h->cs, m)) != VIE_OK) return s;
+  if ((s = dalloc(&h->sn, m)) != VIE_OK) return s;
+  if ((s = dalloc(&h->gv, m + 1)) != VIE_OK) return s;
+  if ((s = dalloc(&h->yv, m)) != VIE_OK) return s;
+  if ((s = dalloc(&h->hcol, m + 1)) != VIE_OK) return s;
+  if ((s = dalloc(&h->htmp, m + 1)) != VIE_OK) return s;
+  if ((s = dalloc(&h->part, (size_t)blocks * (m + 1))) != VIE_OK) return s;
+  if ((s = dalloc(&h->scal, 8)) != VIE_OK) return s;
+  VIE_CUDA(cudaMallocHost((void **)&h->h_pinned, sizeof(double) * (m + 1 + 8)));
+  h->gm_m = m;
+  return VIE_OK;
+}
+
+vie_status harvest_events(vie_handle *h) {
+  for (auto &ev : h->events) {
+    if (!ev.pending) continue;
+    VIE_CUDA(cudaEventSynchronize(ev.e[3]));
+    float a = 0.f, k = 0.f;
+    VIE_CUDA(cudaEventElapsedTime(&a, ev.e[0], ev.e[3]));
+    VIE_CUDA(cudaEventElapsedTime(&k, ev.e[1], ev.e[2]));
+    h->t_apply_ms += a;
+    h->t_kernel_ms += k;
+    ev.pending = false;
+  }
+  return VIE_OK;
+}
+
+// One operator application on device vectors.
+vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStream_t st,
+                     bool timed) {
+  ApplyEvents *ev = nullptr;
+  if (timed) {
+    if (h->events.empty()) {
+      h->events.resize(8);
+      for (auto &e : h->events)
+        for (auto &x : e.e) VIE_CUDA(cudaEventCreate(&x));
+    }
+    ev = &h->events[h->ev_next];
+    if (ev->pending) {
+      vie_status s = harvest_events(h);
+      if (s != VIE_OK) return s;
+    }
+    h->ev_next = (h->ev_next + 1) % h->events.size();
+    VIE_CUDA(cudaEventRecord(ev->e[0], st));
+  }
+  const int prec = h->opts.precision;
+  const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
+  vie_status s = launch_source_prep(h->N, op, h->sig_s, g, prec, h->src, st);
+  if (s != VIE_OK) return s;
+  if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
+  s = launch_pairs(h->med, h->plan, h->opts.steps, closed, prec, h->src, h->partial, st);
+  if (s != VIE_OK) return s;
+  if (timed) VIE_CUDA(cudaEventRecord(ev->e[2], st));
+  s = launch_reduce(h->N, h->plan.splits, op, h->partial, h->diag, h->sig_s, g, y, st);
+  if (s != VIE_OK) return s;
+  if (timed) {
+    VIE_CUDA(cudaEventRecord(ev->e[3], st));
+    ev->pending = true;
+  }
+  h->n_apply++;
+  return VIE_OK;
+}
+
+// ||x||^2 into dev scalar *out (part: dot partials buffer).
+vie_status norm2_dev(vie_handle *h, const double *x, double *out, cudaStream_t st) {
+  const int blocks = dot_blocks(h->N);
+  vie_status s = launch_dots(x, 1, h->N, x, h->N, h->part, blocks, st);
+  if (s != VIE_OK) return s;
+  return launch_dots_finish(h->part, blocks, 1, out, 0, st);
+}
+
+vie_status read_scalar(vie_handle *h, const double *dev, double *val, cudaStream_t st) {
+  VIE_CUDA(cudaMemcpyAsync(h->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  *val = h->h_pinned[0];
+  return VIE_OK;
+}
+
+bool all_finite(const double *a, long n) {
+  for (long i = 0; i < n; ++i)
+    if (!isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vie_last_error(void) { return g_last_error.c_str(); }
+
+const char *vie_version(void) { return "vie-gb300 0.1 (sm_103a)"; }
+
+unsigned long long vie_kernel_launches(void) { return g_launches.load(); }
+
+void vie_default_opts(vie_opts *o) {
+  if (!o) return;
+  o->steps = 64;
+  o->tau_mode = VIE_TAU_MARCH;
+  o->precision = VIE_PREC_FP32;
+  o->device = 0;
+}
+
+void vie_default_gmres_opts(vie_gmres_opts *o) {
+  if (!o) return;
+  o->rtol = 1e-6;
+  o->restart = 64;
+  o->maxit = 1000;
+  o->zero_x0 = 1;
+  o->rhs_is_phi = 0;
+  o->time_apply = 0;
+}
+
+vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t,
+                      const double *sigma_s, const vie_opts *o) {
+  g_last_error.clear();
+  if (!out || !g || !sigma_t || !sigma_s) return invalid("vie_create: NULL argument");
+  *out = nullptr;
+  vie_opts opts;
+  vie_default_opts(&opts);
+  if (o) opts = *o;
+  if (g->dim != 2 && g->dim != 3) return invalid("vie_create: dim must be 2 or 3");
+  if (g->n < 1 || (g->dim == 2 && g->n > 4096) || (g->dim == 3 && g->n > 256))
+    return invalid("vie_create: n out of range (2D: 1..4096, 3D: 1..256)");
+  if (opts.steps < 1 || opts.steps > 4096) return invalid("vie_create: steps must be in 1..4096");
+  if (opts.tau_mode != VIE_TAU_MARCH && opts.tau_mode != VIE_TAU_CLOSED)
+    return invalid("vie_create: unknown tau_mode");
+  if (opts.precision != VIE_PREC_FP32 && opts.precision != VIE_PREC_FP64)
+    return invalid("vie_create: unknown precision");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("vie_create: no CUDA device");
+    return VIE_ERR_CUDA;
+  }
+  if (opts.device < 0 || opts.device >= ndev) return invalid("vie_create: bad device ordinal");
+  const long N = g->dim == 2 ? (long)g->n * g->n : (long)g->n * g->n * g->n;
+  if (is_device_ptr(sigma_t) || is_device_ptr(sigma_s))
+    return invalid("vie_create: sigma_t and sigma_s must be host arrays");
+  for (long i = 0; i < N; ++i) {
+    if (!isfinite(sigma_t[i]) || !isfinite(sigma_s[i])) {
+      set_error("vie_create: non-finite coefficient");
+      return VIE_ERR_NONFINITE;
+    }
+    if (sigma_t[i] < 0.0 || sigma_s[i] < 0.0) return invalid("vie_create: negative coefficient");
+    if (opts.tau_mode == VIE_TAU_CLOSED && sigma_t[i] != sigma_t[0])
+      return invalid("vie_create: VIE_TAU_CLOSED needs a constant sigma_t");
+  }
+  DeviceGuard dg(opts.device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  vie_handle *h = new vie_handle();
+  h->device = opts.device;
+  h->dim = g->dim;
+  h->n = g->n;
+  h->P = g->n + 1;
+  h->N = N;
+  h->opts = opts;
+  const long lattice = g->dim == 2 ? (long)h->P * h->P : (long)h->P * h->P * h->P;
+  vie_status s;
+#define TRY(x)            \
+  do {                    \
+    s = (x);              \
+    if (s != VIE_OK) {    \
+      free_all(h);        \
+      delete h;           \
+      return s;           \
+    }                     \
+  } while (0)
+  TRY(dalloc(&h->sig_t, N));
+  TRY(dalloc(&h->sig_s, N));
+  TRY(dalloc(&h->sig32, lattice));
+  TRY(dalloc(&h->sig64, lattice));
+  TRY(dalloc(&h->diag, N));
+  cudaStream_t st = 0;
+  auto cpy = [&](void *d, const void *src, size_t bytes) -> vie_status {
+    VIE_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+    return VIE_OK;
+  };
+  TRY(cpy(h->sig_t, sigma_t, sizeof(double) * N));
+  TRY(cpy(h->sig_s, sigma_s, sizeof(double) * N));
+  TRY(launch_pad_sigma(g->dim, g->n, h->sig_t, h->sig32, h->sig64, st));
+  TRY(launch_selfcell(g->dim, g->n, h->sig_t, h->diag, st));
+  h->med.dim = g->dim;
+  h->med.n = g->n;
+  h->med.P = h->P;
+  h->med.N = N;
+  h->med.sig32 = h->sig32;
+  h->med.sig64 = h->sig64;
+  h->med.sigma_c = (float)sigma_t[0];
+  TRY(plan_pairs(h->med, opts.steps, opts.tau_mode == VIE_TAU_CLOSED, opts.precision,
+                 opts.device, &h->plan));
+  {
+    size_t bytes = (opts.precision == VIE_PREC_FP64 ? sizeof(double) : sizeof(float)) * N;
+    cudaError_t e = cudaMalloc(&h->src, bytes);
+    if (e != cudaSuccess) TRY(cuda_fail(e, "cudaMalloc"));
+  }
+  TRY(dalloc(&h->partial, (size_t)h->plan.splits * N));
+  {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) TRY(cuda_fail(e, "vie_create setup kernels"));
+  }
+#undef TRY
+  *out = h;
+  return VIE_OK;
+}
+
+vie_status vie_destroy(vie_handle *h) {
+  if (!h) return VIE_OK;
+  DeviceGuard dg(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return VIE_OK;
+}
+
+vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream) {
+  if (!h || !d) return invalid("vie_get_diagonal: NULL argument");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (is_device_ptr(d)) {
+    VIE_CUDA(cudaMemcpyAsync(d, h->diag, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, st));
+  } else {
+    VIE_CUDA(cudaMemcpyAsync(d, h->diag, sizeof(double) * h->N, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
+  return VIE_OK;
+}
+
+vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int nrhs,
+                     void *stream) {
+  if (!h || !g || !y) return invalid("vie_apply: NULL argument");
+  if (op != VIE_OP_K_SIGMA_S && op != VIE_OP_I_MINUS_K && op != VIE_OP_A_RAW)
+    return invalid("vie_apply: unknown op");
+  if (nrhs < 1) return invalid("vie_apply: nrhs must be >= 1");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long N = h->N;
+  const size_t total = (size_t)nrhs * N;
+  const bool gd = is_device_ptr(g), yd = is_device_ptr(y);
+  const double *gg = g;
+  double *yy = y;
+  vie_status s;
+  if (!gd) {
+    if ((s = h->stage_a.reserve(total)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, g, sizeof(double) * total, cudaMemcpyHostToDevice, st));
+    gg = h->stage_a.ptr;
+  }
+  if (!yd) {
+    if ((s = h->stage_b.reserve(total)) != VIE_OK) return s;
+    yy = h->stage_b.ptr;
+  }
+  for (int r = 0; r < nrhs; ++r)
+    if ((s = apply_dev(h, op, gg + (size_t)r * N, yy + (size_t)r * N, st, false)) != VIE_OK)
+      return s;
+  if (!yd) {
+    VIE_CUDA(cudaMemcpyAsync(y, yy, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
+  return VIE_OK;
+}
+
+vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_gmres_opts *o,
+                           vie_report *rep, void *stream) {
+  if (!h || !f || !U) return invalid("vie_solve_gmres: NULL argument");
+  vie_gmres_opts opt;
+  vie_default_gmres_opts(&opt);
+  if (o) opt = *o;
+  if (!(opt.rtol > 0.0) || opt.restart < 1 || opt.restart > 256 || opt.maxit < 1)
+    return invalid("vie_solve_gmres: rtol > 0, 1 <= restart <= 256, maxit >= 1 required");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const long N = h->N;
+  const int m = opt.restart;
+  vie_status s;
+  if ((s = ensure_gmres(h, m)) != VIE_OK) return s;
+  h->t_apply_ms = h->t_kernel_ms = 0.0;
+  h->n_apply = 0;
+  const bool timed = opt.time_apply != 0;
+  const bool fd = is_device_ptr(f), ud = is_device_ptr(U);
+  const double *fdev = f;
+  double *x = U;
+  if (!fd) {
+    if ((s = h->stage_a.reserve(N)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, f, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    fdev = h->stage_a.ptr;
+  }
+  if (!ud) {
+    if ((s = h->stage_b.reserve(N)) != VIE_OK) return s;
+    x = h->stage_b.ptr;
+    if (!opt.zero_x0)
+      VIE_CUDA(cudaMemcpyAsync(x, U, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  }
+  if (opt.zero_x0) VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+  // phi = A f (Eq. EQ:ERT Intgrl FMM), unless the caller passed phi.
+  if (opt.rhs_is_phi) {
+    VIE_CUDA(cudaMemcpyAsync(h->phi, fdev, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  } else if ((s = apply_dev(h, VIE_OP_A_RAW, fdev, h->phi, st, timed)) != VIE_OK) {
+    return s;
+  }
+  double bn2 = 0.0;
+  if ((s = norm2_dev(h, h->phi, h->scal, st)) != VIE_OK) return s;
+  if ((s = read_scalar(h, h->scal, &bn2, st)) != VIE_OK) return s;
+  if (!isfinite(bn2)) {
+    set_error("vie_solve_gmres: non-finite right-hand side");
+    return VIE_ERR_NONFINITE;
+  }
+  const double bnorm = sqrt(bn2);
+  vie_report R{};
+  R.relres = 0.0;
+  R.relres_est = 0.0;
+  bool converged = false;
+  if (bnorm == 0.0) {
+    VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+    converged = true;
+  }
+  const int blocks = dot_blocks(N);
+  bool x_is_zero = opt.zero_x0 != 0;
+  while (!converged) {
+    // true residual r = phi - (I - K) x
+    if (x_is_zero) {
+      VIE_CUDA(cudaMemcpyAsync(h->r, h->phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    } else {
+      if ((s = apply_dev(h, VIE_OP_I_MINUS_K, x, h->w, st, timed)) != VIE_OK) return s;
+      if ((s = launch_axpby(1.0, h->phi, -1.0, h->w, h->r, N, st)) != VIE_OK) return s;
+    }
+    x_is_zero = false;
+    double rn2 = 0.0;
+    if ((s = norm2_dev(h, h->r, h->scal + 1, st)) != VIE_OK) return s;
+    if ((s = read_scalar(h, h->scal + 1, &rn2, st)) != VIE_OK) return s;
+    if (!isfinite(rn2)) {
+      set_error("vie_solve_gmres: non-finite residual");
+      return VIE_ERR_NONFINITE;
+    }
+    const double beta = sqrt(rn2);
+    R.relres = beta / bnorm;
+    if (R.relres <= opt.rtol) {
+      converged = true;
+      break;
+    }
+    if (R.iters >= opt.maxit) break;
+    // V_0 = r / beta, gv = beta e_1
+    if ((s = launch_scale(h->r, h->scal + 1, 1, h->V, N, st)) != VIE_OK) return s;
+    for (int i = 0; i <= m; ++i) h->h_pinned[i] = 0.0;
+    h->h_pinned[0] = beta;
+    VIE_CUDA(cudaMemcpyAsync(h->gv, h->h_pinned, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+    int k = 0;
+    while (k < m && R.iters < opt.maxit) {
+      double *vk = h->V + (size_t)k * N;
+      double *vk1 = h->V + (size_t)(k + 1) * N;
+      if ((s = apply_dev(h, VIE_OP_I_MINUS_K, vk, vk1, st, timed)) != VIE_OK) return s;
+      // CGS2: two passes of h = V^T w, w -= V h; hcol accumulates both.
+      if ((s = launch_dots(h->V, k + 1, N, vk1, N, h->part, blocks, st)) != VIE_OK) return s;
+      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->hcol, 0, st)) != VIE_OK) return s;
+      if ((s = launch_orth_update(h->V, k + 1, N, h->hcol, vk1, N, st)) != VIE_OK) return s;
+      if ((s = launch_dots(h->V, k + 1, N, vk1, N, h->part, blocks, st)) != VIE_OK) return s;
+      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->htmp, 0, st)) != VIE_OK) return s;
+      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->hcol, 1, st)) != VIE_OK) return s;
+      if ((s = launch_orth_update(h->V, k + 1, N, h->htmp, vk1, N, st)) != VIE_OK) return s;
+      if ((s = norm2_dev(h, vk1, h->scal + 2, st)) != VIE_OK) return s;
+      if ((s = launch_givens(h->H, m, k, h->hcol, h->scal + 2, h->cs, h->sn, h->gv, bnorm,
+                             h->scal + 3, st)) != VIE_OK)
+        return s;
+      if ((s = launch_scale(vk1, h->scal + 2, 1, vk1, N, st)) != VIE_OK) return s;
+      double est = 0.0;
+      if ((s = read_scalar(h, h->scal + 3, &est, st)) != VIE_OK) return s;
+      if (timed && (s = harvest_events(h)) != VIE_OK) return s;
+      ++k;
+      ++R.iters;
+      R.relres_est = est;
+      if (!isfinite(est)) {
+        set_error("vie_solve_gmres: non-finite Arnoldi step");
+        return VIE_ERR_NONFINITE;
+      }
+      if (est <= opt.rtol) break;
+    }
+    if ((s = launch_backsolve(h->H, m, k, h->gv, h->yv, st)) != VIE_OK) return s;
+    if ((s = launch_lincomb_add(h->V, k, N, h->yv, x, N, st)) != VIE_OK) return s;
+    ++R.restarts;
+  }
+  if (!ud) VIE_CUDA(cudaMemcpyAsync(U, x, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (timed && (s = harvest_events(h)) != VIE_OK) return s;
+  R.converged = converged ? 1 : 0;
+  R.n_apply = h->n_apply;
+  R.t_apply_ms = h->t_apply_ms;
+  R.t_apply_kernel_ms = h->t_kernel_ms;
+  R.t_total_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (rep) *rep = R;
+  if (!converged) {
+    set_error("vie_solve_gmres: maxit reached before rtol");
+    return VIE_ERR_NOT_CONVERGED;
+  }
+  return VIE_OK;
+}
+
+vie_status ert_sweep(vie_handle *h, const double *U, const double *f, const float *dirs, int M,
+                     float *Phi, void *stream) {
+  if (!h || !U || !f || !dirs || !Phi) return invalid("ert_sweep: NULL argument");
+  if (M < 1) return invalid("ert_sweep: M must be >= 1");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long N = h->N;
+  vie_status s;
+  const double *Ud = U, *fd = f;
+  const float *dd = dirs;
+  float *Pd = Phi;
+  if (!is_device_ptr(U)) {
+    if ((s = h->stage_a.reserve(N)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, U, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    Ud = h->stage_a.ptr;
+  }
+  if (!is_device_ptr(f)) {
+    if ((s = h->stage_c.reserve(N)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_c.ptr, f, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    fd = h->stage_c.ptr;
+  }
+  if (!is_device_ptr(dirs)) {
+    for (int m = 0; m < M; ++m) {
+      double n2 = 0.0;
+      for (int d = 0; d < h->dim; ++d) n2 += (double)dirs[m * h->dim + d] * dirs[m * h->dim + d];
+      if (!(fabs(n2 - 1.0) < 1e-5)) return invalid("ert_sweep: directions must be unit vectors");
+    }
+    if ((s = h->stage_f1.reserve((size_t)M * h->dim)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_f1.ptr, dirs, sizeof(float) * M * h->dim,
+                             cudaMemcpyHostToDevice, st));
+    dd = h->stage_f1.ptr;
+  }
+  const bool pd = is_device_ptr(Phi);
+  if (!pd) {
+    if ((s = h->stage_f2.reserve((size_t)M * N)) != VIE_OK) return s;
+    Pd = h->stage_f2.ptr;
+  }
+  if (!h->qpad) {
+    const long lattice = h->dim == 2 ? (long)h->P * h->P : (long)h->P * h->P * h->P;
+    if ((s = dalloc(&h->qpad, lattice)) != VIE_OK) return s;
+  }
+  if ((s = launch_make_q(h->dim, h->n, h->sig_s, Ud, fd, h->qpad, st)) != VIE_OK) return s;
+  if ((s = launch_sweep(h->dim, h->n, h->sig32, h->qpad, dd, M, Pd, st)) != VIE_OK) return s;
+  if (!pd) {
+    VIE_CUDA(cudaMemcpyAsync(Phi, Pd, sizeof(float) * M * N, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
+  return VIE_OK;
+}
+
+}  // extern "C"

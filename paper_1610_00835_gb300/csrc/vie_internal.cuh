@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/vie.h"
+
+namespace vie {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kPairThreads = 256;  // targets per pair-kernel CTA
+
+// Thread-local message behind vie_last_error().
+void set_error(const std::string &msg);
+
+// Map a CUDA error to VIE_ERR_CUDA with a message naming the call site.
+vie_status cuda_fail(cudaError_t e, const char *what);
+
+// Count one kernel launch of this library (reported by vie_kernel_launches).
+void count_launch();
+
+#define VIE_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return ::vie::cuda_fail(_e, #call); \
+  } while (0)
+
+#define VIE_CHECK_LAUNCH(what)                             \
+  do {                                                     \
+    cudaError_t _e = cudaGetLastError();                   \
+    if (_e != cudaSuccess) return ::vie::cuda_fail(_e, what); \
+    ::vie::count_launch();                                 \
+  } while (0)
+
+// Device-side description of one medium, used by the pair kernels.
+struct Medium {
+  int dim;
+  int n;              // cells per side
+  int P;              // n + 1, stride of the padded sigma_t lattice
+  long N;             // n^dim
+  const float *sig32; // padded FP32 sigma_t, P^dim, pad = copy of the edge
+  const double *sig64;// padded FP64 sigma_t
+  float sigma_c;      // constant sigma_t (closed-form tau)
+};
+
+// Launch plan of the FP32 pair kernel for one medium.
+struct PairPlan {
+  int smem_sigma;     // 1: sigma_t staged in shared memory
+  int tiles;          // target tiles of kPairThreads
+  int splits;         // source splits (cross-CTA partial sums)
+  int chunk;          // sources per split
+  int grid;           // CTAs launched
+  size_t smem_bytes;  // dynamic shared memory per CTA
+};
+
+// ---- apply kernels (k_apply.cu)
+vie_status plan_pairs(const Medium &m, int steps, int tau_closed, int precision, int device,
+                      PairPlan *plan);
+// src: per-source value s_k (FP32 for precision FP32, FP64 otherwise), [N]
+// partial: [plan.splits][N] FP64
+vie_status launch_pairs(const Medium &m, const PairPlan &plan, int steps, int tau_closed,
+                        int precision, const void *src, double *partial, cudaStream_t st);
+vie_status launch_source_prep(long N, int op, const double *sigma_s, const double *g,
+                              int precision, void *src, cudaStream_t st);
+vie_status launch_reduce(long N, int splits, int op, const double *partial, const double *diag,
+                         const double *sigma_s, const double *g, double *y, cudaStream_t st);
+vie_status launch_pad_sigma(int dim, int n, const double *sig, float *out32, double *out64,
+                            cudaStream_t st);
+vie_status launch_selfcell(int dim, int n, const double *sigma_t, double *diag,
+                           cudaStream_t st);
+
+// ---- Krylov kernels (k_krylov.cu)
+int dot_blocks(long N);
+vie_status launch_dots(const double *V, int nv, long ldv, const double *w, long N, double *part,
+                       int blocks, cudaStream_t st);
+vie_status launch_dots_finish(const double *part, int blocks, int nv, double *out, int accumulate,
+                              cudaStream_t st);
+vie_status launch_orth_update(const double *V, int nv, long ldv, const double *h, double *w,
+                              long N, cudaStream_t st);
+vie_status launch_scale(const double *x, const double *norm2, int use_sqrt, double *y, long N,
+                        cudaStream_t st);
+vie_status launch_axpby(double a, const double *x, double b, const double *y, double *z, long N,
+                        cudaStream_t st);
+vie_status launch_givens(double *H, int m, int k, const double *hcol, const double *hk1sq,
+                         double *cs, double *sn, double *gv, double bnorm, double *est,
+                         cudaStream_t st);
+vie_status launch_backsolve(const double *H, int m, int k, const double *gv, double *y,
+                            cudaStream_t st);
+vie_status launch_lincomb_add(const double *V, int nv, long ldv, const double *y, double *x,
+                              long N, cudaStream_t st);
+
+// ---- sweep kernels (k_sweep.cu)
+vie_status launch_make_q(int dim, int n, const double *sigma_s, const double *U, const double *f,
+                         float *qpad, cudaStream_t st);
+vie_status launch_sweep(int dim, int n, const float *sigpad, const float *qpad, const float *dirs,
+                        int M, float *Phi, cudaStream_t st);
+
+}  // namespace vie

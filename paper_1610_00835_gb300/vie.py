@@ -1,0 +1,217 @@
+"""ctypes binding of libvie.so: the same names as the C ABI in include/vie.h.
+
+Argument marshalling only: every numeric step runs in the library's CUDA
+kernels.  There is no fallback; if the library is missing or no GPU is
+present the calls raise.  Tensors may be CUDA tensors (used in place, work
+queued on the current torch stream) or CPU tensors / numpy arrays (copied by
+the library through its own device buffers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+VIE_OK, VIE_ERR_INVALID_ARG, VIE_ERR_CUDA, VIE_ERR_OOM = 0, 1, 2, 3
+VIE_ERR_NOT_CONVERGED, VIE_ERR_TIMEOUT, VIE_ERR_NONFINITE, VIE_ERR_UNSUPPORTED = 4, 5, 6, 7
+STATUS_NAMES = {0: "VIE_OK", 1: "VIE_ERR_INVALID_ARG", 2: "VIE_ERR_CUDA", 3: "VIE_ERR_OOM",
+                4: "VIE_ERR_NOT_CONVERGED", 5: "VIE_ERR_TIMEOUT", 6: "VIE_ERR_NONFINITE",
+                7: "VIE_ERR_UNSUPPORTED"}
+VIE_TAU_MARCH, VIE_TAU_CLOSED = 0, 1
+VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
+VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
+
+
+class VieError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vie_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int)]
+
+
+class vie_opts(C.Structure):
+    _fields_ = [("steps", C.c_int), ("tau_mode", C.c_int), ("precision", C.c_int),
+                ("device", C.c_int)]
+
+
+class vie_gmres_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
+                ("zero_x0", C.c_int), ("rhs_is_phi", C.c_int), ("time_apply", C.c_int)]
+
+
+class vie_report(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("n_apply", C.c_int), ("relres", C.c_double), ("relres_est", C.c_double),
+                ("t_total_ms", C.c_double), ("t_apply_ms", C.c_double),
+                ("t_apply_kernel_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every symbol include/vie.h declares, with its ctypes signature.
+_vp = C.c_void_p
+SIGNATURES = {
+    "vie_default_opts": (None, [C.POINTER(vie_opts)]),
+    "vie_default_gmres_opts": (None, [C.POINTER(vie_gmres_opts)]),
+    "vie_create": (C.c_int, [C.POINTER(_vp), C.POINTER(vie_grid), _vp, _vp, C.POINTER(vie_opts)]),
+    "vie_destroy": (C.c_int, [_vp]),
+    "vie_apply": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
+    "vie_solve_gmres": (C.c_int, [_vp, _vp, _vp, C.POINTER(vie_gmres_opts),
+                                  C.POINTER(vie_report), _vp]),
+    "ert_sweep": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "vie_get_diagonal": (C.c_int, [_vp, _vp, _vp]),
+    "vie_last_error": (C.c_char_p, []),
+    "vie_version": (C.c_char_p, []),
+    "vie_kernel_launches": (C.c_ulonglong, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libvie.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libvie.so not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != VIE_OK:
+        raise VieError(status, load().vie_last_error().decode())
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) for a torch tensor or numpy array of `dtype`."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.float64: torch.float64, np.float32: torch.float32}[dtype]
+            if x.dtype != want:
+                raise TypeError(f"expected {want}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return C.c_void_p(x.data_ptr()), x
+    except ImportError:
+        pass
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+    return C.c_void_p(a.ctypes.data), a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class VieHandle:
+    ptr: C.c_void_p
+    dim: int
+    n: int
+
+    @property
+    def N(self) -> int:
+        return self.n ** self.dim
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                vie_destroy(self)
+        except Exception:
+            pass
+
+
+def vie_create(dim: int, n: int, sigma_t, sigma_s, steps: int = 64, tau_mode: int = VIE_TAU_MARCH,
+               precision: int = VIE_PREC_FP32, device: int = 0) -> VieHandle:
+    L = load()
+    st = np.ascontiguousarray(np.asarray(sigma_t, dtype=np.float64).ravel())
+    ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64).ravel())
+    g = vie_grid(dim, n)
+    o = vie_opts(steps, tau_mode, precision, device)
+    h = C.c_void_p()
+    _check(L.vie_create(C.byref(h), C.byref(g), C.c_void_p(st.ctypes.data),
+                        C.c_void_p(ss.ctypes.data), C.byref(o)))
+    return VieHandle(h, dim, n)
+
+
+def vie_destroy(h: VieHandle) -> None:
+    if h.ptr:
+        _check(load().vie_destroy(h.ptr))
+        h.ptr = C.c_void_p()
+
+
+def vie_apply(h: VieHandle, op: int, g, y, nrhs: int = 1, stream=None) -> None:
+    gp, _g = _ptr(g, np.float64)
+    yp, _y = _ptr(y, np.float64)
+    _check(load().vie_apply(h.ptr, op, gp, yp, nrhs, _stream(stream)))
+
+
+def vie_solve_gmres(h: VieHandle, f, U, rtol: float = 1e-6, restart: int = 64, maxit: int = 1000,
+                    zero_x0: bool = True, rhs_is_phi: bool = False, time_apply: bool = False,
+                    stream=None, raise_on_nonconvergence: bool = True) -> dict:
+    fp, _f = _ptr(f, np.float64)
+    up, _u = _ptr(U, np.float64)
+    o = vie_gmres_opts(rtol, restart, maxit, int(zero_x0), int(rhs_is_phi), int(time_apply))
+    rep = vie_report()
+    s = load().vie_solve_gmres(h.ptr, fp, up, C.byref(o), C.byref(rep), _stream(stream))
+    if s == VIE_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+        return rep.as_dict()
+    _check(s)
+    return rep.as_dict()
+
+
+def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
+    up, _u = _ptr(U, np.float64)
+    fp, _f = _ptr(f, np.float64)
+    dp, _d = _ptr(dirs, np.float32)
+    M = int(np.prod(dirs.shape[:-1])) if hasattr(dirs, "shape") else len(dirs) // h.dim
+    pp, _p = _ptr(Phi, np.float32)
+    _check(load().ert_sweep(h.ptr, up, fp, dp, M, pp, _stream(stream)))
+
+
+def vie_get_diagonal(h: VieHandle, d, stream=None) -> None:
+    dp, _d = _ptr(d, np.float64)
+    _check(load().vie_get_diagonal(h.ptr, dp, _stream(stream)))
+
+
+def vie_last_error() -> str:
+    return load().vie_last_error().decode()
+
+
+def vie_version() -> str:
+    return load().vie_version().decode()
+
+
+def vie_kernel_launches() -> int:
+    return int(load().vie_kernel_launches())
