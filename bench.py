@@ -294,8 +294,37 @@ def run_ours(args):
     return 0
 
 
+def run_apply_only(args):
+    """K operator applies on the bench medium (a small driver for profilers)."""
+    import torch
+    import paper_1610_00835_gb300 as P
+
+    m = V.heterogeneous_2d(n=args.n) if args.dim == 2 else V.heterogeneous_3d(n=args.n)
+    h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS)
+    g = torch.as_tensor(m.f, dtype=torch.float64, device="cuda:0")
+    y = torch.empty_like(g)
+    for _ in range(args.warmup):
+        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"mode": "apply-only", "dim": args.dim, "n": m.n, "N": m.N,
+                      "ms_per_apply": ms, "gpair_per_s": m.N * m.N / ms / 1e6}), flush=True)
+    P.vie_destroy(h)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time operator applies only (profiling driver)")
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -303,6 +332,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_only:
+        return run_apply_only(args)
     return run_ours(args)
 
 

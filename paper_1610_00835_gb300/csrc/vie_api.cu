@@ -374,7 +374,7 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
   h->med.N = N;
   h->med.sig32 = h->sig32;
   h->med.sig64 = h->sig64;
-  h->med.sigma_c = (float)sigma_t[0];
+  h->med.sigma_c = sigma_t[0];
   TRY(plan_pairs(h->med, opts.steps, opts.tau_mode == VIE_TAU_CLOSED, opts.precision,
                  opts.device, &h->plan));
   {

@@ -43,7 +43,7 @@ struct Medium {
   long N;             // n^dim
   const float *sig32; // padded FP32 sigma_t, P^dim, pad = copy of the edge
   const double *sig64;// padded FP64 sigma_t
-  float sigma_c;      // constant sigma_t (closed-form tau)
+  double sigma_c;     // constant sigma_t (closed-form tau)
 };
 
 // Launch plan of the FP32 pair kernel for one medium.
