@@ -6,6 +6,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <string>
@@ -115,6 +116,7 @@ struct vie_handle {
   double *diag = nullptr;                     // self-cell d_j [N]
   Medium med{};
   PairPlan plan{};
+  SymPlan sym{};                              // symmetric kernel, when usable
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
   DBuf<double> stage_a, stage_b, stage_c;     // host-pointer staging
@@ -127,6 +129,7 @@ struct vie_handle {
   double *htmp = nullptr, *part = nullptr, *scal = nullptr;
   double *h_pinned = nullptr;                 // host-pinned scalars / gv seed
   // apply timing
+  bool opts_disable_sym = false;              // force the general kernel (tests)
   std::vector<ApplyEvents> events;
   size_t ev_next = 0;
   double t_apply_ms = 0.0, t_kernel_ms = 0.0;
@@ -169,6 +172,7 @@ void free_all(vie_handle *h) {
   h->stage_f1.release();
   h->stage_f2.release();
   dfree(h->qpad);
+  sym_release(&h->sym);
   free_gmres(h);
   for (auto &ev : h->events)
     for (auto &e : ev.e)
@@ -237,10 +241,20 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   vie_status s = launch_source_prep(h->N, op, h->sig_s, g, prec, h->src, st);
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
-  s = launch_pairs(h->med, h->plan, h->opts.steps, closed, prec, h->src, h->partial, st);
+  int slots = h->plan.splits;
+  if (h->sym.usable) {
+    const double hh = 1.0 / h->n;
+    const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
+    const float wcoef = (float)(h->dim == 2 ? hh / (2.0 * kPi) : hh / (4.0 * kPi));
+    s = sym_launch(h->sym, h->dim, h->n, h->N, tau_scale2, wcoef, (const float *)h->src,
+                   h->partial, st);
+    slots = h->sym.T;
+  } else {
+    s = launch_pairs(h->med, h->plan, h->opts.steps, closed, prec, h->src, h->partial, st);
+  }
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[2], st));
-  s = launch_reduce(h->N, h->plan.splits, op, h->partial, h->diag, h->sig_s, g, y, st);
+  s = launch_reduce(h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st);
   if (s != VIE_OK) return s;
   if (timed) {
     VIE_CUDA(cudaEventRecord(ev->e[3], st));
@@ -382,7 +396,10 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     cudaError_t e = cudaMalloc(&h->src, bytes);
     if (e != cudaSuccess) TRY(cuda_fail(e, "cudaMalloc"));
   }
-  TRY(dalloc(&h->partial, (size_t)h->plan.splits * N));
+  if (opts.precision == VIE_PREC_FP32 && opts.tau_mode == VIE_TAU_MARCH && opts.steps == 64 &&
+      !h->opts_disable_sym)
+    TRY(sym_prepare(&h->sym, g->dim, g->n, N, h->sig32, opts.device, st));
+  TRY(dalloc(&h->partial, (size_t)std::max(h->plan.splits, h->sym.usable ? h->sym.T : 0) * N));
   {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) TRY(cuda_fail(e, "vie_create setup kernels"));

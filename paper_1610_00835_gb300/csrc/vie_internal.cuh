@@ -72,6 +72,25 @@ vie_status launch_pad_sigma(int dim, int n, const double *sig, float *out32, dou
 vie_status launch_selfcell(int dim, int n, const double *sigma_t, double *diag,
                            cudaStream_t st);
 
+// ---- symmetric pair kernel (k_pairs_sym.cu): FP32 tiles, S = 64, lattice
+// in shared memory.  partial must hold [T][N] doubles.
+struct SymPlan {
+  int usable = 0;
+  int T = 0, n_items = 0, ldp = 0, plane = 0, grid = 0;
+  size_t smem = 0;
+  long lattice_elems = 0;
+  int2 *items = nullptr;
+  int *counter = nullptr;
+  float *lattice = nullptr;
+  const void *kernel = nullptr;
+};
+size_t sym_smem_bytes(int dim, int n, int *ldp, int *plane);
+vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_padded, int device,
+                       cudaStream_t st);
+void sym_release(SymPlan *sp);
+vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale2, float wcoef,
+                      const float *src, double *partial, cudaStream_t st);
+
 // ---- Krylov kernels (k_krylov.cu)
 int dot_blocks(long N);
 vie_status launch_dots(const double *V, int nv, long ldv, const double *w, long N, double *part,

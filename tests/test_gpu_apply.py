@@ -150,3 +150,16 @@ def test_256_grid_global_sigma_path_sampled_rows():
     rows = _sampled_rows(m.N, 8, 3)
     want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
     assert rel_l2(got[rows], want) < FP32_TOL
+
+
+@pytest.mark.parametrize("n", [31, 33, 64, 65, 96, 150, 200, 224])
+def test_symmetric_kernel_every_lattice_stride(n):
+    # the symmetric FP32 kernel is compiled for lattice strides 33..225; each
+    # size here lands in a different one, with a ragged last tile
+    m = V.bump_medium(2, n, 4, 0.9, seed=4100 + n)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    g = m.f + 0.05 * rng_vec(m.N, n)
+    got = gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)
+    rows = _sampled_rows(m.N, 16, n)
+    want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(got[rows], want) < FP32_TOL
