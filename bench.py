@@ -13,7 +13,9 @@ e2e    = the same through the C ABI from host buffers: vie_create from host
          sigma_t/sigma_s, vie_solve_gmres with host f and host U (copies
          inside), vie_destroy; per step.
 roofline: the pair kernel, FP32-pipe bound; algorithmic work 13 S + 12
-         FP32 lane operations per pair, peak = SMs x 128 lanes x max clock.
+         FP32 lane operations per marched pair.  A_jk = A_kj, so the method
+         marches each unordered pair once: N (N - 1) / 2 marches per apply.
+         Peak = SMs x 128 FP32 lanes x max SM clock.
 cpu_baseline: the FP64 oracle's matrix-free apply on a bounded sample of
          target rows of the same medium, on the host cores.
 
@@ -44,7 +46,7 @@ RTOL = 1e-6
 # Pair-kernel traffic per launch from the ncu capture of this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
 # the current kernel.
-PAIR_KERNEL_DRAM_BYTES = None
+PAIR_KERNEL_DRAM_BYTES = 229376  # k_pairs_sym<2,129,0>, profiles/k_pairs_sym_2d_128.md
 
 
 def ops_per_pair(S: int) -> int:
@@ -242,11 +244,12 @@ def run_ours(args):
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak = sms * 128 * max_mhz * 1e6 / 1e12                     # Tops/s at max clock
-    ops = ops_per_pair(S_STEPS) * float(N) * (N - 1)             # per launch
+    ops = ops_per_pair(S_STEPS) * float(N) * (N - 1) / 2.0       # per launch
     achieved = ops / (kern_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES,
-                "kernel": "k_pairs_f32<2,smem,S=64>", "kernel_ms": kern_ms,
+                "kernel": "k_pairs_sym<2,129,0>", "kernel_ms": kern_ms,
+                "work": "13*S+12 FP32 lane-ops per unordered pair, N(N-1)/2 pairs",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max clock)"}
     if clocks["sm_mhz"]:
         roofline["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
