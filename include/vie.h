@@ -165,6 +165,27 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U,
 vie_status ert_sweep(vie_handle *h, const double *U, const double *f, const float *dirs,
                      int M, float *Phi, void *stream);
 
+/* One operator apply that allocates no device memory, for callers that cannot
+ * call cudaMalloc (a host that owns all device memory through its own pool or
+ * fixed budget, or a latency-critical loop that cannot take an allocation's
+ * implicit synchronisation).  The paper has no counterpart: this is a
+ * deployment variant of vie_apply.
+ *   dim, n           : grid as in vie_grid; n^dim <= 16384 (2D n <= 128,
+ *                      3D n <= 25), else VIE_ERR_INVALID_ARG.
+ *   sigma_t, sigma_s : device FP64 [N] coefficients (caller-owned).
+ *   op, g, y         : as vie_apply with nrhs = 1; g and y device FP64 [N].
+ * Computes what vie_apply computes for a handle made with the default options
+ * (S = 64 march, FP32 tiles), self-cell diagonal included, with every
+ * intermediate in one fixed device array of about 17 MB that the library
+ * image holds on every GPU that loads it until the process exits.  The first
+ * call with a device current looks up that array's address on the device;
+ * make it before any stream capture.  Calls share the array and it keeps the
+ * last call's contents (the work counter is cleared on every call); calls
+ * whose work overlaps on the same GPU race, so serialise them.  Asynchronous
+ * on `stream`.  Errors: INVALID_ARG (sizes, non-device pointers), CUDA. */
+vie_status vie_apply_noalloc(int dim, int n, const double *sigma_t, const double *sigma_s,
+                             vie_op op, const double *g, double *y, void *stream);
+
 /* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);
 

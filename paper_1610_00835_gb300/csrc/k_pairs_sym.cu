@@ -479,3 +479,51 @@ vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale
 }
 
 }  // namespace vie
+
+namespace vie {
+
+// Plan the symmetric kernel on caller-provided device memory: nothing is
+// allocated.  lattice_mem must hold sym_smem_bytes()' lattice part
+// (LDP (n+1) floats in 2D, PLANE (n+1) in 3D); items_mem T (T+1)/2 int2
+// (filled by the caller in the order a = 0.., b = a..T-1); counter_mem two
+// ints set to zero by the caller before the launch.
+vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
+                             int device, int2 *items_mem, int *counter_mem, float *lattice_mem,
+                             cudaStream_t st) {
+  cudaDeviceProp prop;
+  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  int ldp = 0, plane = 0;
+  SymKernel k = pick(dim, n + 1, &ldp, &plane);
+  const size_t smem = sym_smem_bytes(dim, n, nullptr, nullptr);
+  sp->usable = 0;
+  if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
+  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int bps = 0;
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kCtaThreads, smem));
+  if (bps < 1) return VIE_OK;
+  const long P = n + 1;
+  const long lattice = dim == 2 ? (long)ldp * P : (long)plane * P;
+  sp->T = (int)((N + kG - 1) / kG);
+  sp->n_items = sp->T * (sp->T + 1) / 2;
+  sp->items = items_mem;
+  sp->counter = counter_mem;
+  sp->lattice = lattice_mem;
+  {
+    long b = (lattice + 255) / 256;
+    k_restride<<<(int)std::min(b, 4096L), 256, 0, st>>>(dim, (int)P, ldp, plane, sig_padded,
+                                                        lattice_mem, lattice);
+    VIE_CHECK_LAUNCH("k_restride");
+  }
+  sp->lattice_elems = lattice;
+  sp->ldp = ldp;
+  sp->plane = plane;
+  sp->smem = smem;
+  sp->grid = (int)std::min<long>((long)bps * prop.multiProcessorCount,
+                                 (sp->n_items + kGroups - 1) / kGroups);
+  sp->kernel = (const void *)k;
+  sp->usable = 1;
+  return VIE_OK;
+}
+
+}  // namespace vie

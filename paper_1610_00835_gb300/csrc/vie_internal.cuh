@@ -88,6 +88,9 @@ size_t sym_smem_bytes(int dim, int n, int *ldp, int *plane);
 vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_padded, int device,
                        cudaStream_t st);
 void sym_release(SymPlan *sp);
+vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
+                             int device, int2 *items_mem, int *counter_mem, float *lattice_mem,
+                             cudaStream_t st);
 vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale2, float wcoef,
                       const float *src, double *partial, cudaStream_t st);
 

@@ -71,6 +71,7 @@ SIGNATURES = {
     "vie_last_error": (C.c_char_p, []),
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
+    "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -189,6 +190,15 @@ def vie_solve_gmres(h: VieHandle, f, U, rtol: float = 1e-6, restart: int = 64, m
         return rep.as_dict()
     _check(s)
     return rep.as_dict()
+
+
+def vie_apply_noalloc(dim: int, n: int, sigma_t, sigma_s, op: int, g, y, stream=None) -> None:
+    """vie_apply without any device allocation; all arrays must be CUDA tensors."""
+    sp, _s1 = _ptr(sigma_t, np.float64)
+    qp, _s2 = _ptr(sigma_s, np.float64)
+    gp, _g = _ptr(g, np.float64)
+    yp, _y = _ptr(y, np.float64)
+    _check(load().vie_apply_noalloc(dim, n, sp, qp, op, gp, yp, _stream(stream)))
 
 
 def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
