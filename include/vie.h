@@ -115,6 +115,29 @@ typedef enum {
 vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int nrhs,
                      void *stream);
 
+/* Operator storage modes for vie_assemble. */
+enum {
+  VIE_OPERATOR_OTF = 0,          /* entries generated on the fly (default)        */
+  VIE_OPERATOR_FP32 = 1,         /* K assembled in HBM, FP32                      */
+  VIE_OPERATOR_BF16X3 = 2        /* K assembled as BF16 hi + lo; products with
+                                    several right-hand sides on the tensor cores
+                                    as Khi Ghi + Khi Glo + Klo Ghi, FP32 accumulate */
+};
+
+/* Assemble K = [K_jk omega_k] (Section 3.2, Eq. EQ: LINEAR SYSTEM) into device
+ * memory and use it for later VIE_OP_K_SIGMA_S / VIE_OP_I_MINUS_K applies and
+ * solves; the paper caches its kernel evaluations for reuse across GMRES
+ * iterations in the same way (Section 4.2).  Entries are the on-the-fly FP32
+ * values (S = 64 march, self cell on the diagonal); storage is N x LDK with
+ * LDK = N rounded up to 64, 4 bytes per entry in both modes (1.07 GB at
+ * 128^2, 17.2 GB at 256^2).  VIE_OP_A_RAW keeps the on-the-fly path.  One RHS
+ * uses a bandwidth-bound CUDA-core product; vie_apply with nrhs >= 2 in
+ * VIE_OPERATOR_BF16X3 mode uses one tensor-core product for up to 256 RHS.
+ * VIE_OPERATOR_OTF frees the matrix.  Needs FP32 precision, the march and
+ * S = 64 (else VIE_ERR_UNSUPPORTED).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+vie_status vie_assemble(vie_handle *h, int mode, void *stream);
+
 typedef struct {
   double rtol;  /* stop when ||phi - (I-K)U||_2 / ||phi||_2 <= rtol (FP64)   */
   int restart;  /* m, Krylov dimension per cycle (1..256; 64 by default)    */

@@ -1,0 +1,503 @@
+// Products with the assembled operator (Section 3.2, K = [K_jk omega_k]).
+//
+// * k_gemv: y = K g for one right-hand side on the CUDA cores, K in FP32 or
+//   BF16 hi/lo (4 bytes per entry either way); bandwidth bound.
+// * k_gemm_bf16x3: Y = K G for R right-hand sides on the 5th-generation
+//   tensor cores.  K = Khi + Klo and G = Ghi + Glo are BF16 splits of FP32
+//   values; the product keeps Khi Ghi + Khi Glo + Klo Ghi (the dropped
+//   Klo Glo term is below 2^-16 of |K||G|), accumulated in FP32 in tensor
+//   memory.  One CTA computes a 128-row tile of Y for all R columns over one
+//   K-range (split-K); a TMA producer thread streams 64-wide K slices of Khi,
+//   Klo, Ghi, Glo into a 4-stage shared-memory ring (128-byte swizzle), one
+//   thread issues tcgen05.mma (M = 128, N = R, K = 16 per instruction) and
+//   the four warps read the accumulators back with tcgen05.ld.
+//   The tensor cores do not round their FP32 accumulation to nearest, so a
+//   long chain of products into one accumulator drifts low (measured: 3e-5
+//   relative after ~770 chained MMAs).  The dominant Khi Ghi product
+//   therefore rotates over up to four accumulators, the small cross terms go
+//   to a fifth, split-K keeps every chain at or below ~128 MMAs, and the
+//   accumulators are added in FP32 in the epilogue and across splits in FP64.
+//   Every mbarrier wait is bounded by a clock limit; on expiry the CTA sets
+//   an error word, stops issuing work, waits for its issued copies and
+//   products (again bounded), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+namespace {
+
+// ------------------------------------------------------------------ GEMV
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_gemv(const void *__restrict__ K, const void *__restrict__ Klo,
+                                              long ldk, long N, const float *__restrict__ g32,
+                                              const double *__restrict__ g64, int op,
+                                              double *__restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const long warp = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  for (long row = warp; row < N; row += nwarps) {
+    float acc0 = 0.f, acc1 = 0.f;
+    if (BF16) {
+      const uint4 *hi = reinterpret_cast<const uint4 *>((const __nv_bfloat16 *)K + row * ldk);
+      const uint4 *lo = reinterpret_cast<const uint4 *>((const __nv_bfloat16 *)Klo + row * ldk);
+      const long nchunk = ldk / 8;
+      for (long c = lane; c < nchunk; c += 32) {
+        const uint4 h = __ldcs(hi + c), l = __ldcs(lo + c);
+        const float4 ga = __ldg(reinterpret_cast<const float4 *>(g32) + 2 * c);
+        const float4 gb = __ldg(reinterpret_cast<const float4 *>(g32) + 2 * c + 1);
+        const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&h);
+        const __nv_bfloat162 *lp = reinterpret_cast<const __nv_bfloat162 *>(&l);
+        const float gv[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 hf = __bfloat1622float2(hp[e]);
+          const float2 lf = __bfloat1622float2(lp[e]);
+          acc0 = fmaf(hf.x + lf.x, gv[2 * e], acc0);
+          acc1 = fmaf(hf.y + lf.y, gv[2 * e + 1], acc1);
+        }
+      }
+    } else {
+      const float4 *kr = reinterpret_cast<const float4 *>((const float *)K + row * ldk);
+      const long nchunk = ldk / 4;
+      for (long c = lane; c < nchunk; c += 32) {
+        const float4 kv = __ldcs(kr + c);
+        const float4 gv = __ldg(reinterpret_cast<const float4 *>(g32) + c);
+        acc0 = fmaf(kv.x, gv.x, fmaf(kv.z, gv.z, acc0));
+        acc1 = fmaf(kv.y, gv.y, fmaf(kv.w, gv.w, acc1));
+      }
+    }
+    double s = (double)acc0 + (double)acc1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = op == VIE_OP_I_MINUS_K ? g64[row] - s : s;
+  }
+}
+
+// g (FP64 [nrhs][N]) -> FP32 [nrhs][ldk], zero padded
+__global__ void k_to_f32_padded(const double *__restrict__ g, long N, long ldk, int nrhs,
+                                float *__restrict__ out) {
+  const long total = (long)nrhs * ldk;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldk, c = i % ldk;
+    out[i] = c < N ? (float)g[r * N + c] : 0.f;
+  }
+}
+
+// G (FP64 [nrhs][N]) -> BF16 hi/lo [rpad][ldk], zero padded
+__global__ void k_split_bf16(const double *__restrict__ g, long N, long ldk, int nrhs, int rpad,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+  const long total = (long)rpad * ldk;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldk, c = i % ldk;
+    const float v = (r < nrhs && c < N) ? (float)g[r * N + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// y[r][j] = sum_split part[split][r][j]  (then the operator).  A product
+// that gave up on a bounded wait (*err != 0) turns y into NaN, which the
+// Krylov driver reports as VIE_ERR_NONFINITE.
+__global__ void k_gemm_finish(const float *__restrict__ part, int splits, int nrhs, long N,
+                              const double *__restrict__ g, int op, const int *__restrict__ err,
+                              double *__restrict__ y) {
+  const long total = (long)nrhs * N;
+  const bool failed = *err != 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < splits; ++p) s += part[(long)p * total + i];
+    y[i] = failed ? __longlong_as_double(0x7ff8000000000000LL) : (op == VIE_OP_I_MINUS_K ? g[i] - s : s);
+  }
+}
+
+// ------------------------------------------------------------------ GEMM
+
+constexpr int BM = 128;          // rows of Y per CTA (MMA M)
+constexpr int BK = 64;           // K elements per stage: 128 bytes of BF16
+constexpr int MAX_STAGES = 4;
+constexpr int UMMA_K = 16;       // K per tcgen05.mma kind::f16
+constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (about 1 s)
+
+struct GemmArgs {
+  int stages;        // shared-memory ring depth (2..4)
+  int rpad;          // N of the MMA (multiple of 16, <= 256)
+  int nrhs;          // valid columns
+  long N;            // rows of K and Y
+  int kblocks_total; // ldk / BK
+  int kblocks_per_split;
+  int tmem_cols;     // allocated tensor-memory columns (512)
+  int n_main;        // accumulators that take the Khi Ghi product in turn
+  float *part;       // [splits][nrhs][N]
+  int *err;          // error word (0 = ok)
+};
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitLimit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle, rows of 128 bytes, 8-row groups 1024 B apart.
+__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((addr >> 4) & 0x3FFF);        // start address
+  d |= (unsigned long long)(16 >> 4) << 16;               // leading byte offset (unused)
+  d |= (unsigned long long)(1024 >> 4) << 32;             // stride byte offset
+  d |= 1ull << 46;                                        // descriptor version
+  d |= 2ull << 61;                                        // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major.
+__host__ __device__ constexpr unsigned idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                         unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_bf16x3(const __grid_constant__ CUtensorMap map_khi, const __grid_constant__ CUtensorMap map_klo,
+                  const __grid_constant__ CUtensorMap map_ghi, const __grid_constant__ CUtensorMap map_glo,
+                  GemmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzle atoms
+  unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+  const int a_bytes = BM * BK * 2;            // 16 KB per K operand slice
+  const int b_bytes = a.rpad * BK * 2;        // rpad * 128 B per G operand slice
+  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const int STAGES = a.stages;
+  unsigned char *stages = smem;
+  unsigned long long *bars = (unsigned long long *)(smem + STAGES * stage_bytes);
+  // bars[0..S) full, [S..2S) empty, [2S] done
+  unsigned *tmem_slot = (unsigned *)(bars + 2 * STAGES + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tile = blockIdx.x, split = blockIdx.y;
+  const int kb0 = split * a.kblocks_per_split;
+  const int kb1 = min(a.kblocks_total, kb0 + a.kblocks_per_split);
+  const int nkb = max(0, kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(su32(bars + s), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+  const unsigned idesc = idesc_bf16(BM, a.rpad);
+
+  int issued_loads = 0, issued_mma = 0;
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % STAGES, use = i / STAGES;
+      if (use > 0 && !mbar_wait(su32(bars + STAGES + s), (use - 1) & 1, abort_flag)) {
+        atomicExch(a.err, 1);
+        *abort_flag = 1;
+        break;
+      }
+      unsigned char *st = stages + s * stage_bytes;
+      const unsigned full = su32(bars + s);
+      mbar_arrive_expect_tx(full, (unsigned)stage_bytes);
+      const int kx = (kb0 + i) * BK;
+      tma_load_2d(su32(st), &map_khi, full, kx, tile * BM);
+      tma_load_2d(su32(st + a_bytes), &map_klo, full, kx, tile * BM);
+      tma_load_2d(su32(st + 2 * a_bytes), &map_ghi, full, kx, 0);
+      tma_load_2d(su32(st + 2 * a_bytes + b_bytes), &map_glo, full, kx, 0);
+      ++issued_loads;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % STAGES, use = i / STAGES;
+      if (!mbar_wait(su32(bars + s), use & 1, abort_flag)) {
+        atomicExch(a.err, 2);
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char *st = stages + s * stage_bytes;
+      const unsigned a_hi = su32(st), a_lo = su32(st + a_bytes);
+      const unsigned b_hi = su32(st + 2 * a_bytes), b_lo = su32(st + 2 * a_bytes + b_bytes);
+      // accumulator columns: main_q at q * rpad (q < n_main), cross terms after
+      const int q = i % a.n_main;
+      const unsigned d_main = tmem + (unsigned)(q * a.rpad);
+      const unsigned d_cross = tmem + (unsigned)(a.n_main * a.rpad);
+#pragma unroll
+      for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+        const unsigned off = kk * UMMA_K * 2;  // bytes along the swizzled row
+        const unsigned first_main = (i < a.n_main && kk == 0) ? 0u : 1u;
+        const unsigned first_cross = (i == 0 && kk == 0) ? 0u : 1u;
+        mma_bf16(d_main, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, first_main);
+        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, first_cross);
+        mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+      }
+      mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs finish
+      ++issued_mma;
+    }
+    mma_commit(su32(bars + 2 * STAGES));    // accumulator complete
+  }
+  __syncwarp();
+
+  // Epilogue: every warp reads its 32 TMEM lanes (rows) x rpad columns.
+  bool ok = nkb > 0 && mbar_wait(su32(bars + 2 * STAGES), 0, abort_flag);
+  ok = __syncthreads_and(ok) != 0;  // tcgen05.ld below must be warp-uniform
+  if (!ok && nkb > 0 && threadIdx.x == 0) {
+    atomicExch(a.err, 3);
+    *abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const long row = (long)tile * BM + warp * 32 + lane;
+  float *out = a.part + (long)split * a.nrhs * a.N;
+  if (ok) {
+    const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+    const int used = min(nkb, a.n_main);  // main accumulators that were written
+    for (int c0 = 0; c0 < a.rpad; c0 += 16) {
+      float v[16], w[16];
+      tmem_ld16(lane_base + (unsigned)(a.n_main * a.rpad + c0), v);
+      for (int q = 0; q < used; ++q) {
+        tmem_ld16(lane_base + (unsigned)(q * a.rpad + c0), w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += w[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (row < a.N && c0 + i < a.nrhs) out[(long)(c0 + i) * a.N + row] = v[i];
+    }
+  } else if (nkb == 0) {
+    for (int c = 0; c < a.nrhs; ++c)
+      if (row < a.N) out[(long)c * a.N + row] = 0.f;
+  }
+  // On an abort, wait (bounded) for the copies and products already issued so
+  // that nothing lands in shared or tensor memory after the CTA exits.
+  if (!ok && nkb > 0 && threadIdx.x == 0) {
+    const long long t0 = clock64();
+    for (int i = 0; i < issued_loads; ++i) {
+      const int s = i % STAGES, use = i / STAGES;
+      while (!mbar_test(su32(bars + s), use & 1) && clock64() - t0 < kWaitLimit) {
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
+                 : "memory");
+  }
+  (void)issued_mma;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2D BF16 tensor [rows][ld] (ld elements per row), box {64, box_rows}, 128B swizzle.
+vie_status make_map(CUtensorMap *m, const void *base, long ld, long rows, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return VIE_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed");
+    return VIE_ERR_CUDA;
+  }
+  return VIE_OK;
+}
+
+int grid_for(long n, int threads) {
+  long b = (n + threads - 1) / threads;
+  return (int)std::max(1L, std::min(b, 8192L));
+}
+
+}  // namespace
+
+vie_status launch_gemv(const void *k, const void *klo, int bf16, long ldk, long N, const double *g,
+                       float *g32, int op, double *y, cudaStream_t st) {
+  k_to_f32_padded<<<grid_for(ldk, 256), 256, 0, st>>>(g, N, ldk, 1, g32);
+  VIE_CHECK_LAUNCH("k_to_f32_padded");
+  const int blocks = (int)std::min<long>((N + 7) / 8, 152L * 16);
+  if (bf16)
+    k_gemv<true><<<blocks, 256, 0, st>>>(k, klo, ldk, N, g32, g, op, y);
+  else
+    k_gemv<false><<<blocks, 256, 0, st>>>(k, nullptr, ldk, N, g32, g, op, y);
+  VIE_CHECK_LAUNCH("k_gemv");
+  return VIE_OK;
+}
+
+// FP32 split-K partials, rounded up so the BF16 G operands after them start on
+// a 256-byte boundary (TMA wants 16).
+static size_t part_region_bytes(int splits, int nrhs, long N) {
+  return ((sizeof(float) * (size_t)splits * nrhs * N) + 255) & ~(size_t)255;
+}
+
+// Main accumulators for a given width: all five (or fewer) fit in 512 columns.
+static int n_main_for(int rpad) { return std::max(1, std::min(4, 512 / rpad - 1)); }
+
+size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms) {
+  const long tiles = (N + BM - 1) / BM;
+  const int kblocks = (int)(ldk / BK);
+  const int rpad = (nrhs + 15) / 16 * 16;
+  const int nm = n_main_for(rpad);
+  // enough CTAs for two waves, and at most ~128 chained MMAs per accumulator
+  const long by_occupancy = (2L * sms + tiles - 1) / tiles;
+  const long by_chain = (4L * kblocks + (long)nm * 128 - 1) / ((long)nm * 128);
+  int splits = (int)std::max(1L, std::min<long>(kblocks, std::max(by_occupancy, by_chain)));
+  if (splits_out) *splits_out = splits;
+  return part_region_bytes(splits, nrhs, N) + 2 * sizeof(short) * (size_t)rpad * ldk;
+}
+
+vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g,
+                              int nrhs, int op, double *y, void *workspace, int *err,
+                              cudaStream_t st) {
+  if (nrhs < 1 || nrhs > 256) {
+    set_error("BF16 product: 1 <= nrhs <= 256");
+    return VIE_ERR_INVALID_ARG;
+  }
+  int dev = 0, sms = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int splits = 1;
+  gemm_workspace_bytes(N, ldk, nrhs, &splits, sms);
+  const int rpad = (nrhs + 15) / 16 * 16;
+  float *part = (float *)workspace;
+  __nv_bfloat16 *ghi = (__nv_bfloat16 *)((unsigned char *)workspace + part_region_bytes(splits, nrhs, N));
+  __nv_bfloat16 *glo = ghi + (size_t)rpad * ldk;
+  k_split_bf16<<<grid_for((long)rpad * ldk, 256), 256, 0, st>>>(g, N, ldk, nrhs, rpad, ghi, glo);
+  VIE_CHECK_LAUNCH("k_split_bf16");
+  CUtensorMap mkhi, mklo, mghi, mglo;
+  vie_status s;
+  if ((s = make_map(&mkhi, khi, ldk, N, BM)) != VIE_OK) return s;
+  if ((s = make_map(&mklo, klo, ldk, N, BM)) != VIE_OK) return s;
+  if ((s = make_map(&mghi, ghi, ldk, rpad, rpad)) != VIE_OK) return s;
+  if ((s = make_map(&mglo, glo, ldk, rpad, rpad)) != VIE_OK) return s;
+  GemmArgs a;
+  a.rpad = rpad;
+  a.nrhs = nrhs;
+  a.N = N;
+  a.kblocks_total = (int)(ldk / BK);
+  a.kblocks_per_split = (a.kblocks_total + splits - 1) / splits;
+  a.n_main = n_main_for(rpad);
+  a.tmem_cols = 512;  // one CTA per SM (shared memory), so the whole TMEM is free
+  a.part = part;
+  a.err = err;
+  const size_t stage_bytes = (size_t)(2 * BM * BK * 2 + 2 * rpad * BK * 2);
+  int optin = 0;
+  VIE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  a.stages = (int)std::min<size_t>(MAX_STAGES, ((size_t)optin - 1024 - 256) / stage_bytes);
+  if (a.stages < 2) {
+    set_error("BF16 product: not enough shared memory for two stages");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const size_t smem = 1024 + a.stages * stage_bytes + 256;
+  VIE_CUDA(cudaFuncSetAttribute((const void *)k_gemm_bf16x3,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((N + BM - 1) / BM), (unsigned)splits);
+  k_gemm_bf16x3<<<grid, 128, smem, st>>>(mkhi, mklo, mghi, mglo, a);
+  VIE_CHECK_LAUNCH("k_gemm_bf16x3");
+  k_gemm_finish<<<grid_for((long)nrhs * N, 256), 256, 0, st>>>(part, splits, nrhs, N, g, op, err, y);
+  VIE_CHECK_LAUNCH("k_gemm_finish");
+  return VIE_OK;
+}
+
+}  // namespace vie

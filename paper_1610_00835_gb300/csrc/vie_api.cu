@@ -130,6 +130,14 @@ struct vie_handle {
   double *h_pinned = nullptr;                 // host-pinned scalars / gv seed
   // apply timing
   bool opts_disable_sym = false;              // force the general kernel (tests)
+  // assembled operator
+  int asm_mode = VIE_OPERATOR_OTF;
+  long ldk = 0;
+  void *kmat = nullptr;                       // FP32 K or BF16 Khi
+  void *kmat_lo = nullptr;                    // BF16 Klo
+  DBuf<float> g32;                            // FP32 copy of a right-hand side
+  DBuf<unsigned char> gemm_ws;                // split-K partials + BF16 G
+  int *dev_err = nullptr;                     // device error word of the products
   std::vector<ApplyEvents> events;
   size_t ev_next = 0;
   double t_apply_ms = 0.0, t_kernel_ms = 0.0;
@@ -172,6 +180,12 @@ void free_all(vie_handle *h) {
   h->stage_f1.release();
   h->stage_f2.release();
   dfree(h->qpad);
+  if (h->kmat) cudaFree(h->kmat);
+  if (h->kmat_lo) cudaFree(h->kmat_lo);
+  h->kmat = h->kmat_lo = nullptr;
+  h->g32.release();
+  h->gemm_ws.release();
+  dfree(h->dev_err);
   sym_release(&h->sym);
   free_gmres(h);
   for (auto &ev : h->events)
@@ -238,6 +252,21 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   }
   const int prec = h->opts.precision;
   const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
+  if (h->asm_mode != VIE_OPERATOR_OTF && op != VIE_OP_A_RAW) {
+    vie_status s = h->g32.reserve(h->ldk);
+    if (s != VIE_OK) return s;
+    if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
+    s = launch_gemv(h->kmat, h->kmat_lo, h->asm_mode == VIE_OPERATOR_BF16X3, h->ldk, h->N, g,
+                    h->g32.ptr, op, y, st);
+    if (s != VIE_OK) return s;
+    if (timed) {
+      VIE_CUDA(cudaEventRecord(ev->e[2], st));
+      VIE_CUDA(cudaEventRecord(ev->e[3], st));
+      ev->pending = true;
+    }
+    h->n_apply++;
+    return VIE_OK;
+  }
   vie_status s = launch_source_prep(h->N, op, h->sig_s, g, prec, h->src, st);
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
@@ -455,13 +484,71 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
     if ((s = h->stage_b.reserve(total)) != VIE_OK) return s;
     yy = h->stage_b.ptr;
   }
-  for (int r = 0; r < nrhs; ++r)
-    if ((s = apply_dev(h, op, gg + (size_t)r * N, yy + (size_t)r * N, st, false)) != VIE_OK)
-      return s;
+  if (h->asm_mode == VIE_OPERATOR_BF16X3 && op != VIE_OP_A_RAW && nrhs >= 2) {
+    int sms = 0;
+    VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    for (int r0 = 0; r0 < nrhs; r0 += 256) {
+      const int nr = std::min(256, nrhs - r0);
+      if ((s = h->gemm_ws.reserve(gemm_workspace_bytes(N, h->ldk, nr, nullptr, sms))) != VIE_OK)
+        return s;
+      if ((s = launch_gemm_bf16x3(h->kmat, h->kmat_lo, h->ldk, N, gg + (size_t)r0 * N, nr, op,
+                                  yy + (size_t)r0 * N, h->gemm_ws.ptr, h->dev_err, st)) != VIE_OK)
+        return s;
+      h->n_apply += nr;
+    }
+  } else {
+    for (int r = 0; r < nrhs; ++r)
+      if ((s = apply_dev(h, op, gg + (size_t)r * N, yy + (size_t)r * N, st, false)) != VIE_OK)
+        return s;
+  }
   if (!yd) {
     VIE_CUDA(cudaMemcpyAsync(y, yy, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
     VIE_CUDA(cudaStreamSynchronize(st));
   }
+  return VIE_OK;
+}
+
+vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
+  if (!h) return invalid("vie_assemble: NULL handle");
+  if (mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FP32 && mode != VIE_OPERATOR_BF16X3)
+    return invalid("vie_assemble: unknown mode");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->kmat || h->kmat_lo) VIE_CUDA(cudaStreamSynchronize(st));
+  if (h->kmat) cudaFree(h->kmat);
+  if (h->kmat_lo) cudaFree(h->kmat_lo);
+  h->kmat = h->kmat_lo = nullptr;
+  h->asm_mode = VIE_OPERATOR_OTF;
+  if (mode == VIE_OPERATOR_OTF) return VIE_OK;
+  if (!h->sym.usable || h->opts.precision != VIE_PREC_FP32 || h->opts.tau_mode != VIE_TAU_MARCH ||
+      h->opts.steps != 64) {
+    set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "
+              "in shared memory");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const long N = h->N;
+  h->ldk = assembled_ldk(N);
+  const size_t half = sizeof(short) * (size_t)N * h->ldk;
+  vie_status s;
+  if (mode == VIE_OPERATOR_FP32) {
+    VIE_CUDA(cudaMalloc(&h->kmat, 2 * half));
+  } else {
+    VIE_CUDA(cudaMalloc(&h->kmat, half));
+    cudaError_t e = cudaMalloc(&h->kmat_lo, half);
+    if (e != cudaSuccess) {
+      cudaFree(h->kmat);
+      h->kmat = nullptr;
+      return cuda_fail(e, "cudaMalloc");
+    }
+  }
+  if (!h->dev_err && (s = dalloc(&h->dev_err, 1)) != VIE_OK) return s;
+  VIE_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
+  s = launch_assemble(h->sym, h->dim, h->n, N, h->sig_s, h->diag,
+                      mode == VIE_OPERATOR_FP32 ? (float *)h->kmat : nullptr,
+                      mode == VIE_OPERATOR_BF16X3 ? h->kmat : nullptr, h->kmat_lo, h->device, st);
+  if (s != VIE_OK) return s;
+  h->asm_mode = mode;
   return VIE_OK;
 }
 

@@ -94,6 +94,18 @@ vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *s
 vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale2, float wcoef,
                       const float *src, double *partial, cudaStream_t st);
 
+// ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
+long assembled_ldk(long N);
+vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,
+                           const double *diag, float *k32, void *khi, void *klo, int device,
+                           cudaStream_t st);
+vie_status launch_gemv(const void *k, const void *klo, int bf16, long ldk, long N, const double *g,
+                       float *g32, int op, double *y, cudaStream_t st);
+size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms);
+vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g,
+                              int nrhs, int op, double *y, void *workspace, int *err,
+                              cudaStream_t st);
+
 // ---- Krylov kernels (k_krylov.cu)
 int dot_blocks(long N);
 vie_status launch_dots(const double *V, int nv, long ldv, const double *w, long N, double *part,

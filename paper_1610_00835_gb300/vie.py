@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "VIE_OK", 1: "VIE_ERR_INVALID_ARG", 2: "VIE_ERR_CUDA", 3: "VI
 VIE_TAU_MARCH, VIE_TAU_CLOSED = 0, 1
 VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
 VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
+VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3 = 0, 1, 2
 
 
 class VieError(RuntimeError):
@@ -71,6 +72,7 @@ SIGNATURES = {
     "vie_last_error": (C.c_char_p, []),
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
+    "vie_assemble": (C.c_int, [_vp, C.c_int, _vp]),
     "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
@@ -176,6 +178,10 @@ def vie_apply(h: VieHandle, op: int, g, y, nrhs: int = 1, stream=None) -> None:
     gp, _g = _ptr(g, np.float64)
     yp, _y = _ptr(y, np.float64)
     _check(load().vie_apply(h.ptr, op, gp, yp, nrhs, _stream(stream)))
+
+
+def vie_assemble(h: VieHandle, mode: int, stream=None) -> None:
+    _check(load().vie_assemble(h.ptr, mode, _stream(stream)))
 
 
 def vie_solve_gmres(h: VieHandle, f, U, rtol: float = 1e-6, restart: int = 64, maxit: int = 1000,
