@@ -130,7 +130,9 @@ enum {
  * iterations in the same way (Section 4.2).  Entries are the on-the-fly FP32
  * values (S = 64 march, self cell on the diagonal); storage is N x LDK with
  * LDK = N rounded up to 64, 4 bytes per entry in both modes (1.07 GB at
- * 128^2, 17.2 GB at 256^2).  VIE_OP_A_RAW keeps the on-the-fly path.  One RHS
+ * 128^2, 17.2 GB at 256^2).  VIE_OP_A_RAW uses phi = K (sigma_s^{-1} f)
+ * (Eq. EQ:ERT Intgrl FMM) when sigma_s > 0 everywhere, else the on-the-fly
+ * path.  One RHS
  * uses a bandwidth-bound CUDA-core product; vie_apply with nrhs >= 2 in
  * VIE_OPERATOR_BF16X3 mode uses one tensor-core product for up to 256 RHS.
  * VIE_OPERATOR_OTF frees the matrix.  Needs FP32 precision, the march and

@@ -79,6 +79,12 @@ __global__ void __launch_bounds__(256) k_gemv(const void *__restrict__ K, const 
   }
 }
 
+__global__ void k_divide(long N, const double *__restrict__ a, const double *__restrict__ b,
+                         double *__restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    out[i] = a[i] / b[i];
+}
+
 // g (FP64 [nrhs][N]) -> FP32 [nrhs][ldk], zero padded
 __global__ void k_to_f32_padded(const double *__restrict__ g, long N, long ldk, int nrhs,
                                 float *__restrict__ out) {
@@ -411,6 +417,12 @@ int grid_for(long n, int threads) {
 }
 
 }  // namespace
+
+vie_status launch_divide(long N, const double *a, const double *b, double *out, cudaStream_t st) {
+  k_divide<<<grid_for(N, 256), 256, 0, st>>>(N, a, b, out);
+  VIE_CHECK_LAUNCH("k_divide");
+  return VIE_OK;
+}
 
 vie_status launch_gemv(const void *k, const void *klo, int bf16, long ldk, long N, const double *g,
                        float *g32, int op, double *y, cudaStream_t st) {

@@ -138,6 +138,8 @@ struct vie_handle {
   DBuf<float> g32;                            // FP32 copy of a right-hand side
   DBuf<unsigned char> gemm_ws;                // split-K partials + BF16 G
   int *dev_err = nullptr;                     // device error word of the products
+  bool sig_s_positive = false;                // phi = K (f / sigma_s) is available
+  DBuf<double> fscaled;                       // f / sigma_s
   std::vector<ApplyEvents> events;
   size_t ev_next = 0;
   double t_apply_ms = 0.0, t_kernel_ms = 0.0;
@@ -252,9 +254,17 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   }
   const int prec = h->opts.precision;
   const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
-  if (h->asm_mode != VIE_OPERATOR_OTF && op != VIE_OP_A_RAW) {
+  const bool raw_via_k = op == VIE_OP_A_RAW && h->sig_s_positive;
+  if (h->asm_mode != VIE_OPERATOR_OTF && (op != VIE_OP_A_RAW || raw_via_k)) {
     vie_status s = h->g32.reserve(h->ldk);
     if (s != VIE_OK) return s;
+    if (raw_via_k) {
+      // phi = A f = K (sigma_s^{-1} f)  (Eq. EQ:ERT Intgrl FMM)
+      if ((s = h->fscaled.reserve(h->N)) != VIE_OK) return s;
+      if ((s = launch_divide(h->N, g, h->sig_s, h->fscaled.ptr, st)) != VIE_OK) return s;
+      g = h->fscaled.ptr;
+      op = VIE_OP_K_SIGMA_S;
+    }
     if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
     s = launch_gemv(h->kmat, h->kmat_lo, h->asm_mode == VIE_OPERATOR_BF16X3, h->ldk, h->N, g,
                     h->g32.ptr, op, y, st);
@@ -368,7 +378,9 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
   const long N = g->dim == 2 ? (long)g->n * g->n : (long)g->n * g->n * g->n;
   if (is_device_ptr(sigma_t) || is_device_ptr(sigma_s))
     return invalid("vie_create: sigma_t and sigma_s must be host arrays");
+  bool ss_positive = true;
   for (long i = 0; i < N; ++i) {
+    ss_positive = ss_positive && sigma_s[i] > 0.0;
     if (!isfinite(sigma_t[i]) || !isfinite(sigma_s[i])) {
       set_error("vie_create: non-finite coefficient");
       return VIE_ERR_NONFINITE;
@@ -386,6 +398,7 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
   h->P = g->n + 1;
   h->N = N;
   h->opts = opts;
+  h->sig_s_positive = ss_positive;
   const long lattice = g->dim == 2 ? (long)h->P * h->P : (long)h->P * h->P * h->P;
   vie_status s;
 #define TRY(x)            \
@@ -515,11 +528,14 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   DeviceGuard dg(h->device);
   if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  if (h->kmat || h->kmat_lo) VIE_CUDA(cudaStreamSynchronize(st));
-  if (h->kmat) cudaFree(h->kmat);
-  if (h->kmat_lo) cudaFree(h->kmat_lo);
-  h->kmat = h->kmat_lo = nullptr;
-  h->asm_mode = VIE_OPERATOR_OTF;
+  const bool reuse = mode != VIE_OPERATOR_OTF && mode == h->asm_mode && h->kmat;
+  if (!reuse) {
+    if (h->kmat || h->kmat_lo) VIE_CUDA(cudaStreamSynchronize(st));
+    if (h->kmat) cudaFree(h->kmat);
+    if (h->kmat_lo) cudaFree(h->kmat_lo);
+    h->kmat = h->kmat_lo = nullptr;
+    h->asm_mode = VIE_OPERATOR_OTF;
+  }
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
   if (!h->sym.usable || h->opts.precision != VIE_PREC_FP32 || h->opts.tau_mode != VIE_TAU_MARCH ||
       h->opts.steps != 64) {
@@ -531,7 +547,9 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   h->ldk = assembled_ldk(N);
   const size_t half = sizeof(short) * (size_t)N * h->ldk;
   vie_status s;
-  if (mode == VIE_OPERATOR_FP32) {
+  if (reuse) {
+    // same storage, entries recomputed in place
+  } else if (mode == VIE_OPERATOR_FP32) {
     VIE_CUDA(cudaMalloc(&h->kmat, 2 * half));
   } else {
     VIE_CUDA(cudaMalloc(&h->kmat, half));

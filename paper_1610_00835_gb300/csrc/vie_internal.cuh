@@ -101,6 +101,7 @@ vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const doub
                            cudaStream_t st);
 vie_status launch_gemv(const void *k, const void *klo, int bf16, long ldk, long N, const double *g,
                        float *g32, int op, double *y, cudaStream_t st);
+vie_status launch_divide(long N, const double *a, const double *b, double *out, cudaStream_t st);
 size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms);
 vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g,
                               int nrhs, int op, double *y, void *workspace, int *err,

@@ -27,7 +27,7 @@ def test_single_rhs_all_rows(mode, n):
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
     P.vie_assemble(h, mode)
     g = m.f + 0.2 * np.random.default_rng(n).standard_normal(m.N)
-    for op in (P.VIE_OP_K_SIGMA_S, P.VIE_OP_I_MINUS_K):
+    for op in (P.VIE_OP_K_SIGMA_S, P.VIE_OP_I_MINUS_K, P.VIE_OP_A_RAW):
         got = _apply(h, op, g, 1)[0]
         want = O.apply(2, m.sigma_t, m.sigma_s, g, op=op)
         assert rel_l2(got, want) < TOL
