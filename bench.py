@@ -375,20 +375,26 @@ def run_apply_only(args):
 
     m = V.heterogeneous_2d(n=args.n) if args.dim == 2 else V.heterogeneous_3d(n=args.n)
     h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS)
-    g = torch.as_tensor(m.f, dtype=torch.float64, device="cuda:0")
+    mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32,
+            "bf16x3": P.VIE_OPERATOR_BF16X3}[args.operator]
+    P.vie_assemble(h, mode)
+    nrhs = args.nrhs
+    G = V.bump_sources(args.dim, m.n, nrhs, seed=V.seed_for(4)) if nrhs > 1 else m.f[None, :]
+    g = torch.as_tensor(G.ravel(), dtype=torch.float64, device="cuda:0")
     y = torch.empty_like(g)
     for _ in range(args.warmup):
-        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y)
+        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y, nrhs)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y)
+        P.vie_apply(h, P.VIE_OP_K_SIGMA_S, g, y, nrhs)
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
-    print(json.dumps({"mode": "apply-only", "dim": args.dim, "n": m.n, "N": m.N,
-                      "ms_per_apply": ms, "gpair_per_s": m.N * m.N / ms / 1e6}), flush=True)
+    print(json.dumps({"mode": "apply-only", "operator": args.operator, "nrhs": nrhs,
+                      "dim": args.dim, "n": m.n, "N": m.N, "ms_per_apply": ms,
+                      "gpair_per_s": float(m.N) * m.N * nrhs / ms / 1e6}), flush=True)
     P.vie_destroy(h)
     return 0
 
@@ -399,6 +405,8 @@ def main(argv=None):
                     help="time operator applies only (profiling driver)")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3"], default="otf")
+    ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
