@@ -211,6 +211,40 @@ vie_status ert_sweep(vie_handle *h, const double *U, const double *f, const floa
 vie_status vie_apply_noalloc(int dim, int n, const double *sigma_t, const double *sigma_s,
                              vie_op op, const double *g, double *y, void *stream);
 
+/* ---- Batches of media (many uneven 2D grids in one launch). */
+typedef struct vie_batch vie_batch;
+
+/* Create a batch of `count` 2D media (grids[i].dim == 2), each with its own
+ * n and host FP64 coefficients sigma_t[i], sigma_s[i] (copied).  Options must
+ * be FP32 tiles with the S = 64 march.  Vectors of the batch are packed:
+ * medium i occupies cells [offsets[i], offsets[i+1]) (vie_batch_layout).
+ * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
+                            const double *const *sigma_t, const double *const *sigma_s,
+                            const vie_opts *o);
+vie_status vie_batch_destroy(vie_batch *b);
+
+/* Total cells and the count + 1 packed offsets of the media. */
+vie_status vie_batch_layout(vie_batch *b, long long *total_cells, long long *offsets);
+
+/* Apply the operator of every medium (as vie_apply, nrhs = 1) to the packed
+ * FP64 vector g, writing the packed y: one persistent kernel over all media's
+ * tile pairs (dynamic scheduling across media, sigma_t re-staged per medium),
+ * replayed from a CUDA graph that is captured on the first call for a given
+ * (op, g, y) and re-captured when they change.  Host pointers are staged and
+ * the call then synchronises.  Errors: INVALID_ARG, CUDA. */
+vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, void *stream);
+
+/* Time the launch configurations (CTA groups 8/4/2; shared-memory staging of
+ * every lattice that fits, or only up to 128 KB) on this batch and keep the
+ * fastest.  With cache_path, a line "<device>|<n_1>,...,<n_k>, <groups>
+ * <policy>" is read from (a hit skips the timing) or appended to that file.
+ * Errors: INVALID_ARG, CUDA. */
+vie_status vie_batch_autotune(vie_batch *b, const char *cache_path, void *stream);
+
+/* Current configuration: CTA groups and lattice staging policy. */
+vie_status vie_batch_config(vie_batch *b, int *groups, int *smem_policy);
+
 /* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);
 

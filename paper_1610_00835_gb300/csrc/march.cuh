@@ -190,6 +190,53 @@ __device__ __forceinline__ float march64(const Geo &g, float jx, float jy, float
 }
 
 
+// 2D lattice read from global memory (through L1) for grids whose lattice
+// does not fit in shared memory.  Same arithmetic as sample_pair<2, 0, 0>.
+struct GeoG {
+  const float *base;  // element 0
+  unsigned bias;      // 0x4B000000 (1 + ldp), subtracted from the biased index
+  int ldp;
+};
+
+__device__ __forceinline__ u64 sample_pair_g(const GeoG &g, u64 m2, u64 px, u64 py) {
+  const u64 bx = addrm2(px, m2), by = addrm2(py, m2);
+  const u64 ax = sub2(px, sub2(bx, m2)), ay = sub2(py, sub2(by, m2));
+  unsigned x0, x1, y0, y1;
+  upku(bx, x0, x1);
+  upku(by, y0, y1);
+  const float *p0 = g.base + (x0 + (unsigned)g.ldp * y0 - g.bias);
+  const float *p1 = g.base + (x1 + (unsigned)g.ldp * y1 - g.bias);
+  const u64 v00 = pk(__ldg(p0), __ldg(p1)), v10 = pk(__ldg(p0 + 1), __ldg(p1 + 1));
+  const u64 v01 = pk(__ldg(p0 + g.ldp), __ldg(p1 + g.ldp));
+  const u64 v11 = pk(__ldg(p0 + g.ldp + 1), __ldg(p1 + g.ldp + 1));
+  const u64 lo = fma2(ax, sub2(v10, v00), v00);
+  const u64 hi = fma2(ax, sub2(v11, v01), v01);
+  return fma2(ay, sub2(hi, lo), lo);
+}
+
+__device__ __forceinline__ float march64_g(const GeoG &g, float jx, float jy, float dx, float dy) {
+  const u64 m2 = pk(kTwo23, kTwo23);
+  const float sx = dx * (1.0f / kS), sy = dy * (1.0f / kS);
+  u64 px = pk(fmaf(0.5f, sx, jx), fmaf(1.5f, sx, jx));
+  u64 py = pk(fmaf(0.5f, sy, jy), fmaf(1.5f, sy, jy));
+  const u64 tx = pk(2.f * sx, 2.f * sx), ty = pk(2.f * sy, 2.f * sy);
+  u64 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+  for (int i = 0; i < kS / 2; ++i) {
+    const u64 v = sample_pair_g(g, m2, px, py);
+    if (i & 1)
+      acc1 = add2(acc1, v);
+    else
+      acc0 = add2(acc0, v);
+    px = add2(px, tx);
+    py = add2(py, ty);
+  }
+  float a, b, c, d;
+  upk(acc0, a, b);
+  upk(acc1, c, d);
+  return (a + b) + (c + d);
+}
+
 // Base address of a lattice at shared address lat_addr with strides (ldp,
 // plane): element (x, y, z) is read at base + 4 (X + ldp Y + plane Z), X, Y, Z
 // the biased float bits 0x4B000000 + coordinate.

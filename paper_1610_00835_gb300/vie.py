@@ -73,6 +73,13 @@ SIGNATURES = {
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
     "vie_assemble": (C.c_int, [_vp, C.c_int, _vp]),
+    "vie_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(vie_grid),
+                                   C.POINTER(_vp), C.POINTER(_vp), C.POINTER(vie_opts)]),
+    "vie_batch_destroy": (C.c_int, [_vp]),
+    "vie_batch_layout": (C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "vie_batch_apply": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "vie_batch_autotune": (C.c_int, [_vp, C.c_char_p, _vp]),
+    "vie_batch_config": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
@@ -205,6 +212,65 @@ def vie_apply_noalloc(dim: int, n: int, sigma_t, sigma_s, op: int, g, y, stream=
     gp, _g = _ptr(g, np.float64)
     yp, _y = _ptr(y, np.float64)
     _check(load().vie_apply_noalloc(dim, n, sp, qp, op, gp, yp, _stream(stream)))
+
+
+@dataclass
+class VieBatch:
+    ptr: C.c_void_p
+    ns: list
+    offsets: list
+
+    @property
+    def total(self) -> int:
+        return self.offsets[-1]
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                vie_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def vie_batch_create(ns, sigma_t_list, sigma_s_list, device: int = 0) -> VieBatch:
+    L = load()
+    count = len(ns)
+    grids = (vie_grid * count)(*[vie_grid(2, int(n)) for n in ns])
+    st = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in sigma_t_list]
+    ss = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in sigma_s_list]
+    pst = (_vp * count)(*[a.ctypes.data for a in st])
+    pss = (_vp * count)(*[a.ctypes.data for a in ss])
+    o = vie_opts(64, VIE_TAU_MARCH, VIE_PREC_FP32, device)
+    b = C.c_void_p()
+    _check(L.vie_batch_create(C.byref(b), count, grids, pst, pss, C.byref(o)))
+    total = C.c_longlong()
+    offs = (C.c_longlong * (count + 1))()
+    _check(L.vie_batch_layout(b, C.byref(total), offs))
+    return VieBatch(b, list(ns), [int(x) for x in offs])
+
+
+def vie_batch_destroy(b: VieBatch) -> None:
+    if b.ptr:
+        _check(load().vie_batch_destroy(b.ptr))
+        b.ptr = C.c_void_p()
+
+
+def vie_batch_apply(b: VieBatch, op: int, g, y, stream=None) -> None:
+    gp, _g = _ptr(g, np.float64)
+    yp, _y = _ptr(y, np.float64)
+    _check(load().vie_batch_apply(b.ptr, op, gp, yp, _stream(stream)))
+
+
+def vie_batch_autotune(b: VieBatch, cache_path=None, stream=None) -> tuple:
+    path = cache_path.encode() if cache_path else None
+    _check(load().vie_batch_autotune(b.ptr, path, _stream(stream)))
+    return vie_batch_config(b)
+
+
+def vie_batch_config(b: VieBatch) -> tuple:
+    g, p = C.c_int(), C.c_int()
+    _check(load().vie_batch_config(b.ptr, C.byref(g), C.byref(p)))
+    return g.value, p.value
 
 
 def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
