@@ -247,6 +247,33 @@ def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
                          "work": "4 B per K entry (hi + lo) + FP64 G and Y"}}
 
 
+def measure_batch(P, torch, stream, local, reps=3):
+    """16 uneven 2D grids n = 64 ... 256 (Sum N^2 = 1.94e10 pairs) in one
+    persistent launch replayed from a CUDA graph, configuration autotuned."""
+    media = V.uneven_media()
+    ns = [m.n for m in media]
+    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media], device=local)
+    t0 = time.perf_counter()
+    cfg = P.vie_batch_autotune(b)
+    tune_s = time.perf_counter() - t0
+    g = torch.as_tensor(np.concatenate([m.f for m in media]), dtype=torch.float64,
+                        device=f"cuda:{local}")
+    y = torch.empty_like(g)
+    P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / reps
+    pairs = float(sum(m.N * m.N for m in media))
+    P.vie_batch_destroy(b)
+    return {"grids": ns, "pairs": pairs, "ms": ms, "gpair_per_s": pairs / (ms * 1e-3) / 1e9,
+            "config": {"groups_per_cta": cfg[0], "smem_policy": cfg[1]}, "autotune_s": tune_s}
+
+
 def run_ours(args):
     import torch
     import paper_1610_00835_gb300 as P
@@ -322,6 +349,7 @@ def run_ours(args):
 
     chosen = measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
+    batch = measure_batch(P, torch, stream, local)
 
     # end to end through the C ABI from host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -357,6 +385,7 @@ def run_ours(args):
                       "apply_ms": sum(r["t_apply_ms"] for r in reps) / n_apply,
                       "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen},
             "bf16x3_product": product,
+            "batch_uneven_grids": batch,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
         }
