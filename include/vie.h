@@ -161,6 +161,9 @@ typedef struct {
   double t_total_ms;   /* host wall time of the call                          */
   double t_apply_ms;   /* summed CUDA-event time of the applies (time_apply)  */
   double t_apply_kernel_ms; /* of that, the pair kernel alone (time_apply)     */
+  int precond_iters;   /* Arnoldi steps taken with the learned preconditioner  */
+  int fell_back;       /* 1 if the preconditioned iteration stalled and plain
+                          GMRES finished the solve                            */
 } vie_report;
 
 /* Solve (I - K) U = phi by restarted GMRES(m) in FP64 (Algorithm 1, S.2;
@@ -244,6 +247,43 @@ vie_status vie_batch_autotune(vie_batch *b, const char *cache_path, void *stream
 
 /* Current configuration: CTA groups and lattice staging policy. */
 vie_status vie_batch_config(vie_batch *b, int *groups, int *smem_policy);
+
+/* ---- Learned right preconditioner (no paper counterpart; it takes the place
+ * of the paper's FFT and diffusion preconditioners, Section 4.4).
+ * A U-Net with `levels` levels and `channels` channels maps the input
+ * (sigma_t / s_ref, sigma_s / s_ref, b / rms(b)) on an n x n grid to o, and
+ * the preconditioner is M(b) = b + rms(b) o: the network supplies the smooth
+ * part of (I - K)^{-1} b.  Weights are FP32 (training) with a BF16 copy for
+ * inference; accumulation is FP32.  Parameter layout: for every convolution
+ * in the order encoder (level 0 first, two each), decoder (deepest first, two
+ * each), head: weights [Co][Ci][k][k] then bias [Co]. */
+typedef struct vie_unet vie_unet;
+vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned long long seed, int device);
+vie_status vie_unet_destroy(vie_unet *u);
+vie_status vie_unet_num_params(vie_unet *u, long long *n);
+vie_status vie_unet_get_params(vie_unet *u, float *host_params);
+vie_status vie_unet_set_params(vie_unet *u, const float *host_params);
+/* o = Net(x): x device FP32 [B][3][n][n], o device FP32 [B][n][n]; n divisible
+ * by 2^(levels-1); use_bf16 selects the BF16 weights. */
+vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n, int use_bf16, void *stream);
+/* Mean squared error of Net(x) against t (device FP32 [B][n][n]) and, if
+ * grads_host is not NULL, its gradient with respect to every parameter
+ * (host FP32 [num_params]). Synchronous. */
+vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B, int n, float *grads_host,
+                              double *loss, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; returns the loss. */
+vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, int B, int n, float lr,
+                               double *loss, void *stream);
+vie_status vie_unet_save(vie_unet *u, const char *path);
+vie_status vie_unet_load(vie_unet *u, const char *path);
+/* Use `u` as the right preconditioner of vie_solve_gmres on this handle
+ * (flexible GMRES); NULL restores plain GMRES.  2D handles only, n divisible
+ * by 2^(levels-1); s_ref scales the coefficient channels (> 0).  If the
+ * preconditioned residual stalls (two consecutive Arnoldi steps each
+ * reducing it by less than 20 %) or the network output is not finite, the
+ * solve continues with plain GMRES from the current iterate and reports
+ * fell_back = 1.  The network must outlive its use by the handle. */
+vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
 
 /* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);

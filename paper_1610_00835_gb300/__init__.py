@@ -4,6 +4,9 @@ two-step radiative-transfer method of Ren, Zhang & Zhong (arXiv 1610.00835).
 The compute lives in ``libvie.so`` (CUDA, built from ``csrc/``); this package
 is its ctypes binding.  See ``include/vie.h`` for the C ABI.
 """
+from .vie import (VieUnet, vie_set_preconditioner, vie_unet_create, vie_unet_destroy,
+                  vie_unet_forward, vie_unet_get_params, vie_unet_load, vie_unet_loss_grad,
+                  vie_unet_num_params, vie_unet_save, vie_unet_set_params, vie_unet_train_step)
 from .vie import (VieBatch, vie_batch_apply, vie_batch_autotune, vie_batch_config,
                   vie_batch_create, vie_batch_destroy)
 from .vie import (VIE_OPERATOR_BF16X3, VIE_OPERATOR_FP32, VIE_OPERATOR_OTF, VIE_OP_A_RAW, VIE_OP_I_MINUS_K, VIE_OP_K_SIGMA_S, VIE_PREC_FP32,
@@ -11,7 +14,10 @@ from .vie import (VIE_OPERATOR_BF16X3, VIE_OPERATOR_FP32, VIE_OPERATOR_OTF, VIE_
                   load, vie_apply, vie_apply_noalloc, vie_assemble, vie_create, vie_destroy, vie_get_diagonal, vie_last_error,
                   vie_kernel_launches, vie_solve_gmres, vie_version)
 
-__all__ = ["VieBatch", "vie_batch_apply", "vie_batch_autotune", "vie_batch_config",
+__all__ = ["VieUnet", "vie_set_preconditioner", "vie_unet_create", "vie_unet_destroy",
+           "vie_unet_forward", "vie_unet_get_params", "vie_unet_load", "vie_unet_loss_grad",
+           "vie_unet_num_params", "vie_unet_save", "vie_unet_set_params", "vie_unet_train_step",
+           "VieBatch", "vie_batch_apply", "vie_batch_autotune", "vie_batch_config",
            "vie_batch_create", "vie_batch_destroy",
            "VIE_OPERATOR_BF16X3", "VIE_OPERATOR_FP32", "VIE_OPERATOR_OTF", "VIE_OP_A_RAW", "VIE_OP_I_MINUS_K", "VIE_OP_K_SIGMA_S", "VIE_PREC_FP32",
            "VIE_PREC_FP64", "VIE_TAU_CLOSED", "VIE_TAU_MARCH", "VieError", "VieHandle",

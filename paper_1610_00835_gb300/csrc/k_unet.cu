@@ -1,0 +1,861 @@
+// Learned right preconditioner: a small convolutional U-Net, trained and
+// evaluated with this library's own kernels.  The paper preconditions its
+// Krylov solve with FFT and diffusion solvers (Section 4.4); here a network
+// maps (sigma_t, sigma_s, b) to the smooth part of (I - K)^{-1} b, and FGMRES
+// (vie_solve_gmres with a preconditioner set) absorbs that it is nonlinear.
+//
+// Network (L levels, C channels; tensors FP32 NCHW, weights [Co][Ci][k][k]):
+//   encoder l = 0..L-1: a_l = relu(conv3(x_l)), e_l = relu(conv3(a_l)),
+//                       x_0 = input (3 channels), x_l = avgpool2(e_{l-1});
+//   decoder l = L-2..0: c_l = [upsample2(d_{l+1}), e_l], b_l = relu(conv3(c_l)),
+//                       d_l = relu(conv3(b_l)), d_{L-1} = e_{L-1};
+//   output  o = conv1(d_0).
+// e_l (l < L-1) is written straight into the second half of c_l's channels.
+// Training minimises mean((o - t)^2) with Adam; inference can use a BF16 copy
+// of the weights (FP32 accumulation either way).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+namespace {
+
+constexpr int TX = 32, TY = 16;   // output tile of the 3x3 convolution kernels
+constexpr int CIB = 8;            // input channels staged per step
+constexpr int COB = 32;           // output channels per CTA
+
+// ------------------------------------------------------------ kernels
+
+// 3x3 convolution, zero padding 1, + bias (+ relu).  Thread (tx, ty) owns the
+// pixels (x0 + tx, y0 + ty) and (x0 + tx, y0 + ty + 8) for all COB outputs.
+template <bool RELU, typename WT>
+__global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, long in_bs, int Ci,
+                                               const WT *__restrict__ w, const float *__restrict__ bias,
+                                               float *__restrict__ out, long out_bs, int Co, int H,
+                                               int W, int co_blocks) {
+  __shared__ float in_s[CIB][TY + 2][TX + 2];
+  __shared__ __align__(16) float w_s[CIB][9][COB];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;  // ty in 0..7
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int b = blockIdx.z / co_blocks, cb = blockIdx.z % co_blocks;
+  const int co0 = cb * COB;
+  float acc0[COB], acc1[COB];
+#pragma unroll
+  for (int c = 0; c < COB; ++c) acc0[c] = acc1[c] = 0.f;
+  const float *inb = in + b * in_bs;
+  const long plane = (long)H * W;
+  for (int ci0 = 0; ci0 < Ci; ci0 += CIB) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < CIB * (TY + 2) * (TX + 2); i += 256) {
+      const int c = i / ((TY + 2) * (TX + 2)), r = i % ((TY + 2) * (TX + 2));
+      const int yy = r / (TX + 2), xx = r % (TX + 2);
+      const int gy = y0 - 1 + yy, gx = x0 - 1 + xx;
+      float v = 0.f;
+      if (ci0 + c < Ci && gy >= 0 && gy < H && gx >= 0 && gx < W) v = inb[(ci0 + c) * plane + (long)gy * W + gx];
+      in_s[c][yy][xx] = v;
+    }
+    for (int i = threadIdx.x; i < CIB * 9 * COB; i += 256) {
+      const int c = i / (9 * COB), r = i % (9 * COB);
+      const int tap = r / COB, co = r % COB;
+      float v = 0.f;
+      if (ci0 + c < Ci && co0 + co < Co) v = (float)w[((long)(co0 + co) * Ci + ci0 + c) * 9 + tap];
+      w_s[c][tap][co] = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < CIB; ++c) {
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const float v0 = in_s[c][ty + dy][tx + dx];
+        const float v1 = in_s[c][ty + 8 + dy][tx + dx];
+        const float4 *wr = reinterpret_cast<const float4 *>(&w_s[c][tap][0]);
+#pragma unroll
+        for (int q = 0; q < COB / 4; ++q) {
+          const float4 wv = wr[q];
+          acc0[4 * q + 0] = fmaf(v0, wv.x, acc0[4 * q + 0]);
+          acc0[4 * q + 1] = fmaf(v0, wv.y, acc0[4 * q + 1]);
+          acc0[4 * q + 2] = fmaf(v0, wv.z, acc0[4 * q + 2]);
+          acc0[4 * q + 3] = fmaf(v0, wv.w, acc0[4 * q + 3]);
+          acc1[4 * q + 0] = fmaf(v1, wv.x, acc1[4 * q + 0]);
+          acc1[4 * q + 1] = fmaf(v1, wv.y, acc1[4 * q + 1]);
+          acc1[4 * q + 2] = fmaf(v1, wv.z, acc1[4 * q + 2]);
+          acc1[4 * q + 3] = fmaf(v1, wv.w, acc1[4 * q + 3]);
+        }
+      }
+    }
+  }
+  const int x = x0 + tx;
+  float *ob = out + b * out_bs;
+#pragma unroll
+  for (int c = 0; c < COB; ++c) {
+    const int co = co0 + c;
+    if (co >= Co || x >= W) continue;
+    const float bv = bias ? bias[co] : 0.f;
+    const int ya = y0 + ty, yb = y0 + ty + 8;
+    float va = acc0[c] + bv, vb = acc1[c] + bv;
+    if (RELU) {
+      va = fmaxf(va, 0.f);
+      vb = fmaxf(vb, 0.f);
+    }
+    if (ya < H) ob[co * plane + (long)ya * W + x] = va;
+    if (yb < H) ob[co * plane + (long)yb * W + x] = vb;
+  }
+}
+
+// Gradient of a 3x3 convolution's weights and bias over one 32 x 8 pixel tile
+// of one image and 8 input channels; thread (co, ci) keeps its 9 taps and
+// accumulates them into dw with atomics.  A 3 x 3 window of the input slides
+// along x in registers.
+constexpr int WY = 8;
+__global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, long x_bs, int Ci,
+                                                  const float *__restrict__ gy, long g_bs, int Co,
+                                                  int H, int W, float *__restrict__ dw,
+                                                  float *__restrict__ db, int ci_blocks,
+                                                  int co_blocks) {
+  __shared__ float g_s[COB][WY * TX + 1];
+  __shared__ float x_s[CIB][WY + 2][TX + 2];
+  const int co_l = threadIdx.x % 32, ci_l = threadIdx.x / 32;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * WY;
+  int z = blockIdx.z;
+  const int cib = z % ci_blocks;
+  z /= ci_blocks;
+  const int cob = z % co_blocks;
+  const int b = z / co_blocks;
+  const int ci0 = cib * CIB, co0 = cob * COB;
+  const long plane = (long)H * W;
+  for (int i = threadIdx.x; i < COB * WY * TX; i += 256) {
+    const int c = i / (WY * TX), p = i % (WY * TX);
+    const int yy = p / TX, xx = p % TX;
+    const int gyy = y0 + yy, gxx = x0 + xx;
+    float v = 0.f;
+    if (co0 + c < Co && gyy < H && gxx < W) v = gy[b * g_bs + (co0 + c) * plane + (long)gyy * W + gxx];
+    g_s[c][p] = v;
+  }
+  for (int i = threadIdx.x; i < CIB * (WY + 2) * (TX + 2); i += 256) {
+    const int c = i / ((WY + 2) * (TX + 2)), r = i % ((WY + 2) * (TX + 2));
+    const int yy = r / (TX + 2), xx = r % (TX + 2);
+    const int gyy = y0 - 1 + yy, gxx = x0 - 1 + xx;
+    float v = 0.f;
+    if (ci0 + c < Ci && gyy >= 0 && gyy < H && gxx >= 0 && gxx < W)
+      v = x[b * x_bs + (ci0 + c) * plane + (long)gyy * W + gxx];
+    x_s[c][yy][xx] = v;
+  }
+  __syncthreads();
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  float bsum = 0.f;
+  for (int yy = 0; yy < WY; ++yy) {
+    float win[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      win[r][0] = x_s[ci_l][yy + r][0];
+      win[r][1] = x_s[ci_l][yy + r][1];
+    }
+    for (int xx = 0; xx < TX; ++xx) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) win[r][2] = x_s[ci_l][yy + r][xx + 2];
+      const float g = g_s[co_l][yy * TX + xx];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[r * 3 + c] = fmaf(g, win[r][c], acc[r * 3 + c]);
+      bsum += g;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        win[r][0] = win[r][1];
+        win[r][1] = win[r][2];
+      }
+    }
+  }
+  const int co = co0 + co_l, ci = ci0 + ci_l;
+  if (co < Co && ci < Ci) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) atomicAdd(&dw[((long)co * Ci + ci) * 9 + t], acc[t]);
+  }
+  if (db && cib == 0 && ci_l == 0 && co < Co) atomicAdd(&db[co], bsum);
+}
+
+// wt[ci][co][8 - tap] = w[co][ci][tap]: the adjoint of a 3x3 convolution with
+// zero padding is the convolution with the flipped, transposed kernel.
+__global__ void k_flip(const float *__restrict__ w, int Co, int Ci, float *__restrict__ wt) {
+  const long total = (long)Co * Ci * 9;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long co = i / (Ci * 9), r = i % (Ci * 9), ci = r / 9, tap = r % 9;
+    wt[(ci * Co + co) * 9 + (8 - tap)] = w[i];
+  }
+}
+
+// 1x1 convolution to one channel: o = sum_c w_c d_c + b
+template <typename WT>
+__global__ void k_head(const float *__restrict__ d, long d_bs, int C, const WT *__restrict__ w,
+                       const float *__restrict__ bias, float *__restrict__ o, long plane, int B) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * plane; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / plane, p = i % plane;
+    float s = bias[0];
+    for (int c = 0; c < C; ++c) s = fmaf((float)w[c], d[b * d_bs + c * plane + p], s);
+    o[i] = s;
+  }
+}
+
+// head backward: dd_c = w_c go (written), dw_c += sum go d_c, db += sum go
+__global__ void k_head_bwd_data(const float *__restrict__ go, int C, const float *__restrict__ w,
+                                float *__restrict__ dd, long dd_bs, long plane, int B) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * plane * C; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / (plane * C), r = i % (plane * C), c = r / plane, p = r % plane;
+    dd[b * dd_bs + c * plane + p] = w[c] * go[b * plane + p];
+  }
+}
+
+__global__ void k_head_bwd_w(const float *__restrict__ go, const float *__restrict__ d, long d_bs, int C,
+                             long plane, int B, float *__restrict__ dw, float *__restrict__ db) {
+  // one block per channel (+ one for the bias)
+  __shared__ float red[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (long i = threadIdx.x; i < (long)B * plane; i += blockDim.x) {
+    const long b = i / plane, p = i % plane;
+    s += go[i] * (c < C ? d[b * d_bs + c * plane + p] : 1.f);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (c < C)
+      dw[c] += red[0];
+    else
+      db[0] += red[0];
+  }
+}
+
+__global__ void k_avgpool(const float *__restrict__ in, long in_bs, float *__restrict__ out, long out_bs,
+                          int C, int H, int W, int B) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long per = (long)C * Ho * Wo;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / per, r = i % per, c = r / ((long)Ho * Wo), q = r % ((long)Ho * Wo);
+    const long y = q / Wo, x = q % Wo;
+    const float *p = in + b * in_bs + c * (long)H * W + (2 * y) * W + 2 * x;
+    out[b * out_bs + c * (long)Ho * Wo + q] = 0.25f * (p[0] + p[1] + p[W] + p[W + 1]);
+  }
+}
+
+// grad of avgpool: g_in (+)= g_out / 4 on each 2x2 block
+__global__ void k_avgpool_bwd(const float *__restrict__ go, long go_bs, float *__restrict__ gi, long gi_bs,
+                              int C, int H, int W, int B, int accumulate) {
+  const long per = (long)C * H * W;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / per, r = i % per, c = r / ((long)H * W), q = r % ((long)H * W);
+    const long y = q / W, x = q % W;
+    const float v = 0.25f * go[b * go_bs + c * (long)(H / 2) * (W / 2) + (y / 2) * (W / 2) + x / 2];
+    float *dst = gi + b * gi_bs + c * (long)H * W + q;
+    *dst = accumulate ? *dst + v : v;
+  }
+}
+
+__global__ void k_upsample(const float *__restrict__ in, long in_bs, float *__restrict__ out, long out_bs,
+                           int C, int H, int W, int B) {  // H, W: output size
+  const long per = (long)C * H * W;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / per, r = i % per, c = r / ((long)H * W), q = r % ((long)H * W);
+    const long y = q / W, x = q % W;
+    out[b * out_bs + c * (long)H * W + q] = in[b * in_bs + c * (long)(H / 2) * (W / 2) + (y / 2) * (W / 2) + x / 2];
+  }
+}
+
+__global__ void k_upsample_bwd(const float *__restrict__ go, long go_bs, float *__restrict__ gi, long gi_bs,
+                               int C, int H, int W, int B) {  // H, W: upsampled size
+  const int Hi = H / 2, Wi = W / 2;
+  const long per = (long)C * Hi * Wi;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / per, r = i % per, c = r / ((long)Hi * Wi), q = r % ((long)Hi * Wi);
+    const long y = q / Wi, x = q % Wi;
+    const float *p = go + b * go_bs + c * (long)H * W + (2 * y) * W + 2 * x;
+    gi[b * gi_bs + c * (long)Hi * Wi + q] = p[0] + p[1] + p[W] + p[W + 1];
+  }
+}
+
+// g *= (a > 0): relu backward through a stored activation
+__global__ void k_relu_mask(float *__restrict__ g, long g_bs, const float *__restrict__ a, long a_bs,
+                            long per, int B) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
+    const long b = i / per, r = i % per;
+    if (!(a[b * a_bs + r] > 0.f)) g[b * g_bs + r] = 0.f;
+  }
+}
+
+// loss = mean((o - t)^2) (block partials in double), go = 2 (o - t) / n
+__global__ void k_mse(const float *__restrict__ o, const float *__restrict__ t, long n, float *__restrict__ go,
+                      double *__restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float d = o[i] - t[i];
+    s += (double)d * d;
+    go[i] = 2.f * d / (float)n;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, __nv_bfloat16 *__restrict__ pb, long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ p, __nv_bfloat16 *__restrict__ pb, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// Preconditioner input [1][3][n][n]: (sigma_t / s_ref, sigma_s / s_ref, v / rms(v))
+__global__ void k_net_input(const double *__restrict__ st, const double *__restrict__ ss,
+                            const double *__restrict__ v, const double *__restrict__ vnorm2, long N,
+                            float inv_ref, float *__restrict__ x) {
+  const double rms = sqrt(*vnorm2 / (double)N);
+  const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    x[i] = (float)st[i] * inv_ref;
+    x[N + i] = (float)ss[i] * inv_ref;
+    x[2 * N + i] = (float)(v[i] * inv);
+  }
+}
+
+// z = v + rms(v) o
+__global__ void k_net_output(const double *__restrict__ v, const double *__restrict__ vnorm2,
+                             const float *__restrict__ o, long N, double *__restrict__ z) {
+  const double rms = sqrt(*vnorm2 / (double)N);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    z[i] = v[i] + rms * (double)o[i];
+}
+
+int gridn(long n) { return (int)std::max(1L, std::min((n + 255) / 256, 8192L)); }
+
+}  // namespace
+
+// ------------------------------------------------------------ network host
+
+struct ConvLayer {
+  int co, ci, k;
+  long w_off, b_off;  // into the flat parameter array
+};
+
+struct UnetImpl {
+  int L = 4, C = 32, device = 0;
+  std::vector<ConvLayer> layers;
+  long nparams = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *wt = nullptr;
+  __nv_bfloat16 *pb = nullptr;
+  long step = 0;
+  // activations for (B, n)
+  int B = 0, n = 0;
+  std::vector<float *> xin, a, cat, bl, dl, ebot;  // per level
+  std::vector<float *> gx, ga, gcat, gbl, gdl, gebot;
+  float *o = nullptr, *go = nullptr;
+  double *part = nullptr, *h_part = nullptr;
+  float *xin0_owned = nullptr;
+};
+
+namespace {
+
+void free_acts(UnetImpl *u) {
+  auto fr = [](std::vector<float *> &vv) {
+    for (float *&q : vv)
+      if (q) cudaFree(q);
+    vv.clear();
+  };
+  fr(u->xin); fr(u->a); fr(u->cat); fr(u->bl); fr(u->dl); fr(u->ebot);
+  fr(u->gx); fr(u->ga); fr(u->gcat); fr(u->gbl); fr(u->gdl); fr(u->gebot);
+  if (u->o) cudaFree(u->o);
+  if (u->go) cudaFree(u->go);
+  if (u->part) cudaFree(u->part);
+  if (u->h_part) cudaFreeHost(u->h_part);
+  u->o = u->go = nullptr;
+  u->part = nullptr;
+  u->h_part = nullptr;
+  u->B = u->n = 0;
+}
+
+vie_status ensure_acts(UnetImpl *u, int B, int n) {
+  if (u->B >= B && u->n == n) return VIE_OK;
+  free_acts(u);
+  const int L = u->L, C = u->C;
+  auto al = [](float **q, long count) -> vie_status {
+    VIE_CUDA(cudaMalloc((void **)q, sizeof(float) * std::max(1L, count)));
+    return VIE_OK;
+  };
+  u->xin.assign(L, nullptr); u->a.assign(L, nullptr); u->cat.assign(L, nullptr);
+  u->bl.assign(L, nullptr); u->dl.assign(L, nullptr); u->ebot.assign(1, nullptr);
+  u->gx.assign(L, nullptr); u->ga.assign(L, nullptr); u->gcat.assign(L, nullptr);
+  u->gbl.assign(L, nullptr); u->gdl.assign(L, nullptr); u->gebot.assign(1, nullptr);
+  vie_status s;
+  for (int l = 0; l < L; ++l) {
+    const long hw = (long)(n >> l) * (n >> l);
+    const int cin = l == 0 ? 3 : C;
+    if ((s = al(&u->xin[l], (long)B * cin * hw)) != VIE_OK) return s;
+    if ((s = al(&u->a[l], (long)B * C * hw)) != VIE_OK) return s;
+    if ((s = al(&u->gx[l], (long)B * cin * hw)) != VIE_OK) return s;
+    if ((s = al(&u->ga[l], (long)B * C * hw)) != VIE_OK) return s;
+    if (l < L - 1) {
+      if ((s = al(&u->cat[l], (long)B * 2 * C * hw)) != VIE_OK) return s;
+      if ((s = al(&u->bl[l], (long)B * C * hw)) != VIE_OK) return s;
+      if ((s = al(&u->dl[l], (long)B * C * hw)) != VIE_OK) return s;
+      if ((s = al(&u->gcat[l], (long)B * 2 * C * hw)) != VIE_OK) return s;
+      if ((s = al(&u->gbl[l], (long)B * C * hw)) != VIE_OK) return s;
+      if ((s = al(&u->gdl[l], (long)B * C * hw)) != VIE_OK) return s;
+    }
+  }
+  const long hwb = (long)(n >> (L - 1)) * (n >> (L - 1));
+  if ((s = al(&u->ebot[0], (long)B * C * hwb)) != VIE_OK) return s;
+  if ((s = al(&u->gebot[0], (long)B * C * hwb)) != VIE_OK) return s;
+  if ((s = al(&u->o, (long)B * n * n)) != VIE_OK) return s;
+  if ((s = al(&u->go, (long)B * n * n)) != VIE_OK) return s;
+  VIE_CUDA(cudaMalloc((void **)&u->part, sizeof(double) * 1024));
+  VIE_CUDA(cudaMallocHost((void **)&u->h_part, sizeof(double) * 1024));
+  u->B = B;
+  u->n = n;
+  return VIE_OK;
+}
+
+template <typename WT>
+vie_status conv3(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
+                 int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+  const int cob = (Co + COB - 1) / COB;
+  dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B * cob);
+  if (relu)
+    k_conv3<true, WT><<<grid, 256, 0, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, cob);
+  else
+    k_conv3<false, WT><<<grid, 256, 0, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, cob);
+  VIE_CHECK_LAUNCH("k_conv3");
+  return VIE_OK;
+}
+
+// Forward through the network; weights FP32 (pw) or BF16 (pbw).
+template <typename WT>
+vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cudaStream_t st) {
+  const int L = u->L, C = u->C;
+  vie_status s;
+  int li = 0;
+  const float *xl = x;
+  long xl_bs = 3L * n * n;
+  for (int l = 0; l < L; ++l) {
+    const int H = n >> l;
+    const long hw = (long)H * H;
+    const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
+    if ((s = conv3(xl, xl_bs, c1.ci, pw + c1.w_off, u->p + c1.b_off, u->a[l], (long)C * hw, C, H, H, B,
+                   true, st)) != VIE_OK)
+      return s;
+    float *e = l < L - 1 ? u->cat[l] + (long)C * hw : u->ebot[0];
+    const long e_bs = l < L - 1 ? 2L * C * hw : (long)C * hw;
+    if ((s = conv3(u->a[l], (long)C * hw, C, pw + c2.w_off, u->p + c2.b_off, e, e_bs, C, H, H, B, true,
+                   st)) != VIE_OK)
+      return s;
+    if (l < L - 1) {
+      k_avgpool<<<gridn((long)B * C * hw / 4), 256, 0, st>>>(e, e_bs, u->xin[l + 1], (long)C * hw / 4, C, H,
+                                                             H, B);
+      VIE_CHECK_LAUNCH("k_avgpool");
+      xl = u->xin[l + 1];
+      xl_bs = (long)C * hw / 4;
+    }
+  }
+  const float *d = u->ebot[0];
+  long d_bs = (long)C * (n >> (L - 1)) * (n >> (L - 1));
+  for (int l = L - 2; l >= 0; --l) {
+    const int H = n >> l;
+    const long hw = (long)H * H;
+    k_upsample<<<gridn((long)B * C * hw), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
+    VIE_CHECK_LAUNCH("k_upsample");
+    const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
+    if ((s = conv3(u->cat[l], 2L * C * hw, 2 * C, pw + c1.w_off, u->p + c1.b_off, u->bl[l], (long)C * hw, C,
+                   H, H, B, true, st)) != VIE_OK)
+      return s;
+    if ((s = conv3(u->bl[l], (long)C * hw, C, pw + c2.w_off, u->p + c2.b_off, u->dl[l], (long)C * hw, C, H,
+                   H, B, true, st)) != VIE_OK)
+      return s;
+    d = u->dl[l];
+    d_bs = (long)C * hw;
+  }
+  const ConvLayer &hd = u->layers[li];
+  k_head<WT><<<gridn((long)B * n * n), 256, 0, st>>>(d, d_bs, C, pw + hd.w_off, u->p + hd.b_off, u->o,
+                                                     (long)n * n, B);
+  VIE_CHECK_LAUNCH("k_head");
+  return VIE_OK;
+}
+
+// dw/db of a 3x3 convolution and, if gin, the input gradient (adjoint conv).
+vie_status conv3_backward(UnetImpl *u, const ConvLayer &c, const float *in, long in_bs, const float *gout,
+                          long g_bs, float *gin, long gin_bs, int H, int B, cudaStream_t st) {
+  const int cib = (c.ci + CIB - 1) / CIB, cob = (c.co + COB - 1) / COB;
+  dim3 grid((H + TX - 1) / TX, (H + WY - 1) / WY, B * cob * cib);
+  k_conv3_dw<<<grid, 256, 0, st>>>(in, in_bs, c.ci, gout, g_bs, c.co, H, H, u->g + c.w_off, u->g + c.b_off,
+                                  cib, cob);
+  VIE_CHECK_LAUNCH("k_conv3_dw");
+  if (gin) {
+    k_flip<<<gridn((long)c.co * c.ci * 9), 256, 0, st>>>(u->p + c.w_off, c.co, c.ci, u->wt);
+    VIE_CHECK_LAUNCH("k_flip");
+    vie_status s = conv3<float>(gout, g_bs, c.co, u->wt, nullptr, gin, gin_bs, c.ci, H, H, B, false, st);
+    if (s != VIE_OK) return s;
+  }
+  return VIE_OK;
+}
+
+vie_status relu_mask(float *g, long g_bs, const float *a, long a_bs, long per, int B, cudaStream_t st) {
+  k_relu_mask<<<gridn((long)B * per), 256, 0, st>>>(g, g_bs, a, a_bs, per, B);
+  VIE_CHECK_LAUNCH("k_relu_mask");
+  return VIE_OK;
+}
+
+// Backward pass from go (d loss / d o); gradients accumulate into u->g.
+vie_status backward(UnetImpl *u, const float *x, int B, int n, cudaStream_t st) {
+  const int L = u->L, C = u->C;
+  vie_status s;
+  int li = (int)u->layers.size() - 1;
+  const ConvLayer &hd = u->layers[li];
+  const float *d = L > 1 ? u->dl[0] : u->ebot[0];
+  float *gd = L > 1 ? u->gdl[0] : u->gebot[0];
+  const long plane0 = (long)n * n;
+  k_head_bwd_w<<<C + 1, 256, 0, st>>>(u->go, d, (long)C * plane0, C, plane0, B, u->g + hd.w_off,
+                                      u->g + hd.b_off);
+  VIE_CHECK_LAUNCH("k_head_bwd_w");
+  k_head_bwd_data<<<gridn((long)B * C * plane0), 256, 0, st>>>(u->go, C, u->p + hd.w_off, gd, (long)C * plane0,
+                                                                plane0, B);
+  VIE_CHECK_LAUNCH("k_head_bwd_data");
+  --li;
+  // decoder, l = 0 .. L-2 (reverse of the forward order)
+  for (int l = 0; l <= L - 2; ++l) {
+    const int H = n >> l;
+    const long hw = (long)H * H;
+    const ConvLayer &c2 = u->layers[li--];
+    const ConvLayer &c1 = u->layers[li--];
+    if ((s = relu_mask(u->gdl[l], (long)C * hw, u->dl[l], (long)C * hw, (long)C * hw, B, st)) != VIE_OK) return s;
+    if ((s = conv3_backward(u, c2, u->bl[l], (long)C * hw, u->gdl[l], (long)C * hw, u->gbl[l], (long)C * hw, H, B,
+                            st)) != VIE_OK)
+      return s;
+    if ((s = relu_mask(u->gbl[l], (long)C * hw, u->bl[l], (long)C * hw, (long)C * hw, B, st)) != VIE_OK) return s;
+    if ((s = conv3_backward(u, c1, u->cat[l], 2L * C * hw, u->gbl[l], (long)C * hw, u->gcat[l], 2L * C * hw, H, B,
+                            st)) != VIE_OK)
+      return s;
+    // upsample part of the concat -> gradient of d_{l+1}
+    float *gnext = (l + 1 <= L - 2) ? u->gdl[l + 1] : u->gebot[0];
+    k_upsample_bwd<<<gridn((long)B * C * hw / 4), 256, 0, st>>>(u->gcat[l], 2L * C * hw, gnext, (long)C * hw / 4,
+                                                                 C, H, H, B);
+    VIE_CHECK_LAUNCH("k_upsample_bwd");
+  }
+  // encoder, l = L-1 .. 0; grad of e_l: concat slice (l < L-1) + pool path
+  for (int l = L - 1; l >= 0; --l) {
+    const int H = n >> l;
+    const long hw = (long)H * H;
+    const ConvLayer &c1 = u->layers[2 * l], &c2 = u->layers[2 * l + 1];
+    float *ge;
+    long ge_bs;
+    const float *e;
+    long e_bs;
+    if (l < L - 1) {
+      ge = u->gcat[l] + (long)C * hw;
+      ge_bs = 2L * C * hw;
+      e = u->cat[l] + (long)C * hw;
+      e_bs = 2L * C * hw;
+      // + pool path from level l+1's input gradient
+      k_avgpool_bwd<<<gridn((long)B * C * hw), 256, 0, st>>>(u->gx[l + 1], (long)C * hw / 4, ge, ge_bs, C, H, H,
+                                                              B, 1);
+      VIE_CHECK_LAUNCH("k_avgpool_bwd");
+    } else {
+      ge = u->gebot[0];
+      ge_bs = (long)C * hw;
+      e = u->ebot[0];
+      e_bs = (long)C * hw;
+    }
+    if ((s = relu_mask(ge, ge_bs, e, e_bs, (long)C * hw, B, st)) != VIE_OK) return s;
+    if ((s = conv3_backward(u, c2, u->a[l], (long)C * hw, ge, ge_bs, u->ga[l], (long)C * hw, H, B, st)) != VIE_OK)
+      return s;
+    if ((s = relu_mask(u->ga[l], (long)C * hw, u->a[l], (long)C * hw, (long)C * hw, B, st)) != VIE_OK) return s;
+    const float *xl = l == 0 ? x : u->xin[l];
+    const long xl_bs = l == 0 ? 3L * hw : (long)C * hw;
+    if ((s = conv3_backward(u, c1, xl, xl_bs, u->ga[l], (long)C * hw, l > 0 ? u->gx[l] : nullptr,
+                            (long)C * hw, H, B, st)) != VIE_OK)
+      return s;
+  }
+  return VIE_OK;
+}
+
+vie_status loss_grad(UnetImpl *u, const float *x, const float *t, int B, int n, double *loss, cudaStream_t st) {
+  vie_status s;
+  if ((s = ensure_acts(u, B, n)) != VIE_OK) return s;
+  if ((s = forward<float>(u, u->p, x, B, n, st)) != VIE_OK) return s;
+  const long cnt = (long)B * n * n;
+  const int blocks = 512;
+  k_mse<<<blocks, 256, 0, st>>>(u->o, t, cnt, u->go, u->part);
+  VIE_CHECK_LAUNCH("k_mse");
+  VIE_CUDA(cudaMemsetAsync(u->g, 0, sizeof(float) * u->nparams, st));
+  if ((s = backward(u, x, B, n, st)) != VIE_OK) return s;
+  VIE_CUDA(cudaMemcpyAsync(u->h_part, u->part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  double sum = 0.0;
+  for (int i = 0; i < blocks; ++i) sum += u->h_part[i];
+  *loss = sum / (double)cnt;
+  return VIE_OK;
+}
+
+}  // namespace
+
+// ---- used by the FGMRES driver (vie_api.cu)
+vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
+                             const double *v, const double *vnorm2, int n, float *xbuf, double *z,
+                             cudaStream_t st) {
+  vie_status s;
+  if ((s = ensure_acts(u, 1, n)) != VIE_OK) return s;
+  const long N = (long)n * n;
+  k_net_input<<<gridn(N), 256, 0, st>>>(sigma_t, sigma_s, v, vnorm2, N, (float)inv_ref, xbuf);
+  VIE_CHECK_LAUNCH("k_net_input");
+  if ((s = forward<__nv_bfloat16>(u, u->pb, xbuf, 1, n, st)) != VIE_OK) return s;
+  k_net_output<<<gridn(N), 256, 0, st>>>(v, vnorm2, u->o, N, z);
+  VIE_CHECK_LAUNCH("k_net_output");
+  return VIE_OK;
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+struct vie_unet {
+  UnetImpl impl;
+};
+
+namespace vie {
+UnetImpl *unet_impl(vie_unet *u) { return &u->impl; }
+int unet_levels(vie_unet *u) { return u->impl.L; }
+}  // namespace vie
+
+extern "C" {
+
+vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned long long seed, int device) {
+  if (!out || levels < 1 || levels > 6 || channels < 1 || channels > 32) {
+    set_error("vie_unet_create: 1 <= levels <= 6, 1 <= channels <= 32");
+    return VIE_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  VIE_CUDA(cudaSetDevice(device));
+  vie_unet *u = new vie_unet();
+  UnetImpl &U = u->impl;
+  U.L = levels;
+  U.C = channels;
+  U.device = device;
+  long off = 0;
+  auto add = [&](int co, int ci, int k) {
+    ConvLayer c{co, ci, k, off, off + (long)co * ci * k * k};
+    off = c.b_off + co;
+    U.layers.push_back(c);
+  };
+  for (int l = 0; l < levels; ++l) {
+    add(channels, l == 0 ? 3 : channels, 3);
+    add(channels, channels, 3);
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    add(channels, 2 * channels, 3);
+    add(channels, channels, 3);
+  }
+  add(1, channels, 1);
+  U.nparams = off;
+  long max_w = 0;
+  for (auto &c : U.layers) max_w = std::max(max_w, (long)c.co * c.ci * c.k * c.k);
+  // He initialisation from SplitMix64 + Box-Muller, biases zero
+  std::vector<float> h(off, 0.f);
+  unsigned long long state = seed;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (auto &c : U.layers) {
+    const double std = sqrt(2.0 / (c.ci * c.k * c.k));
+    for (long i = 0; i < (long)c.co * c.ci * c.k * c.k; ++i) {
+      const double u1 = next(), u2 = next();
+      h[c.w_off + i] = (float)(std * sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2));
+    }
+  }
+  vie_status s = VIE_OK;
+  cudaError_t e = cudaSuccess;
+  for (float **q : {&U.p, &U.g, &U.m, &U.v})
+    if (e == cudaSuccess) e = cudaMalloc((void **)q, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&U.wt, sizeof(float) * max_w);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&U.pb, sizeof(__nv_bfloat16) * off);
+  if (e == cudaSuccess) e = cudaMemcpy(U.p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(U.m, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(U.v, 0, sizeof(float) * off);
+  if (e != cudaSuccess) s = cuda_fail(e, "vie_unet_create");
+  if (s == VIE_OK) {
+    k_to_bf16<<<gridn(off), 256>>>(U.p, U.pb, off);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) s = cuda_fail(e, "vie_unet_create");
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (s != VIE_OK) {
+    for (void *q : {(void *)U.p, (void *)U.g, (void *)U.m, (void *)U.v, (void *)U.wt, (void *)U.pb})
+      if (q) cudaFree(q);
+    delete u;
+    return s;
+  }
+  *out = u;
+  return VIE_OK;
+}
+
+vie_status vie_unet_destroy(vie_unet *u) {
+  if (!u) return VIE_OK;
+  cudaSetDevice(u->impl.device);
+  cudaDeviceSynchronize();
+  free_acts(&u->impl);
+  for (void *q : {(void *)u->impl.p, (void *)u->impl.g, (void *)u->impl.m, (void *)u->impl.v,
+                  (void *)u->impl.wt, (void *)u->impl.pb})
+    if (q) cudaFree(q);
+  delete u;
+  return VIE_OK;
+}
+
+vie_status vie_unet_num_params(vie_unet *u, long long *n) {
+  if (!u || !n) return VIE_ERR_INVALID_ARG;
+  *n = u->impl.nparams;
+  return VIE_OK;
+}
+
+vie_status vie_unet_get_params(vie_unet *u, float *host) {
+  if (!u || !host) return VIE_ERR_INVALID_ARG;
+  VIE_CUDA(cudaSetDevice(u->impl.device));
+  VIE_CUDA(cudaMemcpy(host, u->impl.p, sizeof(float) * u->impl.nparams, cudaMemcpyDeviceToHost));
+  return VIE_OK;
+}
+
+vie_status vie_unet_set_params(vie_unet *u, const float *host) {
+  if (!u || !host) return VIE_ERR_INVALID_ARG;
+  VIE_CUDA(cudaSetDevice(u->impl.device));
+  VIE_CUDA(cudaMemcpy(u->impl.p, host, sizeof(float) * u->impl.nparams, cudaMemcpyHostToDevice));
+  k_to_bf16<<<gridn(u->impl.nparams), 256>>>(u->impl.p, u->impl.pb, u->impl.nparams);
+  VIE_CHECK_LAUNCH("k_to_bf16");
+  VIE_CUDA(cudaDeviceSynchronize());
+  return VIE_OK;
+}
+
+vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n, int use_bf16, void *stream) {
+  if (!u || !x || !o || B < 1 || n < 1 || (n % (1 << (u->impl.L - 1))) != 0) {
+    set_error("vie_unet_forward: n must be divisible by 2^(levels-1)");
+    return VIE_ERR_INVALID_ARG;
+  }
+  VIE_CUDA(cudaSetDevice(u->impl.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  vie_status s = ensure_acts(&u->impl, B, n);
+  if (s != VIE_OK) return s;
+  s = use_bf16 ? forward<__nv_bfloat16>(&u->impl, u->impl.pb, x, B, n, st)
+               : forward<float>(&u->impl, u->impl.p, x, B, n, st);
+  if (s != VIE_OK) return s;
+  VIE_CUDA(cudaMemcpyAsync(o, u->impl.o, sizeof(float) * (long)B * n * n, cudaMemcpyDeviceToDevice, st));
+  return VIE_OK;
+}
+
+vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B, int n, float *grads_host,
+                              double *loss, void *stream) {
+  if (!u || !x || !t || !loss || B < 1 || (n % (1 << (u->impl.L - 1))) != 0) {
+    set_error("vie_unet_loss_grad: bad arguments");
+    return VIE_ERR_INVALID_ARG;
+  }
+  VIE_CUDA(cudaSetDevice(u->impl.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  vie_status s = loss_grad(&u->impl, x, t, B, n, loss, st);
+  if (s != VIE_OK) return s;
+  if (grads_host)
+    VIE_CUDA(cudaMemcpy(grads_host, u->impl.g, sizeof(float) * u->impl.nparams, cudaMemcpyDeviceToHost));
+  return VIE_OK;
+}
+
+vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, int B, int n, float lr,
+                               double *loss, void *stream) {
+  if (!u || !x || !t || !loss || B < 1 || (n % (1 << (u->impl.L - 1))) != 0 || !(lr > 0.f)) {
+    set_error("vie_unet_train_step: bad arguments");
+    return VIE_ERR_INVALID_ARG;
+  }
+  VIE_CUDA(cudaSetDevice(u->impl.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  UnetImpl &U = u->impl;
+  vie_status s = loss_grad(&U, x, t, B, n, loss, st);
+  if (s != VIE_OK) return s;
+  U.step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)U.step), c2 = 1.f - powf(b2, (float)U.step);
+  k_adam<<<gridn(U.nparams), 256, 0, st>>>(U.p, U.g, U.m, U.v, U.pb, U.nparams, lr, b1, b2, 1e-8f, c1, c2);
+  VIE_CHECK_LAUNCH("k_adam");
+  return VIE_OK;
+}
+
+vie_status vie_unet_save(vie_unet *u, const char *path) {
+  if (!u || !path) return VIE_ERR_INVALID_ARG;
+  std::vector<float> h(u->impl.nparams);
+  vie_status s = vie_unet_get_params(u, h.data());
+  if (s != VIE_OK) return s;
+  FILE *f = fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("vie_unet_save: cannot open ") + path);
+    return VIE_ERR_INVALID_ARG;
+  }
+  const int hdr[4] = {0x54454e55 /* "UNET" */, 1, u->impl.L, u->impl.C};
+  const long long np = u->impl.nparams;
+  bool ok = fwrite(hdr, sizeof hdr, 1, f) == 1 && fwrite(&np, sizeof np, 1, f) == 1 &&
+            fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  fclose(f);
+  if (!ok) {
+    set_error("vie_unet_save: write failed");
+    return VIE_ERR_INVALID_ARG;
+  }
+  return VIE_OK;
+}
+
+vie_status vie_unet_load(vie_unet *u, const char *path) {
+  if (!u || !path) return VIE_ERR_INVALID_ARG;
+  FILE *f = fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("vie_unet_load: cannot open ") + path);
+    return VIE_ERR_INVALID_ARG;
+  }
+  int hdr[4];
+  long long np = 0;
+  std::vector<float> h(u->impl.nparams);
+  bool ok = fread(hdr, sizeof hdr, 1, f) == 1 && fread(&np, sizeof np, 1, f) == 1 && hdr[0] == 0x54454e55 &&
+            hdr[1] == 1 && hdr[2] == u->impl.L && hdr[3] == u->impl.C && np == u->impl.nparams &&
+            fread(h.data(), sizeof(float), h.size(), f) == h.size();
+  fclose(f);
+  if (!ok) {
+    set_error("vie_unet_load: file does not match this network");
+    return VIE_ERR_INVALID_ARG;
+  }
+  return vie_unet_set_params(u, h.data());
+}
+
+}  // extern "C"

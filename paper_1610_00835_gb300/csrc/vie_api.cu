@@ -139,6 +139,11 @@ struct vie_handle {
   DBuf<unsigned char> gemm_ws;                // split-K partials + BF16 G
   int *dev_err = nullptr;                     // device error word of the products
   bool sig_s_positive = false;                // phi = K (f / sigma_s) is available
+  UnetImpl *precond = nullptr;                // learned right preconditioner
+  double precond_inv_ref = 0.2;
+  double *Z = nullptr;                        // FGMRES: preconditioned basis [m][N]
+  int z_m = 0;
+  float *net_x = nullptr;                     // network input [3][N]
   DBuf<double> fscaled;                       // f / sigma_s
   std::vector<ApplyEvents> events;
   size_t ev_next = 0;
@@ -182,6 +187,8 @@ void free_all(vie_handle *h) {
   h->stage_f1.release();
   h->stage_f2.release();
   dfree(h->qpad);
+  dfree(h->Z);
+  dfree(h->net_x);
   if (h->kmat) cudaFree(h->kmat);
   if (h->kmat_lo) cudaFree(h->kmat_lo);
   h->kmat = h->kmat_lo = nullptr;
@@ -570,6 +577,22 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   return VIE_OK;
 }
 
+vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref) {
+  if (!h) return invalid("vie_set_preconditioner: NULL handle");
+  if (!u) {
+    h->precond = nullptr;
+    return VIE_OK;
+  }
+  if (h->dim != 2) return invalid("vie_set_preconditioner: 2D handles only");
+  if (!(s_ref > 0.0)) return invalid("vie_set_preconditioner: s_ref must be > 0");
+  const int levels = unet_levels(u);
+  if (h->n % (1 << (levels - 1)) != 0)
+    return invalid("vie_set_preconditioner: n must be divisible by 2^(levels-1)");
+  h->precond = unet_impl(u);
+  h->precond_inv_ref = 1.0 / s_ref;
+  return VIE_OK;
+}
+
 vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_gmres_opts *o,
                            vie_report *rep, void *stream) {
   if (!h || !f || !U) return invalid("vie_solve_gmres: NULL argument");
@@ -586,6 +609,12 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
   const int m = opt.restart;
   vie_status s;
   if ((s = ensure_gmres(h, m)) != VIE_OK) return s;
+  if (h->precond && h->z_m < m) {
+    dfree(h->Z);
+    if ((s = dalloc(&h->Z, (size_t)m * N)) != VIE_OK) return s;
+    h->z_m = m;
+  }
+  if (h->precond && !h->net_x && (s = dalloc(&h->net_x, (size_t)3 * N)) != VIE_OK) return s;
   h->t_apply_ms = h->t_kernel_ms = 0.0;
   h->n_apply = 0;
   const bool timed = opt.time_apply != 0;
@@ -657,10 +686,24 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
     h->h_pinned[0] = beta;
     VIE_CUDA(cudaMemcpyAsync(h->gv, h->h_pinned, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
     int k = 0;
+    const bool flexible = h->precond && !R.fell_back;
+    double est_prev = 1e300, est_prev2 = 1e300;
+    bool stall = false;
     while (k < m && R.iters < opt.maxit) {
       double *vk = h->V + (size_t)k * N;
       double *vk1 = h->V + (size_t)(k + 1) * N;
-      if ((s = apply_dev(h, VIE_OP_I_MINUS_K, vk, vk1, st, timed)) != VIE_OK) return s;
+      const double *op_in = vk;
+      if (flexible) {
+        // z_k = M(v_k) (right preconditioning, flexible GMRES)
+        double *zk = h->Z + (size_t)k * N;
+        if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
+        if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,
+                                   h->n, h->net_x, zk, st)) != VIE_OK)
+          return s;
+        op_in = zk;
+        ++R.precond_iters;
+      }
+      if ((s = apply_dev(h, VIE_OP_I_MINUS_K, op_in, vk1, st, timed)) != VIE_OK) return s;
       // CGS2: two passes of h = V^T w, w -= V h; hcol accumulates both.
       if ((s = launch_dots(h->V, k + 1, N, vk1, N, h->part, blocks, st)) != VIE_OK) return s;
       if ((s = launch_dots_finish(h->part, blocks, k + 1, h->hcol, 0, st)) != VIE_OK) return s;
@@ -681,13 +724,28 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
       ++R.iters;
       R.relres_est = est;
       if (!isfinite(est)) {
+        if (flexible) {
+          // the network produced a non-finite direction: drop this step
+          --k;
+          stall = true;
+          break;
+        }
         set_error("vie_solve_gmres: non-finite Arnoldi step");
         return VIE_ERR_NONFINITE;
       }
       if (est <= opt.rtol) break;
+      if (flexible && k >= 2 && est > 0.8 * est_prev && est_prev > 0.8 * est_prev2) {
+        stall = true;
+        break;
+      }
+      est_prev2 = est_prev;
+      est_prev = est;
     }
-    if ((s = launch_backsolve(h->H, m, k, h->gv, h->yv, st)) != VIE_OK) return s;
-    if ((s = launch_lincomb_add(h->V, k, N, h->yv, x, N, st)) != VIE_OK) return s;
+    if (k > 0) {
+      if ((s = launch_backsolve(h->H, m, k, h->gv, h->yv, st)) != VIE_OK) return s;
+      if ((s = launch_lincomb_add(flexible ? h->Z : h->V, k, N, h->yv, x, N, st)) != VIE_OK) return s;
+    }
+    if (stall) R.fell_back = 1;
     ++R.restarts;
   }
   if (!ud) VIE_CUDA(cudaMemcpyAsync(U, x, sizeof(double) * N, cudaMemcpyDeviceToHost, st));

@@ -107,6 +107,14 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
                               int nrhs, int op, double *y, void *workspace, int *err,
                               cudaStream_t st);
 
+// ---- learned preconditioner (k_unet.cu)
+struct UnetImpl;
+UnetImpl *unet_impl(vie_unet *u);
+int unet_levels(vie_unet *u);
+vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
+                             const double *v, const double *vnorm2, int n, float *xbuf, double *z,
+                             cudaStream_t st);
+
 // ---- Krylov kernels (k_krylov.cu)
 int dot_blocks(long N);
 vie_status launch_dots(const double *V, int nv, long ldv, const double *w, long N, double *part,

@@ -51,7 +51,8 @@ class vie_report(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("n_apply", C.c_int), ("relres", C.c_double), ("relres_est", C.c_double),
                 ("t_total_ms", C.c_double), ("t_apply_ms", C.c_double),
-                ("t_apply_kernel_ms", C.c_double)]
+                ("t_apply_kernel_ms", C.c_double), ("precond_iters", C.c_int),
+                ("fell_back", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +81,18 @@ SIGNATURES = {
     "vie_batch_apply": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "vie_batch_autotune": (C.c_int, [_vp, C.c_char_p, _vp]),
     "vie_batch_config": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "vie_unet_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_ulonglong, C.c_int]),
+    "vie_unet_destroy": (C.c_int, [_vp]),
+    "vie_unet_num_params": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
+    "vie_unet_get_params": (C.c_int, [_vp, _vp]),
+    "vie_unet_set_params": (C.c_int, [_vp, _vp]),
+    "vie_unet_forward": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "vie_unet_loss_grad": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
+    "vie_unet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float,
+                                      C.POINTER(C.c_double), _vp]),
+    "vie_unet_save": (C.c_int, [_vp, C.c_char_p]),
+    "vie_unet_load": (C.c_int, [_vp, C.c_char_p]),
+    "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
     "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
@@ -271,6 +284,87 @@ def vie_batch_config(b: VieBatch) -> tuple:
     g, p = C.c_int(), C.c_int()
     _check(load().vie_batch_config(b.ptr, C.byref(g), C.byref(p)))
     return g.value, p.value
+
+
+@dataclass
+class VieUnet:
+    ptr: C.c_void_p
+    levels: int
+    channels: int
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                vie_unet_destroy(self)
+        except Exception:
+            pass
+
+
+def vie_unet_create(levels: int = 4, channels: int = 32, seed: int = 0, device: int = 0) -> VieUnet:
+    u = C.c_void_p()
+    _check(load().vie_unet_create(C.byref(u), levels, channels, seed, device))
+    return VieUnet(u, levels, channels)
+
+
+def vie_unet_destroy(u: VieUnet) -> None:
+    if u.ptr:
+        _check(load().vie_unet_destroy(u.ptr))
+        u.ptr = C.c_void_p()
+
+
+def vie_unet_num_params(u: VieUnet) -> int:
+    n = C.c_longlong()
+    _check(load().vie_unet_num_params(u.ptr, C.byref(n)))
+    return n.value
+
+
+def vie_unet_get_params(u: VieUnet) -> np.ndarray:
+    out = np.empty(vie_unet_num_params(u), dtype=np.float32)
+    _check(load().vie_unet_get_params(u.ptr, C.c_void_p(out.ctypes.data)))
+    return out
+
+
+def vie_unet_set_params(u: VieUnet, params) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != vie_unet_num_params(u):
+        raise ValueError("parameter count mismatch")
+    _check(load().vie_unet_set_params(u.ptr, C.c_void_p(a.ctypes.data)))
+
+
+def vie_unet_forward(u: VieUnet, x, o, B: int, n: int, use_bf16: bool = False, stream=None) -> None:
+    xp, _x = _ptr(x, np.float32)
+    op, _o = _ptr(o, np.float32)
+    _check(load().vie_unet_forward(u.ptr, xp, op, B, n, int(use_bf16), _stream(stream)))
+
+
+def vie_unet_loss_grad(u: VieUnet, x, t, B: int, n: int, stream=None):
+    xp, _x = _ptr(x, np.float32)
+    tp, _t = _ptr(t, np.float32)
+    g = np.empty(vie_unet_num_params(u), dtype=np.float32)
+    loss = C.c_double()
+    _check(load().vie_unet_loss_grad(u.ptr, xp, tp, B, n, C.c_void_p(g.ctypes.data), C.byref(loss),
+                                     _stream(stream)))
+    return loss.value, g
+
+
+def vie_unet_train_step(u: VieUnet, x, t, B: int, n: int, lr: float, stream=None) -> float:
+    xp, _x = _ptr(x, np.float32)
+    tp, _t = _ptr(t, np.float32)
+    loss = C.c_double()
+    _check(load().vie_unet_train_step(u.ptr, xp, tp, B, n, lr, C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def vie_unet_save(u: VieUnet, path: str) -> None:
+    _check(load().vie_unet_save(u.ptr, path.encode()))
+
+
+def vie_unet_load(u: VieUnet, path: str) -> None:
+    _check(load().vie_unet_load(u.ptr, path.encode()))
+
+
+def vie_set_preconditioner(h: VieHandle, u, s_ref: float = 5.0) -> None:
+    _check(load().vie_set_preconditioner(h.ptr, u.ptr if u is not None else None, s_ref))
 
 
 def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:

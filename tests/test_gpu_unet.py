@@ -1,0 +1,97 @@
+"""The learned preconditioner's network on the GPU vs the FP64 reference, and FGMRES."""
+import numpy as np
+import pytest
+
+import oracle as O
+import vie_synth as V
+from oracle import unet as R
+
+torch = pytest.importorskip("torch")
+import paper_1610_00835_gb300 as P  # noqa: E402
+from gpu_util import dev, host, rel_l2  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def ref_params(u, levels, channels):
+    flat = P.vie_unet_get_params(u).astype(np.float64)
+    out, off = [], 0
+    for co, ci, k in R.layer_shapes(levels, channels):
+        nw = co * ci * k * k
+        out.append(flat[off:off + nw].reshape(co, ci, k, k))
+        off += nw
+        out.append(flat[off:off + co])
+        off += co
+    assert off == flat.size
+    return out
+
+
+@pytest.mark.parametrize("levels,channels,n,B", [(1, 4, 8, 1), (3, 8, 16, 2), (4, 32, 32, 2),
+                                                 (2, 5, 24, 3)])
+def test_forward_and_gradients_match_reference(levels, channels, n, B):
+    u = P.vie_unet_create(levels, channels, seed=11)
+    rng = np.random.default_rng(levels)
+    params = P.vie_unet_get_params(u)
+    params = params + 0.02 * rng.standard_normal(params.size).astype(np.float32)  # nonzero biases
+    P.vie_unet_set_params(u, params)
+    x = rng.standard_normal((B, 3, n, n)).astype(np.float32)
+    t = rng.standard_normal((B, 1, n, n)).astype(np.float32)
+    o = torch.empty(B * n * n, dtype=torch.float32, device="cuda:0")
+    P.vie_unet_forward(u, dev(x.ravel(), torch.float32), o, B, n)
+    pr = ref_params(u, levels, channels)
+    loss_ref, grads_ref, o_ref = R.loss_and_grads(pr, x.astype(np.float64), t.astype(np.float64), levels)
+    assert rel_l2(host(o), o_ref.ravel()) < 1e-5
+    loss, g = P.vie_unet_loss_grad(u, dev(x.ravel(), torch.float32), dev(t.ravel(), torch.float32), B, n)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    off = 0
+    for gr in grads_ref:
+        k = gr.size
+        assert rel_l2(g[off:off + k], gr.ravel()) < 1e-4
+        off += k
+    # BF16 weights for inference: close to the FP32 forward
+    ob = torch.empty_like(o)
+    P.vie_unet_forward(u, dev(x.ravel(), torch.float32), ob, B, n, use_bf16=True)
+    assert rel_l2(host(ob), host(o)) < 2e-2
+
+
+def test_training_reduces_loss():
+    u = P.vie_unet_create(3, 8, seed=3)
+    rng = np.random.default_rng(5)
+    n, B = 16, 4
+    x = dev(rng.standard_normal((B, 3, n, n)).ravel(), torch.float32)
+    t = dev(np.tile(np.sin(np.linspace(0, 3, n))[None, None, :, None], (B, 1, 1, n)).ravel(), torch.float32)
+    losses = [P.vie_unet_train_step(u, x, t, B, n, 3e-3) for _ in range(150)]
+    assert losses[-1] < 0.2 * losses[0]
+
+
+def test_save_load_roundtrip(tmp_path):
+    u = P.vie_unet_create(2, 4, seed=1)
+    path = str(tmp_path / "net.bin")
+    P.vie_unet_save(u, path)
+    v = P.vie_unet_create(2, 4, seed=2)
+    P.vie_unet_load(v, path)
+    np.testing.assert_array_equal(P.vie_unet_get_params(u), P.vie_unet_get_params(v))
+    w = P.vie_unet_create(3, 4, seed=2)
+    with pytest.raises(P.VieError):
+        P.vie_unet_load(w, path)
+
+
+@pytest.mark.parametrize("scale", [0.0, 1.0, 50.0])
+def test_fgmres_converges_with_any_network(scale):
+    # an untrained (scale 1), zero (scale 0: M = I) or wild (scale 50) network:
+    # flexible GMRES or its plain fallback still reaches the tolerance
+    n = 32
+    m = V.heterogeneous_2d(n=n)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    u = P.vie_unet_create(4, 8, seed=7)
+    P.vie_unet_set_params(u, P.vie_unet_get_params(u) * scale)
+    P.vie_set_preconditioner(h, u)
+    U = np.zeros(m.N)
+    rep = P.vie_solve_gmres(h, m.f, U, rtol=1e-8)
+    assert rep["converged"] and rep["precond_iters"] >= 1
+    phi = O.apply(2, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW)
+    assert rel_l2(U, O.lu_solve(2, m.sigma_t, m.sigma_s, phi)) < 1e-5
+    P.vie_set_preconditioner(h, None)
+    U2 = np.zeros(m.N)
+    rep2 = P.vie_solve_gmres(h, m.f, U2, rtol=1e-8)
+    assert rep2["precond_iters"] == 0
