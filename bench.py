@@ -274,6 +274,45 @@ def measure_batch(P, torch, stream, local, reps=3):
             "config": {"groups_per_cta": cfg[0], "smem_policy": cfg[1]}, "autotune_s": tune_s}
 
 
+def measure_learned(P, torch, local, seeds=(9004, 9005)):
+    """Learned right preconditioner (4-level, 32-channel U-Net trained at 128^2
+    by paper_1610_00835_gb300/train_unet.py) on held-out 256^2 strongly
+    scattering media: FGMRES + network vs GMRES, both with the assembled BF16
+    hi/lo operator, to 1e-6; assembly time reported separately."""
+    weights = os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin")
+    net = P.vie_unet_create(4, 32, device=local)
+    P.vie_unet_load(net, weights)
+    rows = []
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for sd in seeds:
+        m = V.diffusive_training_medium(256, sd)
+        h = P.vie_create(2, 256, m.sigma_t, m.sigma_s, device=local)
+        torch.cuda.synchronize()
+        a.record()
+        P.vie_assemble(h, P.VIE_OPERATOR_BF16X3)
+        b.record()
+        torch.cuda.synchronize()
+        asm = a.elapsed_time(b)
+        f = torch.as_tensor(m.f, dtype=torch.float64, device=f"cuda:{local}")
+        U = torch.empty_like(f)
+        row = {"seed": sd, "assemble_ms": asm}
+        for name, pre in (("gmres", None), ("fgmres_learned", net)):
+            P.vie_set_preconditioner(h, pre, 5.0)
+            P.vie_solve_gmres(h, f, U, rtol=RTOL, restart=128)
+            torch.cuda.synchronize()
+            a.record()
+            rep = P.vie_solve_gmres(h, f, U, rtol=RTOL, restart=128)
+            b.record()
+            torch.cuda.synchronize()
+            row[name] = {"iters": rep["iters"], "ms": a.elapsed_time(b), "relres": rep["relres"],
+                         "fell_back": rep["fell_back"]}
+        P.vie_set_preconditioner(h, None)
+        P.vie_destroy(h)
+        rows.append(row)
+    return {"grid": "256x256 (65536 unknowns), strongly scattering bump media, held out",
+            "operator": "assembled BF16 hi/lo (17.2 GB)", "media": rows}
+
+
 def run_ours(args):
     import torch
     import paper_1610_00835_gb300 as P
@@ -350,6 +389,7 @@ def run_ours(args):
     chosen = measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
     batch = measure_batch(P, torch, stream, local)
+    learned = measure_learned(P, torch, local)
 
     # end to end through the C ABI from host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -386,6 +426,7 @@ def run_ours(args):
                       "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen},
             "bf16x3_product": product,
             "batch_uneven_grids": batch,
+            "learned_preconditioner": learned,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
         }

@@ -271,9 +271,11 @@ vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n,
  * (host FP32 [num_params]). Synchronous. */
 vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B, int n, float *grads_host,
                               double *loss, void *stream);
-/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; returns the loss. */
-vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, int B, int n, float lr,
-                               double *loss, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; returns the loss
+ * mean_b w_b mean_p (o - t)^2, w_b = weights[b] (device FP32 [B]) or 1 if
+ * weights is NULL. */
+vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, const float *weights, int B,
+                               int n, float lr, double *loss, void *stream);
 vie_status vie_unet_save(vie_unet *u, const char *path);
 vie_status vie_unet_load(vie_unet *u, const char *path);
 /* Use `u` as the right preconditioner of vie_solve_gmres on this handle

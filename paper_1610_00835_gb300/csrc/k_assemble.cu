@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(1024, 1) k_assemble_sym(AsmArgs a) {
   float4 *srcs = srcs_all + grp * kG;
   float *tr = tr_all + (grp * 4 + warp) * 32 * 33;
   int *slot = slot_all + 4 * grp;
-  {
+  if (LDP >= 0) {  // LDP < 0: the lattice stays in global memory
     const float4 *g4 = reinterpret_cast<const float4 *>(a.sig);
     const long n4 = a.lattice / 4;
     float4 *l4 = reinterpret_cast<float4 *>(lat);
@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(1024, 1) k_assemble_sym(AsmArgs a) {
   __syncthreads();
   const Geo geo = make_geo((unsigned)__cvta_generic_to_shared(lat), DIM, LDP > 0 ? LDP : a.ldp,
                            PLANE > 0 ? PLANE : a.plane);
+  GeoG geog;
+  geog.base = a.sig;
+  geog.ldp = a.ldp;
+  geog.bias = kTwo23Bits * (1u + (unsigned)a.ldp);
   const int n = a.n;
   const long N = a.N, nn = (long)n * n;
   for (;;) {
@@ -112,7 +116,8 @@ __global__ void __launch_bounds__(1024, 1) k_assemble_sym(AsmArgs a) {
         const float r2 = DIM == 3 ? fmaf(dz, dz, fmaf(dy, dy, dx * dx)) : fmaf(dy, dy, dx * dx);
         const float inv_r = rsqrtf(r2);
         const float r = r2 * inv_r;
-        const float acc = march64<DIM, LDP, PLANE>(geo, jx, jy, jz, dx, dy, dz);
+        const float acc = LDP < 0 ? march64_g(geog, jx, jy, dx, dy)
+                                  : march64<DIM, (LDP < 0 ? 0 : LDP), PLANE>(geo, jx, jy, jz, dx, dy, dz);
         const float ker = DIM == 3 ? inv_r * inv_r : inv_r;
         float w = a.wcoef * exp2f(-a.tau_scale2 * acc * r) * ker;
         w = r2 > 0.f ? w : 0.f;
@@ -165,7 +170,8 @@ __global__ void k_assemble_diag(long N, long ldk, const double *__restrict__ dia
 
 typedef void (*AsmKernel)(AsmArgs);
 
-AsmKernel pick_asm(int dim, int ldp, int plane) {
+AsmKernel pick_asm(int dim, int ldp, int plane, int global) {
+  if (global) return k_assemble_sym<2, -1, 0>;
   if (dim == 2) {
     switch (ldp) {
       case 33: return k_assemble_sym<2, 33, 0>;
@@ -203,14 +209,14 @@ vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const doub
   cudaDeviceProp prop;
   VIE_CUDA(cudaGetDeviceProperties(&prop, device));
   const size_t per_group = sizeof(float4) * kG + sizeof(float) * 4 * 32 * 33 + 4 * sizeof(int);
-  const size_t lat_bytes = sizeof(float) * sp.lattice_elems;
+  const size_t lat_bytes = sp.global_lattice ? 0 : sizeof(float) * sp.lattice_elems;
   int groups = (int)std::min<size_t>(8, (prop.sharedMemPerBlockOptin - lat_bytes) / per_group);
   if (groups < 1) {
     set_error("vie_assemble: lattice too large for the assembly kernel");
     return VIE_ERR_UNSUPPORTED;
   }
   const size_t smem = per_group * groups + lat_bytes + 64;
-  AsmKernel k = pick_asm(dim, sp.ldp, sp.plane);
+  AsmKernel k = pick_asm(dim, sp.ldp, sp.plane, sp.global_lattice);
   VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int bps = 0;

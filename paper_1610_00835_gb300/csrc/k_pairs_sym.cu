@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_pairs_sym(SymArgs a) {
   float *colw = col_all + grp * 4 * kG;
   int *item_slot = item_all + 4 * grp;
 
-  // stage the lattice (whole CTA)
-  {
+  // stage the lattice (whole CTA); LDP < 0: the lattice stays in global memory
+  if (LDP >= 0) {
     const float4 *g4 = reinterpret_cast<const float4 *>(a.sig);
     const long n4 = a.lattice / 4;
     float4 *l4 = reinterpret_cast<float4 *>(lat);
@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_pairs_sym(SymArgs a) {
 
   const Geo geo = make_geo((unsigned)__cvta_generic_to_shared(lat), DIM,
                            LDP > 0 ? LDP : a.ldp, PLANE > 0 ? PLANE : a.plane);
+  GeoG geog;
+  geog.base = a.sig;
+  geog.ldp = a.ldp;
+  geog.bias = kTwo23Bits * (1u + (unsigned)a.ldp);
   const int n = a.n;
   const long N = a.N;
   const long nn = (long)n * n;
@@ -119,7 +123,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_pairs_sym(SymArgs a) {
         const float r2 = DIM == 3 ? fmaf(dz, dz, fmaf(dy, dy, dx * dx)) : fmaf(dy, dy, dx * dx);
         const float inv_r = rsqrtf(r2);
         const float r = r2 * inv_r;
-        const float acc = march64<DIM, LDP, PLANE>(geo, jx, jy, jz, dx, dy, dz);
+        const float acc = LDP < 0 ? march64_g(geog, jx, jy, dx, dy)
+                                  : march64<DIM, (LDP < 0 ? 0 : LDP), PLANE>(geo, jx, jy, jz, dx, dy, dz);
         const float ker = DIM == 3 ? inv_r * inv_r : inv_r;
         float w = a.wcoef * exp2f(-a.tau_scale2 * acc * r) * ker;
         w = r2 > 0.f ? w : 0.f;
@@ -217,6 +222,10 @@ size_t sym_smem_bytes(int dim, int n, int *ldp_out, int *plane_out) {
          sizeof(int) * 4 * kGroups + sizeof(float) * lattice;
 }
 
+static size_t sym_group_bytes() {
+  return sizeof(float4) * kGroups * kG + sizeof(float) * kGroups * 4 * kG + sizeof(int) * 4 * kGroups;
+}
+
 vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
                        int device, cudaStream_t st) {
   cudaDeviceProp prop;
@@ -225,7 +234,16 @@ vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_pad
   SymKernel k = pick(dim, n + 1, &ldp, &plane);
   size_t smem = sym_smem_bytes(dim, n, nullptr, nullptr);
   sp->usable = 0;
-  if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
+  sp->global_lattice = 0;
+  if (smem > (size_t)prop.sharedMemPerBlockOptin) {
+    if (dim != 2) return VIE_OK;
+    // 2D lattice too large for shared memory: read it through L1
+    k = k_pairs_sym<2, -1, 0>;
+    ldp = n + 1;
+    plane = 0;
+    smem = sym_group_bytes();
+    sp->global_lattice = 1;
+  }
   VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int bps = 0;

@@ -295,15 +295,17 @@ __global__ void k_relu_mask(float *__restrict__ g, long g_bs, const float *__res
   }
 }
 
-// loss = mean((o - t)^2) (block partials in double), go = 2 (o - t) / n
-__global__ void k_mse(const float *__restrict__ o, const float *__restrict__ t, long n, float *__restrict__ go,
-                      double *__restrict__ part) {
+// loss = mean(w_b (o - t)^2) (block partials in double), go = 2 w_b (o - t) / n;
+// w_b = sample weight of image b (1 without weights), plane pixels per image
+__global__ void k_mse(const float *__restrict__ o, const float *__restrict__ t, long n, long plane,
+                      const float *__restrict__ wts, float *__restrict__ go, double *__restrict__ part) {
   __shared__ double red[256];
   double s = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const float d = o[i] - t[i];
-    s += (double)d * d;
-    go[i] = 2.f * d / (float)n;
+    const float wb = wts ? wts[i / plane] : 1.f;
+    s += (double)wb * d * d;
+    go[i] = 2.f * wb * d / (float)n;
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -604,13 +606,14 @@ vie_status backward(UnetImpl *u, const float *x, int B, int n, cudaStream_t st) 
   return VIE_OK;
 }
 
-vie_status loss_grad(UnetImpl *u, const float *x, const float *t, int B, int n, double *loss, cudaStream_t st) {
+vie_status loss_grad(UnetImpl *u, const float *x, const float *t, const float *wts, int B, int n, double *loss,
+                     cudaStream_t st) {
   vie_status s;
   if ((s = ensure_acts(u, B, n)) != VIE_OK) return s;
   if ((s = forward<float>(u, u->p, x, B, n, st)) != VIE_OK) return s;
   const long cnt = (long)B * n * n;
   const int blocks = 512;
-  k_mse<<<blocks, 256, 0, st>>>(u->o, t, cnt, u->go, u->part);
+  k_mse<<<blocks, 256, 0, st>>>(u->o, t, cnt, (long)n * n, wts, u->go, u->part);
   VIE_CHECK_LAUNCH("k_mse");
   VIE_CUDA(cudaMemsetAsync(u->g, 0, sizeof(float) * u->nparams, st));
   if ((s = backward(u, x, B, n, st)) != VIE_OK) return s;
@@ -789,15 +792,15 @@ vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B
   }
   VIE_CUDA(cudaSetDevice(u->impl.device));
   cudaStream_t st = (cudaStream_t)stream;
-  vie_status s = loss_grad(&u->impl, x, t, B, n, loss, st);
+  vie_status s = loss_grad(&u->impl, x, t, nullptr, B, n, loss, st);
   if (s != VIE_OK) return s;
   if (grads_host)
     VIE_CUDA(cudaMemcpy(grads_host, u->impl.g, sizeof(float) * u->impl.nparams, cudaMemcpyDeviceToHost));
   return VIE_OK;
 }
 
-vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, int B, int n, float lr,
-                               double *loss, void *stream) {
+vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, const float *weights, int B,
+                               int n, float lr, double *loss, void *stream) {
   if (!u || !x || !t || !loss || B < 1 || (n % (1 << (u->impl.L - 1))) != 0 || !(lr > 0.f)) {
     set_error("vie_unet_train_step: bad arguments");
     return VIE_ERR_INVALID_ARG;
@@ -805,7 +808,7 @@ vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, int 
   VIE_CUDA(cudaSetDevice(u->impl.device));
   cudaStream_t st = (cudaStream_t)stream;
   UnetImpl &U = u->impl;
-  vie_status s = loss_grad(&U, x, t, B, n, loss, st);
+  vie_status s = loss_grad(&U, x, t, weights, B, n, loss, st);
   if (s != VIE_OK) return s;
   U.step += 1;
   const float b1 = 0.9f, b2 = 0.999f;

@@ -76,6 +76,7 @@ vie_status launch_selfcell(int dim, int n, const double *sigma_t, double *diag,
 // in shared memory.  partial must hold [T][N] doubles.
 struct SymPlan {
   int usable = 0;
+  int global_lattice = 0;  // 1: 2D lattice read from global memory (too large to stage)
   int T = 0, n_items = 0, ldp = 0, plane = 0, grid = 0;
   size_t smem = 0;
   long lattice_elems = 0;

@@ -88,7 +88,7 @@ SIGNATURES = {
     "vie_unet_set_params": (C.c_int, [_vp, _vp]),
     "vie_unet_forward": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "vie_unet_loss_grad": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
-    "vie_unet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float,
+    "vie_unet_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float,
                                       C.POINTER(C.c_double), _vp]),
     "vie_unet_save": (C.c_int, [_vp, C.c_char_p]),
     "vie_unet_load": (C.c_int, [_vp, C.c_char_p]),
@@ -347,11 +347,13 @@ def vie_unet_loss_grad(u: VieUnet, x, t, B: int, n: int, stream=None):
     return loss.value, g
 
 
-def vie_unet_train_step(u: VieUnet, x, t, B: int, n: int, lr: float, stream=None) -> float:
+def vie_unet_train_step(u: VieUnet, x, t, B: int, n: int, lr: float, weights=None,
+                        stream=None) -> float:
     xp, _x = _ptr(x, np.float32)
     tp, _t = _ptr(t, np.float32)
+    wp, _w = _ptr(weights, np.float32) if weights is not None else (None, None)
     loss = C.c_double()
-    _check(load().vie_unet_train_step(u.ptr, xp, tp, B, n, lr, C.byref(loss), _stream(stream)))
+    _check(load().vie_unet_train_step(u.ptr, xp, tp, wp, B, n, lr, C.byref(loss), _stream(stream)))
     return loss.value
 
 

@@ -172,6 +172,41 @@ def random_training_medium(n: int, seed: int) -> Medium:
                   {"seed": seed, "ratio": ratio})
 
 
+def diffusive_training_medium(n: int, seed: int) -> Medium:
+    """Strongly scattering bump medium (the regime of the paper's
+    preconditioning experiments, mu_a small against mu_s): sigma_s = s (1 +
+    sum of 1..4 bumps, amplitude U[0.2, 1], width U[0.05, 0.2]), s
+    log-uniform in [4, 16]; sigma_t = sigma_s + mu_a, mu_a ~ U[0.1, 0.5]."""
+    rng = SplitMix64(seed)
+    nb = 1 + int(rng.uniform() * 4)
+    s = math.exp(rng.uniform(math.log(4.0), math.log(16.0)))
+    mu_a = rng.uniform(0.1, 0.5)
+    bumps = draw_bumps(rng, 2, nb, amp=(0.2, 1.0))
+    ss = s * bump_field(2, n, bumps, base=1.0)
+    srcb = draw_bumps(rng, 2, 1 + int(rng.uniform() * 3), amp=(0.5, 1.5))
+    f = bump_field(2, n, srcb)
+    return Medium(2, n, ss + mu_a, ss, f, False, f"diffusive {n}^2 seed={seed}",
+                  {"seed": seed, "s": s, "mu_a": mu_a})
+
+
+def random_rhs(n: int, seed: int) -> np.ndarray:
+    """A smooth right-hand side for (I - K) U = b: 2..5 Gaussian bumps with
+    amplitudes U[-1, 1], widths U[0.03, 0.3], centres U[0.1, 0.9]^2."""
+    rng = SplitMix64(seed)
+    nb = 2 + int(rng.uniform() * 4)
+    bumps = draw_bumps(rng, 2, nb, amp=(-1.0, 1.0), width=(0.03, 0.3), centre=(0.1, 0.9))
+    return bump_field(2, n, bumps)
+
+
+def random_field(n: int, seed: int, width=(0.05, 0.3), count=(4, 16)) -> np.ndarray:
+    """A random field on the n x n centres: count[0]..count[1] Gaussian bumps,
+    amplitudes U[-1, 1], widths U[width], centres U[0, 1]^2."""
+    rng = SplitMix64(seed)
+    nb = count[0] + int(rng.uniform() * (count[1] - count[0] + 1))
+    bumps = draw_bumps(rng, 2, nb, amp=(-1.0, 1.0), width=width, centre=(0.0, 1.0))
+    return bump_field(2, n, bumps)
+
+
 def fibonacci_directions(M: int) -> np.ndarray:
     """[M, 3] unit vectors: z_m = 1 - (2m+1)/M, azimuth m * pi * (3 - sqrt 5)."""
     m = np.arange(M, dtype=np.float64)
