@@ -76,9 +76,19 @@ typedef struct {
   int precision; /* VIE_PREC_FP32: FP32 kernel tiles, FP64 sums across tiles;
                     VIE_PREC_FP64: every pair in FP64                        */
   int device;    /* CUDA device ordinal                                     */
+  int kernel;    /* pair kernel for FP32 tiles: VIE_KERNEL_AUTO picks the
+                    fastest that applies; the others force one (a forced
+                    kernel that does not apply falls back to AUTO)         */
 } vie_opts;
 
-/* Default options: S = 64, march, FP32 tiles, device 0. */
+enum {
+  VIE_KERNEL_AUTO = 0,
+  VIE_KERNEL_SYMMETRIC = 1,     /* tile pairs, each unordered pair once       */
+  VIE_KERNEL_DISPLACEMENT = 2,  /* 2D, S = 64: warps share one displacement   */
+  VIE_KERNEL_GENERAL = 3        /* every ordered pair; any S                  */
+};
+
+/* Default options: S = 64, march, FP32 tiles, device 0, automatic kernel. */
 void vie_default_opts(vie_opts *o);
 
 typedef struct vie_handle vie_handle;

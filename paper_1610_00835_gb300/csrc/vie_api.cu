@@ -117,6 +117,8 @@ struct vie_handle {
   Medium med{};
   PairPlan plan{};
   SymPlan sym{};                              // symmetric kernel, when usable
+  DispPlan disp{};                            // displacement-major kernel, when usable
+  int use_kernel = VIE_KERNEL_GENERAL;        // pair kernel chosen for applies
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
   DBuf<double> stage_a, stage_b, stage_c;     // host-pointer staging
@@ -196,6 +198,7 @@ void free_all(vie_handle *h) {
   h->gemm_ws.release();
   dfree(h->dev_err);
   sym_release(&h->sym);
+  disp_release(&h->disp);
   free_gmres(h);
   for (auto &ev : h->events)
     for (auto &e : ev.e)
@@ -284,14 +287,19 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
     h->n_apply++;
     return VIE_OK;
   }
-  vie_status s = launch_source_prep(h->N, op, h->sig_s, g, prec, h->src, st);
+  vie_status s = h->use_kernel == VIE_KERNEL_DISPLACEMENT
+                     ? disp_source(h->disp, h->N, op, h->sig_s, g, (float *)h->src, st)
+                     : launch_source_prep(h->N, op, h->sig_s, g, prec, h->src, st);
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
   int slots = h->plan.splits;
-  if (h->sym.usable) {
-    const double hh = 1.0 / h->n;
-    const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
-    const float wcoef = (float)(h->dim == 2 ? hh / (2.0 * kPi) : hh / (4.0 * kPi));
+  const double hh = 1.0 / h->n;
+  const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
+  const float wcoef = (float)(h->dim == 2 ? hh / (2.0 * kPi) : hh / (4.0 * kPi));
+  if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) {
+    s = disp_launch(h->disp, h->n, tau_scale2, wcoef, (const float *)h->src, h->partial, st);
+    slots = h->disp.grid;
+  } else if (h->use_kernel == VIE_KERNEL_SYMMETRIC) {
     s = sym_launch(h->sym, h->dim, h->n, h->N, tau_scale2, wcoef, (const float *)h->src,
                    h->partial, st);
     slots = h->sym.T;
@@ -300,7 +308,9 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   }
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[2], st));
-  s = launch_reduce(h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st);
+  s = h->use_kernel == VIE_KERNEL_DISPLACEMENT
+          ? disp_reduce(h->disp, h->N, op, h->partial, h->diag, h->sig_s, g, y, st)
+          : launch_reduce(h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st);
   if (s != VIE_OK) return s;
   if (timed) {
     VIE_CUDA(cudaEventRecord(ev->e[3], st));
@@ -347,6 +357,7 @@ void vie_default_opts(vie_opts *o) {
   o->tau_mode = VIE_TAU_MARCH;
   o->precision = VIE_PREC_FP32;
   o->device = 0;
+  o->kernel = VIE_KERNEL_AUTO;
 }
 
 void vie_default_gmres_opts(vie_gmres_opts *o) {
@@ -375,6 +386,8 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     return invalid("vie_create: unknown tau_mode");
   if (opts.precision != VIE_PREC_FP32 && opts.precision != VIE_PREC_FP64)
     return invalid("vie_create: unknown precision");
+  if (opts.kernel < VIE_KERNEL_AUTO || opts.kernel > VIE_KERNEL_GENERAL)
+    return invalid("vie_create: unknown kernel");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -445,10 +458,24 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     cudaError_t e = cudaMalloc(&h->src, bytes);
     if (e != cudaSuccess) TRY(cuda_fail(e, "cudaMalloc"));
   }
-  if (opts.precision == VIE_PREC_FP32 && opts.tau_mode == VIE_TAU_MARCH && opts.steps == 64 &&
-      !h->opts_disable_sym)
+  const bool fast = opts.precision == VIE_PREC_FP32 && opts.tau_mode == VIE_TAU_MARCH && opts.steps == 64;
+  if (fast && opts.kernel != VIE_KERNEL_GENERAL) {
     TRY(sym_prepare(&h->sym, g->dim, g->n, N, h->sig32, opts.device, st));
-  TRY(dalloc(&h->partial, (size_t)std::max(h->plan.splits, h->sym.usable ? h->sym.T : 0) * N));
+    if (g->dim == 2 && (opts.kernel == VIE_KERNEL_AUTO || opts.kernel == VIE_KERNEL_DISPLACEMENT))
+      TRY(disp_prepare(&h->disp, g->n, h->sig32, opts.device, st));
+  }
+  if (h->disp.usable && opts.kernel != VIE_KERNEL_SYMMETRIC)
+    h->use_kernel = VIE_KERNEL_DISPLACEMENT;
+  else if (h->sym.usable)
+    h->use_kernel = VIE_KERNEL_SYMMETRIC;
+  else
+    h->use_kernel = VIE_KERNEL_GENERAL;
+  {
+    long slots = h->plan.splits;
+    if (h->use_kernel == VIE_KERNEL_SYMMETRIC) slots = std::max<long>(slots, h->sym.T);
+    if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) slots = std::max<long>(slots, h->disp.grid);
+    TRY(dalloc(&h->partial, (size_t)slots * N));
+  }
   {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) TRY(cuda_fail(e, "vie_create setup kernels"));

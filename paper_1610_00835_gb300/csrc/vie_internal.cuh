@@ -95,6 +95,31 @@ vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *s
 vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale2, float wcoef,
                       const float *src, double *partial, cudaStream_t st);
 
+// ---- displacement-major pair kernel (k_pairs_disp.cu): 2D, FP32, S = 64.
+// partial must hold [grid][N] doubles.
+struct DispPlan {
+  int usable = 0;
+  long n_units = 0, lat_elems = 0;
+  int ldp = 0, grid = 0;
+  size_t smem = 0;
+  void *units = nullptr;
+  int *counter = nullptr;
+  void *lattice = nullptr;
+  unsigned *smax = nullptr;   // max |s| of the current apply (float bits)
+  double *scale = nullptr;    // fixed-point scale of the current apply
+  double rbound = 0.0;        // bound on every row sum of A
+  const void *kernel = nullptr;
+};
+size_t disp_smem_bytes(int n);
+vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
+                       float *src, cudaStream_t st);
+vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *partial, const double *diag,
+                       const double *sigma_s, const double *g, double *y, cudaStream_t st);
+vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st);
+void disp_release(DispPlan *dp);
+vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
+                       double *partial, cudaStream_t st);
+
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
 vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,

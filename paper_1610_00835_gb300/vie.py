@@ -25,6 +25,7 @@ VIE_TAU_MARCH, VIE_TAU_CLOSED = 0, 1
 VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
 VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
 VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3 = 0, 1, 2
+VIE_KERNEL_AUTO, VIE_KERNEL_SYMMETRIC, VIE_KERNEL_DISPLACEMENT, VIE_KERNEL_GENERAL = 0, 1, 2, 3
 
 
 class VieError(RuntimeError):
@@ -39,7 +40,7 @@ class vie_grid(C.Structure):
 
 class vie_opts(C.Structure):
     _fields_ = [("steps", C.c_int), ("tau_mode", C.c_int), ("precision", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("kernel", C.c_int)]
 
 
 class vie_gmres_opts(C.Structure):
@@ -176,12 +177,13 @@ class VieHandle:
 
 
 def vie_create(dim: int, n: int, sigma_t, sigma_s, steps: int = 64, tau_mode: int = VIE_TAU_MARCH,
-               precision: int = VIE_PREC_FP32, device: int = 0) -> VieHandle:
+               precision: int = VIE_PREC_FP32, device: int = 0,
+               kernel: int = VIE_KERNEL_AUTO) -> VieHandle:
     L = load()
     st = np.ascontiguousarray(np.asarray(sigma_t, dtype=np.float64).ravel())
     ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64).ravel())
     g = vie_grid(dim, n)
-    o = vie_opts(steps, tau_mode, precision, device)
+    o = vie_opts(steps, tau_mode, precision, device, kernel)
     h = C.c_void_p()
     _check(L.vie_create(C.byref(h), C.byref(g), C.c_void_p(st.ctypes.data),
                         C.c_void_p(ss.ctypes.data), C.byref(o)))
@@ -253,7 +255,7 @@ def vie_batch_create(ns, sigma_t_list, sigma_s_list, device: int = 0) -> VieBatc
     ss = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in sigma_s_list]
     pst = (_vp * count)(*[a.ctypes.data for a in st])
     pss = (_vp * count)(*[a.ctypes.data for a in ss])
-    o = vie_opts(64, VIE_TAU_MARCH, VIE_PREC_FP32, device)
+    o = vie_opts(64, VIE_TAU_MARCH, VIE_PREC_FP32, device, VIE_KERNEL_AUTO)
     b = C.c_void_p()
     _check(L.vie_batch_create(C.byref(b), count, grids, pst, pss, C.byref(o)))
     total = C.c_longlong()

@@ -90,11 +90,39 @@ def test_ops_and_multiple_rhs_and_host_pointers():
     assert rel_l2(a, O.apply(2, m.sigma_t, m.sigma_s, G[0], op=O.OP_A_RAW)) < FP32_TOL
 
 
-def test_deterministic():
+@pytest.mark.parametrize("kernel", [P.VIE_KERNEL_SYMMETRIC, P.VIE_KERNEL_DISPLACEMENT])
+def test_deterministic(kernel):
+    # fixed summation order (tile pairs) or exact fixed-point sums
+    # (displacement kernel): repeated applies are bitwise identical
     m = V.heterogeneous_2d(n=48)
-    h = P.vie_create(2, 48, m.sigma_t, m.sigma_s)
     g = rng_vec(m.N, 9)
+    h = P.vie_create(2, 48, m.sigma_t, m.sigma_s, kernel=kernel)
     np.testing.assert_array_equal(gpu_apply(h, 0, g), gpu_apply(h, 0, g))
+
+
+@pytest.mark.parametrize("kernel", [P.VIE_KERNEL_SYMMETRIC, P.VIE_KERNEL_DISPLACEMENT,
+                                    P.VIE_KERNEL_GENERAL])
+@pytest.mark.parametrize("n", [2, 3, 9, 24, 37, 64])
+def test_2d_every_pair_kernel_all_rows(kernel, n):
+    m = V.heterogeneous_2d(n=n, seed=78)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=kernel)
+    g = rng_vec(m.N, n) + 0.5
+    for op in (P.VIE_OP_K_SIGMA_S, P.VIE_OP_A_RAW):
+        want = O.apply(2, m.sigma_t, m.sigma_s, g, op=op)
+        assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
+
+
+@pytest.mark.parametrize("n", [100, 128, 136])
+def test_displacement_kernel_full_size_sampled_rows(n):
+    m = V.bump_medium(2, n, 4, 0.9, seed=4300 + n)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
+    hs = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
+    g = m.f + 0.05 * rng_vec(m.N, n)
+    got = gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)
+    rows = _sampled_rows(m.N, 16, n)
+    want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(got[rows], want) < FP32_TOL
+    assert rel_l2(got, gpu_apply(hs, P.VIE_OP_K_SIGMA_S, g)) < 2e-6
 
 
 @pytest.mark.parametrize("dim,n", [(2, 9), (3, 5)])

@@ -37,7 +37,9 @@ def test_small_uneven_batch_all_rows_and_single_grid_equality():
         sl = slice(b.offsets[i], b.offsets[i + 1])
         want = O.apply(2, m.sigma_t, m.sigma_s, g[sl])
         assert rel_l2(y[sl], want) < TOL, ns[i]
-        h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s)
+        # the batch runs the tile-pair kernel: same arithmetic as a single-grid
+        # handle forced to it
+        h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
         y1 = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
         P.vie_apply(h, P.VIE_OP_K_SIGMA_S, dev(g[sl]), y1)
         np.testing.assert_allclose(y[sl], host(y1), rtol=1e-12, atol=0)
