@@ -46,7 +46,15 @@ RTOL = 1e-6
 # Pair-kernel traffic per launch from the ncu capture of this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
 # the current kernel.
-PAIR_KERNEL_DRAM_BYTES = 229376  # k_pairs_sym<2,129,0>, profiles/k_pairs_sym_2d_128.md
+PAIR_KERNEL_DRAM_BYTES = {1: 229376}  # k_pairs_sym<2,129,0>: profiles/k_pairs_sym_2d_128.md
+
+
+# Shared-memory bytes one march sample needs, per pair kernel: the tile-pair
+# kernel loads the 4 bilinear corners (16 B); the displacement kernel's
+# thread x-interpolates 9 lattice rows (2 loads each) for 8 stacked targets
+# that share the same displacement (9 B per target).
+SMEM_BYTES_PER_SAMPLE = {1: 16.0, 2: 9.0}
+KERNEL_NAMES = {1: "k_pairs_sym<2,129,0>", 2: "k_pairs_disp<129>", 3: "k_pairs_f32"}
 
 
 def ops_per_pair(S: int) -> int:
@@ -376,15 +384,23 @@ def run_ours(args):
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak = sms * 128 * max_mhz * 1e6 / 1e12                     # Tops/s at max clock
-    ops = ops_per_pair(S_STEPS) * float(N) * (N - 1) / 2.0       # per launch
-    achieved = ops / (kern_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES,
-                "kernel": "k_pairs_sym<2,129,0>", "kernel_ms": kern_ms,
-                "work": "13*S+12 FP32 lane-ops per unordered pair, N(N-1)/2 pairs",
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max clock)"}
+    kernel = P.vie_get_kernel(h)
+    pairs_launch = float(N) * (N - 1) / 2.0                        # unordered pairs marched
+    smem_bytes = pairs_launch * S_STEPS * SMEM_BYTES_PER_SAMPLE.get(kernel, 16.0)
+    smem_peak = sms * 128 * max_mhz * 1e6 / 1e9                    # GB/s, 128 B/clk/SM
+    achieved = smem_bytes / (kern_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved / smem_peak, "traffic": PAIR_KERNEL_DRAM_BYTES.get(kernel),
+                "resource": "shared-memory load bandwidth (the LSU pipe binds this kernel)",
+                "kernel": KERNEL_NAMES.get(kernel, str(kernel)), "kernel_ms": kern_ms,
+                "work": f"{SMEM_BYTES_PER_SAMPLE.get(kernel, 16.0):g} B of shared-memory loads per "
+                        f"march sample, S={S_STEPS} samples per unordered pair, N(N-1)/2 pairs",
+                "peak_basis": f"{sms} SMs x 128 B/clk x {max_mhz:.0f} MHz (max clock)",
+                "fp32_view": {"ops_per_pair": ops_per_pair(S_STEPS),
+                              "achieved_tops": pairs_launch * ops_per_pair(S_STEPS) / (kern_ms * 1e-3) / 1e12,
+                              "peak_tops": peak}}
     if clocks["sm_mhz"]:
-        roofline["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+        roofline["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e9)
 
     chosen = measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)

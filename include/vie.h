@@ -297,6 +297,9 @@ vie_status vie_unet_load(vie_unet *u, const char *path);
  * fell_back = 1.  The network must outlive its use by the handle. */
 vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
 
+/* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
+vie_status vie_get_kernel(vie_handle *h, int *kernel);
+
 /* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);
 

@@ -494,6 +494,12 @@ vie_status vie_destroy(vie_handle *h) {
   return VIE_OK;
 }
 
+vie_status vie_get_kernel(vie_handle *h, int *kernel) {
+  if (!h || !kernel) return invalid("vie_get_kernel: NULL argument");
+  *kernel = h->opts.precision == VIE_PREC_FP32 ? h->use_kernel : VIE_KERNEL_GENERAL;
+  return VIE_OK;
+}
+
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream) {
   if (!h || !d) return invalid("vie_get_diagonal: NULL argument");
   DeviceGuard dg(h->device);

@@ -71,6 +71,7 @@ SIGNATURES = {
                                   C.POINTER(vie_report), _vp]),
     "ert_sweep": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
     "vie_get_diagonal": (C.c_int, [_vp, _vp, _vp]),
+    "vie_get_kernel": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "vie_last_error": (C.c_char_p, []),
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
@@ -383,6 +384,12 @@ def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
 def vie_get_diagonal(h: VieHandle, d, stream=None) -> None:
     dp, _d = _ptr(d, np.float64)
     _check(load().vie_get_diagonal(h.ptr, dp, _stream(stream)))
+
+
+def vie_get_kernel(h: VieHandle) -> int:
+    k = C.c_int()
+    _check(load().vie_get_kernel(h.ptr, C.byref(k)))
+    return k.value
 
 
 def vie_last_error() -> str:
