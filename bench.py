@@ -12,10 +12,13 @@ value  = pairs evaluated per second over the whole job (n_apply * N^2 per
 e2e    = the same through the C ABI from host buffers: vie_create from host
          sigma_t/sigma_s, vie_solve_gmres with host f and host U (copies
          inside), vie_destroy; per step.
-roofline: the pair kernel, FP32-pipe bound; algorithmic work 13 S + 12
-         FP32 lane operations per marched pair.  A_jk = A_kj, so the method
-         marches each unordered pair once: N (N - 1) / 2 marches per apply.
-         Peak = SMs x 128 FP32 lanes x max SM clock.
+roofline: the pair kernel, bound by the FP32 pipe (it is issue-bound: the
+         multiply-adds of the optical depths plus their loads and
+         bookkeeping).  Algorithmic work = the multiply-adds of the tau sums
+         by the method's own count (vie_get_kernel_work): for the
+         displacement kernel sum_D |W_D| x pairs(D), W_D the per-cell sum of
+         the S midpoint samples' bilinear weights.  Peak = SMs x 128 FP32
+         FMA lanes x max SM clock.
 cpu_baseline: the FP64 oracle's matrix-free apply on a bounded sample of
          target rows of the same medium, on the host cores.
 
@@ -46,23 +49,24 @@ RTOL = 1e-6
 # Pair-kernel traffic per launch from the ncu capture of this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
 # the current kernel.
-PAIR_KERNEL_DRAM_BYTES = {1: 229376}  # k_pairs_sym<2,129,0>: profiles/k_pairs_sym_2d_128.md
+PAIR_KERNEL_DRAM_BYTES = {1: 229376,     # k_pairs_sym<2,129,0>: profiles/k_pairs_sym_2d_128.md
+                          2: 59926528}   # k_pairs_disp<143>: profiles/k_pairs_disp_2d_128.md
+KERNEL_NAMES = {1: "k_pairs_sym<2,129,0>", 2: "k_pairs_disp<143>", 3: "k_pairs_f32"}
 
 
-# Shared-memory bytes one march sample needs, per pair kernel: the tile-pair
-# kernel loads the 4 bilinear corners (16 B); the displacement kernel's
-# thread x-interpolates 9 lattice rows (2 loads each) for 8 stacked targets
-# that share the same displacement (9 B per target).
-SMEM_BYTES_PER_SAMPLE = {1: 16.0, 2: 9.0}
-KERNEL_NAMES = {1: "k_pairs_sym<2,129,0>", 2: "k_pairs_disp<129>", 3: "k_pairs_f32"}
+def nvtx_push(torch, name: str) -> None:
+    """Mark a timed step for profilers (ncu --nvtx --nvtx-include timed_step/)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
 
 
-def ops_per_pair(S: int) -> int:
-    """FP32 lane operations the method needs per off-diagonal pair (2D):
-    per march step 2 position FMAs, 2 floor/fraction ops, 2 weight ops,
-    6 for the three lerps and 1 accumulate (13), plus about 12 for r, tau,
-    the kernel weight and the product with the source."""
-    return 13 * S + 12
+def nvtx_pop(torch) -> None:
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def medium(rank: int):
@@ -358,10 +362,12 @@ def run_ours(args):
             flush_l2(flush)
             torch.cuda.synchronize()
             barrier()
+            nvtx_push(torch, "timed_step")
             start.record(stream)
             rep = P.vie_solve_gmres(h, f_dev, U, rtol=RTOL, time_apply=True)
             stop.record(stream)
             torch.cuda.synchronize()
+            nvtx_pop(torch)
             step_ms.append(start.elapsed_time(stop))
             reps.append(rep)
     launches = P.vie_kernel_launches() - launches0
@@ -383,24 +389,19 @@ def run_ours(args):
     sms = props.multi_processor_count
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or 2070.0
-    peak = sms * 128 * max_mhz * 1e6 / 1e12                     # Tops/s at max clock
     kernel = P.vie_get_kernel(h)
-    pairs_launch = float(N) * (N - 1) / 2.0                        # unordered pairs marched
-    smem_bytes = pairs_launch * S_STEPS * SMEM_BYTES_PER_SAMPLE.get(kernel, 16.0)
-    smem_peak = sms * 128 * max_mhz * 1e6 / 1e9                    # GB/s, 128 B/clk/SM
-    achieved = smem_bytes / (kern_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": achieved / smem_peak, "traffic": PAIR_KERNEL_DRAM_BYTES.get(kernel),
-                "resource": "shared-memory load bandwidth (the LSU pipe binds this kernel)",
+    fma = P.vie_get_kernel_work(h)                                 # multiply-adds per apply
+    peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12                    # FP32 TFLOP/s at max clock
+    achieved = 2.0 * fma / (kern_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES.get(kernel),
+                "resource": "FP32 FMA pipe (the kernel is issue-bound: loads and bookkeeping share the issue slots)",
                 "kernel": KERNEL_NAMES.get(kernel, str(kernel)), "kernel_ms": kern_ms,
-                "work": f"{SMEM_BYTES_PER_SAMPLE.get(kernel, 16.0):g} B of shared-memory loads per "
-                        f"march sample, S={S_STEPS} samples per unordered pair, N(N-1)/2 pairs",
-                "peak_basis": f"{sms} SMs x 128 B/clk x {max_mhz:.0f} MHz (max clock)",
-                "fp32_view": {"ops_per_pair": ops_per_pair(S_STEPS),
-                              "achieved_tops": pairs_launch * ops_per_pair(S_STEPS) / (kern_ms * 1e-3) / 1e12,
-                              "peak_tops": peak}}
+                "work": f"{fma:.4g} multiply-adds per apply (tau sums, the method's own count), 2 FLOP each",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max clock)",
+                "gpair_per_s_apply": float(N) * N / (kern_ms * 1e-3) / 1e9}
     if clocks["sm_mhz"]:
-        roofline["frac_at_measured_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e9)
+        roofline["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
     chosen = measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)

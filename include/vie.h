@@ -300,6 +300,15 @@ vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
 /* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
 vie_status vie_get_kernel(vie_handle *h, int *kernel);
 
+/* Multiply-adds that one on-the-fly apply spends on the optical depths, by
+ * the method's own count (a diagnostic for rooflines; no counterpart in the
+ * paper).  Displacement kernel: sum over displacements D of the cells of the
+ * stencil W_D (the per-cell sum of the S midpoint samples' bilinear weights,
+ * Section 3.2 M-iii) times the pairs with that displacement.  Other kernels:
+ * 3 S per unordered pair (three linear blends per bilinear sample; 7 per
+ * trilinear sample in 3D). */
+vie_status vie_get_kernel_work(vie_handle *h, double *fma_per_apply);
+
 /* Read back the self-cell diagonal d_j (FP64 [N], host or device). */
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream);
 

@@ -1,37 +1,61 @@
-// Displacement-major pair kernel: 2D, FP32 tiles, S = 64 march steps.
+// Displacement-major pair kernel with per-displacement stencils: 2D, FP32
+// tiles, S = 64 march steps.
 //
 // It computes the operator of k_apply.cu (Section 2, Eq. EQ:Kernel; Section
-// 3.2, M-iii): y_j = sum_{k != j} A_jk s_k.  On a uniform grid the segment
-// from cell j to cell j + D (D = (dx, dy) in cells) has its midpoint samples
-// at u_j + (i + 1/2) D / S: their integer parts and bilinear weights depend on
-// D and i only.  A warp therefore takes one displacement D and a block of
-// 32 x 8 targets (32 consecutive x per warp, 8 consecutive y per thread):
-// per sample, one thread x-interpolates the 9 lattice rows its 8 targets
-// touch (the two rows of target q + 1 overlap those of target q) and
-// combines neighbouring rows with the warp-uniform y weight.
+// 3.2, M-iii): y_j = sum_{k != j} A_jk s_k, the optical depth of the segment
+// from cell j to cell k = j + D (D = (dx, dy) in cells) taken by the S-step
+// midpoint march of the bilinear interpolant of sigma_t.  On a uniform grid
+// the samples of that march sit at u_j + (i + 1/2) D / S: their integer parts
+// relative to j and their bilinear weights depend on D and i only.  Summing,
+// for each lattice cell c, the weights of the samples that touch it gives a
+// stencil W_D with
+//     sum_i sigma(u_j + (i + 1/2) D / S) = sum_c W_D(c) sigma[j + c]
+// for every j: the same products, grouped by lattice cell.  W_D has at most
+// 4 S cells and far fewer when |D| < S, because consecutive samples share
+// cells.  It is built once per handle on the host in FP64 and stored in FP32.
 //
-// Work units are (D, 32 x 8 block of the targets j with j + D inside the
-// grid) for D in a half plane (dy > 0, or dy = 0 and dx > 0): A_jk = A_kj, so
-// each unordered pair is marched once and feeds y_j (weight s_{j+D}) and
-// y_{j+D} (weight s_j).  Units are sorted by the size of their displacement's
-// rectangle, largest first, and warps take them four at a time from a global
-// counter.  Each CTA sums into a private copy of y in shared memory held in
-// 64-bit fixed point: every term w s is rounded once to a multiple of
-// 1/scale, scale the power of two at or below 2^62 / (max|s| R) with R a
-// bound on every row sum of A,
-// and integer atomic adds are exact in any order.  The result is therefore
-// bitwise reproducible whatever the schedule, and the accumulation error is
-// below N 2^-63 max|s| R.  Each CTA writes its copy (int64) to its
-// partial-sum slot; k_disp_reduce adds the slots in int64 (exact, since the
-// sum of the magnitudes of all terms of a target is below 2^62), converts
-// once to FP64 and adds the self cell.
+// W_D is stored as runs of consecutive cells along one lattice axis (the one
+// that makes the march cheaper, normally the axis closer to D), each run cut
+// into chunks of a fixed length Lc (one of kChunkLengths, chosen per D, few
+// so that the unrolled variants stay small; the last chunk of a
+// run is padded with zero weights).  A warp takes one displacement and a
+// block of 32 x kR targets: 32 consecutive across the run axis (one per lane)
+// and kR consecutive along it, stacked in one thread.  A chunk then takes
+// Lc + kR - 1 lattice loads per thread and kR Lc multiply-adds, all unrolled
+// for the D's chunk length.  Lanes sit on consecutive x (runs along y) or
+// consecutive y with an odd row pitch (runs along x), so every load is free
+// of bank conflicts.
 //
-// Rows of targets beyond the rectangle (ragged blocks) are computed and
-// discarded; the lattice carries 8 extra rows so that their samples stay in
-// bounds, and lanes beyond it use the last valid column.
+// Work units are (D, block of the targets j with j + D inside the grid) for D
+// in a half plane (dy > 0, or dy = 0 and dx > 0): A_jk = A_kj, so each
+// unordered pair is marched once and feeds y_j (weight s_{j+D}) and y_{j+D}
+// (weight s_j).  Units are sorted by estimated cost, largest first, and warps
+// take them four at a time from a global counter.  Each CTA sums into a
+// private copy of y in shared memory held in 64-bit fixed point: every term
+// w s is rounded once to a multiple of 1/scale, scale the power of two at or
+// below 2^62 / (max|s| R) with R a bound on every row sum of A, and integer
+// atomic adds are exact in any order.  The result is therefore bitwise
+// reproducible whatever the schedule, and the accumulation error is below
+// N 2^-63 max|s| R.  Each CTA writes its copy (int64) to its partial-sum slot;
+// k_disp_reduce adds the slots in int64 (exact, since the sum of the
+// magnitudes of all terms of a target is below 2^62), converts once to FP64
+// and adds the self cell.
+//
+// The shared copy of y stores target (x, y) at y n + ((x + c y) mod n), with
+// n + c odd: 32 lanes on one column (runs along x) then hit different banks,
+// and lanes on one row stay contiguous.  Those column-wise lanes read s from a
+// transposed copy, so that their loads stay coalesced.
+//
+// Targets of a block that fall outside the rectangle (ragged blocks) are
+// computed and discarded: lanes beyond it repeat the last valid target, and
+// the lattice carries kPad = (kR - 1) + (Lc - 1) extra rows and columns
+// (repeating the edge) so that stacked targets beyond it and the padding of
+// the last chunk of a run stay in bounds.
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "march.cuh"
@@ -41,47 +65,104 @@ namespace vie {
 
 namespace {
 
-using namespace march;
+using march::kS;
 
-constexpr int kR = 8;          // targets per thread (stacked in y)
+constexpr int kR = 8;          // targets per thread, stacked along the run axis
 constexpr int kThreads = 1024;
-constexpr int kExtraRows = 8;
+constexpr int kChunkLengths[] = {2, 3, 4, 6, 8};
+constexpr int kMaxChunk = 8;   // longest chunk
+constexpr int kPad = kR - 1 + kMaxChunk - 1;  // extra lattice rows and columns
 
 struct DispArgs {
-  const float *lat;            // [(n + 1 + kExtraRows)][ldp] padded sigma_t, ldp = n + 1
+  const float *lat;            // [n + 1 + kPad][ldp] sigma_t on the cell lattice, edge repeated
+  const float4 *stencil;       // run records of every W_D
   const float *src;            // s_k, FP32 [N]
+  const float *src_t;          // s transposed: s at (x, y) is src_t[x n + y]
   unsigned *smax;              // bits of max |s_k| (set by the source kernel)
   double *scale_out;           // fixed-point scale of this apply (for the reduce)
   double rbound;               // bound on sum_k A_jk for every j
   double *partial;             // [gridDim.x][N]
-  const short4 *units;         // (dx, dy, bx, by)
+  const int4 *units;           // {first chunk, dx | dy << 16, lane block | stack block << 16,
+                               //  runs along y | Lc << 1 | chunks << 8}
   int *counter;                // [2]
   long n_units;
-  int n, ldp;
+  int n, ldp, rot;             // rot = c of the rotated layout of y
   long lat_elems;
-  float tau_scale2, wcoef, h;
+  float tau_scale2, wcoef;
 };
 
-template <int OFF>
-__device__ __forceinline__ float lds1(unsigned addr) {
+// slot of target (x, y) in the rotated layout of y (c <= 2, so x + c y < 3 n)
+__host__ __device__ __forceinline__ long yslot(int x, int y, int n, int c) {
+  int t = x + c * y;
+  t = t >= n ? t - n : t;
+  t = t >= n ? t - n : t;
+  return (long)y * n + t;
+}
+
+// lattice value M elements of stride ST (ST = 0: runtime stride st) after addr
+template <int ST, int M>
+__device__ __forceinline__ float lds_at(unsigned addr, int st) {
   float v;
-  asm("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+  if constexpr (ST > 0) {
+    asm("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(4 * ST * M));
+  } else {
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr + 4u * (unsigned)(st * M)));
+  }
   return v;
 }
 
-// L[r] = x-interpolation of lattice row (row of addr) + r, r < R; rows LDP floats apart.
-template <int LDP, int R>
-struct Rows {
-  static __device__ __forceinline__ void load(unsigned addr, float ax, float *L) {
-    Rows<LDP, R - 1>::load(addr, ax, L);
-    const float v0 = lds1<4 * LDP * (R - 1)>(addr), v1 = lds1<4 * LDP * (R - 1) + 4>(addr);
-    L[R - 1] = fmaf(ax, v1 - v0, v0);
+// v[M .. CNT) = the lattice values M .. CNT - 1 strides after addr
+template <int ST, int M, int CNT>
+struct LoadRun {
+  static __device__ __forceinline__ void go(unsigned addr, int st, float *v) {
+    v[M] = lds_at<ST, M>(addr, st);
+    LoadRun<ST, M + 1, CNT>::go(addr, st, v);
   }
 };
-template <int LDP>
-struct Rows<LDP, 0> {
-  static __device__ __forceinline__ void load(unsigned, float, float *) {}
+template <int ST, int CNT>
+struct LoadRun<ST, CNT, CNT> {
+  static __device__ __forceinline__ void go(unsigned, int, float *) {}
 };
+
+// acc[q] += sum over the chunks of W_D of w(c) sigma[target q + c].
+// A chunk record is RS float4s: the offset of its first cell from the target
+// in lattice elements (int bits), then its LC weights, zero-padded.
+template <int LC, int ST>
+__device__ __forceinline__ void march_chunks(const float4 *__restrict__ rec, int chunks, unsigned base,
+                                             int st, float (&acc)[kR]) {
+  constexpr int RS = (LC + 4) / 4;
+#pragma unroll 1
+  for (int c = 0; c < chunks; ++c, rec += RS) {
+    float w[4 * RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+      const float4 f = __ldg(rec + i);
+      w[4 * i] = f.x;
+      w[4 * i + 1] = f.y;
+      w[4 * i + 2] = f.z;
+      w[4 * i + 3] = f.w;
+    }
+    const unsigned addr = base + 4u * (unsigned)__float_as_int(w[0]);
+    float v[LC + kR - 1];
+    LoadRun<ST, 0, LC + kR - 1>::go(addr, st, v);
+#pragma unroll
+    for (int t = 0; t < LC; ++t)
+#pragma unroll
+      for (int q = 0; q < kR; ++q) acc[q] = fmaf(w[1 + t], v[t + q], acc[q]);
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void march_unit(int lc, const float4 *__restrict__ rec, int chunks, unsigned base,
+                                           int st, float (&acc)[kR]) {
+  switch (lc) {
+    case 2: march_chunks<2, ST>(rec, chunks, base, st, acc); break;
+    case 3: march_chunks<3, ST>(rec, chunks, base, st, acc); break;
+    case 4: march_chunks<4, ST>(rec, chunks, base, st, acc); break;
+    case 6: march_chunks<6, ST>(rec, chunks, base, st, acc); break;
+    default: march_chunks<8, ST>(rec, chunks, base, st, acc); break;
+  }
+}
 
 template <int LDP>
 __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
@@ -107,8 +188,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
   const float scale = (float)scale_d;
   const int ldp = LDP > 0 ? LDP : a.ldp;
   const unsigned lat_base = (unsigned)__cvta_generic_to_shared(lat);
-  // element (x, y) at lat_base + 4 (x + ldp y); x, y taken as biased float bits
-  const unsigned base = lat_base - 4u * kTwo23Bits * (1u + (unsigned)ldp);
   long u0 = 0, u_end = 0;
   for (;;) {
     if (u0 >= u_end) {
@@ -119,56 +198,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
       u0 = got;
       u_end = min(got + 4, a.n_units);
     }
-    const short4 un = a.units[u0++];
-    const int dx = un.x, dy = un.y;
+    const int4 un = a.units[u0++];
+    const int dx = (short)(un.y & 0xffff), dy = un.y >> 16;
+    const int lb = un.z & 0xffff, sb = un.z >> 16;
     const int xlo = dx < 0 ? -dx : 0, xhi = dx > 0 ? n - dx : n;
     const int ylo = dy < 0 ? -dy : 0, yhi = dy > 0 ? n - dy : n;
-    const int xr = xlo + un.z * 32 + lane;
-    const bool xvalid = xr < xhi;
-    const int x = xvalid ? xr : xhi - 1;
-    const int y0 = ylo + un.w * kR;
-    const float sx = dx * (1.0f / kS), sy = dy * (1.0f / kS);
-    float px = fmaf(0.5f, sx, (float)x), py = fmaf(0.5f, sy, (float)y0);
+    const bool along_y = (un.w & 1) != 0;
+    const int lc = (un.w >> 1) & 15, chunks = un.w >> 8;
+    // lane coordinate (clamped to the rectangle) and the first stacked target
+    int x, y;
+    bool lvalid;
+    if (along_y) {
+      const int xr = xlo + 32 * lb + lane;
+      lvalid = xr < xhi;
+      x = lvalid ? xr : xhi - 1;
+      y = ylo + kR * sb;
+    } else {
+      const int yr = ylo + 32 * lb + lane;
+      lvalid = yr < yhi;
+      y = lvalid ? yr : yhi - 1;
+      x = xlo + kR * sb;
+    }
+    const unsigned base = lat_base + 4u * (unsigned)(x + ldp * y);
+    {
+      // bring this D's chunk records into L1 (one 128-byte line per lane)
+      const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
+      const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
+      for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
+    }
     float acc[kR];
 #pragma unroll
     for (int q = 0; q < kR; ++q) acc[q] = 0.f;
-#pragma unroll 4
-    for (int i = 0; i < kS; ++i) {
-      const float bx = __fadd_rd(px, kTwo23), by = __fadd_rd(py, kTwo23);
-      const float ax = px - (bx - kTwo23), ay = py - (by - kTwo23);
-      const unsigned addr = base + 4u * __float_as_uint(bx) + (4u * (unsigned)ldp) * __float_as_uint(by);
-      float L[kR + 1];
-      if (LDP > 0) {
-        Rows<(LDP > 0 ? LDP : 1), kR + 1>::load(addr, ax, L);
-      } else {
-#pragma unroll
-        for (int r = 0; r <= kR; ++r) {
-          float v0, v1;
-          const unsigned ar = addr + 4u * ldp * r;
-          asm("ld.shared.f32 %0, [%1];" : "=f"(v0) : "r"(ar));
-          asm("ld.shared.f32 %0, [%1+4];" : "=f"(v1) : "r"(ar));
-          L[r] = fmaf(ax, v1 - v0, v0);
-        }
-      }
-      const float w0 = 1.0f - ay;
-#pragma unroll
-      for (int q = 0; q < kR; ++q) acc[q] = fmaf(ay, L[q + 1], fmaf(w0, L[q], acc[q]));
-      px += sx;
-      py += sy;
-    }
+    if (along_y)
+      march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
+    else
+      march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
     const float r2 = (float)(dx * dx + dy * dy);
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
     const float wk = a.wcoef * inv_r;
 #pragma unroll
     for (int q = 0; q < kR; ++q) {
-      const int y = y0 + q;
-      if (xvalid && y < yhi) {
-        const long j = (long)y * n + x;
-        const long k = j + (long)dy * n + dx;
+      const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
+      if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
+        const float sj = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
+        const float sk = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
+                                 : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
         const float w = wk * exp2f(tscale * acc[q]) * scale;
-        atomicAdd(&ysh[j], (unsigned long long)__float2ll_rn(w * __ldg(a.src + k)));
-        atomicAdd(&ysh[k], (unsigned long long)__float2ll_rn(w * __ldg(a.src + j)));
+        atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
+        atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
       }
     }
   }
@@ -187,39 +265,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
   }
 }
 
-// the padded FP32 lattice (stride P = n + 1) with kExtraRows more rows
-// repeating row n
-__global__ void k_make_rows(int n, const float *__restrict__ pad, int rows, float *__restrict__ out) {
+// the padded FP32 lattice (pitch P = n + 1) extended to rows x ldp, repeating
+// its last row and column
+__global__ void k_make_lattice(int n, const float *__restrict__ pad, int rows, int ldp,
+                               float *__restrict__ out) {
   const int P = n + 1;
-  const long total = (long)rows * P;
+  const long total = (long)rows * ldp;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / P), x = (int)(i % P);
-    out[i] = pad[(long)min(y, P - 1) * P + x];
+    const int y = (int)(i / ldp), x = (int)(i % ldp);
+    out[i] = pad[(long)min(y, P - 1) * P + min(x, P - 1)];
   }
 }
 
 // y_j = (sum_slot part[slot][j]) / scale + d_j s_j, integer sum over the slots
-__global__ void k_disp_reduce(long N, int slots, int op, const unsigned long long *__restrict__ part,
+// (the slots hold y in the rotated layout)
+__global__ void k_disp_reduce(long N, int n, int rot, int slots, int op, const unsigned long long *__restrict__ part,
                               const double *__restrict__ scale, const double *__restrict__ diag,
                               const double *__restrict__ ss, const double *__restrict__ g,
                               double *__restrict__ y) {
   const double inv = 1.0 / *scale;
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
+    const long js = yslot((int)(j % n), (int)(j / n), n, rot);
     unsigned long long acc = 0ull;
-    for (int p = 0; p < slots; ++p) acc += part[(long)p * N + j];
+    for (int p = 0; p < slots; ++p) acc += part[(long)p * N + js];
     const double sj = op == VIE_OP_A_RAW ? g[j] : ss[j] * g[j];
     const double v = (double)(long long)acc * inv + diag[j] * sj;
     y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
   }
 }
 
-// s = sigma_s g (or g) in FP32, and max |s| (float bits, atomicMax)
-__global__ void k_disp_source(long N, int op, const double *__restrict__ ss, const double *__restrict__ g,
-                              float *__restrict__ s, unsigned *__restrict__ smax) {
+// s = sigma_s g (or g) in FP32, its transpose, and max |s| (float bits, atomicMax)
+__global__ void k_disp_source(long N, int n, int op, const double *__restrict__ ss, const double *__restrict__ g,
+                              float *__restrict__ s, float *__restrict__ s_t, unsigned *__restrict__ smax) {
   unsigned m = 0u;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
     const float v = (float)(op == VIE_OP_A_RAW ? g[i] : ss[i] * g[i]);
     s[i] = v;
+    s_t[(i % n) * n + i / n] = v;
     m = max(m, __float_as_uint(fabsf(v)));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -230,71 +312,253 @@ typedef void (*DispKernel)(DispArgs);
 
 DispKernel pick_disp(int ldp) {
   switch (ldp) {
-    case 65: return k_pairs_disp<65>;
-    case 129: return k_pairs_disp<129>;
+    case 79: return k_pairs_disp<79>;
+    case 143: return k_pairs_disp<143>;
     default: return k_pairs_disp<0>;
   }
+}
+
+// lattice pitch: room for kPad stacked targets past the grid, odd so that 32
+// consecutive rows of one column fall in 32 different banks
+int disp_ldp(int n) {
+  const int p = n + 1 + kPad;
+  return p | 1;
+}
+
+struct Cell {
+  int cx, cy;
+  double w;
+};
+
+// W_D: the bilinear weights of the S midpoint samples (i + 1/2) D / S summed
+// per lattice cell (Section 3.2, M-iii), cells with zero weight left out;
+// sorted by (cx, cy) when runs go along y, by (cy, cx) when they go along x
+void stencil_cells(int dx, int dy, bool along_y, std::vector<Cell> &out) {
+  std::vector<Cell> raw;
+  raw.reserve(4 * kS);
+  for (int i = 0; i < kS; ++i) {
+    const double px = (i + 0.5) * dx / kS, py = (i + 0.5) * dy / kS;
+    const double fx = floor(px), fy = floor(py), ax = px - fx, ay = py - fy;
+    const int ix = (int)fx, iy = (int)fy;
+    const double w[4] = {(1.0 - ax) * (1.0 - ay), ax * (1.0 - ay), (1.0 - ax) * ay, ax * ay};
+    for (int c = 0; c < 4; ++c)
+      if (w[c] != 0.0) raw.push_back({ix + (c & 1), iy + (c >> 1), w[c]});
+  }
+  std::sort(raw.begin(), raw.end(), [along_y](const Cell &p, const Cell &q) {
+    return along_y ? (p.cx != q.cx ? p.cx < q.cx : p.cy < q.cy) : (p.cy != q.cy ? p.cy < q.cy : p.cx < q.cx);
+  });
+  out.clear();
+  for (const Cell &c : raw) {
+    if (!out.empty() && out.back().cx == c.cx && out.back().cy == c.cy)
+      out.back().w += c.w;
+    else
+      out.push_back(c);
+  }
+}
+
+// run lengths of sorted cells (a run: consecutive cells along the run axis)
+void stencil_runs(const std::vector<Cell> &cells, bool along_y, std::vector<int> &starts) {
+  starts.clear();
+  for (size_t i = 0; i < cells.size(); ++i) {
+    const bool cont = i > 0 && (along_y ? cells[i].cx == cells[i - 1].cx && cells[i].cy == cells[i - 1].cy + 1
+                                        : cells[i].cy == cells[i - 1].cy && cells[i].cx == cells[i - 1].cx + 1);
+    if (!cont) starts.push_back((int)i);
+  }
+  starts.push_back((int)cells.size());
+}
+
+// chunk length and estimated instructions per thread of one unit when the
+// runs are cut into chunks of Lc cells: per chunk its record loads and loop,
+// Lc + kR - 1 lattice loads and kR Lc multiply-adds
+struct Plan {
+  int lc;
+  long chunks, cost;
+};
+Plan chunk_plan(const std::vector<int> &starts) {
+  Plan best{0, 0, -1};
+  for (int lc : kChunkLengths) {
+    long ch = 0;
+    for (size_t r = 0; r + 1 < starts.size(); ++r) ch += (starts[r + 1] - starts[r] + lc - 1) / lc;
+    const long cost = ch * (6 + (lc + 4) / 4 + (lc + kR - 1) + (long)kR * lc) + 60;
+    if (best.cost < 0 || cost < best.cost) best = {lc, ch, cost};
+  }
+  return best;
 }
 
 }  // namespace
 
 size_t disp_smem_bytes(int n) {
-  const long rows = n + 1 + kExtraRows;
-  return sizeof(float) * (size_t)rows * (n + 1) + sizeof(unsigned long long) * (size_t)n * n + 16;
+  const long rows = n + 1 + kPad, N = (long)n * n;
+  return sizeof(float) * (size_t)rows * disp_ldp(n) + sizeof(unsigned long long) * (size_t)(N + (N & 1)) + 16;
 }
+
+namespace {
+
+// The stencils and the sorted work units depend on n only, not on the
+// medium: they are built once per (device, n) and shared by every handle of
+// that size (kept after the last handle goes, at most kGeoKeep unused ones).
+struct Geometry {
+  int device = -1, n = 0, refs = 0;
+  int4 *units = nullptr;
+  float *stencil = nullptr;
+  long n_units = 0;
+  size_t stencil_bytes = 0;
+  double taps = 0.0;
+};
+std::mutex g_geo_mu;
+std::vector<Geometry *> g_geo;
+constexpr int kGeoKeep = 4;
+
+void geometry_free(Geometry *g) {
+  if (g->units) cudaFree(g->units);
+  if (g->stencil) cudaFree(g->stencil);
+  delete g;
+}
+
+// drop the oldest unused entries beyond kGeoKeep (caller holds g_geo_mu)
+void geometry_trim() {
+  int unused = 0;
+  for (Geometry *g : g_geo) unused += g->refs == 0;
+  for (size_t i = 0; i < g_geo.size() && unused > kGeoKeep;) {
+    if (g_geo[i]->refs == 0) {
+      geometry_free(g_geo[i]);
+      g_geo.erase(g_geo.begin() + i);
+      --unused;
+    } else {
+      ++i;
+    }
+  }
+}
+
+vie_status geometry_build(int n, int ldp, Geometry *geo) {
+  // stencils and work units, the run axis of each D chosen by estimated cost
+  struct U {
+    int4 u;
+    long cost;
+  };
+  std::vector<U> units;
+  std::vector<float> rec;
+  std::vector<Cell> cy_cells, cx_cells;
+  std::vector<int> cy_runs, cx_runs;
+  double taps = 0.0;
+  for (int dy = 0; dy < n; ++dy)
+    for (int dx = -(n - 1); dx < n; ++dx) {
+      if (dy == 0 && dx <= 0) continue;
+      const int wx = n - std::abs(dx), wy = n - dy;
+      stencil_cells(dx, dy, true, cy_cells);
+      stencil_runs(cy_cells, true, cy_runs);
+      stencil_cells(dx, dy, false, cx_cells);
+      stencil_runs(cx_cells, false, cx_runs);
+      const long uy = (long)((wx + 31) / 32) * ((wy + kR - 1) / kR);
+      const long ux = (long)((wy + 31) / 32) * ((wx + kR - 1) / kR);
+      const Plan py = chunk_plan(cy_runs), px = chunk_plan(cx_runs);
+      const bool along_y = uy * py.cost <= ux * px.cost;
+      const std::vector<Cell> &cells = along_y ? cy_cells : cx_cells;
+      taps += (double)cells.size() * wx * wy;
+      const std::vector<int> &runs = along_y ? cy_runs : cx_runs;
+      const Plan &pl = along_y ? py : px;
+      const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
+      for (size_t r = 0; r + 1 < runs.size(); ++r)
+        for (int c0 = runs[r]; c0 < runs[r + 1]; c0 += pl.lc) {
+          const int eoff = cells[c0].cx + ldp * cells[c0].cy;
+          float obits;
+          memcpy(&obits, &eoff, sizeof obits);
+          rec.push_back(obits);
+          for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < runs[r + 1] ? (float)cells[c0 + i].w : 0.f);
+          for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
+        }
+      const int lanes = along_y ? wx : wy, stack = along_y ? wy : wx;
+      const int w = (along_y ? 1 : 0) | (pl.lc << 1) | ((int)pl.chunks << 8);
+      for (int sb = 0; sb < (stack + kR - 1) / kR; ++sb)
+        for (int lb = 0; lb < (lanes + 31) / 32; ++lb)
+          units.push_back({make_int4(off, (dx & 0xffff) | (dy << 16), lb | (sb << 16), w), pl.cost});
+    }
+  for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
+  std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
+  std::vector<int4> uv(units.size());
+  for (size_t i = 0; i < units.size(); ++i) uv[i] = units[i].u;
+  VIE_CUDA(cudaMalloc((void **)&geo->units, sizeof(int4) * uv.size()));
+  VIE_CUDA(cudaMemcpy(geo->units, uv.data(), sizeof(int4) * uv.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(cudaMalloc((void **)&geo->stencil, sizeof(float) * rec.size()));
+  VIE_CUDA(cudaMemcpy(geo->stencil, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice));
+  geo->n_units = (long)uv.size();
+  geo->stencil_bytes = sizeof(float) * rec.size();
+  geo->taps = taps;
+  return VIE_OK;
+}
+
+vie_status geometry_acquire(int device, int n, int ldp, Geometry **out) {
+  std::lock_guard<std::mutex> lock(g_geo_mu);
+  for (Geometry *g : g_geo)
+    if (g->device == device && g->n == n) {
+      ++g->refs;
+      *out = g;
+      return VIE_OK;
+    }
+  Geometry *g = new Geometry;
+  g->device = device;
+  g->n = n;
+  const vie_status s = geometry_build(n, ldp, g);
+  if (s != VIE_OK) {
+    geometry_free(g);
+    return s;
+  }
+  g->refs = 1;
+  g_geo.push_back(g);
+  geometry_trim();
+  *out = g;
+  return VIE_OK;
+}
+
+void geometry_release(Geometry *g) {
+  std::lock_guard<std::mutex> lock(g_geo_mu);
+  --g->refs;
+  geometry_trim();
+}
+
+}  // namespace
 
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st) {
   dp->usable = 0;
-  if (n < 2) return VIE_OK;
+  if (n < 2 || n > 4096) return VIE_OK;
   cudaDeviceProp prop;
   VIE_CUDA(cudaGetDeviceProperties(&prop, device));
   const size_t smem = disp_smem_bytes(n);
   if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
-  const int ldp = n + 1, rows = n + 1 + kExtraRows;
+  const int ldp = disp_ldp(n), rows = n + 1 + kPad;
   DispKernel k = pick_disp(ldp);
   VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads, smem));
   if (bps < 1) return VIE_OK;
-  // work units, largest displacement rectangles first
-  struct D {
-    int dx, dy;
-    long area;
-  };
-  std::vector<D> ds;
-  for (int dy = 0; dy < n; ++dy)
-    for (int dx = -(n - 1); dx < n; ++dx) {
-      if (dy == 0 && dx <= 0) continue;
-      ds.push_back({dx, dy, (long)(n - std::abs(dx)) * (n - dy)});
-    }
-  std::stable_sort(ds.begin(), ds.end(), [](const D &p, const D &q) { return p.area > q.area; });
-  std::vector<short4> units;
-  for (const D &d : ds) {
-    const int wx = n - std::abs(d.dx), wy = n - d.dy;
-    const int bxs = (wx + 31) / 32, bys = (wy + kR - 1) / kR;
-    for (int by = 0; by < bys; ++by)
-      for (int bx = 0; bx < bxs; ++bx)
-        units.push_back(make_short4((short)d.dx, (short)d.dy, (short)bx, (short)by));
-  }
-  VIE_CUDA(cudaMalloc((void **)&dp->units, sizeof(short4) * units.size()));
-  VIE_CUDA(cudaMemcpy(dp->units, units.data(), sizeof(short4) * units.size(), cudaMemcpyHostToDevice));
+  Geometry *geo = nullptr;
+  vie_status s = geometry_acquire(device, n, ldp, &geo);
+  if (s != VIE_OK) return s;
+  dp->geometry = geo;
+  dp->units = geo->units;
+  dp->stencil = geo->stencil;
+  dp->n_units = geo->n_units;
+  dp->taps = geo->taps;
+  dp->stencil_bytes = geo->stencil_bytes;
   VIE_CUDA(cudaMalloc((void **)&dp->counter, 2 * sizeof(int)));
   VIE_CUDA(cudaMemset(dp->counter, 0, 2 * sizeof(int)));
   const long lat_elems = (long)rows * ldp;
   VIE_CUDA(cudaMalloc((void **)&dp->lattice, sizeof(float) * lat_elems));
-  k_make_rows<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows,
-                                                                              (float *)dp->lattice);
-  VIE_CHECK_LAUNCH("k_make_rows");
+  k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp,
+                                                                                (float *)dp->lattice);
+  VIE_CHECK_LAUNCH("k_make_lattice");
   VIE_CUDA(cudaMalloc((void **)&dp->smax, sizeof(unsigned)));
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
+  VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
   // every row sum of A is below sum over all nonzero displacements of h / (2 pi r)
   double rb = 0.0;
   for (int dy = -(n - 1); dy < n; ++dy)
     for (int dx = -(n - 1); dx < n; ++dx)
       if (dx || dy) rb += 1.0 / sqrt((double)dx * dx + (double)dy * dy);
   dp->rbound = rb / (2.0 * kPi * n);
-  dp->n_units = (long)units.size();
+  dp->n = n;
+  dp->rot = (n & 1) ? 2 : 1;  // n + rot odd
   dp->lat_elems = lat_elems;
   dp->ldp = ldp;
   dp->smem = smem;
@@ -305,14 +569,18 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
 }
 
 void disp_release(DispPlan *dp) {
-  if (dp->units) cudaFree(dp->units);
+  if (dp->geometry) geometry_release((Geometry *)dp->geometry);
   if (dp->counter) cudaFree(dp->counter);
   if (dp->lattice) cudaFree(dp->lattice);
   if (dp->smax) cudaFree(dp->smax);
   if (dp->scale) cudaFree(dp->scale);
+  if (dp->src_t) cudaFree(dp->src_t);
+  dp->geometry = nullptr;
+  dp->src_t = nullptr;
   dp->smax = nullptr;
   dp->scale = nullptr;
   dp->units = nullptr;
+  dp->stencil = nullptr;
   dp->counter = nullptr;
   dp->lattice = nullptr;
   dp->usable = 0;
@@ -321,7 +589,7 @@ void disp_release(DispPlan *dp) {
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st) {
   const int blocks = (int)std::min((N + 255) / 256, 1024L);
-  k_disp_source<<<blocks, 256, 0, st>>>(N, op, sigma_s, g, src, dp.smax);
+  k_disp_source<<<blocks, 256, 0, st>>>(N, dp.n, op, sigma_s, g, src, dp.src_t, dp.smax);
   VIE_CHECK_LAUNCH("k_disp_source");
   return VIE_OK;
 }
@@ -329,7 +597,7 @@ vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s
 vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *partial, const double *diag,
                        const double *sigma_s, const double *g, double *y, cudaStream_t st) {
   const int blocks = (int)std::min((N + 255) / 256, 4096L);
-  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.grid, op, (const unsigned long long *)partial, dp.scale, diag,
+  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, dp.grid, op, (const unsigned long long *)partial, dp.scale, diag,
                                         sigma_s, g, y);
   VIE_CHECK_LAUNCH("k_disp_reduce");
   return VIE_OK;
@@ -339,12 +607,15 @@ vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef,
                        double *partial, cudaStream_t st) {
   DispArgs a;
   a.lat = (const float *)dp.lattice;
+  a.stencil = (const float4 *)dp.stencil;
   a.src = src;
+  a.src_t = dp.src_t;
+  a.rot = dp.rot;
   a.smax = dp.smax;
   a.scale_out = dp.scale;
   a.rbound = dp.rbound;
   a.partial = partial;
-  a.units = (const short4 *)dp.units;
+  a.units = (const int4 *)dp.units;
   a.counter = dp.counter;
   a.n_units = dp.n_units;
   a.n = n;
@@ -352,7 +623,6 @@ vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef,
   a.lat_elems = dp.lat_elems;
   a.tau_scale2 = tau_scale2;
   a.wcoef = wcoef;
-  a.h = 1.0f / n;
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kThreads), args, dp.smem, st));
   count_launch();

@@ -500,6 +500,16 @@ vie_status vie_get_kernel(vie_handle *h, int *kernel) {
   return VIE_OK;
 }
 
+vie_status vie_get_kernel_work(vie_handle *h, double *fma_per_apply) {
+  if (!h || !fma_per_apply) return invalid("vie_get_kernel_work: NULL argument");
+  int k = VIE_KERNEL_GENERAL;
+  vie_get_kernel(h, &k);
+  const double pairs = 0.5 * (double)h->N * (double)(h->N - 1);
+  *fma_per_apply = k == VIE_KERNEL_DISPLACEMENT ? h->disp.taps
+                                                : pairs * h->opts.steps * (h->dim == 3 ? 7.0 : 3.0);
+  return VIE_OK;
+}
+
 vie_status vie_get_diagonal(vie_handle *h, double *d, void *stream) {
   if (!h || !d) return invalid("vie_get_diagonal: NULL argument");
   DeviceGuard dg(h->device);

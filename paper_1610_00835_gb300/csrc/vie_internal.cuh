@@ -100,14 +100,19 @@ vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale
 struct DispPlan {
   int usable = 0;
   long n_units = 0, lat_elems = 0;
-  int ldp = 0, grid = 0;
+  int ldp = 0, grid = 0, n = 0, rot = 1;
   size_t smem = 0;
+  float *src_t = nullptr;     // s transposed (FP32 [N])
+  void *geometry = nullptr;   // shared stencils and units of this n (owned by a cache)
   void *units = nullptr;
+  void *stencil = nullptr;    // per-displacement chunk records (float4)
+  size_t stencil_bytes = 0;
   int *counter = nullptr;
   void *lattice = nullptr;
   unsigned *smax = nullptr;   // max |s| of the current apply (float bits)
   double *scale = nullptr;    // fixed-point scale of the current apply
   double rbound = 0.0;        // bound on every row sum of A
+  double taps = 0.0;          // multiply-adds of the tau sums per apply: sum_D |W_D| pairs(D)
   const void *kernel = nullptr;
 };
 size_t disp_smem_bytes(int n);

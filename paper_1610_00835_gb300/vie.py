@@ -72,6 +72,7 @@ SIGNATURES = {
     "ert_sweep": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
     "vie_get_diagonal": (C.c_int, [_vp, _vp, _vp]),
     "vie_get_kernel": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "vie_get_kernel_work": (C.c_int, [_vp, C.POINTER(C.c_double)]),
     "vie_last_error": (C.c_char_p, []),
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
@@ -390,6 +391,12 @@ def vie_get_kernel(h: VieHandle) -> int:
     k = C.c_int()
     _check(load().vie_get_kernel(h.ptr, C.byref(k)))
     return k.value
+
+
+def vie_get_kernel_work(h: VieHandle) -> float:
+    w = C.c_double()
+    _check(load().vie_get_kernel_work(h.ptr, C.byref(w)))
+    return w.value
 
 
 def vie_last_error() -> str:

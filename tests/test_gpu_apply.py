@@ -112,10 +112,12 @@ def test_2d_every_pair_kernel_all_rows(kernel, n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [100, 128, 136])
+@pytest.mark.parametrize("n", [100, 128, 133])
 def test_displacement_kernel_full_size_sampled_rows(n):
+    # 133 is the largest grid whose lattice and fixed-point y fit one SM
     m = V.bump_medium(2, n, 4, 0.9, seed=4300 + n)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
+    assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
     hs = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
     g = m.f + 0.05 * rng_vec(m.N, n)
     got = gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)
@@ -123,6 +125,19 @@ def test_displacement_kernel_full_size_sampled_rows(n):
     want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
     assert rel_l2(got[rows], want) < FP32_TOL
     assert rel_l2(got, gpu_apply(hs, P.VIE_OP_K_SIGMA_S, g)) < 2e-6
+
+
+def test_displacement_kernel_falls_back_beyond_shared_memory():
+    # n = 136 does not fit one SM's shared memory: the handle takes the
+    # tile-pair kernel and still matches the oracle
+    n = 136
+    m = V.bump_medium(2, n, 4, 0.9, seed=4436)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
+    assert P.vie_get_kernel(h) == P.VIE_KERNEL_SYMMETRIC
+    g = m.f + 0.05 * rng_vec(m.N, n)
+    rows = _sampled_rows(m.N, 8, n)
+    want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)[rows], want) < FP32_TOL
 
 
 @pytest.mark.parametrize("dim,n", [(2, 9), (3, 5)])
