@@ -152,10 +152,23 @@ def cpu_baseline_sample(m, seconds: float = 12.0) -> dict:
     t0 = time.perf_counter()
     O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows, diag=diag)
     dt = time.perf_counter() - t0
-    return {"value": len(rows) * m.N / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": f"{len(rows)} target rows x {m.N} sources of the 128x128 medium, "
-                      f"S={S_STEPS}, FP64 matrix-free apply ({dt:.1f} s)"}
+    out = {"value": len(rows) * m.N / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
+           "kind": "oracle",
+           "sample": f"{len(rows)} target rows x {m.N} sources of the 128x128 medium, "
+                     f"S={S_STEPS}, FP64 matrix-free apply ({dt:.1f} s)"}
+    # the same on one core (the paper's runs were single-threaded), a smaller sample
+    threads = O.num_threads()
+    O.set_threads(1)
+    try:
+        rows1 = np.linspace(0, m.N - 1, max(4, count // (4 * threads))).astype(np.int64)
+        t0 = time.perf_counter()
+        O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows1, diag=diag)
+        dt1 = time.perf_counter() - t0
+    finally:
+        O.set_threads(threads)
+    out["one_core"] = {"value": len(rows1) * m.N / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                       "sample": f"{len(rows1)} target rows ({dt1:.1f} s)"}
+    return out
 
 
 def run_reference(args):
@@ -193,21 +206,39 @@ def run_reference(args):
     return 0
 
 
-def measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local):
-    """Chosen solver: assemble K as BF16 hi/lo (one march per unordered pair),
-    then FP64 GMRES(64) whose applies are HBM-bound products with the stored K
-    (phi = K(f / sigma_s)).  Assembly is inside every timed step."""
+def oracle_solution(rank: int):
+    """The FP64 oracle's U for the benchmark medium (rank 0's seed), written by
+    tests/golden/make_bench_solution.py; None for other media."""
+    path = os.path.join(ROOT, "tests", "golden", "bench_U_2d_128.npy")
+    if rank != 0 or not os.path.exists(path):
+        return None
+    return np.load(path)
+
+
+def err_vs_oracle(U, U_or):
+    if U_or is None:
+        return None
+    u = U.detach().cpu().numpy() if hasattr(U, "detach") else np.asarray(U)
+    return float(np.linalg.norm(u - U_or) / np.linalg.norm(U_or))
+
+
+def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or, net=None):
+    """Assemble K once per step (one march per unordered pair; BF16 hi/lo or
+    FP32), then FP64 GMRES(64) -- or FGMRES with the learned preconditioner --
+    whose applies are HBM-bound products with the stored K (phi = K(f /
+    sigma_s)).  Assembly is inside every timed step."""
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c = torch.cuda.Event(enable_timing=True)
+    P.vie_set_preconditioner(h, net, 5.0)
     for _ in range(max(1, args.warmup)):
-        P.vie_assemble(h, P.VIE_OPERATOR_BF16X3)
+        P.vie_assemble(h, operator)
         P.vie_solve_gmres(h, f_dev, U, rtol=RTOL)
     ms, asm_ms, reps = [], [], []
     for _ in range(max(3, args.steps // 4)):
         flush_l2(flush)
         torch.cuda.synchronize()
         a.record(stream)
-        P.vie_assemble(h, P.VIE_OPERATOR_BF16X3)
+        P.vie_assemble(h, operator)
         b.record(stream)
         rep = P.vie_solve_gmres(h, f_dev, U, rtol=RTOL, time_apply=True)
         c.record(stream)
@@ -215,12 +246,18 @@ def measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local):
         ms.append(a.elapsed_time(c))
         asm_ms.append(a.elapsed_time(b))
         reps.append(rep)
+    P.vie_set_preconditioner(h, None)
     P.vie_assemble(h, P.VIE_OPERATOR_OTF)
     last = reps[-1]
-    return {"solver": "assembled BF16 hi/lo operator + FP64 GMRES(64)",
+    name = {P.VIE_OPERATOR_BF16X3: "assembled BF16 hi/lo operator (row-major, 1.07 GB)",
+            P.VIE_OPERATOR_FP32: "assembled FP32 operator (row-major, 1.07 GB)",
+            P.VIE_OPERATOR_PAIRS32: "assembled FP32 pair weights (displacement-major, each unordered pair once, 0.54 GB)"}
+    return {"solver": name[operator] + (" + FGMRES(64), learned U-Net preconditioner" if net is not None
+                                        else " + FP64 GMRES(64)"),
             "solve_ms": statistics.median(ms), "assemble_ms": statistics.median(asm_ms),
             "iters": last["iters"], "n_apply": last["n_apply"], "relres": last["relres"],
-            "apply_ms": last["t_apply_ms"] / max(1, last["n_apply"])}
+            "fell_back": last["fell_back"], "apply_ms": last["t_apply_ms"] / max(1, last["n_apply"]),
+            "err_vs_oracle": err_vs_oracle(U, U_or)}
 
 
 def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
@@ -353,6 +390,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         P.vie_solve_gmres(h, f_dev, U, rtol=RTOL)
     torch.cuda.synchronize()
+    U_or = oracle_solution(rank)
     launches0 = P.vie_kernel_launches()
     step_ms, reps = [], []
     start = torch.cuda.Event(enable_timing=True)
@@ -371,6 +409,7 @@ def run_ours(args):
             step_ms.append(start.elapsed_time(stop))
             reps.append(rep)
     launches = P.vie_kernel_launches() - launches0
+    err_plain = err_vs_oracle(U, U_or)
     total_ms = sum(step_ms)
     pairs = sum(r["n_apply"] for r in reps) * float(N) * N
     if dist is not None:
@@ -403,7 +442,14 @@ def run_ours(args):
     if clocks["sm_mhz"]:
         roofline["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
-    chosen = measure_chosen(P, torch, h, f_dev, U, flush, stream, args, local)
+    chosen = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3, U_or)
+    asm_pairs = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_PAIRS32, U_or)
+    asm_fp32 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_FP32, U_or)
+    net = P.vie_unet_create(4, 32, device=local)
+    P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
+    learned_128 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3,
+                                    U_or, net=net)
+    P.vie_unet_destroy(net)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
     batch = measure_batch(P, torch, stream, local)
     learned = measure_learned(P, torch, local)
@@ -430,7 +476,8 @@ def run_ours(args):
         last = reps[-1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 tiles / f64 krylov",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "S": S_STEPS, "rtol": RTOL,
@@ -440,7 +487,12 @@ def run_ours(args):
             "solve": {"iters": last["iters"], "n_apply": last["n_apply"],
                       "relres": last["relres"], "solve_ms_plain": total_ms / args.steps,
                       "apply_ms": sum(r["t_apply_ms"] for r in reps) / n_apply,
-                      "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen},
+                      "err_vs_oracle": err_plain,
+                      "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen,
+                      "assembled_pairs32": asm_pairs, "assembled_fp32": asm_fp32,
+                      "chosen_learned": learned_128,
+                      "oracle_U": "tests/golden/bench_U_2d_128.npy (FP64 oracle, rtol 1e-11)"
+                      if U_or is not None else None},
             "bf16x3_product": product,
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
@@ -463,7 +515,7 @@ def run_apply_only(args):
     m = V.heterogeneous_2d(n=args.n) if args.dim == 2 else V.heterogeneous_3d(n=args.n)
     h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS)
     mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32,
-            "bf16x3": P.VIE_OPERATOR_BF16X3}[args.operator]
+            "bf16x3": P.VIE_OPERATOR_BF16X3, "pairs32": P.VIE_OPERATOR_PAIRS32}[args.operator]
     P.vie_assemble(h, mode)
     nrhs = args.nrhs
     G = V.bump_sources(args.dim, m.n, nrhs, seed=V.seed_for(4)) if nrhs > 1 else m.f[None, :]
@@ -492,7 +544,7 @@ def main(argv=None):
                     help="time operator applies only (profiling driver)")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3"], default="otf")
+    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32"], default="otf")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

@@ -129,12 +129,25 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
 enum {
   VIE_OPERATOR_OTF = 0,          /* entries generated on the fly (default)        */
   VIE_OPERATOR_FP32 = 1,         /* K assembled in HBM, FP32                      */
-  VIE_OPERATOR_BF16X3 = 2        /* K assembled as BF16 hi + lo; products with
+  VIE_OPERATOR_BF16X3 = 2,       /* K assembled as BF16 hi + lo; products with
                                     several right-hand sides on the tensor cores
                                     as Khi Ghi + Khi Glo + Klo Ghi, FP32 accumulate */
+  VIE_OPERATOR_PAIRS32 = 3       /* A_jk of every unordered pair once, FP32,
+                                    displacement-major (2D handles that use the
+                                    displacement kernel): applies stream it */
 };
 
-/* Assemble K = [K_jk omega_k] (Section 3.2, Eq. EQ: LINEAR SYSTEM) into device
+/* VIE_OPERATOR_PAIRS32: the weights A_jk = A_kj (Section 2, Eq. EQ:Kernel with
+ * the M-iii collocation of Section 3.2) of the N (N - 1) / 2 unordered pairs,
+ * each stored once in FP32 (537 MB at 128^2), grouped by displacement D = k - j:
+ * for each D of the half plane (dy > 0, or dy = 0 and dx > 0) the rectangle of
+ * targets j with j + D in the grid.  Every apply (any vie_op, nrhs applies for
+ * nrhs right-hand sides) reads them once and accumulates exactly as the
+ * on-the-fly displacement kernel does, so its results are bitwise equal to
+ * the on-the-fly applies of the same handle.  Only for handles whose
+ * vie_get_kernel is VIE_KERNEL_DISPLACEMENT (else VIE_ERR_UNSUPPORTED).
+ *
+ * Assemble K = [K_jk omega_k] (Section 3.2, Eq. EQ: LINEAR SYSTEM) into device
  * memory and use it for later VIE_OP_K_SIGMA_S / VIE_OP_I_MINUS_K applies and
  * solves; the paper caches its kernel evaluations for reuse across GMRES
  * iterations in the same way (Section 4.2).  Entries are the on-the-fly FP32

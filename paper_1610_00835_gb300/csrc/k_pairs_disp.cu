@@ -51,6 +51,7 @@
 // the lattice carries kPad = (kR - 1) + (Lc - 1) extra rows and columns
 // (repeating the edge) so that stacked targets beyond it and the padding of
 // the last chunk of a run stay in bounds.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -85,6 +86,8 @@ struct DispArgs {
   const int4 *units;           // {first chunk, dx | dy << 16, lane block | stack block << 16,
                                //  runs along y | Lc << 1 | chunks << 8}
   int *counter;                // [2]
+  float *wbuf;                 // stored weights (store: written, stream: read)
+  const long long *doff;       // first stored weight of each D of the half plane
   long n_units;
   int n, ldp, rot;             // rot = c of the rotated layout of y
   long lat_elems;
@@ -164,27 +167,45 @@ __device__ __forceinline__ void march_unit(int lc, const float4 *__restrict__ re
   }
 }
 
-template <int LDP>
-__global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
+// What one launch does with the pairs of its units.
+enum DispMode {
+  kApply = 0,   // march, then y_j += w s_k and y_k += w s_j (fixed point)
+  kStore = 1,   // march, then store w (FP32, displacement-major) for later applies
+  kStream = 2   // read the stored w, then y_j += w s_k and y_k += w s_j
+};
+
+// index of D = (dx, dy) in the half plane, in the order the geometry lists them
+__device__ __forceinline__ int disp_index(int dx, int dy, int n) {
+  return dy == 0 ? dx - 1 : (n - 1) + (dy - 1) * (2 * n - 1) + (dx + n - 1);
+}
+
+template <int LDP, int MODE>
+__device__ __forceinline__ void disp_body(const DispArgs &a) {
   extern __shared__ float4 smem4[];
-  unsigned long long *ysh = reinterpret_cast<unsigned long long *>(smem4);  // [N] fixed point
   const int n = a.n;
   const long N = (long)n * n;
-  float *lat = reinterpret_cast<float *>(ysh + N + (N & 1));  // 16-byte aligned for float4 staging
+  // shared memory: y (int64 fixed point, [N]) unless storing, then the lattice unless streaming
+  unsigned long long *ysh = reinterpret_cast<unsigned long long *>(smem4);
+  float *lat = MODE == kStore ? reinterpret_cast<float *>(smem4)
+                              : reinterpret_cast<float *>(ysh + N + (N & 1));  // 16-byte aligned
   const int tid = threadIdx.x, lane = tid & 31;
-  {
+  if constexpr (MODE != kStream) {
     const float4 *g4 = reinterpret_cast<const float4 *>(a.lat);
     float4 *l4 = reinterpret_cast<float4 *>(lat);
     const long n4 = a.lat_elems / 4;
     for (long i = tid; i < n4; i += kThreads) l4[i] = g4[i];
     for (long i = n4 * 4 + tid; i < a.lat_elems; i += kThreads) lat[i] = a.lat[i];
+  }
+  if constexpr (MODE != kStore) {
     for (long i = tid; i < N; i += kThreads) ysh[i] = 0ull;
   }
   __syncthreads();
   // power-of-two scale: 2^k <= 2^62 / (max|s| R), so w * scale is exact
-  const float smax = __uint_as_float(*a.smax);
-  const double scale_d =
-      smax > 0.f ? ldexp(1.0, ilogb(4.611686018427387904e18 / ((double)smax * a.rbound))) : 1.0;
+  double scale_d = 1.0;
+  if constexpr (MODE != kStore) {
+    const float smax = __uint_as_float(*a.smax);
+    if (smax > 0.f) scale_d = ldexp(1.0, ilogb(4.611686018427387904e18 / ((double)smax * a.rbound)));
+  }
   const float scale = (float)scale_d;
   const int ldp = LDP > 0 ? LDP : a.ldp;
   const unsigned lat_base = (unsigned)__cvta_generic_to_shared(lat);
@@ -219,50 +240,215 @@ __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
       y = lvalid ? yr : yhi - 1;
       x = xlo + kR * sb;
     }
-    const unsigned base = lat_base + 4u * (unsigned)(x + ldp * y);
-    {
-      // bring this D's chunk records into L1 (one 128-byte line per lane)
-      const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
-      const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
-      for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
-    }
     float acc[kR];
 #pragma unroll
     for (int q = 0; q < kR; ++q) acc[q] = 0.f;
-    if (along_y)
-      march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
-    else
-      march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+    if constexpr (MODE != kStream) {
+      const unsigned base = lat_base + 4u * (unsigned)(x + ldp * y);
+      {
+        // bring this D's chunk records into L1 (one 128-byte line per lane)
+        const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
+        const int lines =
+            (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
+        for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
+      }
+      if (along_y)
+        march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
+      else
+        march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+    }
     const float r2 = (float)(dx * dx + dy * dy);
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
     const float wk = a.wcoef * inv_r;
+    // stored weights of D: its rectangle of targets, row-major (lanes along x
+    // write 128 contiguous bytes; lanes along y each write their 8 targets)
+    long woff = 0;
+    if constexpr (MODE != kApply) woff = a.doff[disp_index(dx, dy, n)];
+    const int wx = xhi - xlo;
+    if constexpr (MODE == kStream) {
+      // four targets at a time: their global loads are issued before their atomics
 #pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
-      if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
-        const float sj = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
-        const float sk = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
-                                 : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
-        const float w = wk * exp2f(tscale * acc[q]) * scale;
-        atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
-        atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
+      for (int q0 = 0; q0 < kR; q0 += 4) {
+        float wv[4], sjv[4], skv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = q0 + i;
+          const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
+          wv[i] = sjv[i] = skv[i] = 0.f;
+          if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
+            const long wi = woff + (long)(yq - ylo) * wx + (xq - xlo);
+            wv[i] = __ldcs(a.wbuf + wi);
+            sjv[i] = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
+            skv[i] = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
+                             : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = q0 + i;
+          const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
+          if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
+            const float w = wv[i] * scale;
+            atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * skv[i]));
+            atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sjv[i]));
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
+        if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
+          const float wq = wk * exp2f(tscale * acc[q]);
+          if constexpr (MODE == kStore) {
+            a.wbuf[woff + (long)(yq - ylo) * wx + (xq - xlo)] = wq;
+          } else {
+            const float sj = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
+            const float sk = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
+                                     : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
+            const float w = wq * scale;
+            atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
+            atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
+          }
+        }
       }
     }
   }
+  // every warp of this CTA is past its last unit before the CTA counts as done
+  // (the last CTA resets the unit counter for the next launch)
   __syncthreads();
-  unsigned long long *out = reinterpret_cast<unsigned long long *>(a.partial) + (long)blockIdx.x * N;
-  for (long i = tid; i < N; i += kThreads) out[i] = ysh[i];
-  if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
+  if constexpr (MODE != kStore) {
+    unsigned long long *out = reinterpret_cast<unsigned long long *>(a.partial) + (long)blockIdx.x * N;
+    for (long i = tid; i < N; i += kThreads) out[i] = ysh[i];
+    if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
+  }
   if (tid == 0) {
     __threadfence();
     if (atomicAdd(a.counter + 1, 1) == (int)gridDim.x - 1) {
       a.counter[0] = 0;
       a.counter[1] = 0;
-      *a.smax = 0u;  // every CTA read it before this, the next source kernel sets it
+      if (MODE != kStore) *a.smax = 0u;  // every CTA read it before this, the next source kernel sets it
       __threadfence();
     }
   }
+}
+
+template <int LDP>
+__global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
+  disp_body<LDP, kApply>(a);
+}
+
+template <int LDP>
+__global__ void __launch_bounds__(kThreads, 1) k_store_disp(DispArgs a) {
+  disp_body<LDP, kStore>(a);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_stream_disp(DispArgs a) {
+  disp_body<1, kStream>(a);
+}
+
+// bf16 bits of v rounded to nearest even (finite v), in integer arithmetic
+__device__ __forceinline__ unsigned short bf16_bits_rn(float v) {
+  const unsigned u = __float_as_uint(v);
+  return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void put_entry(long idx, float v, float *k32, unsigned short *khi, unsigned short *klo) {
+  if constexpr (BF16) {
+    const unsigned short hi = bf16_bits_rn(v);
+    khi[idx] = hi;
+    klo[idx] = bf16_bits_rn(v - __uint_as_float((unsigned)hi << 16));
+  } else {
+    k32[idx] = v;
+  }
+}
+
+// K_jk = A_jk sigma_s,k (j != k) and K_jj = d_j sigma_s,j, row-major N x ldk
+// (FP32, or BF16 hi + lo with lo = bf16(v - hi)), from the stored pair
+// weights, each read once.  An item is (dy, target row yj): the stored rows
+// "D = (dx, dy), targets (., yj)" of every dx go to shared memory
+// (T[dx + n - 1][xj]), then
+//   K[j][k]  = T sigma_s,k  for j = (xj, yj), k = (xk, yj + dy), and
+//   K[k][j]  = T sigma_s,j  for the same pairs seen from k,
+// each written as whole row segments of n columns.  Every ordered pair is
+// written once: by its own D when D is in the half plane, else from -D.  For
+// dy = 0 the row of j gets its columns k > j from the first part and k < j
+// from the second, and the diagonal K_jj = d_j sigma_s,j.
+
+template <bool BF16>
+__global__ void __launch_bounds__(1024, 1) k_expand_pairs(int n, const float *__restrict__ w,
+                                                          const long long *__restrict__ doff,
+                                                          const float *__restrict__ ss,
+                                                          const double *__restrict__ diag,
+                                                          const double *__restrict__ ss64, long ldk, float *k32,
+                                                          unsigned short *khi, unsigned short *klo) {
+  extern __shared__ float T[];  // [2n - 1][p]
+  const int p = n + 2;           // strides p and 1 - p: at most one is even (2-way conflicts)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const int items = n * (n + 1) / 2;
+  // item t -> (dy, yj), rows of dy holding n - dy items; advanced by gridDim.x per step
+  int dy = 0, yj = blockIdx.x;
+  while (dy < n && yj >= n - dy) {
+    yj -= n - dy;
+    ++dy;
+  }
+  for (int t = blockIdx.x; t < items; t += gridDim.x) {
+    if (t != (int)blockIdx.x) {
+      yj += gridDim.x;
+      while (dy < n && yj >= n - dy) {
+        yj -= n - dy;
+        ++dy;
+      }
+    }
+    const int yk = yj + dy;
+    for (int dx = -(n - 1) + warp; dx < n; dx += warps) {
+      if (dy == 0 && dx <= 0) continue;
+      const int xlo = dx < 0 ? -dx : 0, wx = n - (dx < 0 ? -dx : dx);
+      const float *row = w + doff[disp_index(dx, dy, n)] + (long)yj * wx;
+      float *trow = T + (dx + n - 1) * p + xlo;
+      for (int x = lane; x < wx; x += 32) trow[x] = __ldcs(row + x);
+    }
+    __syncthreads();
+    const long jrow = (long)n * yj, krow = (long)n * yk;
+    const float *ssj = ss + jrow, *ssk = ss + krow;
+    if (dy > 0) {
+      // every (xj, xk) is a pair of this item
+      for (int xj = warp; xj < n; xj += warps) {
+        const float *tb = T + (n - 1 - xj) * p + xj;  // T[(xk - xj + n - 1) p + xj]
+        const long rb = (jrow + xj) * ldk + krow;
+        for (int xk = lane; xk < n; xk += 32) put_entry<BF16>(rb + xk, tb[xk * p] * ssk[xk], k32, khi, klo);
+      }
+      for (int xk = warp; xk < n; xk += warps) {
+        const float *tb = T + (xk + n - 1) * p;  // T[(xk - xj + n - 1) p + xj]
+        const long rb = (krow + xk) * ldk + jrow;
+        for (int xj = lane; xj < n; xj += 32) put_entry<BF16>(rb + xj, tb[xj * (1 - p)] * ssj[xj], k32, khi, klo);
+      }
+    } else {
+      // one grid row: columns right of the diagonal from j, left of it from k
+      for (int r = warp; r < n; r += warps) {
+        const long rb = (jrow + r) * ldk + jrow;
+        for (int x = lane; x < n; x += 32) {
+          if (x == r) continue;
+          const float v = x > r ? T[(x - r + n - 1) * p + r] : T[(r - x + n - 1) * p + x];
+          put_entry<BF16>(rb + x, v * ssj[x], k32, khi, klo);
+        }
+      }
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const long j = jrow + r;
+        put_entry<BF16>(j * ldk + j, (float)(diag[j] * ss64[j]), k32, khi, klo);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// FP32 copy of sigma_s (the expansion multiplies in FP32, as the on-the-fly
+// kernels do)
+__global__ void k_to_f32(long N, const double *__restrict__ x, float *__restrict__ y) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 // the padded FP32 lattice (pitch P = n + 1) extended to rows x ldp, repeating
@@ -315,6 +501,14 @@ DispKernel pick_disp(int ldp) {
     case 79: return k_pairs_disp<79>;
     case 143: return k_pairs_disp<143>;
     default: return k_pairs_disp<0>;
+  }
+}
+
+DispKernel pick_store(int ldp) {
+  switch (ldp) {
+    case 79: return k_store_disp<79>;
+    case 143: return k_store_disp<143>;
+    default: return k_store_disp<0>;
   }
 }
 
@@ -401,6 +595,7 @@ struct Geometry {
   int device = -1, n = 0, refs = 0;
   int4 *units = nullptr;
   float *stencil = nullptr;
+  long long *doff = nullptr;  // first stored weight of each D (displacement-major storage)
   long n_units = 0;
   size_t stencil_bytes = 0;
   double taps = 0.0;
@@ -412,6 +607,7 @@ constexpr int kGeoKeep = 4;
 void geometry_free(Geometry *g) {
   if (g->units) cudaFree(g->units);
   if (g->stencil) cudaFree(g->stencil);
+  if (g->doff) cudaFree(g->doff);
   delete g;
 }
 
@@ -440,11 +636,15 @@ vie_status geometry_build(int n, int ldp, Geometry *geo) {
   std::vector<float> rec;
   std::vector<Cell> cy_cells, cx_cells;
   std::vector<int> cy_runs, cx_runs;
+  std::vector<long long> doff;
+  long long stored = 0;
   double taps = 0.0;
   for (int dy = 0; dy < n; ++dy)
     for (int dx = -(n - 1); dx < n; ++dx) {
       if (dy == 0 && dx <= 0) continue;
       const int wx = n - std::abs(dx), wy = n - dy;
+      doff.push_back(stored);
+      stored += (long long)wx * wy;
       stencil_cells(dx, dy, true, cy_cells);
       stencil_runs(cy_cells, true, cy_runs);
       stencil_cells(dx, dy, false, cx_cells);
@@ -481,6 +681,8 @@ vie_status geometry_build(int n, int ldp, Geometry *geo) {
   VIE_CUDA(cudaMemcpy(geo->units, uv.data(), sizeof(int4) * uv.size(), cudaMemcpyHostToDevice));
   VIE_CUDA(cudaMalloc((void **)&geo->stencil, sizeof(float) * rec.size()));
   VIE_CUDA(cudaMemcpy(geo->stencil, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(cudaMalloc((void **)&geo->doff, sizeof(long long) * doff.size()));
+  VIE_CUDA(cudaMemcpy(geo->doff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice));
   geo->n_units = (long)uv.size();
   geo->stencil_bytes = sizeof(float) * rec.size();
   geo->taps = taps;
@@ -531,10 +733,23 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads, smem));
   if (bps < 1) return VIE_OK;
+  // the store and stream kernels of the displacement-major operator
+  const long N = (long)n * n;
+  const size_t smem_store = sizeof(float) * (size_t)rows * ldp + 16;
+  const size_t smem_stream = sizeof(unsigned long long) * (size_t)(N + (N & 1)) + 16;
+  DispKernel ks = pick_store(ldp);
+  VIE_CUDA(cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_store));
+  VIE_CUDA(cudaFuncSetAttribute((const void *)k_stream_disp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_stream));
+  int bps_store = 0, bps_stream = 0;
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_store, ks, kThreads, smem_store));
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_stream, k_stream_disp, kThreads, smem_stream));
+  if (bps_store < 1 || bps_stream < 1) return VIE_OK;
   Geometry *geo = nullptr;
   vie_status s = geometry_acquire(device, n, ldp, &geo);
   if (s != VIE_OK) return s;
   dp->geometry = geo;
+  dp->doff = geo->doff;
   dp->units = geo->units;
   dp->stencil = geo->stencil;
   dp->n_units = geo->n_units;
@@ -551,6 +766,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
   VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
+  VIE_CUDA(cudaMalloc((void **)&dp->ss32, sizeof(float) * (size_t)n * n));
   // every row sum of A is below sum over all nonzero displacements of h / (2 pi r)
   double rb = 0.0;
   for (int dy = -(n - 1); dy < n; ++dy)
@@ -564,6 +780,13 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   dp->smem = smem;
   dp->grid = bps * prop.multiProcessorCount;
   dp->kernel = (const void *)k;
+  dp->kernel_store = (const void *)ks;
+  dp->smem_store = smem_store;
+  dp->grid_store = bps_store * prop.multiProcessorCount;
+  dp->kernel_stream = (const void *)k_stream_disp;
+  dp->smem_stream = smem_stream;
+  dp->grid_stream = std::min(bps_stream * prop.multiProcessorCount, dp->grid);  // partial slots: grid
+  dp->stored = N * (N - 1) / 2;
   dp->usable = 1;
   return VIE_OK;
 }
@@ -575,12 +798,15 @@ void disp_release(DispPlan *dp) {
   if (dp->smax) cudaFree(dp->smax);
   if (dp->scale) cudaFree(dp->scale);
   if (dp->src_t) cudaFree(dp->src_t);
+  if (dp->ss32) cudaFree(dp->ss32);
+  dp->ss32 = nullptr;
   dp->geometry = nullptr;
   dp->src_t = nullptr;
   dp->smax = nullptr;
   dp->scale = nullptr;
   dp->units = nullptr;
   dp->stencil = nullptr;
+  dp->doff = nullptr;
   dp->counter = nullptr;
   dp->lattice = nullptr;
   dp->usable = 0;
@@ -594,17 +820,53 @@ vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s
   return VIE_OK;
 }
 
-vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *partial, const double *diag,
-                       const double *sigma_s, const double *g, double *y, cudaStream_t st) {
+vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const double *sigma_s, const double *diag,
+                       long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st) {
+  const long N = (long)n * n;
+  const size_t esz = k32 ? sizeof(float) : sizeof(__nv_bfloat16);
+  if (ldk > N) {
+    // zero the padding columns [N, ldk) of every row
+    if (k32) VIE_CUDA(cudaMemset2DAsync(k32 + N, ldk * esz, 0, (ldk - N) * esz, N, st));
+    if (khi) {
+      VIE_CUDA(cudaMemset2DAsync((__nv_bfloat16 *)khi + N, ldk * esz, 0, (ldk - N) * esz, N, st));
+      VIE_CUDA(cudaMemset2DAsync((__nv_bfloat16 *)klo + N, ldk * esz, 0, (ldk - N) * esz, N, st));
+    }
+  }
+  cudaDeviceProp prop;
+  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  const size_t smem = sizeof(float) * (size_t)(2 * n - 1) * (n + 2);
+  if (smem > (size_t)prop.sharedMemPerBlockOptin) {
+    set_error("vie_assemble: grid too large for the pair-weight expansion");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const void *kx = k32 ? (const void *)k_expand_pairs<false> : (const void *)k_expand_pairs<true>;
+  VIE_CUDA(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_to_f32<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, sigma_s, dp.ss32);
+  VIE_CHECK_LAUNCH("k_to_f32");
+  const int grid = prop.multiProcessorCount;
+  if (k32)
+    k_expand_pairs<false><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, k32, nullptr,
+                                                    nullptr);
+  else
+    k_expand_pairs<true><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, nullptr,
+                                                   (unsigned short *)khi, (unsigned short *)klo);
+  VIE_CHECK_LAUNCH("k_expand_pairs");
+  return VIE_OK;
+}
+
+vie_status disp_reduce(const DispPlan &dp, long N, int slots, int op, const double *partial,
+                       const double *diag, const double *sigma_s, const double *g, double *y, cudaStream_t st) {
   const int blocks = (int)std::min((N + 255) / 256, 4096L);
-  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, dp.grid, op, (const unsigned long long *)partial, dp.scale, diag,
+  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, slots, op, (const unsigned long long *)partial, dp.scale, diag,
                                         sigma_s, g, y);
   VIE_CHECK_LAUNCH("k_disp_reduce");
   return VIE_OK;
 }
 
-vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
-                       double *partial, cudaStream_t st) {
+namespace {
+
+DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src, double *partial,
+                   float *wbuf) {
   DispArgs a;
   a.lat = (const float *)dp.lattice;
   a.stencil = (const float4 *)dp.stencil;
@@ -617,14 +879,41 @@ vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef,
   a.partial = partial;
   a.units = (const int4 *)dp.units;
   a.counter = dp.counter;
+  a.wbuf = wbuf;
+  a.doff = dp.doff;
   a.n_units = dp.n_units;
   a.n = n;
   a.ldp = dp.ldp;
   a.lat_elems = dp.lat_elems;
   a.tau_scale2 = tau_scale2;
   a.wcoef = wcoef;
+  return a;
+}
+
+}  // namespace
+
+vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
+                       double *partial, cudaStream_t st) {
+  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, src, partial, nullptr);
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kThreads), args, dp.smem, st));
+  count_launch();
+  return VIE_OK;
+}
+
+vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st) {
+  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, nullptr, nullptr, wbuf);
+  void *args[] = {&a};
+  VIE_CUDA(cudaLaunchKernel(dp.kernel_store, dim3(dp.grid_store), dim3(kThreads), args, dp.smem_store, st));
+  count_launch();
+  return VIE_OK;
+}
+
+vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, double *partial,
+                       cudaStream_t st) {
+  DispArgs a = disp_args(dp, n, 0.f, 0.f, src, partial, const_cast<float *>(wbuf));
+  void *args[] = {&a};
+  VIE_CUDA(cudaLaunchKernel(dp.kernel_stream, dim3(dp.grid_stream), dim3(kThreads), args, dp.smem_stream, st));
   count_launch();
   return VIE_OK;
 }

@@ -134,6 +134,7 @@ struct vie_handle {
   bool opts_disable_sym = false;              // force the general kernel (tests)
   // assembled operator
   int asm_mode = VIE_OPERATOR_OTF;
+  void *pairs = nullptr;                      // pair weights the dense assembly expands (displacement kernel)
   long ldk = 0;
   void *kmat = nullptr;                       // FP32 K or BF16 Khi
   void *kmat_lo = nullptr;                    // BF16 Klo
@@ -182,6 +183,8 @@ void free_all(vie_handle *h) {
   dfree(h->diag);
   if (h->src) cudaFree(h->src);
   h->src = nullptr;
+  if (h->pairs) cudaFree(h->pairs);
+  h->pairs = nullptr;
   dfree(h->partial);
   h->stage_a.release();
   h->stage_b.release();
@@ -265,7 +268,8 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   const int prec = h->opts.precision;
   const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
   const bool raw_via_k = op == VIE_OP_A_RAW && h->sig_s_positive;
-  if (h->asm_mode != VIE_OPERATOR_OTF && (op != VIE_OP_A_RAW || raw_via_k)) {
+  const bool dense = h->asm_mode == VIE_OPERATOR_FP32 || h->asm_mode == VIE_OPERATOR_BF16X3;
+  if (dense && (op != VIE_OP_A_RAW || raw_via_k)) {
     vie_status s = h->g32.reserve(h->ldk);
     if (s != VIE_OK) return s;
     if (raw_via_k) {
@@ -297,8 +301,13 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
   const float wcoef = (float)(h->dim == 2 ? hh / (2.0 * kPi) : hh / (4.0 * kPi));
   if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) {
-    s = disp_launch(h->disp, h->n, tau_scale2, wcoef, (const float *)h->src, h->partial, st);
-    slots = h->disp.grid;
+    if (h->asm_mode == VIE_OPERATOR_PAIRS32) {
+      s = disp_stream(h->disp, h->n, (const float *)h->kmat, (const float *)h->src, h->partial, st);
+      slots = h->disp.grid_stream;
+    } else {
+      s = disp_launch(h->disp, h->n, tau_scale2, wcoef, (const float *)h->src, h->partial, st);
+      slots = h->disp.grid;
+    }
   } else if (h->use_kernel == VIE_KERNEL_SYMMETRIC) {
     s = sym_launch(h->sym, h->dim, h->n, h->N, tau_scale2, wcoef, (const float *)h->src,
                    h->partial, st);
@@ -309,7 +318,7 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[2], st));
   s = h->use_kernel == VIE_KERNEL_DISPLACEMENT
-          ? disp_reduce(h->disp, h->N, op, h->partial, h->diag, h->sig_s, g, y, st)
+          ? disp_reduce(h->disp, h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st)
           : launch_reduce(h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st);
   if (s != VIE_OK) return s;
   if (timed) {
@@ -573,7 +582,8 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
 
 vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   if (!h) return invalid("vie_assemble: NULL handle");
-  if (mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FP32 && mode != VIE_OPERATOR_BF16X3)
+  if (mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FP32 && mode != VIE_OPERATOR_BF16X3 &&
+      mode != VIE_OPERATOR_PAIRS32)
     return invalid("vie_assemble: unknown mode");
   DeviceGuard dg(h->device);
   if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
@@ -587,8 +597,24 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     h->asm_mode = VIE_OPERATOR_OTF;
   }
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
-  if (!h->sym.usable || h->opts.precision != VIE_PREC_FP32 || h->opts.tau_mode != VIE_TAU_MARCH ||
-      h->opts.steps != 64) {
+  if (mode == VIE_OPERATOR_PAIRS32) {
+    // every unordered pair's FP32 weight, displacement-major (the displacement kernel's march)
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT) {
+      set_error("vie_assemble: VIE_OPERATOR_PAIRS32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
+                "n <= 133)");
+      return VIE_ERR_UNSUPPORTED;
+    }
+    if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * (size_t)h->disp.stored));
+    const double hh = 1.0 / h->n;
+    const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
+    const float wcoef = (float)(hh / (2.0 * kPi));
+    vie_status s = disp_store(h->disp, h->n, tau_scale2, wcoef, (float *)h->kmat, st);
+    if (s != VIE_OK) return s;
+    h->asm_mode = mode;
+    return VIE_OK;
+  }
+  if ((!h->sym.usable && h->use_kernel != VIE_KERNEL_DISPLACEMENT) || h->opts.precision != VIE_PREC_FP32 ||
+      h->opts.tau_mode != VIE_TAU_MARCH || h->opts.steps != 64) {
     set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "
               "in shared memory");
     return VIE_ERR_UNSUPPORTED;
@@ -612,9 +638,21 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   }
   if (!h->dev_err && (s = dalloc(&h->dev_err, 1)) != VIE_OK) return s;
   VIE_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
-  s = launch_assemble(h->sym, h->dim, h->n, N, h->sig_s, h->diag,
-                      mode == VIE_OPERATOR_FP32 ? (float *)h->kmat : nullptr,
-                      mode == VIE_OPERATOR_BF16X3 ? h->kmat : nullptr, h->kmat_lo, h->device, st);
+  float *k32 = mode == VIE_OPERATOR_FP32 ? (float *)h->kmat : nullptr;
+  void *khi = mode == VIE_OPERATOR_BF16X3 ? h->kmat : nullptr;
+  if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) {
+    // march every unordered pair once into the pair weights, then expand them into K
+    if (!h->pairs) VIE_CUDA(cudaMalloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
+    const double hh = 1.0 / h->n;
+    const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
+    const float wcoef = (float)(hh / (2.0 * kPi));
+    s = disp_store(h->disp, h->n, tau_scale2, wcoef, (float *)h->pairs, st);
+    if (s != VIE_OK) return s;
+    s = disp_expand(h->disp, h->n, (const float *)h->pairs, h->sig_s, h->diag, h->ldk, k32, khi, h->kmat_lo,
+                    h->device, st);
+  } else {
+    s = launch_assemble(h->sym, h->dim, h->n, N, h->sig_s, h->diag, k32, khi, h->kmat_lo, h->device, st);
+  }
   if (s != VIE_OK) return s;
   h->asm_mode = mode;
   return VIE_OK;

@@ -103,6 +103,7 @@ struct DispPlan {
   int ldp = 0, grid = 0, n = 0, rot = 1;
   size_t smem = 0;
   float *src_t = nullptr;     // s transposed (FP32 [N])
+  float *ss32 = nullptr;      // sigma_s in FP32 (for the expansion into K)
   void *geometry = nullptr;   // shared stencils and units of this n (owned by a cache)
   void *units = nullptr;
   void *stencil = nullptr;    // per-displacement chunk records (float4)
@@ -114,16 +115,27 @@ struct DispPlan {
   double rbound = 0.0;        // bound on every row sum of A
   double taps = 0.0;          // multiply-adds of the tau sums per apply: sum_D |W_D| pairs(D)
   const void *kernel = nullptr;
+  // displacement-major assembled operator: every unordered pair's FP32 weight
+  const void *kernel_store = nullptr, *kernel_stream = nullptr;
+  size_t smem_store = 0, smem_stream = 0;
+  int grid_store = 0, grid_stream = 0;
+  long long stored = 0;       // weights stored: N (N - 1) / 2
+  const long long *doff = nullptr;
 };
 size_t disp_smem_bytes(int n);
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st);
-vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *partial, const double *diag,
-                       const double *sigma_s, const double *g, double *y, cudaStream_t st);
+vie_status disp_reduce(const DispPlan &dp, long N, int slots, int op, const double *partial,
+                       const double *diag, const double *sigma_s, const double *g, double *y, cudaStream_t st);
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st);
 void disp_release(DispPlan *dp);
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
                        double *partial, cudaStream_t st);
+vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st);
+vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const double *sigma_s, const double *diag,
+                       long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
+vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, double *partial,
+                       cudaStream_t st);
 
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);

@@ -20,7 +20,7 @@ def _apply(h, op, G, nrhs):
     return host(y).reshape(nrhs, -1)
 
 
-@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3])
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32])
 @pytest.mark.parametrize("n", [7, 24, 45])
 def test_single_rhs_all_rows(mode, n):
     m = V.heterogeneous_2d(n=n, seed=91)
@@ -72,7 +72,7 @@ def test_config4_full_size_64_sources_sampled_rows():
         assert rel_l2(got[r], y_otf[r]) < TOL
 
 
-@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3])
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32])
 def test_gmres_with_assembled_operator(mode):
     n = 32
     m = V.heterogeneous_2d(n=n)
@@ -91,3 +91,50 @@ def test_gmres_with_assembled_operator(mode):
     U2 = np.zeros(m.N)
     P.vie_solve_gmres(h, m.f, U2, rtol=1e-9)
     np.testing.assert_array_equal(U2, U_otf)
+
+
+@pytest.mark.parametrize("n", [2, 3, 9, 37, 64, 128, 133])
+def test_pairs32_bitwise_equal_to_on_the_fly(n):
+    # the stored weights are the on-the-fly kernel's FP32 weights and the
+    # accumulation is the same exact fixed-point sum: identical results
+    m = V.heterogeneous_2d(n=n, seed=93)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
+    G = np.stack([m.f, np.random.default_rng(n).standard_normal(m.N)])
+    ops = (P.VIE_OP_K_SIGMA_S, P.VIE_OP_I_MINUS_K, P.VIE_OP_A_RAW)
+    otf = [_apply(h, op, G, 2) for op in ops]
+    P.vie_assemble(h, P.VIE_OPERATOR_PAIRS32)
+    for op, want in zip(ops, otf):
+        np.testing.assert_array_equal(_apply(h, op, G, 2), want)
+    P.vie_assemble(h, P.VIE_OPERATOR_PAIRS32)   # re-assembled in place
+    np.testing.assert_array_equal(_apply(h, ops[0], G, 2), otf[0])
+
+
+def test_pairs32_switches_with_other_modes():
+    n = 24
+    m = V.heterogeneous_2d(n=n, seed=94)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    g = m.f[None, :]
+    want = O.apply(2, m.sigma_t, m.sigma_s, m.f)
+    for mode in (P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_OTF):
+        P.vie_assemble(h, mode)
+        assert rel_l2(_apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0], want) < TOL
+
+
+@pytest.mark.parametrize("case", ["3d", "symmetric", "too_large"])
+def test_pairs32_unsupported_without_the_displacement_kernel(case):
+    if case == "3d":
+        m = V.heterogeneous_3d(n=5)
+        h = P.vie_create(3, 5, m.sigma_t, m.sigma_s)
+    elif case == "symmetric":
+        m = V.heterogeneous_2d(n=16)
+        h = P.vie_create(2, 16, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
+    else:
+        m = V.heterogeneous_2d(n=136)
+        h = P.vie_create(2, 136, m.sigma_t, m.sigma_s)
+    with pytest.raises(P.VieError) as e:
+        P.vie_assemble(h, P.VIE_OPERATOR_PAIRS32)
+    assert e.value.status == P.vie.VIE_ERR_UNSUPPORTED
+    # the handle still applies on the fly
+    y = _apply(h, P.VIE_OP_K_SIGMA_S, m.f[None, :], 1)[0]
+    assert np.all(np.isfinite(y))

@@ -93,3 +93,22 @@ def test_config2_full_size_solve_sampled_residual():
     phi = O.apply(2, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW, rows=rows)
     lhs = O.apply(2, m.sigma_t, m.sigma_s, u, op=O.OP_I_MINUS_K, rows=rows)
     assert np.max(np.abs(phi - lhs)) <= 2e-5 * np.max(np.abs(phi))
+
+
+def test_bench_medium_solution_matches_oracle_solution():
+    # the benchmark's solve (128^2, seed 2000) against the FP64 oracle's U
+    # stored by tests/golden/make_bench_solution.py: plain on-the-fly GMRES and
+    # the assembled BF16 hi/lo operator
+    import os
+    U_or = np.load(os.path.join(os.path.dirname(__file__), "golden", "bench_U_2d_128.npy"))
+    m = V.heterogeneous_2d(n=128, seed=V.seed_for(2, 0))
+    h = P.vie_create(2, 128, m.sigma_t, m.sigma_s)
+    U = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
+    rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
+    assert rep["converged"]
+    assert rel_l2(host(U), U_or) < 1e-5
+    for mode in (P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32):
+        P.vie_assemble(h, mode)
+        rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
+        assert rep["converged"]
+        assert rel_l2(host(U), U_or) < 1e-5
