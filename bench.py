@@ -251,7 +251,8 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
     last = reps[-1]
     name = {P.VIE_OPERATOR_BF16X3: "assembled BF16 hi/lo operator (row-major, 1.07 GB)",
             P.VIE_OPERATOR_FP32: "assembled FP32 operator (row-major, 1.07 GB)",
-            P.VIE_OPERATOR_PAIRS32: "assembled FP32 pair weights (displacement-major, each unordered pair once, 0.54 GB)"}
+            P.VIE_OPERATOR_PAIRS32: "assembled FP32 pair weights (displacement-major, each unordered pair once, 0.54 GB)",
+            P.VIE_OPERATOR_SYM32: "assembled FP32 A in symmetric grid-row blocks (each unordered pair of rows once, 0.54 GB)"}
     return {"solver": name[operator] + (" + FGMRES(64), learned U-Net preconditioner" if net is not None
                                         else " + FP64 GMRES(64)"),
             "solve_ms": statistics.median(ms), "assemble_ms": statistics.median(asm_ms),
@@ -362,6 +363,55 @@ def measure_learned(P, torch, local, seeds=(9004, 9005)):
             "operator": "assembled BF16 hi/lo (17.2 GB)", "media": rows}
 
 
+def measure_other_configs(P, torch, local, reps=3):
+    """The two other single-GPU workloads of the method: the homogeneous 32^2
+    medium in FP64 with the closed-form tau (GMRES to 1e-10), and the 32^3
+    heterogeneous medium (FP32 tiles, S = 64): one apply, the GMRES solve to
+    1e-6, and the step-two sweep on 128 Fibonacci directions (Algorithm 1,
+    S.3).  Median of `reps` runs after one warm-up, CUDA events."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), out
+
+    dev = f"cuda:{local}"
+    m1 = V.homogeneous_medium(2, 32, 1.1, 1.0)
+    h1 = P.vie_create(2, 32, m1.sigma_t, m1.sigma_s, tau_mode=P.VIE_TAU_CLOSED, precision=P.VIE_PREC_FP64,
+                      device=local)
+    f1 = torch.as_tensor(m1.f, dtype=torch.float64, device=dev)
+    U1 = torch.empty_like(f1)
+    ms1, rep1 = timed(lambda: P.vie_solve_gmres(h1, f1, U1, rtol=1e-10))
+    P.vie_destroy(h1)
+    m3 = V.heterogeneous_3d(n=32)
+    h3 = P.vie_create(3, 32, m3.sigma_t, m3.sigma_s, device=local)
+    f3 = torch.as_tensor(m3.f, dtype=torch.float64, device=dev)
+    U3 = torch.empty_like(f3)
+    y3 = torch.empty_like(f3)
+    ms_apply, _ = timed(lambda: P.vie_apply(h3, P.VIE_OP_K_SIGMA_S, f3, y3, 1))
+    ms3, rep3 = timed(lambda: P.vie_solve_gmres(h3, f3, U3, rtol=RTOL))
+    M = 128
+    dirs = torch.as_tensor(V.fibonacci_directions(M).astype(np.float32), device=dev)  # [M, 3]
+    Phi = torch.empty(M * m3.N, dtype=torch.float32, device=dev)
+    ms_sweep, _ = timed(lambda: P.ert_sweep(h3, U3, f3, dirs, Phi))
+    P.vie_destroy(h3)
+    return {"homogeneous_32x32_fp64": {"tau": "closed form", "rtol": 1e-10, "solve_ms": ms1,
+                                       "iters": rep1["iters"], "relres": rep1["relres"]},
+            "heterogeneous_32x32x32": {"N": m3.N, "apply_ms": ms_apply,
+                                       "apply_gpair_per_s": float(m3.N) * m3.N / ms_apply / 1e6,
+                                       "solve_ms": ms3, "iters": rep3["iters"], "relres": rep3["relres"],
+                                       "sweep_directions": M, "sweep_ms": ms_sweep,
+                                       "sweep_rays_per_s": M * m3.N / ms_sweep * 1e3}}
+
+
 def run_ours(args):
     import torch
     import paper_1610_00835_gb300 as P
@@ -442,16 +492,18 @@ def run_ours(args):
     if clocks["sm_mhz"]:
         roofline["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
-    chosen = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3, U_or)
+    chosen = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32, U_or)
+    asm_bf16 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3, U_or)
     asm_pairs = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_PAIRS32, U_or)
     asm_fp32 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_FP32, U_or)
     net = P.vie_unet_create(4, 32, device=local)
     P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
-    learned_128 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3,
+    learned_128 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32,
                                     U_or, net=net)
     P.vie_unet_destroy(net)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
     batch = measure_batch(P, torch, stream, local)
+    others = measure_other_configs(P, torch, local)
     learned = measure_learned(P, torch, local)
 
     # end to end through the C ABI from host buffers
@@ -489,13 +541,14 @@ def run_ours(args):
                       "apply_ms": sum(r["t_apply_ms"] for r in reps) / n_apply,
                       "err_vs_oracle": err_plain,
                       "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen,
-                      "assembled_pairs32": asm_pairs, "assembled_fp32": asm_fp32,
+                      "assembled_bf16x3": asm_bf16, "assembled_pairs32": asm_pairs, "assembled_fp32": asm_fp32,
                       "chosen_learned": learned_128,
                       "oracle_U": "tests/golden/bench_U_2d_128.npy (FP64 oracle, rtol 1e-11)"
                       if U_or is not None else None},
             "bf16x3_product": product,
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
+            "other_workloads": others,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
         }
@@ -514,8 +567,8 @@ def run_apply_only(args):
 
     m = V.heterogeneous_2d(n=args.n) if args.dim == 2 else V.heterogeneous_3d(n=args.n)
     h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS)
-    mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32,
-            "bf16x3": P.VIE_OPERATOR_BF16X3, "pairs32": P.VIE_OPERATOR_PAIRS32}[args.operator]
+    mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32, "bf16x3": P.VIE_OPERATOR_BF16X3,
+            "pairs32": P.VIE_OPERATOR_PAIRS32, "sym32": P.VIE_OPERATOR_SYM32}[args.operator]
     P.vie_assemble(h, mode)
     nrhs = args.nrhs
     G = V.bump_sources(args.dim, m.n, nrhs, seed=V.seed_for(4)) if nrhs > 1 else m.f[None, :]
@@ -544,7 +597,7 @@ def main(argv=None):
                     help="time operator applies only (profiling driver)")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32"], default="otf")
+    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32"], default="otf")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

@@ -132,11 +132,23 @@ enum {
   VIE_OPERATOR_BF16X3 = 2,       /* K assembled as BF16 hi + lo; products with
                                     several right-hand sides on the tensor cores
                                     as Khi Ghi + Khi Glo + Klo Ghi, FP32 accumulate */
-  VIE_OPERATOR_PAIRS32 = 3       /* A_jk of every unordered pair once, FP32,
+  VIE_OPERATOR_PAIRS32 = 3,      /* A_jk of every unordered pair once, FP32,
                                     displacement-major (2D handles that use the
                                     displacement kernel): applies stream it */
+  VIE_OPERATOR_SYM32 = 4         /* A (symmetric) in FP32 blocks, one per pair of
+                                    grid rows yj <= yk (same handles): applies
+                                    read each block once, y = A (sigma_s g) */
 };
 
+/* VIE_OPERATOR_SYM32: A_jk = A_kj (Section 2, Eq. EQ:Kernel; M-iii of
+ * Section 3.2) with the self cell d_j on the diagonal, FP32, stored once per
+ * unordered pair of grid rows: for yj <= yk the n x n block of targets on row yj
+ * and sources on row yk (n (n + 1) / 2 blocks, 541 MB at 128^2).  An apply forms
+ * s = sigma_s g (or g for VIE_OP_A_RAW) in FP32, takes from every block its row
+ * sums (for row yj) and column sums (for row yk) in FP32, and adds each
+ * target's n block sums in a fixed order in FP64: deterministic, half the bytes
+ * of the dense K per apply.  Same handles as VIE_OPERATOR_PAIRS32.
+ *
 /* VIE_OPERATOR_PAIRS32: the weights A_jk = A_kj (Section 2, Eq. EQ:Kernel with
  * the M-iii collocation of Section 3.2) of the N (N - 1) / 2 unordered pairs,
  * each stored once in FP32 (537 MB at 128^2), grouped by displacement D = k - j:

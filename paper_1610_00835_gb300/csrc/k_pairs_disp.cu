@@ -354,9 +354,16 @@ __device__ __forceinline__ unsigned short bf16_bits_rn(float v) {
   return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
 }
 
-template <bool BF16>
+// output forms of the expansion
+enum ExpandOut {
+  kDenseF32 = 0,   // K row-major, FP32
+  kDenseBF16 = 1,  // K row-major, BF16 hi + lo
+  kSymBlocks = 2   // A (no sigma_s) in the n (n + 1) / 2 blocks of grid-row pairs yj <= yk
+};
+
+template <int OUT>
 __device__ __forceinline__ void put_entry(long idx, float v, float *k32, unsigned short *khi, unsigned short *klo) {
-  if constexpr (BF16) {
+  if constexpr (OUT == kDenseBF16) {
     const unsigned short hi = bf16_bits_rn(v);
     khi[idx] = hi;
     klo[idx] = bf16_bits_rn(v - __uint_as_float((unsigned)hi << 16));
@@ -377,7 +384,11 @@ __device__ __forceinline__ void put_entry(long idx, float v, float *k32, unsigne
 // dy = 0 the row of j gets its columns k > j from the first part and k < j
 // from the second, and the diagonal K_jj = d_j sigma_s,j.
 
-template <bool BF16>
+//
+// kSymBlocks writes A itself (A_jk = A_kj, no sigma_s): block t = item (dy, yj),
+// n x n row-major at t n^2, row xj, column xk; only the first part (and for
+// dy = 0 the whole block with its diagonal d_j).
+template <int OUT>
 __global__ void __launch_bounds__(1024, 1) k_expand_pairs(int n, const float *__restrict__ w,
                                                           const long long *__restrict__ doff,
                                                           const float *__restrict__ ss,
@@ -413,17 +424,33 @@ __global__ void __launch_bounds__(1024, 1) k_expand_pairs(int n, const float *__
     __syncthreads();
     const long jrow = (long)n * yj, krow = (long)n * yk;
     const float *ssj = ss + jrow, *ssk = ss + krow;
-    if (dy > 0) {
+    if constexpr (OUT == kSymBlocks) {
+      float *blk = k32 + (long)t * n * n;
+      for (int xj = warp; xj < n; xj += warps) {
+        float *out = blk + (long)xj * n;
+        for (int xk = lane; xk < n; xk += 32) {
+          const int dx = xk - xj;
+          float v;
+          if (dy > 0 || dx > 0)
+            v = T[(dx + n - 1) * p + xj];
+          else if (dx < 0)
+            v = T[(-dx + n - 1) * p + xk];  // A_jk = A_kj, stored under (-dx, 0) for target xk
+          else
+            v = (float)diag[jrow + xj];
+          out[xk] = v;
+        }
+      }
+    } else if (dy > 0) {
       // every (xj, xk) is a pair of this item
       for (int xj = warp; xj < n; xj += warps) {
         const float *tb = T + (n - 1 - xj) * p + xj;  // T[(xk - xj + n - 1) p + xj]
         const long rb = (jrow + xj) * ldk + krow;
-        for (int xk = lane; xk < n; xk += 32) put_entry<BF16>(rb + xk, tb[xk * p] * ssk[xk], k32, khi, klo);
+        for (int xk = lane; xk < n; xk += 32) put_entry<OUT>(rb + xk, tb[xk * p] * ssk[xk], k32, khi, klo);
       }
       for (int xk = warp; xk < n; xk += warps) {
         const float *tb = T + (xk + n - 1) * p;  // T[(xk - xj + n - 1) p + xj]
         const long rb = (krow + xk) * ldk + jrow;
-        for (int xj = lane; xj < n; xj += 32) put_entry<BF16>(rb + xj, tb[xj * (1 - p)] * ssj[xj], k32, khi, klo);
+        for (int xj = lane; xj < n; xj += 32) put_entry<OUT>(rb + xj, tb[xj * (1 - p)] * ssj[xj], k32, khi, klo);
       }
     } else {
       // one grid row: columns right of the diagonal from j, left of it from k
@@ -432,16 +459,131 @@ __global__ void __launch_bounds__(1024, 1) k_expand_pairs(int n, const float *__
         for (int x = lane; x < n; x += 32) {
           if (x == r) continue;
           const float v = x > r ? T[(x - r + n - 1) * p + r] : T[(r - x + n - 1) * p + x];
-          put_entry<BF16>(rb + x, v * ssj[x], k32, khi, klo);
+          put_entry<OUT>(rb + x, v * ssj[x], k32, khi, klo);
         }
       }
       for (int r = threadIdx.x; r < n; r += blockDim.x) {
         const long j = jrow + r;
-        put_entry<BF16>(j * ldk + j, (float)(diag[j] * ss64[j]), k32, khi, klo);
+        put_entry<OUT>(j * ldk + j, (float)(diag[j] * ss64[j]), k32, khi, klo);
       }
     }
     __syncthreads();
   }
+}
+
+// ---- applies of A stored as symmetric blocks (the kSymBlocks expansion)
+//
+// y = A s with s = sigma_s g (or g): block t = (dy, yj) holds A_jk for j on
+// grid row yj, k on grid row yj + dy.  k_symv_blocks reads each block once and
+// writes P[t][0, n) = its row sums against s on row yj + dy and, for dy > 0,
+// P[t][n, 2n) = its column sums against s on row yj (A_kj = A_jk); all sums
+// in a fixed order.  k_symv_reduce adds, for each target, the partials of the
+// n blocks that touch its grid row, in block order.
+constexpr int kSymvCols = 5;  // columns per lane: n <= 32 kSymvCols
+
+__device__ __forceinline__ int symv_item(int dy, int yj, int n) { return dy * n - dy * (dy - 1) / 2 + yj; }
+
+__global__ void __launch_bounds__(256) k_symv_blocks(int n, const float *__restrict__ A, const float *__restrict__ s,
+                                                     float *__restrict__ P) {
+  __shared__ float colpart[8][32 * kSymvCols];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = n * (n + 1) / 2;
+  int dy = 0, yj = blockIdx.x;
+  while (dy < n && yj >= n - dy) {
+    yj -= n - dy;
+    ++dy;
+  }
+  for (int t = blockIdx.x; t < items; t += gridDim.x) {
+    if (t != (int)blockIdx.x) {
+      yj += gridDim.x;
+      while (dy < n && yj >= n - dy) {
+        yj -= n - dy;
+        ++dy;
+      }
+    }
+    const float *blk = A + (long)t * n * n;
+    const float *sJ = s + (long)n * yj, *sK = s + (long)n * (yj + dy);
+    float sk[kSymvCols], ca[kSymvCols];
+#pragma unroll
+    for (int i = 0; i < kSymvCols; ++i) {
+      const int c = lane + 32 * i;
+      sk[i] = c < n ? sK[c] : 0.f;
+      ca[i] = 0.f;
+    }
+    // four rows of the block per warp in flight
+    for (int r0 = 4 * warp; r0 < n; r0 += 32) {
+      float a[4][kSymvCols];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int i = 0; i < kSymvCols; ++i) {
+          const int r = r0 + u, c = lane + 32 * i;
+          a[u][i] = r < n && c < n ? __ldcs(blk + (long)r * n + c) : 0.f;
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        const float sjr = r < n ? sJ[r] : 0.f;
+        float rs = 0.f;
+#pragma unroll
+        for (int i = 0; i < kSymvCols; ++i) {
+          rs = fmaf(a[u][i], sk[i], rs);
+          ca[i] = fmaf(a[u][i], sjr, ca[i]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (lane == 0 && r < n) P[(long)t * 2 * n + r] = rs;
+      }
+    }
+    if (dy > 0) {  // uniform over the CTA
+#pragma unroll
+      for (int i = 0; i < kSymvCols; ++i) colpart[warp][lane + 32 * i] = ca[i];
+      __syncthreads();
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        float v = 0.f;
+#pragma unroll
+        for (int w8 = 0; w8 < 8; ++w8) v += colpart[w8][c];
+        P[(long)t * 2 * n + n + c] = v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// four threads per target (one quarter of its n block sums each, 64 targets per
+// CTA), their sums added in part order
+__global__ void __launch_bounds__(256) k_symv_reduce(int n, int op, const float *__restrict__ P,
+                                                     const double *__restrict__ g, double *__restrict__ y) {
+  __shared__ double part[4][64];
+  const long N = (long)n * n;
+  const int tx = threadIdx.x & 63, q = threadIdx.x >> 6;
+  for (long j0 = blockIdx.x * 64L; j0 < N; j0 += gridDim.x * 64L) {
+    const long j = j0 + tx;
+    double acc = 0.0;
+    if (j < N) {
+      const int x = (int)(j % n), yl = (int)(j / n);
+      // the target's n blocks: (yl, yl + dy) for dy < n - yl (row sums), then
+      // (yl - dy, yl) for 1 <= dy <= yl (column sums); part q takes every 4th
+      for (int b = q; b < n; b += 4) {
+        const int dy = b < n - yl ? b : b - (n - yl) + 1;
+        acc += b < n - yl ? P[(long)symv_item(dy, yl, n) * 2 * n + x]
+                          : P[(long)symv_item(dy, yl - dy, n) * 2 * n + n + x];
+      }
+    }
+    part[q][tx] = acc;
+    __syncthreads();
+    if (q == 0 && j < N) {
+      const double v = ((part[0][tx] + part[1][tx]) + part[2][tx]) + part[3][tx];
+      y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_symv_source(long N, int op, const double *__restrict__ ss, const double *__restrict__ g,
+                              float *__restrict__ s) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    s[i] = (float)(op == VIE_OP_A_RAW ? g[i] : ss[i] * g[i]);
 }
 
 // FP32 copy of sigma_s (the expansion multiplies in FP32, as the on-the-fly
@@ -824,7 +966,7 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
                        long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st) {
   const long N = (long)n * n;
   const size_t esz = k32 ? sizeof(float) : sizeof(__nv_bfloat16);
-  if (ldk > N) {
+  if (ldk > N) {  // dense K (ldk = 0: symmetric blocks)
     // zero the padding columns [N, ldk) of every row
     if (k32) VIE_CUDA(cudaMemset2DAsync(k32 + N, ldk * esz, 0, (ldk - N) * esz, N, st));
     if (khi) {
@@ -839,18 +981,46 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
     set_error("vie_assemble: grid too large for the pair-weight expansion");
     return VIE_ERR_UNSUPPORTED;
   }
-  const void *kx = k32 ? (const void *)k_expand_pairs<false> : (const void *)k_expand_pairs<true>;
+  const int out = ldk == 0 ? kSymBlocks : k32 ? kDenseF32 : kDenseBF16;
+  const void *kx = out == kSymBlocks  ? (const void *)k_expand_pairs<kSymBlocks>
+                   : out == kDenseF32 ? (const void *)k_expand_pairs<kDenseF32>
+                                      : (const void *)k_expand_pairs<kDenseBF16>;
   VIE_CUDA(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_to_f32<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, sigma_s, dp.ss32);
   VIE_CHECK_LAUNCH("k_to_f32");
   const int grid = prop.multiProcessorCount;
-  if (k32)
-    k_expand_pairs<false><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, k32, nullptr,
-                                                    nullptr);
+  if (out == kSymBlocks)
+    k_expand_pairs<kSymBlocks><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, 0, k32, nullptr,
+                                                         nullptr);
+  else if (out == kDenseF32)
+    k_expand_pairs<kDenseF32><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, k32,
+                                                        nullptr, nullptr);
   else
-    k_expand_pairs<true><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, nullptr,
-                                                   (unsigned short *)khi, (unsigned short *)klo);
+    k_expand_pairs<kDenseBF16><<<grid, 1024, smem, st>>>(n, wbuf, dp.doff, dp.ss32, diag, sigma_s, ldk, nullptr,
+                                                         (unsigned short *)khi, (unsigned short *)klo);
   VIE_CHECK_LAUNCH("k_expand_pairs");
+  return VIE_OK;
+}
+
+size_t symv_block_floats(int n) { return (size_t)n * (n + 1) / 2 * n * n; }
+size_t symv_partial_floats(int n) { return (size_t)n * (n + 1) / 2 * 2 * n; }
+
+vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, const float *blocks, float *s,
+                      float *partial, double *y, int device, cudaStream_t st) {
+  if (n > 32 * kSymvCols) {
+    set_error("symmetric blocks: n too large");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const long N = (long)n * n;
+  cudaDeviceProp prop;
+  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  k_symv_source<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, op, sigma_s, g, s);
+  VIE_CHECK_LAUNCH("k_symv_source");
+  const int items = n * (n + 1) / 2;
+  k_symv_blocks<<<std::min(items, 8 * prop.multiProcessorCount), 256, 0, st>>>(n, blocks, s, partial);
+  VIE_CHECK_LAUNCH("k_symv_blocks");
+  k_symv_reduce<<<(int)std::min((N + 63) / 64, 4096L), 256, 0, st>>>(n, op, partial, g, y);
+  VIE_CHECK_LAUNCH("k_symv_reduce");
   return VIE_OK;
 }
 

@@ -135,6 +135,7 @@ struct vie_handle {
   // assembled operator
   int asm_mode = VIE_OPERATOR_OTF;
   void *pairs = nullptr;                      // pair weights the dense assembly expands (displacement kernel)
+  float *sym_partial = nullptr;               // row/column sums of the symmetric blocks (VIE_OPERATOR_SYM32)
   long ldk = 0;
   void *kmat = nullptr;                       // FP32 K or BF16 Khi
   void *kmat_lo = nullptr;                    // BF16 Klo
@@ -185,6 +186,8 @@ void free_all(vie_handle *h) {
   h->src = nullptr;
   if (h->pairs) cudaFree(h->pairs);
   h->pairs = nullptr;
+  if (h->sym_partial) cudaFree(h->sym_partial);
+  h->sym_partial = nullptr;
   dfree(h->partial);
   h->stage_a.release();
   h->stage_b.release();
@@ -268,6 +271,19 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   const int prec = h->opts.precision;
   const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
   const bool raw_via_k = op == VIE_OP_A_RAW && h->sig_s_positive;
+  if (h->asm_mode == VIE_OPERATOR_SYM32) {
+    if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
+    vie_status s = symv_apply(h->n, op, h->sig_s, g, (const float *)h->kmat, (float *)h->src, h->sym_partial, y,
+                              h->device, st);
+    if (s != VIE_OK) return s;
+    if (timed) {
+      VIE_CUDA(cudaEventRecord(ev->e[2], st));
+      VIE_CUDA(cudaEventRecord(ev->e[3], st));
+      ev->pending = true;
+    }
+    h->n_apply++;
+    return VIE_OK;
+  }
   const bool dense = h->asm_mode == VIE_OPERATOR_FP32 || h->asm_mode == VIE_OPERATOR_BF16X3;
   if (dense && (op != VIE_OP_A_RAW || raw_via_k)) {
     vie_status s = h->g32.reserve(h->ldk);
@@ -583,7 +599,7 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
 vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   if (!h) return invalid("vie_assemble: NULL handle");
   if (mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FP32 && mode != VIE_OPERATOR_BF16X3 &&
-      mode != VIE_OPERATOR_PAIRS32)
+      mode != VIE_OPERATOR_PAIRS32 && mode != VIE_OPERATOR_SYM32)
     return invalid("vie_assemble: unknown mode");
   DeviceGuard dg(h->device);
   if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
@@ -597,6 +613,27 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     h->asm_mode = VIE_OPERATOR_OTF;
   }
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
+  if (mode == VIE_OPERATOR_SYM32) {
+    // A in the symmetric blocks of grid-row pairs: the pair weights, expanded
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT) {
+      set_error("vie_assemble: VIE_OPERATOR_SYM32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
+                "n <= 133)");
+      return VIE_ERR_UNSUPPORTED;
+    }
+    if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * symv_block_floats(h->n)));
+    if (!h->sym_partial) VIE_CUDA(cudaMalloc((void **)&h->sym_partial, sizeof(float) * symv_partial_floats(h->n)));
+    if (!h->pairs) VIE_CUDA(cudaMalloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
+    const double hh = 1.0 / h->n;
+    const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
+    const float wcoef = (float)(hh / (2.0 * kPi));
+    vie_status s = disp_store(h->disp, h->n, tau_scale2, wcoef, (float *)h->pairs, st);
+    if (s != VIE_OK) return s;
+    s = disp_expand(h->disp, h->n, (const float *)h->pairs, h->sig_s, h->diag, 0, (float *)h->kmat, nullptr,
+                    nullptr, h->device, st);
+    if (s != VIE_OK) return s;
+    h->asm_mode = mode;
+    return VIE_OK;
+  }
   if (mode == VIE_OPERATOR_PAIRS32) {
     // every unordered pair's FP32 weight, displacement-major (the displacement kernel's march)
     if (h->use_kernel != VIE_KERNEL_DISPLACEMENT) {

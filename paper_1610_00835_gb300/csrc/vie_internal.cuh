@@ -132,6 +132,10 @@ void disp_release(DispPlan *dp);
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
                        double *partial, cudaStream_t st);
 vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st);
+size_t symv_block_floats(int n);
+size_t symv_partial_floats(int n);
+vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, const float *blocks, float *s,
+                      float *partial, double *y, int device, cudaStream_t st);
 vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const double *sigma_s, const double *diag,
                        long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
 vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, double *partial,

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "VIE_OK", 1: "VIE_ERR_INVALID_ARG", 2: "VIE_ERR_CUDA", 3: "VI
 VIE_TAU_MARCH, VIE_TAU_CLOSED = 0, 1
 VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
 VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
-VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3, VIE_OPERATOR_PAIRS32 = 0, 1, 2, 3
+VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3, VIE_OPERATOR_PAIRS32, VIE_OPERATOR_SYM32 = 0, 1, 2, 3, 4
 VIE_KERNEL_AUTO, VIE_KERNEL_SYMMETRIC, VIE_KERNEL_DISPLACEMENT, VIE_KERNEL_GENERAL = 0, 1, 2, 3
 
 

@@ -20,8 +20,9 @@ def _apply(h, op, G, nrhs):
     return host(y).reshape(nrhs, -1)
 
 
-@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32])
-@pytest.mark.parametrize("n", [7, 24, 45])
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32,
+                                  P.VIE_OPERATOR_SYM32])
+@pytest.mark.parametrize("n", [2, 7, 24, 45])
 def test_single_rhs_all_rows(mode, n):
     m = V.heterogeneous_2d(n=n, seed=91)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
@@ -72,7 +73,8 @@ def test_config4_full_size_64_sources_sampled_rows():
         assert rel_l2(got[r], y_otf[r]) < TOL
 
 
-@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32])
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32,
+                                  P.VIE_OPERATOR_SYM32])
 def test_gmres_with_assembled_operator(mode):
     n = 32
     m = V.heterogeneous_2d(n=n)
@@ -116,13 +118,15 @@ def test_pairs32_switches_with_other_modes():
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
     g = m.f[None, :]
     want = O.apply(2, m.sigma_t, m.sigma_s, m.f)
-    for mode in (P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_OTF):
+    for mode in (P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_SYM32, P.VIE_OPERATOR_PAIRS32,
+                 P.VIE_OPERATOR_SYM32, P.VIE_OPERATOR_OTF):
         P.vie_assemble(h, mode)
         assert rel_l2(_apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0], want) < TOL
 
 
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_SYM32])
 @pytest.mark.parametrize("case", ["3d", "symmetric", "too_large"])
-def test_pairs32_unsupported_without_the_displacement_kernel(case):
+def test_pairs32_unsupported_without_the_displacement_kernel(case, mode):
     if case == "3d":
         m = V.heterogeneous_3d(n=5)
         h = P.vie_create(3, 5, m.sigma_t, m.sigma_s)
@@ -133,8 +137,28 @@ def test_pairs32_unsupported_without_the_displacement_kernel(case):
         m = V.heterogeneous_2d(n=136)
         h = P.vie_create(2, 136, m.sigma_t, m.sigma_s)
     with pytest.raises(P.VieError) as e:
-        P.vie_assemble(h, P.VIE_OPERATOR_PAIRS32)
+        P.vie_assemble(h, mode)
     assert e.value.status == P.vie.VIE_ERR_UNSUPPORTED
     # the handle still applies on the fly
     y = _apply(h, P.VIE_OP_K_SIGMA_S, m.f[None, :], 1)[0]
     assert np.all(np.isfinite(y))
+
+
+@pytest.mark.parametrize("n", [16, 128, 133])
+def test_sym32_full_size_rows_and_symmetry(n):
+    # the symmetric blocks against the oracle on sampled rows at full sizes, and
+    # against the dense FP32 K applied to the same vector
+    m = V.bump_medium(2, n, 4, 0.9, seed=4500 + n)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    g = m.f + 0.05 * np.random.default_rng(n).standard_normal(m.N)
+    P.vie_assemble(h, P.VIE_OPERATOR_SYM32)
+    got = _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]
+    rows = np.unique(np.concatenate([np.random.default_rng(n + 1).choice(m.N, 12, replace=False),
+                                     [0, m.N - 1, m.N // 2]]))
+    want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(got[rows], want) < TOL
+    P.vie_assemble(h, P.VIE_OPERATOR_FP32)
+    assert rel_l2(got, _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]) < 2e-6
+    P.vie_assemble(h, P.VIE_OPERATOR_SYM32)
+    again = _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]
+    np.testing.assert_array_equal(again, got)  # fixed summation order

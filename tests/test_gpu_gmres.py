@@ -107,7 +107,7 @@ def test_bench_medium_solution_matches_oracle_solution():
     rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
     assert rep["converged"]
     assert rel_l2(host(U), U_or) < 1e-5
-    for mode in (P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32):
+    for mode in (P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_PAIRS32, P.VIE_OPERATOR_SYM32):
         P.vie_assemble(h, mode)
         rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
         assert rep["converged"]
