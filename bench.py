@@ -237,12 +237,14 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
     for _ in range(max(3, args.steps // 4)):
         flush_l2(flush)
         torch.cuda.synchronize()
+        nvtx_push(torch, "assembled_step")
         a.record(stream)
         P.vie_assemble(h, operator)
         b.record(stream)
         rep = P.vie_solve_gmres(h, f_dev, U, rtol=RTOL, time_apply=True)
         c.record(stream)
         torch.cuda.synchronize()
+        nvtx_pop(torch)
         ms.append(a.elapsed_time(c))
         asm_ms.append(a.elapsed_time(b))
         reps.append(rep)

@@ -221,23 +221,31 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     }
     const int4 un = a.units[u0++];
     const int dx = (short)(un.y & 0xffff), dy = un.y >> 16;
-    const int lb = un.z & 0xffff, sb = un.z >> 16;
+    const int lb = un.z & 0xffff, sb0 = un.z >> 16;
     const int xlo = dx < 0 ? -dx : 0, xhi = dx > 0 ? n - dx : n;
     const int ylo = dy < 0 ? -dy : 0, yhi = dy > 0 ? n - dy : n;
     const bool along_y = (un.w & 1) != 0;
-    const int lc = (un.w >> 1) & 15, chunks = un.w >> 8;
+    const int lc = (un.w >> 1) & 15, lg = (un.w >> 5) & 3, chunks = un.w >> 8;
+    // lane groups: 1, 2 or 4 groups of 32 >> lg lanes, group g on stack block
+    // sb0 + s g (s = 2 for pairs, ldp mod 4 for quads: the groups then load
+    // from disjoint banks); a group past the last stack block is masked off
+    const int gw = 32 >> lg, g = lane >> (5 - lg), lig = lane & (gw - 1);
+    const int sstride = lg == 1 ? 2 : (a.ldp & 3);  // the lattice pitch, also in the stream kernel
+    const int nsb = ((along_y ? yhi - ylo : xhi - xlo) + kR - 1) / kR;
+    int sb = sb0 + sstride * g;
+    bool lvalid = sb < nsb;
+    if (!lvalid) sb = sb0;
     // lane coordinate (clamped to the rectangle) and the first stacked target
     int x, y;
-    bool lvalid;
     if (along_y) {
-      const int xr = xlo + 32 * lb + lane;
-      lvalid = xr < xhi;
-      x = lvalid ? xr : xhi - 1;
+      const int xr = xlo + 32 * lb + lig;
+      lvalid = lvalid && xr < xhi;
+      x = xr < xhi ? xr : xhi - 1;
       y = ylo + kR * sb;
     } else {
-      const int yr = ylo + 32 * lb + lane;
-      lvalid = yr < yhi;
-      y = lvalid ? yr : yhi - 1;
+      const int yr = ylo + 32 * lb + lig;
+      lvalid = lvalid && yr < yhi;
+      y = yr < yhi ? yr : yhi - 1;
       x = xlo + kR * sb;
     }
     float acc[kR];
@@ -810,10 +818,21 @@ vie_status geometry_build(int n, int ldp, Geometry *geo) {
           for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
         }
       const int lanes = along_y ? wx : wy, stack = along_y ? wy : wx;
+      const int nsb = (stack + kR - 1) / kR, full = lanes / 32, rem = lanes % 32;
       const int w = (along_y ? 1 : 0) | (pl.lc << 1) | ((int)pl.chunks << 8);
-      for (int sb = 0; sb < (stack + kR - 1) / kR; ++sb)
-        for (int lb = 0; lb < (lanes + 31) / 32; ++lb)
-          units.push_back({make_int4(off, (dx & 0xffff) | (dy << 16), lb | (sb << 16), w), pl.cost});
+      const int dxy = (dx & 0xffff) | (dy << 16);
+      for (int sb = 0; sb < nsb; ++sb)
+        for (int lb = 0; lb < full; ++lb) units.push_back({make_int4(off, dxy, lb | (sb << 16), w), pl.cost});
+      if (rem > 0) {
+        // the ragged last lane block: 2 or 4 stack blocks share a warp when it
+        // is at most 16 or 8 lanes wide (stack blocks sb, sb + s, ...)
+        const int lg = rem <= 8 ? 2 : rem <= 16 ? 1 : 0, G = 1 << lg;
+        const int sstride = lg == 1 ? 2 : (ldp & 3);
+        const int span = lg == 0 ? 1 : G * sstride;
+        for (int base = 0; base < nsb; base += span)
+          for (int j = 0; j < (lg == 0 ? 1 : sstride) && base + j < nsb; ++j)
+            units.push_back({make_int4(off, dxy, full | ((base + j) << 16), w | (lg << 5)), pl.cost});
+      }
     }
   for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
   std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
