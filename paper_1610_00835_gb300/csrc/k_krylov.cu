@@ -88,15 +88,14 @@ __global__ void k_axpby(double a, const double *__restrict__ x, double b,
 }
 
 // Column k of the Hessenberg matrix H ((m+1) x m, column-major): entries
-// 0..k from hcol, entry k+1 = sqrt(*hk1sq).  Apply the k earlier rotations,
+// 0..k from hcol, entry k+1 = sqrt(hk1sq).  Apply the k earlier rotations,
 // build rotation k, rotate the residual vector gv, and write
-// |gv[k+1]| / bnorm to *est.
-__global__ void k_givens(double *H, int m, int k, const double *hcol, const double *hk1sq,
-                         double *cs, double *sn, double *gv, double bnorm, double *est) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// |gv[k+1]| / bnorm to *est.  One thread.
+__device__ void givens_step(double *H, int m, int k, const double *hcol, double hk1sq, double *cs, double *sn,
+                            double *gv, double bnorm, double *est) {
   double *c = H + (long)k * (m + 1);
   for (int i = 0; i <= k; ++i) c[i] = hcol[i];
-  c[k + 1] = sqrt(*hk1sq);
+  c[k + 1] = sqrt(hk1sq);
   for (int i = 0; i < k; ++i) {
     double a = c[i], b = c[i + 1];
     c[i] = cs[i] * a + sn[i] * b;
@@ -113,6 +112,50 @@ __global__ void k_givens(double *H, int m, int k, const double *hcol, const doub
   gv[k] = cc * g;
   gv[k + 1] = -ss * g;
   *est = fabs(gv[k + 1]) / bnorm;
+}
+
+__global__ void k_givens(double *H, int m, int k, const double *hcol, const double *hk1sq,
+                         double *cs, double *sn, double *gv, double bnorm, double *est) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  givens_step(H, m, k, hcol, *hk1sq, cs, sn, gv, bnorm, est);
+}
+
+// k_dots and k_dots_finish in one launch: the last block to finish (by an
+// atomic ticket, reset for the next launch) sums the block partials in block
+// order, the same order as k_dots_finish: out1[v] = s and/or out2[v] += s.
+// With gv != nullptr (nv = 1, V = w) the sum is ||w||^2 and the last block
+// then takes the Givens step of column k with it.
+__global__ void __launch_bounds__(kDotThreads) k_dots_last(const double *__restrict__ V, int nv, long ldv,
+                                                           const double *__restrict__ w, long N, double *part,
+                                                           int *ticket, double *out1, double *out2, double *H,
+                                                           int m, int k, const double *hcol, double *cs,
+                                                           double *sn, double *gv, double bnorm, double *est) {
+  __shared__ double red[kDotThreads / 32];
+  __shared__ int last;
+  const long stride = (long)gridDim.x * blockDim.x;
+  const long i0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  for (int v = 0; v < nv; ++v) {
+    const double *x = V + (long)v * ldv;
+    double sum = 0.0;
+    for (long i = i0; i < N; i += stride) sum += x[i] * w[i];
+    sum = block_sum(sum, red);
+    if (threadIdx.x == 0) part[(long)blockIdx.x * nv + v] = sum;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double sum = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(part + (long)b * nv + v);
+    if (out1) out1[v] = sum;
+    if (out2) out2[v] += sum;
+    if (gv && v == 0) givens_step(H, m, k, hcol, sum, cs, sn, gv, bnorm, est);
+  }
+  if (threadIdx.x == 0) *ticket = 0;
 }
 
 // Solve the k x k upper-triangular system R y = gv[0..k-1], R = H[0..k-1][0..k-1].
@@ -142,6 +185,23 @@ vie_status launch_dots(const double *V, int nv, long ldv, const double *w, long 
                        int blocks, cudaStream_t st) {
   k_dots<<<blocks, kDotThreads, 0, st>>>(V, nv, ldv, w, N, part);
   VIE_CHECK_LAUNCH("k_dots");
+  return VIE_OK;
+}
+
+vie_status launch_dots_last(const double *V, int nv, long ldv, const double *w, long N, double *part,
+                            int blocks, int *ticket, double *out1, double *out2, cudaStream_t st) {
+  k_dots_last<<<blocks, kDotThreads, 0, st>>>(V, nv, ldv, w, N, part, ticket, out1, out2, nullptr, 0, 0,
+                                              nullptr, nullptr, nullptr, nullptr, 0.0, nullptr);
+  VIE_CHECK_LAUNCH("k_dots_last");
+  return VIE_OK;
+}
+
+vie_status launch_norm2_givens(const double *w, long N, double *part, int blocks, int *ticket, double *norm2,
+                               double *H, int m, int k, const double *hcol, double *cs, double *sn, double *gv,
+                               double bnorm, double *est, cudaStream_t st) {
+  k_dots_last<<<blocks, kDotThreads, 0, st>>>(w, 1, N, w, N, part, ticket, norm2, nullptr, H, m, k, hcol, cs, sn,
+                                              gv, bnorm, est);
+  VIE_CHECK_LAUNCH("k_dots_last");
   return VIE_OK;
 }
 

@@ -142,6 +142,7 @@ struct vie_handle {
   DBuf<float> g32;                            // FP32 copy of a right-hand side
   DBuf<unsigned char> gemm_ws;                // split-K partials + BF16 G
   int *dev_err = nullptr;                     // device error word of the products
+  int *ticket = nullptr;                      // block ticket of the fused dot kernels (0 between launches)
   bool sig_s_positive = false;                // phi = K (f / sigma_s) is available
   UnetImpl *precond = nullptr;                // learned right preconditioner
   double precond_inv_ref = 0.2;
@@ -203,6 +204,7 @@ void free_all(vie_handle *h) {
   h->g32.release();
   h->gemm_ws.release();
   dfree(h->dev_err);
+  dfree(h->ticket);
   sym_release(&h->sym);
   disp_release(&h->disp);
   free_gmres(h);
@@ -231,6 +233,10 @@ vie_status ensure_gmres(vie_handle *h, int m) {
   if ((s = dalloc(&h->htmp, m + 1)) != VIE_OK) return s;
   if ((s = dalloc(&h->part, (size_t)blocks * (m + 1))) != VIE_OK) return s;
   if ((s = dalloc(&h->scal, 8)) != VIE_OK) return s;
+  if (!h->ticket) {
+    if ((s = dalloc(&h->ticket, 1)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemset(h->ticket, 0, sizeof(int)));
+  }
   VIE_CUDA(cudaMallocHost((void **)&h->h_pinned, sizeof(double) * (m + 1 + 8)));
   h->gm_m = m;
   return VIE_OK;
@@ -823,16 +829,17 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
       }
       if ((s = apply_dev(h, VIE_OP_I_MINUS_K, op_in, vk1, st, timed)) != VIE_OK) return s;
       // CGS2: two passes of h = V^T w, w -= V h; hcol accumulates both.
-      if ((s = launch_dots(h->V, k + 1, N, vk1, N, h->part, blocks, st)) != VIE_OK) return s;
-      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->hcol, 0, st)) != VIE_OK) return s;
+      // (each dot pass is one launch: its last block sums the block partials)
+      if ((s = launch_dots_last(h->V, k + 1, N, vk1, N, h->part, blocks, h->ticket, h->hcol, nullptr, st)) !=
+          VIE_OK)
+        return s;
       if ((s = launch_orth_update(h->V, k + 1, N, h->hcol, vk1, N, st)) != VIE_OK) return s;
-      if ((s = launch_dots(h->V, k + 1, N, vk1, N, h->part, blocks, st)) != VIE_OK) return s;
-      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->htmp, 0, st)) != VIE_OK) return s;
-      if ((s = launch_dots_finish(h->part, blocks, k + 1, h->hcol, 1, st)) != VIE_OK) return s;
+      if ((s = launch_dots_last(h->V, k + 1, N, vk1, N, h->part, blocks, h->ticket, h->htmp, h->hcol, st)) !=
+          VIE_OK)
+        return s;
       if ((s = launch_orth_update(h->V, k + 1, N, h->htmp, vk1, N, st)) != VIE_OK) return s;
-      if ((s = norm2_dev(h, vk1, h->scal + 2, st)) != VIE_OK) return s;
-      if ((s = launch_givens(h->H, m, k, h->hcol, h->scal + 2, h->cs, h->sn, h->gv, bnorm,
-                             h->scal + 3, st)) != VIE_OK)
+      if ((s = launch_norm2_givens(vk1, N, h->part, blocks, h->ticket, h->scal + 2, h->H, m, k, h->hcol, h->cs,
+                                   h->sn, h->gv, bnorm, h->scal + 3, st)) != VIE_OK)
         return s;
       if ((s = launch_scale(vk1, h->scal + 2, 1, vk1, N, st)) != VIE_OK) return s;
       double est = 0.0;

@@ -170,6 +170,11 @@ vie_status launch_dots_finish(const double *part, int blocks, int nv, double *ou
                               cudaStream_t st);
 vie_status launch_orth_update(const double *V, int nv, long ldv, const double *h, double *w,
                               long N, cudaStream_t st);
+vie_status launch_dots_last(const double *V, int nv, long ldv, const double *w, long N, double *part,
+                            int blocks, int *ticket, double *out1, double *out2, cudaStream_t st);
+vie_status launch_norm2_givens(const double *w, long N, double *part, int blocks, int *ticket, double *norm2,
+                               double *H, int m, int k, const double *hcol, double *cs, double *sn, double *gv,
+                               double bnorm, double *est, cudaStream_t st);
 vie_status launch_scale(const double *x, const double *norm2, int use_sqrt, double *y, long N,
                         cudaStream_t st);
 vie_status launch_axpby(double a, const double *x, double b, const double *y, double *z, long N,
