@@ -36,10 +36,10 @@
 // below 2^62 / (max|s| R) with R a bound on every row sum of A, and integer
 // atomic adds are exact in any order.  The result is therefore bitwise
 // reproducible whatever the schedule, and the accumulation error is below
-// N 2^-63 max|s| R.  Each CTA writes its copy (int64) to its partial-sum slot;
-// k_disp_reduce adds the slots in int64 (exact, since the sum of the
-// magnitudes of all terms of a target is below 2^62), converts once to FP64
-// and adds the self cell.
+// N 2^-63 max|s| R.  Each CTA adds its copy into one int64 array with integer
+// atomics (exact, since the sum of the magnitudes of all terms of a target is
+// below 2^62); k_disp_reduce converts each sum once to FP64, adds the self
+// cell and clears the array for the next apply.
 //
 // The shared copy of y stores target (x, y) at y n + ((x + c y) mod n), with
 // n + c odd: 32 lanes on one column (runs along x) then hit different banks,
@@ -82,7 +82,7 @@ struct DispArgs {
   unsigned *smax;              // bits of max |s_k| (set by the source kernel)
   double *scale_out;           // fixed-point scale of this apply (for the reduce)
   double rbound;               // bound on sum_k A_jk for every j
-  double *partial;             // [gridDim.x][N]
+  unsigned long long *yacc;    // [N] int64 sum of every CTA's y (rotated layout), zero between applies
   const int4 *units;           // {first chunk, dx | dy << 16, lane block | stack block << 16,
                                //  runs along y | Lc << 1 | chunks << 8}
   int *counter;                // [2]
@@ -327,8 +327,10 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   // (the last CTA resets the unit counter for the next launch)
   __syncthreads();
   if constexpr (MODE != kStore) {
-    unsigned long long *out = reinterpret_cast<unsigned long long *>(a.partial) + (long)blockIdx.x * N;
-    for (long i = tid; i < N; i += kThreads) out[i] = ysh[i];
+    for (long i = tid; i < N; i += kThreads) {
+      const unsigned long long v = ysh[i];
+      if (v) atomicAdd(a.yacc + i, v);  // integer sums: exact in any order
+    }
     if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
   }
   if (tid == 0) {
@@ -613,17 +615,17 @@ __global__ void k_make_lattice(int n, const float *__restrict__ pad, int rows, i
   }
 }
 
-// y_j = (sum_slot part[slot][j]) / scale + d_j s_j, integer sum over the slots
-// (the slots hold y in the rotated layout)
-__global__ void k_disp_reduce(long N, int n, int rot, int slots, int op, const unsigned long long *__restrict__ part,
+// y_j = yacc[j] / scale + d_j s_j (yacc in the rotated layout), and yacc back
+// to zero for the next apply
+__global__ void k_disp_reduce(long N, int n, int rot, int op, unsigned long long *__restrict__ yacc,
                               const double *__restrict__ scale, const double *__restrict__ diag,
                               const double *__restrict__ ss, const double *__restrict__ g,
                               double *__restrict__ y) {
   const double inv = 1.0 / *scale;
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
     const long js = yslot((int)(j % n), (int)(j / n), n, rot);
-    unsigned long long acc = 0ull;
-    for (int p = 0; p < slots; ++p) acc += part[(long)p * N + js];
+    const unsigned long long acc = yacc[js];
+    yacc[js] = 0ull;
     const double sj = op == VIE_OP_A_RAW ? g[j] : ss[j] * g[j];
     const double v = (double)(long long)acc * inv + diag[j] * sj;
     y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
@@ -928,6 +930,8 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
   VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
   VIE_CUDA(cudaMalloc((void **)&dp->ss32, sizeof(float) * (size_t)n * n));
+  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * (size_t)n * n));
+  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * (size_t)n * n));
   // every row sum of A is below sum over all nonzero displacements of h / (2 pi r)
   double rb = 0.0;
   for (int dy = -(n - 1); dy < n; ++dy)
@@ -960,6 +964,8 @@ void disp_release(DispPlan *dp) {
   if (dp->scale) cudaFree(dp->scale);
   if (dp->src_t) cudaFree(dp->src_t);
   if (dp->ss32) cudaFree(dp->ss32);
+  if (dp->yacc) cudaFree(dp->yacc);
+  dp->yacc = nullptr;
   dp->ss32 = nullptr;
   dp->geometry = nullptr;
   dp->src_t = nullptr;
@@ -1043,10 +1049,10 @@ vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, con
   return VIE_OK;
 }
 
-vie_status disp_reduce(const DispPlan &dp, long N, int slots, int op, const double *partial,
-                       const double *diag, const double *sigma_s, const double *g, double *y, cudaStream_t st) {
+vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *diag, const double *sigma_s,
+                       const double *g, double *y, cudaStream_t st) {
   const int blocks = (int)std::min((N + 255) / 256, 4096L);
-  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, slots, op, (const unsigned long long *)partial, dp.scale, diag,
+  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, op, (unsigned long long *)dp.yacc, dp.scale, diag,
                                         sigma_s, g, y);
   VIE_CHECK_LAUNCH("k_disp_reduce");
   return VIE_OK;
@@ -1054,8 +1060,7 @@ vie_status disp_reduce(const DispPlan &dp, long N, int slots, int op, const doub
 
 namespace {
 
-DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src, double *partial,
-                   float *wbuf) {
+DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src, float *wbuf) {
   DispArgs a;
   a.lat = (const float *)dp.lattice;
   a.stencil = (const float4 *)dp.stencil;
@@ -1065,7 +1070,7 @@ DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, con
   a.smax = dp.smax;
   a.scale_out = dp.scale;
   a.rbound = dp.rbound;
-  a.partial = partial;
+  a.yacc = (unsigned long long *)dp.yacc;
   a.units = (const int4 *)dp.units;
   a.counter = dp.counter;
   a.wbuf = wbuf;
@@ -1082,8 +1087,8 @@ DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, con
 }  // namespace
 
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
-                       double *partial, cudaStream_t st) {
-  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, src, partial, nullptr);
+                       cudaStream_t st) {
+  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, src, nullptr);
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kThreads), args, dp.smem, st));
   count_launch();
@@ -1091,16 +1096,15 @@ vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef,
 }
 
 vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st) {
-  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, nullptr, nullptr, wbuf);
+  DispArgs a = disp_args(dp, n, tau_scale2, wcoef, nullptr, wbuf);
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(dp.kernel_store, dim3(dp.grid_store), dim3(kThreads), args, dp.smem_store, st));
   count_launch();
   return VIE_OK;
 }
 
-vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, double *partial,
-                       cudaStream_t st) {
-  DispArgs a = disp_args(dp, n, 0.f, 0.f, src, partial, const_cast<float *>(wbuf));
+vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, cudaStream_t st) {
+  DispArgs a = disp_args(dp, n, 0.f, 0.f, src, const_cast<float *>(wbuf));
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(dp.kernel_stream, dim3(dp.grid_stream), dim3(kThreads), args, dp.smem_stream, st));
   count_launch();

@@ -324,11 +324,9 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   const float wcoef = (float)(h->dim == 2 ? hh / (2.0 * kPi) : hh / (4.0 * kPi));
   if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) {
     if (h->asm_mode == VIE_OPERATOR_PAIRS32) {
-      s = disp_stream(h->disp, h->n, (const float *)h->kmat, (const float *)h->src, h->partial, st);
-      slots = h->disp.grid_stream;
+      s = disp_stream(h->disp, h->n, (const float *)h->kmat, (const float *)h->src, st);
     } else {
-      s = disp_launch(h->disp, h->n, tau_scale2, wcoef, (const float *)h->src, h->partial, st);
-      slots = h->disp.grid;
+      s = disp_launch(h->disp, h->n, tau_scale2, wcoef, (const float *)h->src, st);
     }
   } else if (h->use_kernel == VIE_KERNEL_SYMMETRIC) {
     s = sym_launch(h->sym, h->dim, h->n, h->N, tau_scale2, wcoef, (const float *)h->src,
@@ -340,7 +338,7 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   if (s != VIE_OK) return s;
   if (timed) VIE_CUDA(cudaEventRecord(ev->e[2], st));
   s = h->use_kernel == VIE_KERNEL_DISPLACEMENT
-          ? disp_reduce(h->disp, h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st)
+          ? disp_reduce(h->disp, h->N, op, h->diag, h->sig_s, g, y, st)
           : launch_reduce(h->N, slots, op, h->partial, h->diag, h->sig_s, g, y, st);
   if (s != VIE_OK) return s;
   if (timed) {
@@ -504,7 +502,6 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
   {
     long slots = h->plan.splits;
     if (h->use_kernel == VIE_KERNEL_SYMMETRIC) slots = std::max<long>(slots, h->sym.T);
-    if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) slots = std::max<long>(slots, h->disp.grid);
     TRY(dalloc(&h->partial, (size_t)slots * N));
   }
   {

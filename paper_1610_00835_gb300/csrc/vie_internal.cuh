@@ -104,6 +104,7 @@ struct DispPlan {
   size_t smem = 0;
   float *src_t = nullptr;     // s transposed (FP32 [N])
   float *ss32 = nullptr;      // sigma_s in FP32 (for the expansion into K)
+  void *yacc = nullptr;       // int64 [N]: the CTAs' fixed-point sums, zero between applies
   void *geometry = nullptr;   // shared stencils and units of this n (owned by a cache)
   void *units = nullptr;
   void *stencil = nullptr;    // per-displacement chunk records (float4)
@@ -125,12 +126,12 @@ struct DispPlan {
 size_t disp_smem_bytes(int n);
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st);
-vie_status disp_reduce(const DispPlan &dp, long N, int slots, int op, const double *partial,
-                       const double *diag, const double *sigma_s, const double *g, double *y, cudaStream_t st);
+vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *diag, const double *sigma_s,
+                       const double *g, double *y, cudaStream_t st);
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st);
 void disp_release(DispPlan *dp);
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
-                       double *partial, cudaStream_t st);
+                       cudaStream_t st);
 vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st);
 size_t symv_block_floats(int n);
 size_t symv_partial_floats(int n);
@@ -138,8 +139,7 @@ vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, con
                       float *partial, double *y, int device, cudaStream_t st);
 vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const double *sigma_s, const double *diag,
                        long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
-vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, double *partial,
-                       cudaStream_t st);
+vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, cudaStream_t st);
 
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
