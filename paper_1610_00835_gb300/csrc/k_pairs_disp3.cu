@@ -1,0 +1,544 @@
+// Displacement-major pair kernel in 3D (n <= 32, FP32 tiles, S = 64).
+//
+// The 3D form of k_pairs_disp.cu (Section 2, Eq. EQ:Kernel; Section 3.2,
+// M-iii): y_j = sum_{k != j} A_jk s_k with A_jk = h^3 e^{-tau} / (4 pi r^2)
+// and tau the S-step midpoint march of the trilinear interpolant of sigma_t.
+// The S samples of the segment from j to j + D sit at (i + 1/2) D / S from j,
+// so their trilinear weights, summed per lattice cell, give a stencil W_D with
+// sum_i sigma(u_j + (i + 1/2) D / S) = sum_c W_D(c) sigma[j + c] for every j.
+//
+// W_D is stored as runs along one axis, cut into chunks of Lc cells (the same
+// records and unrolled march as in 2D, disp_march.cuh).  Three orientations,
+// chosen per D by estimated cost: runs along z with lanes on x (units fix a y),
+// runs along y with lanes on x (units fix a z), runs along x with lanes on y
+// (units fix a z).  A thread stacks kR targets along the run axis.  When the
+// lane extent of D is below 32, a warp holds 32 / gw lane groups of width gw
+// (gw the power of two at or above it) at third-axis coordinates gw apart:
+// with the odd pitches n + 1 and (n + 1)^2 the groups fall in distinct banks.
+//
+// The lattice is the padded (n + 1)^3 sigma_t array, linear (x fastest), with
+// kPad3 zero planes appended: reads of discarded stacked targets and of the
+// zero-weight tail of a chunk only run forward along the run axis, by at most
+// kPad3 strides, so every read stays in shared memory.  The weights of valid
+// targets only touch the (n + 1)^3 part.
+//
+// Only D in a half space is marched (A_jk = A_kj); each pair adds w s_k to y_j
+// and w s_j to y_k in 64-bit fixed point (the scale of the 2D kernel) with
+// integer atomics on one global array: exact, so applies are bitwise
+// reproducible.  k_disp3_reduce converts each sum once, adds the self cell and
+// clears the array.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "disp_march.cuh"
+#include "march.cuh"
+#include "vie_internal.cuh"
+
+namespace vie {
+
+namespace {
+
+using dmarch::kChunkLengths;
+using dmarch::kMaxChunk;
+using dmarch::kR;
+using dmarch::march_unit;
+using march::kS;
+
+constexpr int kThreads3 = 1024;
+constexpr int kPad3 = kR - 1 + kMaxChunk - 1;  // zero planes after the lattice
+constexpr int kMaxN3 = 32;                     // one lane block per unit
+
+struct Disp3Args {
+  const float *lat;          // [(n + 1 + kPad3) (n + 1)^2] sigma_t, x fastest
+  const float4 *stencil;     // chunk records of every W_D
+  const float *src;          // s, FP32 [N], x fastest
+  const float *src_t;        // s with y fastest: s(x, y, z) = src_t[(z n + x) n + y]
+  unsigned *smax;            // bits of max |s| (set by the source kernel)
+  double *scale_out;         // fixed-point scale of this apply
+  double rbound;             // bound on every row sum of A
+  unsigned long long *yacc;  // [N] int64 sums, zero between applies
+  const int4 *units;         // see disp3_build
+  int *counter;              // [2]
+  long n_units;
+  int n, ldp, plane;
+  long lat_elems;
+  float tau_scale2, wcoef;
+};
+
+template <int LDP, int PLANE>
+__global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
+  extern __shared__ float4 smem4[];
+  float *lat = reinterpret_cast<float *>(smem4);
+  const int tid = threadIdx.x, lane = tid & 31;
+  {
+    const float4 *g4 = reinterpret_cast<const float4 *>(a.lat);
+    const long n4 = a.lat_elems / 4;
+    for (long i = tid; i < n4; i += kThreads3) smem4[i] = g4[i];
+    for (long i = n4 * 4 + tid; i < a.lat_elems; i += kThreads3) lat[i] = a.lat[i];
+  }
+  __syncthreads();
+  const float smax = __uint_as_float(*a.smax);
+  const double scale_d =
+      smax > 0.f ? ldexp(1.0, ilogb(4.611686018427387904e18 / ((double)smax * a.rbound))) : 1.0;
+  const float scale = (float)scale_d;
+  const int n = a.n;
+  const int ldp = LDP > 0 ? LDP : a.ldp, plane = PLANE > 0 ? PLANE : a.plane;
+  const unsigned lat_base = (unsigned)__cvta_generic_to_shared(lat);
+  long u0 = 0, u_end = 0;
+  for (;;) {
+    if (u0 >= u_end) {
+      long got = 0;
+      if (lane == 0) got = atomicAdd(a.counter, 4);
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (got >= a.n_units) break;
+      u0 = got;
+      u_end = min(got + 4, a.n_units);
+    }
+    const int4 un = a.units[u0++];
+    const int dx = (signed char)(un.y & 0xff), dy = (signed char)((un.y >> 8) & 0xff);
+    const int dz = (signed char)((un.y >> 16) & 0xff);
+    const int orient = (un.y >> 24) & 3, lg = (un.y >> 26) & 7;
+    const int sb = un.z & 0xff, c3 = (un.z >> 8) & 0xff;
+    const int lc = un.w & 15, chunks = un.w >> 4;
+    const int xlo = max(0, -dx), xhi = n - max(0, dx);
+    const int ylo = max(0, -dy), yhi = n - max(0, dy);
+    const int zlo = max(0, -dz), zhi = n - max(0, dz);
+    // lane, stack (run) and third axes of this orientation
+    const int llo = orient == 2 ? ylo : xlo, lhi = orient == 2 ? yhi : xhi;
+    const int slo = orient == 0 ? zlo : orient == 1 ? ylo : xlo;
+    const int shi = orient == 0 ? zhi : orient == 1 ? yhi : xhi;
+    const int thi = orient == 0 ? yhi : zhi;
+    const int gw = 32 >> lg, g = lane >> (5 - lg), lig = lane & (gw - 1);
+    int c = c3 + gw * g;
+    bool lvalid = c < thi;
+    if (!lvalid) c = c3;
+    int la = llo + lig;
+    lvalid = lvalid && la < lhi;
+    la = min(la, lhi - 1);
+    const int b0 = slo + kR * sb;
+    int x, y, z;
+    if (orient == 0) {
+      x = la; z = b0; y = c;
+    } else if (orient == 1) {
+      x = la; y = b0; z = c;
+    } else {
+      y = la; x = b0; z = c;
+    }
+    const unsigned base = lat_base + 4u * (unsigned)(x + ldp * y + plane * z);
+    {
+      // bring this D's chunk records into L1 (one 128-byte line per lane)
+      const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
+      const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
+      for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
+    }
+    float acc[kR];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) acc[q] = 0.f;
+    if (orient == 0)
+      march_unit<PLANE>(lc, a.stencil + un.x, chunks, base, plane, acc);
+    else if (orient == 1)
+      march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
+    else
+      march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+    const float r2 = (float)(dx * dx + dy * dy + dz * dz);
+    const float inv_r = rsqrtf(r2);
+    const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
+    const float wk = a.wcoef * inv_r * inv_r;
+    const long dk = dx + (long)n * (dy + (long)n * dz);
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      if (lvalid && b0 + q < shi) {
+        const int xq = orient == 2 ? x + q : x, yq = orient == 1 ? y + q : y, zq = orient == 0 ? z + q : z;
+        const long j = xq + (long)n * (yq + (long)n * zq), k = j + dk;
+        float sj, sk;
+        if (orient == 2) {
+          sj = __ldg(a.src_t + ((long)zq * n + xq) * n + yq);
+          sk = __ldg(a.src_t + ((long)(zq + dz) * n + xq + dx) * n + yq + dy);
+        } else {
+          sj = __ldg(a.src + j);
+          sk = __ldg(a.src + k);
+        }
+        const float w = wk * exp2f(tscale * acc[q]) * scale;
+        atomicAdd(a.yacc + j, (unsigned long long)__float2ll_rn(w * sk));
+        atomicAdd(a.yacc + k, (unsigned long long)__float2ll_rn(w * sj));
+      }
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.counter + 1, 1) == (int)gridDim.x - 1) {
+      a.counter[0] = 0;
+      a.counter[1] = 0;
+      *a.smax = 0u;  // every CTA read it before this, the next source kernel sets it
+      __threadfence();
+    }
+  }
+}
+
+// the padded lattice (pitch n + 1, x fastest) followed by kPad3 zero planes
+__global__ void k_make_lattice3(long lat, long total, const float *__restrict__ pad, float *__restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    out[i] = i < lat ? pad[i] : 0.f;
+}
+
+// s = sigma_s g (or g) in FP32, its copy with y fastest, and max |s|
+__global__ void k_disp3_source(long N, int n, int op, const double *__restrict__ ss, const double *__restrict__ g,
+                               float *__restrict__ s, float *__restrict__ s_t, unsigned *__restrict__ smax) {
+  unsigned m = 0u;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const float v = (float)(op == VIE_OP_A_RAW ? g[i] : ss[i] * g[i]);
+    s[i] = v;
+    const long x = i % n, y = (i / n) % n, z = i / ((long)n * n);
+    s_t[(z * n + x) * n + y] = v;
+    m = max(m, __float_as_uint(fabsf(v)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(smax, m);
+}
+
+// y_j = yacc[j] / scale + d_j s_j, and yacc back to zero
+__global__ void k_disp3_reduce(long N, int op, unsigned long long *__restrict__ yacc,
+                               const double *__restrict__ scale, const double *__restrict__ diag,
+                               const double *__restrict__ ss, const double *__restrict__ g,
+                               double *__restrict__ y) {
+  const double inv = 1.0 / *scale;
+  for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
+    const unsigned long long acc = yacc[j];
+    yacc[j] = 0ull;
+    const double sj = op == VIE_OP_A_RAW ? g[j] : ss[j] * g[j];
+    const double v = (double)(long long)acc * inv + diag[j] * sj;
+    y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
+  }
+}
+
+typedef void (*Disp3Kernel)(Disp3Args);
+
+Disp3Kernel pick_disp3(int n) { return n == 32 ? k_pairs_disp3<33, 1089> : k_pairs_disp3<0, 0>; }
+
+// ---- geometry (host): stencils, chunk records and work units, per (device, n)
+
+struct Run3 {
+  int cx, cy, cz, len;
+  std::vector<double> w;
+};
+
+// W_D on its box of cells [min(0, d), max(0, d)] per axis: the trilinear
+// weights of the S midpoint samples (i + 1/2) D / S summed per cell (Section
+// 3.2, M-iii), cells of zero weight excluded from the runs
+void stencil3(int dx, int dy, int dz, std::vector<double> &box, int &ox, int &oy, int &oz, int &bx, int &by,
+              int &bz) {
+  ox = std::min(0, dx), oy = std::min(0, dy), oz = std::min(0, dz);
+  bx = std::abs(dx) + 1, by = std::abs(dy) + 1, bz = std::abs(dz) + 1;
+  box.assign((size_t)bx * by * bz, 0.0);
+  for (int i = 0; i < kS; ++i) {
+    const double px = (i + 0.5) * dx / kS, py = (i + 0.5) * dy / kS, pz = (i + 0.5) * dz / kS;
+    const double fx = floor(px), fy = floor(py), fz = floor(pz);
+    const double ax = px - fx, ay = py - fy, az = pz - fz;
+    for (int c = 0; c < 8; ++c) {
+      const double w = (c & 1 ? ax : 1.0 - ax) * (c & 2 ? ay : 1.0 - ay) * (c & 4 ? az : 1.0 - az);
+      if (w == 0.0) continue;
+      const int cx = (int)fx + (c & 1) - ox, cy = (int)fy + ((c >> 1) & 1) - oy, cz = (int)fz + (c >> 2) - oz;
+      box[((size_t)cz * by + cy) * bx + cx] += w;
+    }
+  }
+}
+
+// runs of nonzero cells along axis ax (0 x, 1 y, 2 z) of the box
+void box_runs(const std::vector<double> &box, int ox, int oy, int oz, int bx, int by, int bz, int ax,
+              std::vector<Run3> &runs) {
+  runs.clear();
+  const int ext[3] = {bx, by, bz};
+  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;  // the two other axes
+  int p[3];
+  for (p[a2] = 0; p[a2] < ext[a2]; ++p[a2])
+    for (p[a1] = 0; p[a1] < ext[a1]; ++p[a1]) {
+      Run3 *cur = nullptr;
+      for (p[ax] = 0; p[ax] < ext[ax]; ++p[ax]) {
+        const double w = box[((size_t)p[2] * by + p[1]) * bx + p[0]];
+        if (w != 0.0) {
+          if (!cur) {
+            runs.push_back({p[0] + ox, p[1] + oy, p[2] + oz, 0, {}});
+            cur = &runs.back();
+          }
+          cur->w.push_back(w);
+          cur->len++;
+        } else {
+          cur = nullptr;
+        }
+      }
+    }
+}
+
+struct Plan3 {
+  int lc;
+  long chunks, cost;
+};
+
+Plan3 chunk_plan3(const std::vector<Run3> &runs) {
+  Plan3 best{0, 0, -1};
+  for (int lc : kChunkLengths) {
+    long ch = 0;
+    for (const Run3 &r : runs) ch += (r.len + lc - 1) / lc;
+    const long cost = ch * (6 + (lc + 4) / 4 + (lc + kR - 1) + (long)kR * lc) + 60;
+    if (best.cost < 0 || cost < best.cost) best = {lc, ch, cost};
+  }
+  return best;
+}
+
+int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+struct Geometry3 {
+  int device = -1, n = 0, refs = 0;
+  int4 *units = nullptr;
+  float *stencil = nullptr;
+  long n_units = 0;
+  double taps = 0.0;
+};
+std::mutex g_geo3_mu;
+std::vector<Geometry3 *> g_geo3;
+constexpr int kGeo3Keep = 2;
+
+void geometry3_free(Geometry3 *g) {
+  if (g->units) cudaFree(g->units);
+  if (g->stencil) cudaFree(g->stencil);
+  delete g;
+}
+
+void geometry3_trim() {
+  int unused = 0;
+  for (Geometry3 *g : g_geo3) unused += g->refs == 0;
+  for (size_t i = 0; i < g_geo3.size() && unused > kGeo3Keep;) {
+    if (g_geo3[i]->refs == 0) {
+      geometry3_free(g_geo3[i]);
+      g_geo3.erase(g_geo3.begin() + i);
+      --unused;
+    } else {
+      ++i;
+    }
+  }
+}
+
+// Units (int4): x = first chunk record (float4 index); y = dx | dy << 8 | dz << 16
+// (8-bit two's complement) | orientation << 24 | log2(lane groups) << 26;
+// z = stack block | first third-axis coordinate << 8; w = Lc | chunks << 4.
+vie_status geometry3_build(int n, Geometry3 *geo) {
+  const int ldp = n + 1, plane = ldp * ldp;
+  struct U {
+    int4 u;
+    long cost;
+  };
+  std::vector<U> units;
+  std::vector<float> rec;
+  std::vector<double> box;
+  std::vector<Run3> runs[3];
+  double taps = 0.0;
+  for (int dz = 0; dz < n; ++dz)
+    for (int dy = -(n - 1); dy < n; ++dy)
+      for (int dx = -(n - 1); dx < n; ++dx) {
+        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+        const int wx = n - std::abs(dx), wy = n - std::abs(dy), wz = n - dz;
+        int ox, oy, oz, bx, by, bz;
+        stencil3(dx, dy, dz, box, ox, oy, oz, bx, by, bz);
+        long nnz = 0;
+        for (double v : box) nnz += v != 0.0;
+        taps += (double)nnz * wx * wy * wz;
+        // orientations: 0 runs z / lanes x / third y; 1 runs y / lanes x / third z; 2 runs x / lanes y / third z
+        const int run_axis[3] = {2, 1, 0};
+        const int lanes_of[3] = {wx, wx, wy}, stack_of[3] = {wz, wy, wx}, third_of[3] = {wy, wz, wz};
+        int best = -1;
+        long best_cost = 0;
+        Plan3 plans[3];
+        for (int o = 0; o < 3; ++o) {
+          box_runs(box, ox, oy, oz, bx, by, bz, run_axis[o], runs[o]);
+          plans[o] = chunk_plan3(runs[o]);
+          const long nunits = (long)((stack_of[o] + kR - 1) / kR) * std::min(pow2ceil(lanes_of[o]), third_of[o]);
+          const long cost = nunits * plans[o].cost;
+          if (best < 0 || cost < best_cost) {
+            best = o;
+            best_cost = cost;
+          }
+        }
+        const Plan3 &pl = plans[best];
+        const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
+        for (const Run3 &r : runs[best]) {
+          for (int c0 = 0; c0 < r.len; c0 += pl.lc) {
+            int cx = r.cx, cy = r.cy, cz = r.cz;
+            if (run_axis[best] == 0) cx += c0;
+            if (run_axis[best] == 1) cy += c0;
+            if (run_axis[best] == 2) cz += c0;
+            const int eoff = cx + ldp * cy + plane * cz;
+            float obits;
+            memcpy(&obits, &eoff, sizeof obits);
+            rec.push_back(obits);
+            for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < r.len ? (float)r.w[c0 + i] : 0.f);
+            for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
+          }
+        }
+        const int lanes = lanes_of[best], third = third_of[best];
+        const int gw = pow2ceil(lanes), lg = 5 - __builtin_ctz(gw);  // 32 / gw lane groups
+        const int tlo = best == 0 ? std::max(0, -dy) : 0;           // third axis y (orientation 0) or z
+        const int nsb = (stack_of[best] + kR - 1) / kR;
+        const int dxyz = (dx & 0xff) | ((dy & 0xff) << 8) | ((dz & 0xff) << 16) | (best << 24) | (lg << 26);
+        const int w = pl.lc | ((int)pl.chunks << 4);
+        for (int sb = 0; sb < nsb; ++sb)
+          for (int j = 0; j < gw && j < third; ++j)
+            units.push_back({make_int4(off, dxyz, sb | ((tlo + j) << 8), w), pl.cost});
+      }
+  for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
+  std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
+  std::vector<int4> uv(units.size());
+  for (size_t i = 0; i < units.size(); ++i) uv[i] = units[i].u;
+  VIE_CUDA(cudaMalloc((void **)&geo->units, sizeof(int4) * uv.size()));
+  VIE_CUDA(cudaMemcpy(geo->units, uv.data(), sizeof(int4) * uv.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(cudaMalloc((void **)&geo->stencil, sizeof(float) * rec.size()));
+  VIE_CUDA(cudaMemcpy(geo->stencil, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice));
+  geo->n_units = (long)uv.size();
+  geo->taps = taps;
+  return VIE_OK;
+}
+
+vie_status geometry3_acquire(int device, int n, Geometry3 **out) {
+  std::lock_guard<std::mutex> lock(g_geo3_mu);
+  for (Geometry3 *g : g_geo3)
+    if (g->device == device && g->n == n) {
+      ++g->refs;
+      *out = g;
+      return VIE_OK;
+    }
+  Geometry3 *g = new Geometry3;
+  g->device = device;
+  g->n = n;
+  const vie_status s = geometry3_build(n, g);
+  if (s != VIE_OK) {
+    geometry3_free(g);
+    return s;
+  }
+  g->refs = 1;
+  g_geo3.push_back(g);
+  geometry3_trim();
+  *out = g;
+  return VIE_OK;
+}
+
+void geometry3_release(Geometry3 *g) {
+  std::lock_guard<std::mutex> lock(g_geo3_mu);
+  --g->refs;
+  geometry3_trim();
+}
+
+}  // namespace
+
+size_t disp3_smem_bytes(int n) {
+  const long p = n + 1;
+  return sizeof(float) * (size_t)(p * p * (p + kPad3));
+}
+
+vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int device, cudaStream_t st) {
+  dp->usable = 0;
+  if (n < 2 || n > kMaxN3) return VIE_OK;
+  cudaDeviceProp prop;
+  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  const size_t smem = disp3_smem_bytes(n);
+  if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
+  Disp3Kernel k = pick_disp3(n);
+  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int bps = 0;
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads3, smem));
+  if (bps < 1) return VIE_OK;
+  Geometry3 *geo = nullptr;
+  vie_status s = geometry3_acquire(device, n, &geo);
+  if (s != VIE_OK) return s;
+  dp->geometry = geo;
+  dp->units = geo->units;
+  dp->stencil = geo->stencil;
+  dp->n_units = geo->n_units;
+  dp->taps = geo->taps;
+  const long N = (long)n * n * n, p = n + 1;
+  const long lat = p * p * p, lat_elems = p * p * (p + kPad3);
+  VIE_CUDA(cudaMalloc((void **)&dp->counter, 2 * sizeof(int)));
+  VIE_CUDA(cudaMemset(dp->counter, 0, 2 * sizeof(int)));
+  VIE_CUDA(cudaMalloc((void **)&dp->lattice, sizeof(float) * lat_elems));
+  k_make_lattice3<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(lat, lat_elems, sig_padded,
+                                                                                 (float *)dp->lattice);
+  VIE_CHECK_LAUNCH("k_make_lattice3");
+  VIE_CUDA(cudaMalloc((void **)&dp->smax, sizeof(unsigned)));
+  VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
+  VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
+  VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)N));
+  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * (size_t)N));
+  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * (size_t)N));
+  // every row sum of A is below sum over all nonzero displacements of h / (4 pi |D|^2)
+  double rb = 0.0;
+  for (int dz = -(n - 1); dz < n; ++dz)
+    for (int dy = -(n - 1); dy < n; ++dy)
+      for (int dx = -(n - 1); dx < n; ++dx)
+        if (dx || dy || dz) rb += 1.0 / ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+  dp->rbound = rb / (4.0 * kPi * n);
+  dp->n = n;
+  dp->lat_elems = lat_elems;
+  dp->smem = smem;
+  dp->grid = bps * prop.multiProcessorCount;
+  dp->kernel = (const void *)k;
+  dp->usable = 1;
+  return VIE_OK;
+}
+
+void disp3_release(DispPlan3 *dp) {
+  if (dp->geometry) geometry3_release((Geometry3 *)dp->geometry);
+  if (dp->counter) cudaFree(dp->counter);
+  if (dp->lattice) cudaFree(dp->lattice);
+  if (dp->smax) cudaFree(dp->smax);
+  if (dp->scale) cudaFree(dp->scale);
+  if (dp->src_t) cudaFree(dp->src_t);
+  if (dp->yacc) cudaFree(dp->yacc);
+  *dp = DispPlan3{};
+}
+
+vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const double *g, const double *diag,
+                       float *src, float tau_scale2, float wcoef, double *y, cudaEvent_t mid0, cudaEvent_t mid1,
+                       cudaStream_t st) {
+  const int n = dp.n;
+  const long N = (long)n * n * n;
+  const int blocks = (int)std::min((N + 255) / 256, 1024L);
+  k_disp3_source<<<blocks, 256, 0, st>>>(N, n, op, sigma_s, g, src, dp.src_t, dp.smax);
+  VIE_CHECK_LAUNCH("k_disp3_source");
+  if (mid0) VIE_CUDA(cudaEventRecord(mid0, st));
+  Disp3Args a;
+  a.lat = (const float *)dp.lattice;
+  a.stencil = (const float4 *)dp.stencil;
+  a.src = src;
+  a.src_t = dp.src_t;
+  a.smax = dp.smax;
+  a.scale_out = dp.scale;
+  a.rbound = dp.rbound;
+  a.yacc = dp.yacc;
+  a.units = (const int4 *)dp.units;
+  a.counter = dp.counter;
+  a.n_units = dp.n_units;
+  a.n = n;
+  a.ldp = n + 1;
+  a.plane = (n + 1) * (n + 1);
+  a.lat_elems = dp.lat_elems;
+  a.tau_scale2 = tau_scale2;
+  a.wcoef = wcoef;
+  void *args[] = {&a};
+  VIE_CUDA(cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kThreads3), args, dp.smem, st));
+  count_launch();
+  if (mid1) VIE_CUDA(cudaEventRecord(mid1, st));
+  k_disp3_reduce<<<(int)std::min((N + 255) / 256, 4096L), 256, 0, st>>>(N, op, dp.yacc, dp.scale, diag, sigma_s,
+                                                                        g, y);
+  VIE_CHECK_LAUNCH("k_disp3_reduce");
+  return VIE_OK;
+}
+
+}  // namespace vie

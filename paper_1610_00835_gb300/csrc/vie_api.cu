@@ -118,6 +118,7 @@ struct vie_handle {
   PairPlan plan{};
   SymPlan sym{};                              // symmetric kernel, when usable
   DispPlan disp{};                            // displacement-major kernel, when usable
+  DispPlan3 disp3{};                          // its 3D form, when usable
   int use_kernel = VIE_KERNEL_GENERAL;        // pair kernel chosen for applies
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
@@ -207,6 +208,7 @@ void free_all(vie_handle *h) {
   dfree(h->ticket);
   sym_release(&h->sym);
   disp_release(&h->disp);
+  disp3_release(&h->disp3);
   free_gmres(h);
   for (auto &ev : h->events)
     for (auto &e : ev.e)
@@ -307,6 +309,19 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
     if (s != VIE_OK) return s;
     if (timed) {
       VIE_CUDA(cudaEventRecord(ev->e[2], st));
+      VIE_CUDA(cudaEventRecord(ev->e[3], st));
+      ev->pending = true;
+    }
+    h->n_apply++;
+    return VIE_OK;
+  }
+  if (h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 3) {
+    const double hh = 1.0 / h->n;
+    vie_status s = disp3_apply(h->disp3, op, h->sig_s, g, h->diag, (float *)h->src,
+                               (float)(hh / h->opts.steps * 1.4426950408889634), (float)(hh / (4.0 * kPi)), y,
+                               timed ? ev->e[1] : nullptr, timed ? ev->e[2] : nullptr, st);
+    if (s != VIE_OK) return s;
+    if (timed) {
       VIE_CUDA(cudaEventRecord(ev->e[3], st));
       ev->pending = true;
     }
@@ -492,8 +507,10 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     TRY(sym_prepare(&h->sym, g->dim, g->n, N, h->sig32, opts.device, st));
     if (g->dim == 2 && (opts.kernel == VIE_KERNEL_AUTO || opts.kernel == VIE_KERNEL_DISPLACEMENT))
       TRY(disp_prepare(&h->disp, g->n, h->sig32, opts.device, st));
+    if (g->dim == 3 && (opts.kernel == VIE_KERNEL_AUTO || opts.kernel == VIE_KERNEL_DISPLACEMENT))
+      TRY(disp3_prepare(&h->disp3, g->n, h->sig32, opts.device, st));
   }
-  if (h->disp.usable && opts.kernel != VIE_KERNEL_SYMMETRIC)
+  if ((h->disp.usable || h->disp3.usable) && opts.kernel != VIE_KERNEL_SYMMETRIC)
     h->use_kernel = VIE_KERNEL_DISPLACEMENT;
   else if (h->sym.usable)
     h->use_kernel = VIE_KERNEL_SYMMETRIC;
@@ -533,8 +550,9 @@ vie_status vie_get_kernel_work(vie_handle *h, double *fma_per_apply) {
   int k = VIE_KERNEL_GENERAL;
   vie_get_kernel(h, &k);
   const double pairs = 0.5 * (double)h->N * (double)(h->N - 1);
-  *fma_per_apply = k == VIE_KERNEL_DISPLACEMENT ? h->disp.taps
-                                                : pairs * h->opts.steps * (h->dim == 3 ? 7.0 : 3.0);
+  *fma_per_apply = k != VIE_KERNEL_DISPLACEMENT ? pairs * h->opts.steps * (h->dim == 3 ? 7.0 : 3.0)
+                   : h->dim == 3                ? h->disp3.taps
+                                                : h->disp.taps;
   return VIE_OK;
 }
 
@@ -618,7 +636,7 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
   if (mode == VIE_OPERATOR_SYM32) {
     // A in the symmetric blocks of grid-row pairs: the pair weights, expanded
-    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT) {
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2) {
       set_error("vie_assemble: VIE_OPERATOR_SYM32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
                 "n <= 133)");
       return VIE_ERR_UNSUPPORTED;
@@ -639,7 +657,7 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   }
   if (mode == VIE_OPERATOR_PAIRS32) {
     // every unordered pair's FP32 weight, displacement-major (the displacement kernel's march)
-    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT) {
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2) {
       set_error("vie_assemble: VIE_OPERATOR_PAIRS32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
                 "n <= 133)");
       return VIE_ERR_UNSUPPORTED;
@@ -653,7 +671,8 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     h->asm_mode = mode;
     return VIE_OK;
   }
-  if ((!h->sym.usable && h->use_kernel != VIE_KERNEL_DISPLACEMENT) || h->opts.precision != VIE_PREC_FP32 ||
+  const bool disp2 = h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 2;
+  if ((!h->sym.usable && !disp2) || h->opts.precision != VIE_PREC_FP32 ||
       h->opts.tau_mode != VIE_TAU_MARCH || h->opts.steps != 64) {
     set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "
               "in shared memory");
@@ -680,7 +699,7 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   VIE_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
   float *k32 = mode == VIE_OPERATOR_FP32 ? (float *)h->kmat : nullptr;
   void *khi = mode == VIE_OPERATOR_BF16X3 ? h->kmat : nullptr;
-  if (h->use_kernel == VIE_KERNEL_DISPLACEMENT) {
+  if (disp2) {
     // march every unordered pair once into the pair weights, then expand them into K
     if (!h->pairs) VIE_CUDA(cudaMalloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
     const double hh = 1.0 / h->n;

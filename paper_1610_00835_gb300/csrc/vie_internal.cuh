@@ -123,6 +123,28 @@ struct DispPlan {
   long long stored = 0;       // weights stored: N (N - 1) / 2
   const long long *doff = nullptr;
 };
+// 3D displacement-major kernel (k_pairs_disp3.cu), grids up to 32^3
+struct DispPlan3 {
+  int usable = 0, n = 0, grid = 0;
+  size_t smem = 0;
+  long n_units = 0, lat_elems = 0;
+  double taps = 0.0, rbound = 0.0;
+  void *geometry = nullptr;   // shared stencils and units of this n (owned by a cache)
+  void *units = nullptr, *stencil = nullptr, *lattice = nullptr;
+  int *counter = nullptr;
+  unsigned *smax = nullptr;
+  double *scale = nullptr;
+  float *src_t = nullptr;
+  unsigned long long *yacc = nullptr;
+  const void *kernel = nullptr;
+};
+size_t disp3_smem_bytes(int n);
+vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int device, cudaStream_t st);
+void disp3_release(DispPlan3 *dp);
+vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const double *g, const double *diag,
+                       float *src, float tau_scale2, float wcoef, double *y, cudaEvent_t mid0, cudaEvent_t mid1,
+                       cudaStream_t st);
+
 size_t disp_smem_bytes(int n);
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st);

@@ -174,6 +174,35 @@ def test_config2_full_size_sampled_rows():
     assert rel_l2(got[rows], want) < FP32_TOL
 
 
+@pytest.mark.parametrize("n", [2, 3, 8, 32])
+def test_3d_displacement_kernel_against_tile_pairs_and_oracle(n):
+    # 3D grids up to 32^3 take the displacement kernel; it agrees with the
+    # tile-pair kernel, the oracle (sampled rows) and itself (bitwise)
+    m = V.heterogeneous_3d(n=n, seed=90 + n)
+    h = P.vie_create(3, n, m.sigma_t, m.sigma_s)
+    assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
+    hs = P.vie_create(3, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
+    assert P.vie_get_kernel(hs) == P.VIE_KERNEL_SYMMETRIC
+    g = m.f + 0.1 * rng_vec(m.N, n)
+    for op in (P.VIE_OP_K_SIGMA_S, P.VIE_OP_A_RAW, P.VIE_OP_I_MINUS_K):
+        got = gpu_apply(h, op, g)
+        assert rel_l2(got, gpu_apply(hs, op, g)) < 2e-6
+        np.testing.assert_array_equal(gpu_apply(h, op, g), got)
+    rows = _sampled_rows(m.N, min(12, m.N), n + 3)
+    want = O.apply(3, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)[rows], want) < FP32_TOL
+
+
+def test_3d_beyond_32_takes_another_kernel():
+    m = V.heterogeneous_3d(n=33, seed=97)
+    h = P.vie_create(3, 33, m.sigma_t, m.sigma_s)
+    assert P.vie_get_kernel(h) != P.VIE_KERNEL_DISPLACEMENT
+    g = m.f
+    rows = _sampled_rows(m.N, 6, 33)
+    want = O.apply(3, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)[rows], want) < FP32_TOL
+
+
 def test_config3_full_size_sampled_rows():
     m = V.heterogeneous_3d()
     h = P.vie_create(3, m.n, m.sigma_t, m.sigma_s)
