@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "disp_march.cuh"
@@ -61,7 +62,7 @@ struct Disp3Args {
   double *scale_out;         // fixed-point scale of this apply
   double rbound;             // bound on every row sum of A
   unsigned long long *yacc;  // [N] int64 sums, zero between applies
-  const int4 *units;         // see disp3_build
+  const int4 *units;         // see geometry3_build
   int *counter;              // [2]
   long n_units;
   int n, ldp, plane;
@@ -224,8 +225,7 @@ Disp3Kernel pick_disp3(int n) { return n == 32 ? k_pairs_disp3<33, 1089> : k_pai
 // ---- geometry (host): stencils, chunk records and work units, per (device, n)
 
 struct Run3 {
-  int cx, cy, cz, len;
-  std::vector<double> w;
+  int cx, cy, cz, len, woff;  // first cell, cells, first weight in the shared weight list
 };
 
 // W_D on its box of cells [min(0, d), max(0, d)] per axis: the trilinear
@@ -251,25 +251,26 @@ void stencil3(int dx, int dy, int dz, std::vector<double> &box, int &ox, int &oy
 
 // runs of nonzero cells along axis ax (0 x, 1 y, 2 z) of the box
 void box_runs(const std::vector<double> &box, int ox, int oy, int oz, int bx, int by, int bz, int ax,
-              std::vector<Run3> &runs) {
+              std::vector<Run3> &runs, std::vector<double> &wts) {
   runs.clear();
+  wts.clear();
   const int ext[3] = {bx, by, bz};
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;  // the two other axes
   int p[3];
   for (p[a2] = 0; p[a2] < ext[a2]; ++p[a2])
     for (p[a1] = 0; p[a1] < ext[a1]; ++p[a1]) {
-      Run3 *cur = nullptr;
+      bool open = false;
       for (p[ax] = 0; p[ax] < ext[ax]; ++p[ax]) {
         const double w = box[((size_t)p[2] * by + p[1]) * bx + p[0]];
         if (w != 0.0) {
-          if (!cur) {
-            runs.push_back({p[0] + ox, p[1] + oy, p[2] + oz, 0, {}});
-            cur = &runs.back();
+          if (!open) {
+            runs.push_back({p[0] + ox, p[1] + oy, p[2] + oz, 0, (int)wts.size()});
+            open = true;
           }
-          cur->w.push_back(w);
-          cur->len++;
+          wts.push_back(w);
+          runs.back().len++;
         } else {
-          cur = nullptr;
+          open = false;
         }
       }
     }
@@ -328,74 +329,108 @@ void geometry3_trim() {
   }
 }
 
+struct Unit3 {
+  int4 u;
+  long cost;
+};
+
+// the records and units of the displacements with one dz (record offsets local
+// to this plane's record list)
+struct Plane3 {
+  std::vector<Unit3> units;
+  std::vector<float> rec;
+  double taps = 0.0;
+};
+
+void build_plane3(int n, int dz, Plane3 &out) {
+  const int ldp = n + 1, plane = ldp * ldp;
+  std::vector<double> box;
+  std::vector<Run3> runs[3];
+  std::vector<double> wts[3];
+  std::vector<Unit3> &units = out.units;
+  std::vector<float> &rec = out.rec;
+  for (int dy = -(n - 1); dy < n; ++dy)
+    for (int dx = -(n - 1); dx < n; ++dx) {
+      if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+      const int wx = n - std::abs(dx), wy = n - std::abs(dy), wz = n - dz;
+      int ox, oy, oz, bx, by, bz;
+      stencil3(dx, dy, dz, box, ox, oy, oz, bx, by, bz);
+      long nnz = 0;
+      for (double v : box) nnz += v != 0.0;
+      out.taps += (double)nnz * wx * wy * wz;
+      // orientations: 0 runs z / lanes x / third y; 1 runs y / lanes x / third z; 2 runs x / lanes y / third z
+      const int run_axis[3] = {2, 1, 0};
+      const int lanes_of[3] = {wx, wx, wy}, stack_of[3] = {wz, wy, wx}, third_of[3] = {wy, wz, wz};
+      int best = -1;
+      long best_cost = 0;
+      Plan3 plans[3];
+      for (int o = 0; o < 3; ++o) {
+        box_runs(box, ox, oy, oz, bx, by, bz, run_axis[o], runs[o], wts[o]);
+        plans[o] = chunk_plan3(runs[o]);
+        const long nunits = (long)((stack_of[o] + kR - 1) / kR) * std::min(pow2ceil(lanes_of[o]), third_of[o]);
+        const long cost = nunits * plans[o].cost;
+        if (best < 0 || cost < best_cost) {
+          best = o;
+          best_cost = cost;
+        }
+      }
+      const Plan3 &pl = plans[best];
+      const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
+      for (const Run3 &r : runs[best]) {
+        for (int c0 = 0; c0 < r.len; c0 += pl.lc) {
+          int cx = r.cx, cy = r.cy, cz = r.cz;
+          if (run_axis[best] == 0) cx += c0;
+          if (run_axis[best] == 1) cy += c0;
+          if (run_axis[best] == 2) cz += c0;
+          const int eoff = cx + ldp * cy + plane * cz;
+          float obits;
+          memcpy(&obits, &eoff, sizeof obits);
+          rec.push_back(obits);
+          for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < r.len ? (float)wts[best][r.woff + c0 + i] : 0.f);
+          for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
+        }
+      }
+      const int lanes = lanes_of[best], third = third_of[best];
+      const int gw = pow2ceil(lanes), lg = 5 - __builtin_ctz(gw);  // 32 / gw lane groups
+      const int tlo = best == 0 ? std::max(0, -dy) : 0;           // third axis y (orientation 0) or z
+      const int nsb = (stack_of[best] + kR - 1) / kR;
+      const int dxyz = (dx & 0xff) | ((dy & 0xff) << 8) | ((dz & 0xff) << 16) | (best << 24) | (lg << 26);
+      const int w = pl.lc | ((int)pl.chunks << 4);
+      for (int sb = 0; sb < nsb; ++sb)
+        for (int j = 0; j < gw && j < third; ++j)
+          units.push_back({make_int4(off, dxyz, sb | ((tlo + j) << 8), w), pl.cost});
+    }
+}
+
 // Units (int4): x = first chunk record (float4 index); y = dx | dy << 8 | dz << 16
 // (8-bit two's complement) | orientation << 24 | log2(lane groups) << 26;
 // z = stack block | first third-axis coordinate << 8; w = Lc | chunks << 4.
+// The planes dz are built on host threads and joined in dz order.
 vie_status geometry3_build(int n, Geometry3 *geo) {
-  const int ldp = n + 1, plane = ldp * ldp;
-  struct U {
-    int4 u;
-    long cost;
-  };
-  std::vector<U> units;
+  std::vector<Plane3> planes(n);
+  const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&, t]() {
+      for (int dz = t; dz < n; dz += nt) build_plane3(n, dz, planes[dz]);
+    });
+  for (std::thread &th : pool) th.join();
+  std::vector<Unit3> units;
   std::vector<float> rec;
-  std::vector<double> box;
-  std::vector<Run3> runs[3];
   double taps = 0.0;
-  for (int dz = 0; dz < n; ++dz)
-    for (int dy = -(n - 1); dy < n; ++dy)
-      for (int dx = -(n - 1); dx < n; ++dx) {
-        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
-        const int wx = n - std::abs(dx), wy = n - std::abs(dy), wz = n - dz;
-        int ox, oy, oz, bx, by, bz;
-        stencil3(dx, dy, dz, box, ox, oy, oz, bx, by, bz);
-        long nnz = 0;
-        for (double v : box) nnz += v != 0.0;
-        taps += (double)nnz * wx * wy * wz;
-        // orientations: 0 runs z / lanes x / third y; 1 runs y / lanes x / third z; 2 runs x / lanes y / third z
-        const int run_axis[3] = {2, 1, 0};
-        const int lanes_of[3] = {wx, wx, wy}, stack_of[3] = {wz, wy, wx}, third_of[3] = {wy, wz, wz};
-        int best = -1;
-        long best_cost = 0;
-        Plan3 plans[3];
-        for (int o = 0; o < 3; ++o) {
-          box_runs(box, ox, oy, oz, bx, by, bz, run_axis[o], runs[o]);
-          plans[o] = chunk_plan3(runs[o]);
-          const long nunits = (long)((stack_of[o] + kR - 1) / kR) * std::min(pow2ceil(lanes_of[o]), third_of[o]);
-          const long cost = nunits * plans[o].cost;
-          if (best < 0 || cost < best_cost) {
-            best = o;
-            best_cost = cost;
-          }
-        }
-        const Plan3 &pl = plans[best];
-        const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
-        for (const Run3 &r : runs[best]) {
-          for (int c0 = 0; c0 < r.len; c0 += pl.lc) {
-            int cx = r.cx, cy = r.cy, cz = r.cz;
-            if (run_axis[best] == 0) cx += c0;
-            if (run_axis[best] == 1) cy += c0;
-            if (run_axis[best] == 2) cz += c0;
-            const int eoff = cx + ldp * cy + plane * cz;
-            float obits;
-            memcpy(&obits, &eoff, sizeof obits);
-            rec.push_back(obits);
-            for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < r.len ? (float)r.w[c0 + i] : 0.f);
-            for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
-          }
-        }
-        const int lanes = lanes_of[best], third = third_of[best];
-        const int gw = pow2ceil(lanes), lg = 5 - __builtin_ctz(gw);  // 32 / gw lane groups
-        const int tlo = best == 0 ? std::max(0, -dy) : 0;           // third axis y (orientation 0) or z
-        const int nsb = (stack_of[best] + kR - 1) / kR;
-        const int dxyz = (dx & 0xff) | ((dy & 0xff) << 8) | ((dz & 0xff) << 16) | (best << 24) | (lg << 26);
-        const int w = pl.lc | ((int)pl.chunks << 4);
-        for (int sb = 0; sb < nsb; ++sb)
-          for (int j = 0; j < gw && j < third; ++j)
-            units.push_back({make_int4(off, dxyz, sb | ((tlo + j) << 8), w), pl.cost});
-      }
+  for (int dz = 0; dz < n; ++dz) {
+    const int base = (int)(rec.size() / 4);
+    for (Unit3 u : planes[dz].units) {
+      u.u.x += base;
+      units.push_back(u);
+    }
+    rec.insert(rec.end(), planes[dz].rec.begin(), planes[dz].rec.end());
+    taps += planes[dz].taps;
+    std::vector<Unit3>().swap(planes[dz].units);
+    std::vector<float>().swap(planes[dz].rec);
+  }
   for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
-  std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
+  std::stable_sort(units.begin(), units.end(), [](const Unit3 &p, const Unit3 &q) { return p.cost > q.cost; });
   std::vector<int4> uv(units.size());
   for (size_t i = 0; i < units.size(); ++i) uv[i] = units[i].u;
   VIE_CUDA(cudaMalloc((void **)&geo->units, sizeof(int4) * uv.size()));
