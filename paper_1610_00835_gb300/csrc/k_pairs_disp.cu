@@ -73,6 +73,8 @@ using dmarch::kChunkLengths;
 using dmarch::kMaxChunk;
 using dmarch::kR;
 using dmarch::march_unit;
+using dmarch::red_add;
+using dmarch::red_add_shared;
 constexpr int kThreads = 1024;
 constexpr int kPad = kR - 1 + kMaxChunk - 1;  // extra lattice rows and columns
 
@@ -235,8 +237,8 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
           const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
           if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
             const float w = wv[i] * scale;
-            atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * skv[i]));
-            atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sjv[i]));
+            red_add_shared(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * skv[i]));
+            red_add_shared(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sjv[i]));
           }
         }
       }
@@ -253,8 +255,8 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
             const float sk = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
                                      : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
             const float w = wq * scale;
-            atomicAdd(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
-            atomicAdd(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
+            red_add_shared(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
+            red_add_shared(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
           }
         }
       }
@@ -266,7 +268,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   if constexpr (MODE != kStore) {
     for (long i = tid; i < N; i += kThreads) {
       const unsigned long long v = ysh[i];
-      if (v) atomicAdd(a.yacc + i, v);  // integer sums: exact in any order
+      if (v) red_add(a.yacc + i, v);  // integer sums: exact in any order
     }
     if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
   }

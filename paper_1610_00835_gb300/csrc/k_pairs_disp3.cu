@@ -24,9 +24,10 @@
 //
 // Only D in a half space is marched (A_jk = A_kj); each pair adds w s_k to y_j
 // and w s_j to y_k in 64-bit fixed point (the scale of the 2D kernel) with
-// integer atomics on one global array: exact, so applies are bitwise
-// reproducible.  k_disp3_reduce converts each sum once, adds the self cell and
-// clears the array.
+// integer atomics on global memory: exact, so applies are bitwise
+// reproducible.  Runs along x put their sums in a second array with y fastest,
+// so a warp's atomics always cover contiguous words.  k_disp3_reduce adds the
+// two sums of each target, converts once, adds the self cell and clears both.
 #include <math.h>
 
 #include <algorithm>
@@ -47,6 +48,7 @@ using dmarch::kChunkLengths;
 using dmarch::kMaxChunk;
 using dmarch::kR;
 using dmarch::march_unit;
+using dmarch::red_add;
 using march::kS;
 
 constexpr int kThreads3 = 1024;
@@ -61,7 +63,7 @@ struct Disp3Args {
   unsigned *smax;            // bits of max |s| (set by the source kernel)
   double *scale_out;         // fixed-point scale of this apply
   double rbound;             // bound on every row sum of A
-  unsigned long long *yacc;  // [N] int64 sums, zero between applies
+  unsigned long long *yacc;  // [2 N] int64 sums (x fastest, then y fastest), zero between applies
   const int4 *units;         // see geometry3_build
   int *counter;              // [2]
   long n_units;
@@ -149,23 +151,24 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
     const float wk = a.wcoef * inv_r * inv_r;
-    const long dk = dx + (long)n * (dy + (long)n * dz);
+    // targets and partners in the layout whose fastest axis carries the lanes:
+    // x fastest (s, the first half of yacc) or, for runs along x, y fastest
+    // (s_t, the second half), so the atomics of a warp hit contiguous words
+    const long nn = (long)n * n;
+    const bool ty = orient == 2;
+    const float *sv = ty ? a.src_t : a.src;
+    unsigned long long *ya = ty ? a.yacc + nn * n : a.yacc;
+    const long j0 = ty ? ((long)z * n + x) * n + y : x + (long)n * (y + (long)n * z);
+    const long jstep = orient == 0 ? nn : n;
+    const long dk = ty ? dy + (long)n * (dx + (long)n * dz) : dx + (long)n * (dy + (long)n * dz);
 #pragma unroll
     for (int q = 0; q < kR; ++q) {
       if (lvalid && b0 + q < shi) {
-        const int xq = orient == 2 ? x + q : x, yq = orient == 1 ? y + q : y, zq = orient == 0 ? z + q : z;
-        const long j = xq + (long)n * (yq + (long)n * zq), k = j + dk;
-        float sj, sk;
-        if (orient == 2) {
-          sj = __ldg(a.src_t + ((long)zq * n + xq) * n + yq);
-          sk = __ldg(a.src_t + ((long)(zq + dz) * n + xq + dx) * n + yq + dy);
-        } else {
-          sj = __ldg(a.src + j);
-          sk = __ldg(a.src + k);
-        }
+        const long j = j0 + q * jstep, k = j + dk;
+        const float sj = __ldg(sv + j), sk = __ldg(sv + k);
         const float w = wk * exp2f(tscale * acc[q]) * scale;
-        atomicAdd(a.yacc + j, (unsigned long long)__float2ll_rn(w * sk));
-        atomicAdd(a.yacc + k, (unsigned long long)__float2ll_rn(w * sj));
+        red_add(ya + j, (unsigned long long)__float2ll_rn(w * sk));
+        red_add(ya + k, (unsigned long long)__float2ll_rn(w * sj));
       }
     }
   }
@@ -203,15 +206,19 @@ __global__ void k_disp3_source(long N, int n, int op, const double *__restrict__
   if ((threadIdx.x & 31) == 0) atomicMax(smax, m);
 }
 
-// y_j = yacc[j] / scale + d_j s_j, and yacc back to zero
-__global__ void k_disp3_reduce(long N, int op, unsigned long long *__restrict__ yacc,
+// y_j = (both sums of j) / scale + d_j s_j, and yacc back to zero.  yacc holds
+// N sums with x fastest, then N with y fastest (the runs along x).
+__global__ void k_disp3_reduce(long N, int n, int op, unsigned long long *__restrict__ yacc,
                                const double *__restrict__ scale, const double *__restrict__ diag,
                                const double *__restrict__ ss, const double *__restrict__ g,
                                double *__restrict__ y) {
   const double inv = 1.0 / *scale;
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
-    const unsigned long long acc = yacc[j];
+    const long x = j % n, yy = (j / n) % n, z = j / ((long)n * n);
+    const long jt = N + (z * n + x) * n + yy;
+    const unsigned long long acc = yacc[j] + yacc[jt];
     yacc[j] = 0ull;
+    yacc[jt] = 0ull;
     const double sj = op == VIE_OP_A_RAW ? g[j] : ss[j] * g[j];
     const double v = (double)(long long)acc * inv + diag[j] * sj;
     y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
@@ -510,8 +517,8 @@ vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int devi
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
   VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)N));
-  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * (size_t)N));
-  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * (size_t)N));
+  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)N));
+  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * 2 * (size_t)N));
   // every row sum of A is below sum over all nonzero displacements of h / (4 pi |D|^2)
   double rb = 0.0;
   for (int dz = -(n - 1); dz < n; ++dz)
@@ -570,8 +577,8 @@ vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const
   VIE_CUDA(cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kThreads3), args, dp.smem, st));
   count_launch();
   if (mid1) VIE_CUDA(cudaEventRecord(mid1, st));
-  k_disp3_reduce<<<(int)std::min((N + 255) / 256, 4096L), 256, 0, st>>>(N, op, dp.yacc, dp.scale, diag, sigma_s,
-                                                                        g, y);
+  k_disp3_reduce<<<(int)std::min((N + 255) / 256, 4096L), 256, 0, st>>>(N, n, op, dp.yacc, dp.scale, diag,
+                                                                        sigma_s, g, y);
   VIE_CHECK_LAUNCH("k_disp3_reduce");
   return VIE_OK;
 }
