@@ -65,15 +65,12 @@ __device__ __forceinline__ void march_chunks(const float4 *__restrict__ rec, int
   }
 }
 
-// Integer adds whose old value nobody reads: the reduction form, with no
+// Integer add whose old value nobody reads: the reduction form, with no
 // value coming back to the issuing warp.  No memory clobber, so the compiler
-// may still move the (read-only) source loads around them; the kernels read
-// the sums only after a CTA barrier (shared) or in a later launch (global).
+// may still move the (read-only) source loads around it; the sums are read
+// only by a later launch.
 __device__ __forceinline__ void red_add(unsigned long long *p, unsigned long long v) {
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v));
-}
-__device__ __forceinline__ void red_add_shared(unsigned long long *p, unsigned long long v) {
-  asm volatile("red.shared.add.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v));
 }
 
 template <int ST>

@@ -30,21 +30,20 @@
 // in a half plane (dy > 0, or dy = 0 and dx > 0): A_jk = A_kj, so each
 // unordered pair is marched once and feeds y_j (weight s_{j+D}) and y_{j+D}
 // (weight s_j).  Units are sorted by estimated cost, largest first, and warps
-// take them four at a time from a global counter.  Each CTA sums into a
-// private copy of y in shared memory held in 64-bit fixed point: every term
-// w s is rounded once to a multiple of 1/scale, scale the power of two at or
-// below 2^62 / (max|s| R) with R a bound on every row sum of A, and integer
-// atomic adds are exact in any order.  The result is therefore bitwise
+// take them four at a time from a global counter.  Every term w s is rounded
+// once to a multiple of 1/scale (64-bit fixed point, scale the power of two
+// at or below 2^62 / (max|s| R), R a bound on every row sum of A) and added
+// with an integer reduction (red.add, no value returned) into a global int64
+// array: integer sums are exact in any order, so the result is bitwise
 // reproducible whatever the schedule, and the accumulation error is below
-// N 2^-63 max|s| R.  Each CTA adds its copy into one int64 array with integer
-// atomics (exact, since the sum of the magnitudes of all terms of a target is
-// below 2^62); k_disp_reduce converts each sum once to FP64, adds the self
-// cell and clears the array for the next apply.
+// N 2^-63 max|s| R.  k_disp_reduce converts each sum once to FP64, adds the
+// self cell and clears the array for the next apply.  Shared memory holds the
+// lattice alone, which leaves the rest of the SM's L1 to the chunk records.
 //
-// The shared copy of y stores target (x, y) at y n + ((x + c y) mod n), with
-// n + c odd: 32 lanes on one column (runs along x) then hit different banks,
-// and lanes on one row stay contiguous.  Those column-wise lanes read s from a
-// transposed copy, so that their loads stay coalesced.
+// The array has two halves: targets on consecutive x (runs along y) sum into
+// the first, x fastest; targets on consecutive y (runs along x) into the
+// second, y fastest.  Either way a warp's 32 atomics cover contiguous words,
+// and the sources come from s or its transposed copy in the same layout.
 //
 // Targets of a block that fall outside the rectangle (ragged blocks) are
 // computed and discarded: lanes beyond it repeat the last valid target, and
@@ -74,7 +73,6 @@ using dmarch::kMaxChunk;
 using dmarch::kR;
 using dmarch::march_unit;
 using dmarch::red_add;
-using dmarch::red_add_shared;
 constexpr int kThreads = 1024;
 constexpr int kPad = kR - 1 + kMaxChunk - 1;  // extra lattice rows and columns
 
@@ -86,25 +84,17 @@ struct DispArgs {
   unsigned *smax;              // bits of max |s_k| (set by the source kernel)
   double *scale_out;           // fixed-point scale of this apply (for the reduce)
   double rbound;               // bound on sum_k A_jk for every j
-  unsigned long long *yacc;    // [N] int64 sum of every CTA's y (rotated layout), zero between applies
+  unsigned long long *yacc;    // [2 N] int64 sums (x fastest, then y fastest), zero between applies
   const int4 *units;           // {first chunk, dx | dy << 16, lane block | stack block << 16,
                                //  runs along y | Lc << 1 | chunks << 8}
   int *counter;                // [2]
   float *wbuf;                 // stored weights (store: written, stream: read)
   const long long *doff;       // first stored weight of each D of the half plane
   long n_units;
-  int n, ldp, rot;             // rot = c of the rotated layout of y
+  int n, ldp;
   long lat_elems;
   float tau_scale2, wcoef;
 };
-
-// slot of target (x, y) in the rotated layout of y (c <= 2, so x + c y < 3 n)
-__host__ __device__ __forceinline__ long yslot(int x, int y, int n, int c) {
-  int t = x + c * y;
-  t = t >= n ? t - n : t;
-  t = t >= n ? t - n : t;
-  return (long)y * n + t;
-}
 
 // What one launch does with the pairs of its units.
 enum DispMode {
@@ -123,10 +113,8 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   extern __shared__ float4 smem4[];
   const int n = a.n;
   const long N = (long)n * n;
-  // shared memory: y (int64 fixed point, [N]) unless storing, then the lattice unless streaming
-  unsigned long long *ysh = reinterpret_cast<unsigned long long *>(smem4);
-  float *lat = MODE == kStore ? reinterpret_cast<float *>(smem4)
-                              : reinterpret_cast<float *>(ysh + N + (N & 1));  // 16-byte aligned
+  // shared memory: the lattice (none when streaming)
+  float *lat = reinterpret_cast<float *>(smem4);
   const int tid = threadIdx.x, lane = tid & 31;
   if constexpr (MODE != kStream) {
     const float4 *g4 = reinterpret_cast<const float4 *>(a.lat);
@@ -134,9 +122,6 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     const long n4 = a.lat_elems / 4;
     for (long i = tid; i < n4; i += kThreads) l4[i] = g4[i];
     for (long i = n4 * 4 + tid; i < a.lat_elems; i += kThreads) lat[i] = a.lat[i];
-  }
-  if constexpr (MODE != kStore) {
-    for (long i = tid; i < N; i += kThreads) ysh[i] = 0ull;
   }
   __syncthreads();
   // power-of-two scale: 2^k <= 2^62 / (max|s| R), so w * scale is exact
@@ -213,6 +198,14 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     long woff = 0;
     if constexpr (MODE != kApply) woff = a.doff[disp_index(dx, dy, n)];
     const int wx = xhi - xlo;
+    // sums of targets on consecutive x (runs along y) go to yacc with x
+    // fastest, those on consecutive y (runs along x) to its second half with
+    // y fastest, so a warp's atomics cover contiguous words; s and its
+    // transpose follow the same layouts.  Stacked targets are n apart in both.
+    const float *sv = along_y ? a.src : a.src_t;
+    unsigned long long *ya = along_y ? a.yacc : a.yacc + N;
+    const long j0 = along_y ? (long)y * n + x : (long)x * n + y;
+    const long dk = along_y ? (long)dy * n + dx : (long)dx * n + dy;
     if constexpr (MODE == kStream) {
       // four targets at a time: their global loads are issued before their atomics
 #pragma unroll
@@ -226,9 +219,8 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
           if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
             const long wi = woff + (long)(yq - ylo) * wx + (xq - xlo);
             wv[i] = __ldcs(a.wbuf + wi);
-            sjv[i] = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
-            skv[i] = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
-                             : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
+            sjv[i] = __ldg(sv + j0 + (long)q * n);
+            skv[i] = __ldg(sv + j0 + (long)q * n + dk);
           }
         }
 #pragma unroll
@@ -237,8 +229,9 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
           const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
           if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
             const float w = wv[i] * scale;
-            red_add_shared(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * skv[i]));
-            red_add_shared(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sjv[i]));
+            const long j = j0 + (long)q * n;
+            red_add(ya + j, (unsigned long long)__float2ll_rn(w * skv[i]));
+            red_add(ya + j + dk, (unsigned long long)__float2ll_rn(w * sjv[i]));
           }
         }
       }
@@ -251,12 +244,11 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
           if constexpr (MODE == kStore) {
             a.wbuf[woff + (long)(yq - ylo) * wx + (xq - xlo)] = wq;
           } else {
-            const float sj = along_y ? __ldg(a.src + (long)yq * n + xq) : __ldg(a.src_t + (long)xq * n + yq);
-            const float sk = along_y ? __ldg(a.src + (long)(yq + dy) * n + xq + dx)
-                                     : __ldg(a.src_t + (long)(xq + dx) * n + yq + dy);
+            const long j = j0 + (long)q * n;
+            const float sj = __ldg(sv + j), sk = __ldg(sv + j + dk);
             const float w = wq * scale;
-            red_add_shared(&ysh[yslot(xq, yq, n, a.rot)], (unsigned long long)__float2ll_rn(w * sk));
-            red_add_shared(&ysh[yslot(xq + dx, yq + dy, n, a.rot)], (unsigned long long)__float2ll_rn(w * sj));
+            red_add(ya + j, (unsigned long long)__float2ll_rn(w * sk));
+            red_add(ya + j + dk, (unsigned long long)__float2ll_rn(w * sj));
           }
         }
       }
@@ -266,10 +258,6 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   // (the last CTA resets the unit counter for the next launch)
   __syncthreads();
   if constexpr (MODE != kStore) {
-    for (long i = tid; i < N; i += kThreads) {
-      const unsigned long long v = ysh[i];
-      if (v) red_add(a.yacc + i, v);  // integer sums: exact in any order
-    }
     if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
   }
   if (tid == 0) {
@@ -554,17 +542,18 @@ __global__ void k_make_lattice(int n, const float *__restrict__ pad, int rows, i
   }
 }
 
-// y_j = yacc[j] / scale + d_j s_j (yacc in the rotated layout), and yacc back
-// to zero for the next apply
-__global__ void k_disp_reduce(long N, int n, int rot, int op, unsigned long long *__restrict__ yacc,
+// y_j = (both sums of j) / scale + d_j s_j, and yacc back to zero for the
+// next apply.  yacc holds N sums with x fastest, then N with y fastest.
+__global__ void k_disp_reduce(long N, int n, int op, unsigned long long *__restrict__ yacc,
                               const double *__restrict__ scale, const double *__restrict__ diag,
                               const double *__restrict__ ss, const double *__restrict__ g,
                               double *__restrict__ y) {
   const double inv = 1.0 / *scale;
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
-    const long js = yslot((int)(j % n), (int)(j / n), n, rot);
-    const unsigned long long acc = yacc[js];
-    yacc[js] = 0ull;
+    const long jt = N + (j % n) * n + j / n;
+    const unsigned long long acc = yacc[j] + yacc[jt];
+    yacc[j] = 0ull;
+    yacc[jt] = 0ull;
     const double sj = op == VIE_OP_A_RAW ? g[j] : ss[j] * g[j];
     const double v = (double)(long long)acc * inv + diag[j] * sj;
     y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
@@ -672,9 +661,18 @@ Plan chunk_plan(const std::vector<int> &starts) {
 
 }  // namespace
 
+// the expansion's sheared tile: 2 n - 1 diagonals of n + 2 floats
+static size_t expand_smem_bytes(int n) { return sizeof(float) * (size_t)(2 * n - 1) * (n + 2); }
+
+bool disp_expand_fits(int n, int device) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
+  return expand_smem_bytes(n) <= (size_t)optin;
+}
+
 size_t disp_smem_bytes(int n) {
-  const long rows = n + 1 + kPad, N = (long)n * n;
-  return sizeof(float) * (size_t)rows * disp_ldp(n) + sizeof(unsigned long long) * (size_t)(N + (N & 1)) + 16;
+  const long rows = n + 1 + kPad;
+  return sizeof(float) * (size_t)rows * disp_ldp(n) + 16;
 }
 
 namespace {
@@ -838,7 +836,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   // the store and stream kernels of the displacement-major operator
   const long N = (long)n * n;
   const size_t smem_store = sizeof(float) * (size_t)rows * ldp + 16;
-  const size_t smem_stream = sizeof(unsigned long long) * (size_t)(N + (N & 1)) + 16;
+  const size_t smem_stream = 16;
   DispKernel ks = pick_store(ldp);
   VIE_CUDA(cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_store));
   VIE_CUDA(cudaFuncSetAttribute((const void *)k_stream_disp, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -869,8 +867,8 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
   VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
   VIE_CUDA(cudaMalloc((void **)&dp->ss32, sizeof(float) * (size_t)n * n));
-  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * (size_t)n * n));
-  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * (size_t)n * n));
+  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)n * n));
+  VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * 2 * (size_t)n * n));
   // every row sum of A is below sum over all nonzero displacements of h / (2 pi r)
   double rb = 0.0;
   for (int dy = -(n - 1); dy < n; ++dy)
@@ -878,7 +876,6 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
       if (dx || dy) rb += 1.0 / sqrt((double)dx * dx + (double)dy * dy);
   dp->rbound = rb / (2.0 * kPi * n);
   dp->n = n;
-  dp->rot = (n & 1) ? 2 : 1;  // n + rot odd
   dp->lat_elems = lat_elems;
   dp->ldp = ldp;
   dp->smem = smem;
@@ -889,7 +886,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   dp->grid_store = bps_store * prop.multiProcessorCount;
   dp->kernel_stream = (const void *)k_stream_disp;
   dp->smem_stream = smem_stream;
-  dp->grid_stream = std::min(bps_stream * prop.multiProcessorCount, dp->grid);  // partial slots: grid
+  dp->grid_stream = std::min(bps_stream * prop.multiProcessorCount, dp->grid);
   dp->stored = N * (N - 1) / 2;
   dp->usable = 1;
   return VIE_OK;
@@ -940,7 +937,7 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
   }
   cudaDeviceProp prop;
   VIE_CUDA(cudaGetDeviceProperties(&prop, device));
-  const size_t smem = sizeof(float) * (size_t)(2 * n - 1) * (n + 2);
+  const size_t smem = expand_smem_bytes(n);
   if (smem > (size_t)prop.sharedMemPerBlockOptin) {
     set_error("vie_assemble: grid too large for the pair-weight expansion");
     return VIE_ERR_UNSUPPORTED;
@@ -966,6 +963,7 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
   return VIE_OK;
 }
 
+int symv_max_n() { return 32 * kSymvCols; }
 size_t symv_block_floats(int n) { return (size_t)n * (n + 1) / 2 * n * n; }
 size_t symv_partial_floats(int n) { return (size_t)n * (n + 1) / 2 * 2 * n; }
 
@@ -991,8 +989,8 @@ vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, con
 vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *diag, const double *sigma_s,
                        const double *g, double *y, cudaStream_t st) {
   const int blocks = (int)std::min((N + 255) / 256, 4096L);
-  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, dp.rot, op, (unsigned long long *)dp.yacc, dp.scale, diag,
-                                        sigma_s, g, y);
+  k_disp_reduce<<<blocks, 256, 0, st>>>(N, dp.n, op, (unsigned long long *)dp.yacc, dp.scale, diag, sigma_s,
+                                        g, y);
   VIE_CHECK_LAUNCH("k_disp_reduce");
   return VIE_OK;
 }
@@ -1005,7 +1003,6 @@ DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, con
   a.stencil = (const float4 *)dp.stencil;
   a.src = src;
   a.src_t = dp.src_t;
-  a.rot = dp.rot;
   a.smax = dp.smax;
   a.scale_out = dp.scale;
   a.rbound = dp.rbound;

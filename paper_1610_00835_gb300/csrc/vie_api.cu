@@ -636,9 +636,10 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
   if (mode == VIE_OPERATOR_SYM32) {
     // A in the symmetric blocks of grid-row pairs: the pair weights, expanded
-    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2) {
-      set_error("vie_assemble: VIE_OPERATOR_SYM32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
-                "n <= 133)");
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2 || !disp_expand_fits(h->n, h->device) ||
+        h->n > symv_max_n()) {
+      set_error("vie_assemble: VIE_OPERATOR_SYM32 needs the displacement kernel, its expansion and the "
+                "block product (2D, FP32 tiles, S = 64, n <= 160)");
       return VIE_ERR_UNSUPPORTED;
     }
     if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * symv_block_floats(h->n)));
@@ -659,7 +660,7 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     // every unordered pair's FP32 weight, displacement-major (the displacement kernel's march)
     if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2) {
       set_error("vie_assemble: VIE_OPERATOR_PAIRS32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
-                "n <= 133)");
+                "n <= 226)");
       return VIE_ERR_UNSUPPORTED;
     }
     if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * (size_t)h->disp.stored));
@@ -671,7 +672,10 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     h->asm_mode = mode;
     return VIE_OK;
   }
-  const bool disp2 = h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 2;
+  // dense K from the displacement kernel's pair weights where the expansion
+  // has room for the grid, else from the tile-pair assembler
+  const bool disp2 =
+      h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 2 && disp_expand_fits(h->n, h->device);
   if ((!h->sym.usable && !disp2) || h->opts.precision != VIE_PREC_FP32 ||
       h->opts.tau_mode != VIE_TAU_MARCH || h->opts.steps != 64) {
     set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "

@@ -100,11 +100,11 @@ vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale
 struct DispPlan {
   int usable = 0;
   long n_units = 0, lat_elems = 0;
-  int ldp = 0, grid = 0, n = 0, rot = 1;
+  int ldp = 0, grid = 0, n = 0;
   size_t smem = 0;
   float *src_t = nullptr;     // s transposed (FP32 [N])
   float *ss32 = nullptr;      // sigma_s in FP32 (for the expansion into K)
-  void *yacc = nullptr;       // int64 [N]: the CTAs' fixed-point sums, zero between applies
+  void *yacc = nullptr;       // int64 [2 N]: fixed-point sums (x fastest, then y fastest), zero between applies
   void *geometry = nullptr;   // shared stencils and units of this n (owned by a cache)
   void *units = nullptr;
   void *stencil = nullptr;    // per-displacement chunk records (float4)
@@ -146,6 +146,7 @@ vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const
                        cudaStream_t st);
 
 size_t disp_smem_bytes(int n);
+bool disp_expand_fits(int n, int device);  // k_expand_pairs has room for the grid (n <= 169)
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st);
 vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *diag, const double *sigma_s,
@@ -155,6 +156,7 @@ void disp_release(DispPlan *dp);
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
                        cudaStream_t st);
 vie_status disp_store(const DispPlan &dp, int n, float tau_scale2, float wcoef, float *wbuf, cudaStream_t st);
+int symv_max_n();  // largest grid the symmetric-block product takes (160)
 size_t symv_block_floats(int n);
 size_t symv_partial_floats(int n);
 vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, const float *blocks, float *s,

@@ -112,9 +112,9 @@ def test_2d_every_pair_kernel_all_rows(kernel, n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [100, 128, 133])
+@pytest.mark.parametrize("n", [100, 128, 133, 226])
 def test_displacement_kernel_full_size_sampled_rows(n):
-    # 133 is the largest grid whose lattice and fixed-point y fit one SM
+    # 226 is the largest grid whose lattice fits one SM's shared memory
     m = V.bump_medium(2, n, 4, 0.9, seed=4300 + n)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
     assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
@@ -128,9 +128,9 @@ def test_displacement_kernel_full_size_sampled_rows(n):
 
 
 def test_displacement_kernel_falls_back_beyond_shared_memory():
-    # n = 136 does not fit one SM's shared memory: the handle takes the
+    # n = 227 does not fit one SM's shared memory: the handle takes the
     # tile-pair kernel and still matches the oracle
-    n = 136
+    n = 227
     m = V.bump_medium(2, n, 4, 0.9, seed=4436)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
     assert P.vie_get_kernel(h) == P.VIE_KERNEL_SYMMETRIC

@@ -95,7 +95,7 @@ def test_gmres_with_assembled_operator(mode):
     np.testing.assert_array_equal(U2, U_otf)
 
 
-@pytest.mark.parametrize("n", [2, 3, 9, 37, 64, 128, 133])
+@pytest.mark.parametrize("n", [2, 3, 9, 37, 64, 128, 133, 226])
 def test_pairs32_bitwise_equal_to_on_the_fly(n):
     # the stored weights are the on-the-fly kernel's FP32 weights and the
     # accumulation is the same exact fixed-point sum: identical results
@@ -134,8 +134,8 @@ def test_pairs32_unsupported_without_the_displacement_kernel(case, mode):
         m = V.heterogeneous_2d(n=16)
         h = P.vie_create(2, 16, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
     else:
-        m = V.heterogeneous_2d(n=136)
-        h = P.vie_create(2, 136, m.sigma_t, m.sigma_s)
+        m = V.heterogeneous_2d(n=227)
+        h = P.vie_create(2, 227, m.sigma_t, m.sigma_s)
     with pytest.raises(P.VieError) as e:
         P.vie_assemble(h, mode)
     assert e.value.status == P.vie.VIE_ERR_UNSUPPORTED
@@ -144,7 +144,7 @@ def test_pairs32_unsupported_without_the_displacement_kernel(case, mode):
     assert np.all(np.isfinite(y))
 
 
-@pytest.mark.parametrize("n", [16, 128, 133])
+@pytest.mark.parametrize("n", [16, 128, 133, 160])
 def test_sym32_full_size_rows_and_symmetry(n):
     # the symmetric blocks against the oracle on sampled rows at full sizes, and
     # against the dense FP32 K applied to the same vector
@@ -162,3 +162,26 @@ def test_sym32_full_size_rows_and_symmetry(n):
     P.vie_assemble(h, P.VIE_OPERATOR_SYM32)
     again = _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]
     np.testing.assert_array_equal(again, got)  # fixed summation order
+
+
+def test_past_the_expansion_dense_k_comes_from_the_tile_assembler():
+    # n = 170: the displacement kernel and the pair weights still apply, the
+    # symmetric blocks are refused (past n = 160, and their expansion has no
+    # room), and dense K is assembled by the tile-pair assembler instead
+    n = 170
+    m = V.bump_medium(2, n, 4, 0.9, seed=4670)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
+    g = m.f + 0.05 * np.random.default_rng(n).standard_normal(m.N)
+    otf = _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]
+    with pytest.raises(P.VieError) as e:
+        P.vie_assemble(h, P.VIE_OPERATOR_SYM32)
+    assert e.value.status == P.vie.VIE_ERR_UNSUPPORTED
+    P.vie_assemble(h, P.VIE_OPERATOR_PAIRS32)
+    np.testing.assert_array_equal(_apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0], otf)
+    P.vie_assemble(h, P.VIE_OPERATOR_FP32)
+    dense = _apply(h, P.VIE_OP_K_SIGMA_S, g, 1)[0]
+    assert rel_l2(dense, otf) < 2e-6
+    rows = np.unique(np.concatenate([np.random.default_rng(n + 1).choice(m.N, 8, replace=False), [0, m.N - 1]]))
+    want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+    assert rel_l2(dense[rows], want) < TOL
