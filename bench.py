@@ -399,6 +399,7 @@ def measure_other_configs(P, torch, local, reps=3):
     U3 = torch.empty_like(f3)
     y3 = torch.empty_like(f3)
     ms_apply, _ = timed(lambda: P.vie_apply(h3, P.VIE_OP_K_SIGMA_S, f3, y3, 1))
+    work3 = P.vie_get_kernel_work(h3)   # multiply-adds of the tau sums per apply
     ms3, rep3 = timed(lambda: P.vie_solve_gmres(h3, f3, U3, rtol=RTOL))
     M = 128
     dirs = torch.as_tensor(V.fibonacci_directions(M).astype(np.float32), device=dev)  # [M, 3]
@@ -409,6 +410,8 @@ def measure_other_configs(P, torch, local, reps=3):
                                        "iters": rep1["iters"], "relres": rep1["relres"]},
             "heterogeneous_32x32x32": {"N": m3.N, "apply_ms": ms_apply,
                                        "apply_gpair_per_s": float(m3.N) * m3.N / ms_apply / 1e6,
+                                       "tau_multiply_adds": work3,
+                                       "apply_tflops": 2.0 * work3 / ms_apply / 1e9,
                                        "solve_ms": ms3, "iters": rep3["iters"], "relres": rep3["relres"],
                                        "sweep_directions": M, "sweep_ms": ms_sweep,
                                        "sweep_rays_per_s": M * m3.N / ms_sweep * 1e3}}
