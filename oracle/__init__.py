@@ -20,6 +20,7 @@ import numpy as np
 from . import build as _build
 
 TAU_MARCH, TAU_CLOSED, TAU_EXACT = 0, 1, 2
+DISC_MII = 16   # or'ed into `mode`: approach M-ii (2D) instead of M-iii
 OP_K_SIGMA_S, OP_I_MINUS_K, OP_A_RAW = 0, 1, 2
 
 _lib = None
@@ -38,6 +39,8 @@ def lib():
         L.or_tau_march.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, C.c_int]
         L.or_tau_exact.restype = C.c_double
         L.or_tau_exact.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+        L.or_cell_integral2.restype = C.c_double
+        L.or_cell_integral2.argtypes = [C.c_double, C.c_double, C.c_double]
         L.or_selfcell.restype = C.c_double
         L.or_selfcell.argtypes = [C.c_int, C.c_double, C.c_double]
         L.or_entry.restype = C.c_double
@@ -107,6 +110,11 @@ def tau_exact(dim, sigma, x, y):
     return lib().or_tau_exact(dim, dim_n(s, dim), sp, ap, bp)
 
 
+def cell_integral2(t1, t2, h):
+    """int over the square of side h centred at (t1, t2) of |z|^{-1} dz (2D)."""
+    return lib().or_cell_integral2(float(t1), float(t2), float(h))
+
+
 def selfcell(dim, h, sigma):
     return lib().or_selfcell(dim, float(h), float(sigma))
 
@@ -124,7 +132,8 @@ def entry(dim, sigma_t, j, k, mode=TAU_MARCH, S=64):
 
 
 def assemble(dim, sigma_t, mode=TAU_MARCH, S=64):
-    """Dense A (N x N): off-diagonal M-iii weights, self-cell diagonal."""
+    """Dense A (N x N): off-diagonal M-iii weights and self-cell diagonal, or
+    every entry by M-ii when ``mode`` carries DISC_MII."""
     s, sp = _d(sigma_t)
     N = s.size
     A = np.empty((N, N), dtype=np.float64)

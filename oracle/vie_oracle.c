@@ -27,6 +27,11 @@
  *               j == k:  d_j = int_{T_j} exp(-sigma_t,j |z|)/(|S^{d-1}||z|^{d-1}) dz
  *               (self cell computed explicitly, sigma frozen at the centre)
  *               |S^1| = 2 pi, |S^2| = 4 pi.
+ *               With the flag OR_DISC_MII in `mode` (2D only), approach
+ *               M-ii with the kernel of Remark REM: NEW KERNEL instead:
+ *               A_jk = exp(-tau_jk) / (2 pi) int_{T_k} |x_j - z|^{-1} dz for
+ *               every j and k (tau_jj = 0), the cell integral in the
+ *               closed form of that remark.
  *   K_jk      : A_jk sigma_s,k       (the matrix [K_jk omega_k] of
  *               Eq. EQ: LINEAR SYSTEM; omega_k = h^d is inside A).
  *   phi       : A f  (Eq. EQ:ERT Intgrl FMM: phi = K(mu_s^{-1} f); the
@@ -53,6 +58,8 @@
 #define OR_PI 3.14159265358979323846
 
 enum { OR_TAU_MARCH = 0, OR_TAU_CLOSED = 1, OR_TAU_EXACT = 2 };
+/* `mode` = tau mode | OR_DISC_MII (discretisation M-ii instead of M-iii) */
+enum { OR_TAU_MASK = 15, OR_DISC_MII = 16 };
 enum { OR_OP_K_SIGMA_S = 0, OR_OP_I_MINUS_K = 1, OR_OP_A_RAW = 2 };
 
 int or_num_threads(void) {
@@ -267,18 +274,47 @@ static double sphere_area(int dim) { return dim == 2 ? 2.0 * OR_PI : 4.0 * OR_PI
 
 static double tau_of(int dim, int n, const double *st, int mode, int S,
                      const double *x, const double *y) {
+  mode &= OR_TAU_MASK;
   if (mode == OR_TAU_CLOSED) return st[0] * dist(dim, x, y);
   if (mode == OR_TAU_EXACT) return or_tau_exact(dim, n, st, x, y);
   return or_tau_march(dim, n, st, x, y, S);
 }
 
-/* A_jk: off-diagonal M-iii weight h^d e^{-tau}/(|S| r^{d-1}); the diagonal is
- * the self-cell value d_j. */
+/* F(r, s) of Remark REM: NEW KERNEL (Section 3.2): an antiderivative of
+ * 1/sqrt(r^2 + s^2) in r and in s, odd in each argument.  It vanishes where
+ * r = 0 or s = 0 (the sign factors), which also covers the r log r terms. */
+static double paper_F(double r, double s) {
+  if (r == 0.0 || s == 0.0) return 0.0;
+  double ar = fabs(r), as = fabs(s), rho = sqrt(r * r + s * s);
+  double v = ar * log(as + rho) + as * log(ar + rho) - ar * log(ar) - as * log(as);
+  return ((r > 0) == (s > 0)) ? v : -v;
+}
+
+/* int over the square of side h centred at t = (t1, t2) of |z|^{-1} dz: the
+ * four-corner sum of F in the remark (2D). */
+double or_cell_integral2(double t1, double t2, double h) {
+  double acc = 0.0;
+  for (int i = -1; i <= 1; i += 2)
+    for (int jj = -1; jj <= 1; jj += 2)
+      acc += i * jj * paper_F(t1 + i * 0.5 * h, t2 + jj * 0.5 * h);
+  return acc;
+}
+
+/* A_jk.  M-iii: off-diagonal weight h^d e^{-tau}/(|S| r^{d-1}), the diagonal
+ * the self-cell value d_j.  M-ii (2D): e^{-tau} / (2 pi) times the cell
+ * integral of |x_j - z|^{-1} over T_k, the same formula on the diagonal. */
 double or_entry(int dim, int n, const double *st, int mode, int S, long j,
                 long k) {
   double h = 1.0 / n;
-  if (j == k) return or_selfcell(dim, h, st[j]);
   double x[3], y[3];
+  if (mode & OR_DISC_MII) {
+    if (dim != 2) return NAN;
+    centre(dim, n, j, x);
+    centre(dim, n, k, y);
+    double tau = j == k ? 0.0 : tau_of(dim, n, st, mode, S, x, y);
+    return exp(-tau) * or_cell_integral2(y[0] - x[0], y[1] - x[1], h) / sphere_area(dim);
+  }
+  if (j == k) return or_selfcell(dim, h, st[j]);
   centre(dim, n, j, x);
   centre(dim, n, k, y);
   double r = dist(dim, x, y);
@@ -298,11 +334,21 @@ void or_selfcells(int dim, int n, const double *st, double *d) {
   for (long j = 0; j < N; ++j) d[j] = or_selfcell(dim, h, st[j]);
 }
 
+/* Diagonal A_jj of the discretisation `mode` for every cell. */
+static void diagonal(int dim, int n, const double *st, int mode, double *d) {
+  if (!(mode & OR_DISC_MII)) {
+    or_selfcells(dim, n, st, d);
+    return;
+  }
+  long N = npow(n, dim);
+  for (long j = 0; j < N; ++j) d[j] = or_entry(dim, n, st, mode, 64, j, j);
+}
+
 /* Dense A (N x N, row-major, A[j*N + k]). */
 void or_assemble(int dim, int n, const double *st, int mode, int S, double *A) {
   long N = npow(n, dim);
   double *d = (double *)malloc(sizeof(double) * N);
-  or_selfcells(dim, n, st, d);
+  diagonal(dim, n, st, mode, d);
 #pragma omp parallel for schedule(dynamic, 4)
   for (long j = 0; j < N; ++j)
     for (long k = 0; k < N; ++k)
@@ -314,7 +360,8 @@ void or_assemble(int dim, int n, const double *st, int mode, int S, double *A) {
  *   op K_SIGMA_S : y_j = sum_k A_jk sigma_s,k g_k
  *   op I_MINUS_K : y_j = g_j - sum_k A_jk sigma_s,k g_k
  *   op A_RAW     : y_j = sum_k A_jk g_k          (phi = A f)
- * `diag` may hold precomputed d_j (NULL: computed here per row). */
+ * `diag` may hold precomputed d_j (NULL: computed here per row); M-ii
+ * ignores it and takes every entry, the diagonal included, from or_entry. */
 void or_apply(int dim, int n, const double *st, const double *ss, int mode,
               int S, int op, const double *diag, const double *g,
               const long *rows, long nrows, double *y) {
@@ -326,8 +373,9 @@ void or_apply(int dim, int n, const double *st, const double *ss, int mode,
     long j = rows ? rows[r] : r;
     double acc = 0.0;
     for (long k = 0; k < N; ++k) {
-      double a = (k == j) ? (diag ? diag[j] : or_selfcell(dim, h, st[j]))
-                          : or_entry(dim, n, st, mode, S, j, k);
+      double a = (k == j && !(mode & OR_DISC_MII))
+                     ? (diag ? diag[j] : or_selfcell(dim, h, st[j]))
+                     : or_entry(dim, n, st, mode, S, j, k);
       double s = (op == OR_OP_A_RAW) ? 1.0 : ss[k];
       acc += a * s * g[k];
     }
@@ -383,7 +431,7 @@ int or_gmres(int dim, int n, const double *st, const double *ss, int mode,
   double *diag = NULL;
   if (!dense) {
     diag = (double *)malloc(sizeof(double) * N);
-    or_selfcells(dim, n, st, diag);
+    diagonal(dim, n, st, mode, diag);
     c.diag = diag;
   }
   double *V = (double *)malloc(sizeof(double) * N * (m + 1));

@@ -237,6 +237,91 @@ def test_row_sum_gaussian_weight_closed_form(dim, sizes):
     assert errs[-1] < 1.5 / sizes[-1]
 
 
+# ------------------------------------------------- M-ii (Remark REM: NEW KERNEL)
+
+@pytest.mark.parametrize("h", [1 / 64, 0.1, 0.5])
+def test_mii_cell_integral_centre_closed_form(h):
+    # int_{[-a,a]^2} |z|^{-1} dz = 8 a ln(1 + sqrt 2) (polar integral over the
+    # eight triangles of the square), a = h / 2
+    assert O.cell_integral2(0.0, 0.0, h) == pytest.approx(4 * h * math.log(1 + math.sqrt(2)), rel=1e-13)
+
+
+def _gauss_legendre_cell(t1, t2, h, sub=8, q=16):
+    # composite tensor Gauss-Legendre quadrature of |z|^{-1} over the square of
+    # side h centred at (t1, t2) (smooth there: the square avoids the origin)
+    x, wq = np.polynomial.legendre.leggauss(q)
+    edges = np.linspace(-h / 2, h / 2, sub + 1)
+    pts, wts = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        pts.append((a + b) / 2 + (b - a) / 2 * x)
+        wts.append((b - a) / 2 * wq)
+    p, w = np.concatenate(pts), np.concatenate(wts)
+    zx, zy = np.meshgrid(t1 + p, t2 + p, indexing="ij")
+    return float(np.sum(np.outer(w, w) / np.hypot(zx, zy)))
+
+
+@pytest.mark.parametrize("t", [(1, 0), (0, -1), (1, 1), (-2, 1), (5, -3), (0, 7)])
+def test_mii_cell_integral_against_quadrature(t):
+    h = 0.1
+    t1, t2 = t[0] * h, t[1] * h
+    assert O.cell_integral2(t1, t2, h) == pytest.approx(_gauss_legendre_cell(t1, t2, h), rel=1e-11)
+
+
+def test_mii_cell_integral_far_field_expansion():
+    # the cell average of 1/|t + z| is 1/|t| + (h^2/24) Laplacian(1/|t|) + O(|t|^-5),
+    # and in 2D Laplacian(1/r) = 1/r^3: after the two leading terms the rest
+    # falls like |t|^-5
+    h = 0.01
+    rest = []
+    for m in (10, 20, 40):
+        t1, t2 = 0.6 * m * h, 0.8 * m * h
+        r = m * h
+        rest.append(O.cell_integral2(t1, t2, h) - h * h * (1 / r + h * h / (24 * r ** 3)))
+    assert rest[0] / rest[1] == pytest.approx(32, rel=0.15)
+    assert rest[1] / rest[2] == pytest.approx(32, rel=0.15)
+
+
+def test_mii_reciprocity_and_diagonal():
+    # A_jk = A_kj (the cell integral is even in t, tau symmetric); the diagonal
+    # is the cell integral at t = 0 over 2 pi, i.e. the self cell without
+    # attenuation
+    n = 7
+    st = V.bump_medium(2, n, 3, 0.9, seed=71).sigma_t
+    A = O.assemble(2, st, mode=O.TAU_MARCH | O.DISC_MII)
+    np.testing.assert_allclose(A, A.T, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(np.diag(A), O.selfcell(2, 1 / n, 0.0), rtol=1e-13)
+
+
+def test_mii_row_sum_gaussian_weight_second_order():
+    # The Gaussian-weight closed form of the M-iii test above: M-ii converges
+    # at the h^2 (1 + log h) rate that Eq. EQ: ERROR states for it
+    sigma, w = 1.1, 0.08
+    want = w * math.sqrt(math.pi / 2) * math.exp(sigma ** 2 * w ** 2 / 2) * math.erfc(
+        sigma * w / math.sqrt(2))
+    sizes = (41, 81, 161)
+    errs = []
+    for n in sizes:
+        st = np.full(n * n, sigma)
+        xs = V.cell_centres(2, n)
+        c = n * n // 2
+        g = np.exp(-np.sum((xs - xs[c]) ** 2, axis=1) / (2 * w * w))
+        got = O.apply(2, st, st, g, op=O.OP_A_RAW, mode=O.TAU_CLOSED | O.DISC_MII, rows=[c])[0]
+        errs.append(abs(got - want) / want)
+    order = math.log(errs[-2] / errs[-1]) / math.log(sizes[-1] / sizes[-2])
+    assert 1.6 < order < 2.3
+    assert errs[-1] < 7 / sizes[-1] ** 2 < errs[0]
+
+
+def test_mii_gmres_matches_lu():
+    n = 9
+    m = V.bump_medium(2, n, 3, 0.9, seed=72)
+    mode = O.TAU_MARCH | O.DISC_MII
+    phi = O.apply(2, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW, mode=mode)
+    U, it, rr, ok = O.gmres(2, m.sigma_t, m.sigma_s, phi, rtol=1e-12, mode=mode)
+    assert ok
+    np.testing.assert_allclose(U, O.lu_solve(2, m.sigma_t, m.sigma_s, phi, mode=mode), rtol=1e-9, atol=0)
+
+
 def test_sigma_s_zero_is_pure_absorption():
     # sigma_s = 0: K = 0 and U = phi; GMRES stops at once.
     m = V.heterogeneous_2d(n=12)
