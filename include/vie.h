@@ -29,7 +29,10 @@
  *   - A_jk = h^d exp(-tau_jk) / (|S^{d-1}| r_jk^{d-1}) for j != k and the
  *     self-cell integral d_j = int_{T_j} e^{-sigma_t,j |z|} / (|S^{d-1}|
  *     |z|^{d-1}) dz for j == k; K_jk = A_jk sigma_s,k.  |S^1| = 2 pi,
- *     |S^2| = 4 pi.
+ *     |S^2| = 4 pi.  With VIE_DISC_MII (2D): approach M-ii of Section 3.2
+ *     with the kernel of Remark REM: NEW KERNEL instead,
+ *     A_jk = exp(-tau_jk) / (2 pi) int_{T_k} |x_j - z|^{-1} dz for every j
+ *     and k (tau_jj = 0), the cell integral in closed form.
  *   - Every call returns a vie_status; on failure vie_last_error() gives a
  *     message (thread-local).  No C++ exception crosses this boundary.
  *   - Vectors (g, y, f, U, Phi) may be host or device pointers; the library
@@ -69,6 +72,12 @@ typedef struct {
 
 enum { VIE_TAU_MARCH = 0, VIE_TAU_CLOSED = 1 };
 enum { VIE_PREC_FP32 = 0, VIE_PREC_FP64 = 1 };
+/* Discretisation of Section 3.2: M-iii (collocation, the default), or M-ii
+ * (the cell integral of |x_j - z|^{1-d} exact, Remark REM: NEW KERNEL; error
+ * O(h^2 (1 + log h)) against O(h), Eq. EQ: ERROR).  M-ii is built for 2D
+ * grids with FP32 tiles, the S = 64 march and the displacement kernel
+ * (n <= 226); other combinations return VIE_ERR_UNSUPPORTED at create. */
+enum { VIE_DISC_MIII = 0, VIE_DISC_MII = 1 };
 
 typedef struct {
   int steps;     /* S, midpoint-march steps for tau (>= 1; 64 by default)   */
@@ -79,6 +88,7 @@ typedef struct {
   int kernel;    /* pair kernel for FP32 tiles: VIE_KERNEL_AUTO picks the
                     fastest that applies; the others force one (a forced
                     kernel that does not apply falls back to AUTO)         */
+  int disc;      /* VIE_DISC_MIII (default) or VIE_DISC_MII                  */
 } vie_opts;
 
 enum {
@@ -88,7 +98,8 @@ enum {
   VIE_KERNEL_GENERAL = 3        /* every ordered pair; any S                  */
 };
 
-/* Default options: S = 64, march, FP32 tiles, device 0, automatic kernel. */
+/* Default options: S = 64, march, FP32 tiles, device 0, automatic kernel,
+ * M-iii. */
 void vie_default_opts(vie_opts *o);
 
 typedef struct vie_handle vie_handle;
@@ -101,7 +112,8 @@ typedef struct vie_handle vie_handle;
  * Both arrays are copied; the caller keeps ownership.  The self-cell
  * diagonal d_j is computed on the device here (FP64 Gauss-Legendre).
  * Errors: INVALID_ARG (sizes, negative coefficient, non-constant sigma_t
- * with VIE_TAU_CLOSED), NONFINITE, OOM, CUDA. */
+ * with VIE_TAU_CLOSED, unknown disc), UNSUPPORTED (VIE_DISC_MII outside its
+ * combination), NONFINITE, OOM, CUDA. */
 vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t,
                       const double *sigma_s, const vie_opts *o);
 
@@ -254,7 +266,7 @@ typedef struct vie_batch vie_batch;
 
 /* Create a batch of `count` 2D media (grids[i].dim == 2), each with its own
  * n and host FP64 coefficients sigma_t[i], sigma_s[i] (copied).  Options must
- * be FP32 tiles with the S = 64 march.  Vectors of the batch are packed:
+ * be FP32 tiles with the S = 64 march and M-iii.  Vectors of the batch are packed:
  * medium i occupies cells [offsets[i], offsets[i+1]) (vie_batch_layout).
  * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
 vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,

@@ -4,8 +4,8 @@ two-step radiative-transfer method of Ren, Zhang & Zhong (arXiv 1610.00835).
 The compute lives in ``libvie.so`` (CUDA, built from ``csrc/``); this package
 is its ctypes binding.  See ``include/vie.h`` for the C ABI.
 """
-from .vie import (VIE_KERNEL_AUTO, VIE_KERNEL_DISPLACEMENT, VIE_KERNEL_GENERAL,
-                  VIE_KERNEL_SYMMETRIC)
+from .vie import (VIE_DISC_MII, VIE_DISC_MIII, VIE_KERNEL_AUTO, VIE_KERNEL_DISPLACEMENT,
+                  VIE_KERNEL_GENERAL, VIE_KERNEL_SYMMETRIC)
 from .vie import (VieUnet, vie_set_preconditioner, vie_unet_create, vie_unet_destroy,
                   vie_unet_forward, vie_unet_get_params, vie_unet_load, vie_unet_loss_grad,
                   vie_unet_num_params, vie_unet_save, vie_unet_set_params, vie_unet_train_step)
@@ -16,7 +16,7 @@ from .vie import (VIE_OPERATOR_BF16X3, VIE_OPERATOR_FP32, VIE_OPERATOR_PAIRS32, 
                   load, vie_apply, vie_apply_noalloc, vie_get_kernel, vie_get_kernel_work, vie_assemble, vie_create, vie_destroy, vie_get_diagonal, vie_last_error,
                   vie_kernel_launches, vie_solve_gmres, vie_version)
 
-__all__ = ["VIE_KERNEL_AUTO", "VIE_KERNEL_DISPLACEMENT", "VIE_KERNEL_GENERAL",
+__all__ = ["VIE_DISC_MII", "VIE_DISC_MIII", "VIE_KERNEL_AUTO", "VIE_KERNEL_DISPLACEMENT", "VIE_KERNEL_GENERAL",
            "VIE_KERNEL_SYMMETRIC", "VieUnet", "vie_set_preconditioner", "vie_unet_create", "vie_unet_destroy",
            "vie_unet_forward", "vie_unet_get_params", "vie_unet_load", "vie_unet_loss_grad",
            "vie_unet_num_params", "vie_unet_save", "vie_unet_set_params", "vie_unet_train_step",

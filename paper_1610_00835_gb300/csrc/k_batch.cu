@@ -383,8 +383,9 @@ vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
   vie_opts opts;
   vie_default_opts(&opts);
   if (o) opts = *o;
-  if (opts.steps != 64 || opts.tau_mode != VIE_TAU_MARCH || opts.precision != VIE_PREC_FP32)
-    return bad("vie_batch_create: the batch supports FP32 tiles with the S = 64 march");
+  if (opts.steps != 64 || opts.tau_mode != VIE_TAU_MARCH || opts.precision != VIE_PREC_FP32 ||
+      opts.disc != VIE_DISC_MIII)
+    return bad("vie_batch_create: the batch supports FP32 tiles with the S = 64 march and M-iii");
   for (int i = 0; i < count; ++i) {
     if (grids[i].dim != 2 || grids[i].n < 1 || grids[i].n > 4096)
       return bad("vie_batch_create: 2D grids with 1 <= n <= 4096");

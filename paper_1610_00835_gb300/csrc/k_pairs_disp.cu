@@ -81,6 +81,8 @@ struct DispArgs {
   const float4 *stencil;       // run records of every W_D
   const float *src;            // s_k, FP32 [N]
   const float *src_t;          // s transposed: s at (x, y) is src_t[x n + y]
+  const float *wtab;           // M-ii: h / (2 pi) times the cell integral of 1/|z| per D
+                               // of the half plane (disp_index order); null for M-iii
   unsigned *smax;              // bits of max |s_k| (set by the source kernel)
   double *scale_out;           // fixed-point scale of this apply (for the reduce)
   double rbound;               // bound on sum_k A_jk for every j
@@ -192,7 +194,9 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     const float r2 = (float)(dx * dx + dy * dy);
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
-    const float wk = a.wcoef * inv_r;
+    // M-iii: h^2 / (2 pi r) = (h / 2 pi) / |D|; M-ii: the closed-form cell
+    // integral of |x_j - z|^{-1} over T_k (Remark REM: NEW KERNEL), per D
+    const float wk = a.wtab ? __ldg(a.wtab + disp_index(dx, dy, n)) : a.wcoef * inv_r;
     // stored weights of D: its rectangle of targets, row-major (lanes along x
     // write 128 contiguous bytes; lanes along y each write their 8 targets)
     long woff = 0;
@@ -820,6 +824,48 @@ void geometry_release(Geometry *g) {
 
 }  // namespace
 
+// Integral of 1/|z| over the unit square centred at (t1, t2).  The function
+// P(u, v) = u asinh(v / |u|) + v asinh(u / |v|) (0 where u or v is 0) has
+// d2P/dudv = 1 / sqrt(u^2 + v^2) and is odd in u and in v, so the integral is
+// the signed sum of P over the square's corners: the closed form of Remark
+// REM: NEW KERNEL (its F written with asinh), in FP64.
+static double unit_cell_integral(double t1, double t2) {
+  auto P = [](double u, double v) {
+    if (u == 0.0 || v == 0.0) return 0.0;
+    return u * asinh(v / fabs(u)) + v * asinh(u / fabs(v));
+  };
+  double acc = 0.0;
+  for (int a = -1; a <= 1; a += 2)
+    for (int b = -1; b <= 1; b += 2) acc += a * b * P(t1 + 0.5 * a, t2 + 0.5 * b);
+  return acc;
+}
+
+vie_status disp_mii_prepare(DispPlan *dp, int n, double *diag_value, cudaStream_t st) {
+  // per D of the half plane in disp_index order: dy = 0, dx = 1 .. n - 1;
+  // then dy = 1 .. n - 1, dx = -(n - 1) .. n - 1.  A_jk = e^{-tau} times
+  // (h / 2 pi) G(D), G the unit-cell integral (it scales with h).
+  const double hh = 1.0 / n, c = hh / (2.0 * kPi);
+  std::vector<float> tab;
+  tab.reserve((size_t)(n - 1) + (size_t)(n - 1) * (2 * n - 1));
+  double rb = 0.0;  // bound on every row sum: all nonzero D of the full plane
+  for (int dx = 1; dx < n; ++dx) tab.push_back((float)(c * unit_cell_integral(dx, 0)));
+  for (int dy = 1; dy < n; ++dy)
+    for (int dx = -(n - 1); dx < n; ++dx) tab.push_back((float)(c * unit_cell_integral(dx, dy)));
+  for (int dy = -(n - 1); dy < n; ++dy)
+    for (int dx = -(n - 1); dx < n; ++dx)
+      if (dx || dy) rb += c * unit_cell_integral(dx, dy);
+  *diag_value = c * unit_cell_integral(0.0, 0.0);
+  if (dp->wtab) cudaFree((void *)dp->wtab);
+  dp->wtab = nullptr;
+  float *d = nullptr;
+  VIE_CUDA(cudaMalloc((void **)&d, sizeof(float) * tab.size()));
+  dp->wtab = d;
+  VIE_CUDA(cudaMemcpyAsync(d, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  dp->rbound = std::max(dp->rbound, rb);
+  return VIE_OK;
+}
+
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st) {
   dp->usable = 0;
   if (n < 2 || n > 4096) return VIE_OK;
@@ -901,6 +947,8 @@ void disp_release(DispPlan *dp) {
   if (dp->src_t) cudaFree(dp->src_t);
   if (dp->ss32) cudaFree(dp->ss32);
   if (dp->yacc) cudaFree(dp->yacc);
+  if (dp->wtab) cudaFree((void *)dp->wtab);
+  dp->wtab = nullptr;
   dp->yacc = nullptr;
   dp->ss32 = nullptr;
   dp->geometry = nullptr;
@@ -1011,6 +1059,7 @@ DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, con
   a.counter = dp.counter;
   a.wbuf = wbuf;
   a.doff = dp.doff;
+  a.wtab = dp.wtab;
   a.n_units = dp.n_units;
   a.n = n;
   a.ldp = dp.ldp;

@@ -402,6 +402,7 @@ void vie_default_opts(vie_opts *o) {
   o->precision = VIE_PREC_FP32;
   o->device = 0;
   o->kernel = VIE_KERNEL_AUTO;
+  o->disc = VIE_DISC_MIII;
 }
 
 void vie_default_gmres_opts(vie_gmres_opts *o) {
@@ -432,6 +433,7 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     return invalid("vie_create: unknown precision");
   if (opts.kernel < VIE_KERNEL_AUTO || opts.kernel > VIE_KERNEL_GENERAL)
     return invalid("vie_create: unknown kernel");
+  if (opts.disc != VIE_DISC_MIII && opts.disc != VIE_DISC_MII) return invalid("vie_create: unknown disc");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -516,6 +518,21 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
     h->use_kernel = VIE_KERNEL_SYMMETRIC;
   else
     h->use_kernel = VIE_KERNEL_GENERAL;
+  if (opts.disc == VIE_DISC_MII) {
+    // M-ii: the displacement kernel with per-D weights, and the diagonal
+    // (h / 2 pi) times the cell integral at t = 0 for every cell
+    if (g->dim != 2 || h->use_kernel != VIE_KERNEL_DISPLACEMENT) {
+      free_all(h);
+      delete h;
+      set_error("vie_create: VIE_DISC_MII needs a 2D grid with FP32 tiles, the S = 64 march and the "
+                "displacement kernel (n <= 226)");
+      return VIE_ERR_UNSUPPORTED;
+    }
+    double dval = 0.0;
+    TRY(disp_mii_prepare(&h->disp, g->n, &dval, st));
+    std::vector<double> dv((size_t)N, dval);
+    TRY(cpy(h->diag, dv.data(), sizeof(double) * N));
+  }
   {
     long slots = h->plan.splits;
     if (h->use_kernel == VIE_KERNEL_SYMMETRIC) slots = std::max<long>(slots, h->sym.T);
@@ -673,9 +690,13 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
     return VIE_OK;
   }
   // dense K from the displacement kernel's pair weights where the expansion
-  // has room for the grid, else from the tile-pair assembler
+  // has room for the grid, else from the tile-pair assembler (M-iii only)
   const bool disp2 =
       h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 2 && disp_expand_fits(h->n, h->device);
+  if (!disp2 && h->opts.disc == VIE_DISC_MII) {
+    set_error("vie_assemble: dense K with VIE_DISC_MII needs the pair-weight expansion (n <= 169)");
+    return VIE_ERR_UNSUPPORTED;
+  }
   if ((!h->sym.usable && !disp2) || h->opts.precision != VIE_PREC_FP32 ||
       h->opts.tau_mode != VIE_TAU_MARCH || h->opts.steps != 64) {
     set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "

@@ -122,6 +122,7 @@ struct DispPlan {
   int grid_store = 0, grid_stream = 0;
   long long stored = 0;       // weights stored: N (N - 1) / 2
   const long long *doff = nullptr;
+  const float *wtab = nullptr;  // M-ii: per-D weight (h / 2 pi) x cell integral; null for M-iii
 };
 // 3D displacement-major kernel (k_pairs_disp3.cu), grids up to 32^3
 struct DispPlan3 {
@@ -152,6 +153,9 @@ vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s
 vie_status disp_reduce(const DispPlan &dp, long N, int op, const double *diag, const double *sigma_s,
                        const double *g, double *y, cudaStream_t st);
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st);
+// M-ii (Remark REM: NEW KERNEL): the per-D weight table of the plan and the
+// diagonal value A_jj (the same for every cell); widens rbound to its row sums
+vie_status disp_mii_prepare(DispPlan *dp, int n, double *diag_value, cudaStream_t st);
 void disp_release(DispPlan *dp);
 vie_status disp_launch(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src,
                        cudaStream_t st);

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "VIE_OK", 1: "VIE_ERR_INVALID_ARG", 2: "VIE_ERR_CUDA", 3: "VI
                 7: "VIE_ERR_UNSUPPORTED"}
 VIE_TAU_MARCH, VIE_TAU_CLOSED = 0, 1
 VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
+VIE_DISC_MIII, VIE_DISC_MII = 0, 1
 VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
 VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3, VIE_OPERATOR_PAIRS32, VIE_OPERATOR_SYM32 = 0, 1, 2, 3, 4
 VIE_KERNEL_AUTO, VIE_KERNEL_SYMMETRIC, VIE_KERNEL_DISPLACEMENT, VIE_KERNEL_GENERAL = 0, 1, 2, 3
@@ -40,7 +41,7 @@ class vie_grid(C.Structure):
 
 class vie_opts(C.Structure):
     _fields_ = [("steps", C.c_int), ("tau_mode", C.c_int), ("precision", C.c_int),
-                ("device", C.c_int), ("kernel", C.c_int)]
+                ("device", C.c_int), ("kernel", C.c_int), ("disc", C.c_int)]
 
 
 class vie_gmres_opts(C.Structure):
@@ -180,12 +181,12 @@ class VieHandle:
 
 def vie_create(dim: int, n: int, sigma_t, sigma_s, steps: int = 64, tau_mode: int = VIE_TAU_MARCH,
                precision: int = VIE_PREC_FP32, device: int = 0,
-               kernel: int = VIE_KERNEL_AUTO) -> VieHandle:
+               kernel: int = VIE_KERNEL_AUTO, disc: int = VIE_DISC_MIII) -> VieHandle:
     L = load()
     st = np.ascontiguousarray(np.asarray(sigma_t, dtype=np.float64).ravel())
     ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64).ravel())
     g = vie_grid(dim, n)
-    o = vie_opts(steps, tau_mode, precision, device, kernel)
+    o = vie_opts(steps, tau_mode, precision, device, kernel, disc)
     h = C.c_void_p()
     _check(L.vie_create(C.byref(h), C.byref(g), C.c_void_p(st.ctypes.data),
                         C.c_void_p(ss.ctypes.data), C.byref(o)))
