@@ -334,6 +334,26 @@ vie_status vie_unet_load(vie_unet *u, const char *path);
  * fell_back = 1.  The network must outlive its use by the handle. */
 vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
 
+/* The FFT preconditioner of Section 4.4 (Eqs. EQ: FFT and EQ:SOL FFT) as the
+ * right preconditioner of vie_solve_gmres (flexible GMRES, with the same
+ * stall fallback as above); enable = 0 removes it.  It replaces sigma_t and
+ * sigma_s by their means over the grid, extends the resulting convolution
+ * periodically to an m x m torus (m the power of two >= 2 n), extends the
+ * vector by zero, and inverts the periodic operator by FFT:
+ *   z = P F^{-1}( F(P^{-1} v) / F(delta - mean(sigma_s) W~) ),
+ * W~ the homogeneous medium's A (of the handle's discretisation) as a
+ * function of the displacement.  The symbol is computed once here on the
+ * host in FP64 (synchronous); applies run three FP32 FFT launches on the
+ * device.  It replaces a learned preconditioner set on the handle, and
+ * vie_set_preconditioner replaces it.  2D handles, n <= 2048.
+ * Errors: INVALID_ARG (3D; mean sigma_s >= mean sigma_t leaves the periodic
+ * operator singular), UNSUPPORTED (n > 2048), OOM, CUDA. */
+vie_status vie_set_fft_preconditioner(vie_handle *h, int enable, void *stream);
+
+/* z = M v with the FFT preconditioner alone (v, z FP64 [N], host or device,
+ * not overlapping).  Errors: INVALID_ARG (none set), CUDA. */
+vie_status vie_fft_precondition(vie_handle *h, const double *v, double *z, void *stream);
+
 /* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
 vie_status vie_get_kernel(vie_handle *h, int *kernel);
 

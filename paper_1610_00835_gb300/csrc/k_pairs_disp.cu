@@ -829,7 +829,7 @@ void geometry_release(Geometry *g) {
 // d2P/dudv = 1 / sqrt(u^2 + v^2) and is odd in u and in v, so the integral is
 // the signed sum of P over the square's corners: the closed form of Remark
 // REM: NEW KERNEL (its F written with asinh), in FP64.
-static double unit_cell_integral(double t1, double t2) {
+double unit_cell_integral(double t1, double t2) {
   auto P = [](double u, double v) {
     if (u == 0.0 || v == 0.0) return 0.0;
     return u * asinh(v / fabs(u)) + v * asinh(u / fabs(v));

@@ -119,6 +119,7 @@ struct vie_handle {
   SymPlan sym{};                              // symmetric kernel, when usable
   DispPlan disp{};                            // displacement-major kernel, when usable
   DispPlan3 disp3{};                          // its 3D form, when usable
+  FftPre fft{};                               // FFT preconditioner (Section 4.4), when set
   int use_kernel = VIE_KERNEL_GENERAL;        // pair kernel chosen for applies
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
@@ -208,6 +209,7 @@ void free_all(vie_handle *h) {
   dfree(h->ticket);
   sym_release(&h->sym);
   disp_release(&h->disp);
+  fft_release(&h->fft);
   disp3_release(&h->disp3);
   free_gmres(h);
   for (auto &ev : h->events)
@@ -755,6 +757,64 @@ vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref) {
     return invalid("vie_set_preconditioner: n must be divisible by 2^(levels-1)");
   h->precond = unet_impl(u);
   h->precond_inv_ref = 1.0 / s_ref;
+  fft_release(&h->fft);  // one preconditioner at a time
+  return VIE_OK;
+}
+
+vie_status vie_set_fft_preconditioner(vie_handle *h, int enable, void *stream) {
+  if (!h) return invalid("vie_set_fft_preconditioner: NULL handle");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!enable) {
+    VIE_CUDA(cudaStreamSynchronize(st));
+    fft_release(&h->fft);
+    return VIE_OK;
+  }
+  if (h->dim != 2) return invalid("vie_set_fft_preconditioner: 2D handles only");
+  // the mean coefficients of the medium (Section 4.4: mu -> its mean over Omega)
+  std::vector<double> t((size_t)h->N), ss((size_t)h->N);
+  VIE_CUDA(cudaMemcpy(t.data(), h->sig_t, sizeof(double) * h->N, cudaMemcpyDeviceToHost));
+  VIE_CUDA(cudaMemcpy(ss.data(), h->sig_s, sizeof(double) * h->N, cudaMemcpyDeviceToHost));
+  double mu = 0.0, mu_s = 0.0;
+  for (long i = 0; i < h->N; ++i) {
+    mu += t[i];
+    mu_s += ss[i];
+  }
+  mu /= (double)h->N;
+  mu_s /= (double)h->N;
+  VIE_CUDA(cudaStreamSynchronize(st));
+  vie_status s = fft_prepare(&h->fft, h->n, mu, mu_s, h->opts.disc == VIE_DISC_MII, st);
+  if (s != VIE_OK) return s;
+  h->precond = nullptr;  // one preconditioner at a time
+  return VIE_OK;
+}
+
+vie_status vie_fft_precondition(vie_handle *h, const double *v, double *z, void *stream) {
+  if (!h || !v || !z) return invalid("vie_fft_precondition: NULL argument");
+  if (!h->fft.on) return invalid("vie_fft_precondition: no FFT preconditioner (vie_set_fft_preconditioner)");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long N = h->N;
+  const bool vd = is_device_ptr(v), zd = is_device_ptr(z);
+  const double *vv = v;
+  double *zz = z;
+  vie_status s;
+  if (!vd) {
+    if ((s = h->stage_a.reserve(N)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, v, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    vv = h->stage_a.ptr;
+  }
+  if (!zd) {
+    if ((s = h->stage_b.reserve(N)) != VIE_OK) return s;
+    zz = h->stage_b.ptr;
+  }
+  if ((s = fft_precondition(h->fft, vv, zz, st)) != VIE_OK) return s;
+  if (!zd) {
+    VIE_CUDA(cudaMemcpyAsync(z, zz, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
   return VIE_OK;
 }
 
@@ -774,7 +834,8 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
   const int m = opt.restart;
   vie_status s;
   if ((s = ensure_gmres(h, m)) != VIE_OK) return s;
-  if (h->precond && h->z_m < m) {
+  const bool has_precond = h->precond || h->fft.on;
+  if (has_precond && h->z_m < m) {
     dfree(h->Z);
     if ((s = dalloc(&h->Z, (size_t)m * N)) != VIE_OK) return s;
     h->z_m = m;
@@ -851,7 +912,7 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
     h->h_pinned[0] = beta;
     VIE_CUDA(cudaMemcpyAsync(h->gv, h->h_pinned, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
     int k = 0;
-    const bool flexible = h->precond && !R.fell_back;
+    const bool flexible = has_precond && !R.fell_back;
     double est_prev = 1e300, est_prev2 = 1e300;
     bool stall = false;
     while (k < m && R.iters < opt.maxit) {
@@ -861,10 +922,15 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
       if (flexible) {
         // z_k = M(v_k) (right preconditioning, flexible GMRES)
         double *zk = h->Z + (size_t)k * N;
-        if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
-        if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,
-                                   h->n, h->net_x, zk, st)) != VIE_OK)
-          return s;
+        if (h->fft.on) {
+          // the FFT preconditioner (Section 4.4, Eq. EQ:SOL FFT)
+          if ((s = fft_precondition(h->fft, vk, zk, st)) != VIE_OK) return s;
+        } else {
+          if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
+          if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,
+                                     h->n, h->net_x, zk, st)) != VIE_OK)
+            return s;
+        }
         op_in = zk;
         ++R.precond_iters;
       }
@@ -891,7 +957,7 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
       R.relres_est = est;
       if (!isfinite(est)) {
         if (flexible) {
-          // the network produced a non-finite direction: drop this step
+          // the preconditioner produced a non-finite direction: drop this step
           --k;
           stall = true;
           break;

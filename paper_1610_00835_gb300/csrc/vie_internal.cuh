@@ -169,6 +169,23 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
                        long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
 vie_status disp_stream(const DispPlan &dp, int n, const float *wbuf, const float *src, cudaStream_t st);
 
+// integral of 1/|z| over the unit square centred at (t1, t2), FP64 (the
+// closed form of Remark REM: NEW KERNEL; k_pairs_disp.cu)
+double unit_cell_integral(double t1, double t2);
+
+// ---- FFT preconditioner (k_fftpre.cu): Section 4.4, Eqs. EQ: FFT, EQ:SOL FFT
+struct FftPre {
+  int on = 0, n = 0, m = 0, logm = 0;  // m: torus side, the power of two >= 2 n
+  double mu = 0.0, mu_s = 0.0;         // mean sigma_t and sigma_s
+  float *inv_lambda = nullptr;         // [m][m] 1 / (1 - mu_s F(W~)), FP32
+  float2 *tw = nullptr;                // [m / 2] e^{-2 pi i k / m}
+  float2 *buf = nullptr;               // [n][m] complex work lines
+};
+vie_status fft_prepare(FftPre *fp, int n, double mu, double mu_s, int mii, cudaStream_t st);
+void fft_release(FftPre *fp);
+// z = P F^{-1}(F(P^{-1} v) / lambda); v, z FP64 device [n * n]
+vie_status fft_precondition(const FftPre &fp, const double *v, double *z, cudaStream_t st);
+
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
 vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,

@@ -97,6 +97,8 @@ SIGNATURES = {
     "vie_unet_save": (C.c_int, [_vp, C.c_char_p]),
     "vie_unet_load": (C.c_int, [_vp, C.c_char_p]),
     "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
+    "vie_set_fft_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
+    "vie_fft_precondition": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
@@ -372,6 +374,16 @@ def vie_unet_load(u: VieUnet, path: str) -> None:
 
 def vie_set_preconditioner(h: VieHandle, u, s_ref: float = 5.0) -> None:
     _check(load().vie_set_preconditioner(h.ptr, u.ptr if u is not None else None, s_ref))
+
+
+def vie_set_fft_preconditioner(h: VieHandle, enable: bool = True, stream=None) -> None:
+    _check(load().vie_set_fft_preconditioner(h.ptr, int(bool(enable)), _stream(stream)))
+
+
+def vie_fft_precondition(h: VieHandle, v, z, stream=None) -> None:
+    vp, _v = _ptr(v, np.float64)
+    zp, _z = _ptr(z, np.float64)
+    _check(load().vie_fft_precondition(h.ptr, vp, zp, _stream(stream)))
 
 
 def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
