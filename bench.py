@@ -222,7 +222,7 @@ def err_vs_oracle(U, U_or):
     return float(np.linalg.norm(u - U_or) / np.linalg.norm(U_or))
 
 
-def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or, net=None):
+def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or, net=None, fft=False):
     """Assemble K once per step (one march per unordered pair; BF16 hi/lo or
     FP32), then FP64 GMRES(64) -- or FGMRES with the learned preconditioner --
     whose applies are HBM-bound products with the stored K (phi = K(f /
@@ -230,6 +230,8 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c = torch.cuda.Event(enable_timing=True)
     P.vie_set_preconditioner(h, net, 5.0)
+    if fft:
+        P.vie_set_fft_preconditioner(h)
     for _ in range(max(1, args.warmup)):
         P.vie_assemble(h, operator)
         P.vie_solve_gmres(h, f_dev, U, rtol=RTOL)
@@ -249,6 +251,7 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
         asm_ms.append(a.elapsed_time(b))
         reps.append(rep)
     P.vie_set_preconditioner(h, None)
+    P.vie_set_fft_preconditioner(h, False)
     P.vie_assemble(h, P.VIE_OPERATOR_OTF)
     last = reps[-1]
     name = {P.VIE_OPERATOR_BF16X3: "assembled BF16 hi/lo operator (row-major, 1.07 GB)",
@@ -256,11 +259,49 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
             P.VIE_OPERATOR_PAIRS32: "assembled FP32 pair weights (displacement-major, each unordered pair once, 0.54 GB)",
             P.VIE_OPERATOR_SYM32: "assembled FP32 A in symmetric grid-row blocks (each unordered pair of rows once, 0.54 GB)"}
     return {"solver": name[operator] + (" + FGMRES(64), learned U-Net preconditioner" if net is not None
+                                        else " + FGMRES(64), FFT preconditioner" if fft
                                         else " + FP64 GMRES(64)"),
             "solve_ms": statistics.median(ms), "assemble_ms": statistics.median(asm_ms),
             "iters": last["iters"], "n_apply": last["n_apply"], "relres": last["relres"],
             "fell_back": last["fell_back"], "apply_ms": last["t_apply_ms"] / max(1, last["n_apply"]),
             "err_vs_oracle": err_vs_oracle(U, U_or)}
+
+
+def measure_mii(P, torch, m, f_dev, flush, stream, args, local, rank, U_miii):
+    """Approach M-ii (Section 3.2, Remark REM: NEW KERNEL) on the benchmark
+    medium: the plain on-the-fly solve and the chosen assembled solve, each
+    against the FP64 oracle's M-ii solution (tests/golden/bench_U_2d_128_mii.npy),
+    and the relative difference from the M-iii solution (the discretisation
+    change itself)."""
+    hm = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS, device=local, disc=P.VIE_DISC_MII)
+    U = torch.empty(m.N, dtype=torch.float64, device=f"cuda:{local}")
+    path = os.path.join(ROOT, "tests", "golden", "bench_U_2d_128_mii.npy")
+    U_or = np.load(path) if rank == 0 and os.path.exists(path) else None
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(1, args.warmup)):
+        P.vie_solve_gmres(hm, f_dev, U, rtol=RTOL)
+    ms, rep = [], None
+    for _ in range(max(3, args.steps // 4)):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        a.record(stream)
+        rep = P.vie_solve_gmres(hm, f_dev, U, rtol=RTOL)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    plain = {"solver": "plain: FP64 GMRES(64), on-the-fly FP32 operator, M-ii weights",
+             "solve_ms": statistics.median(ms), "iters": rep["iters"], "n_apply": rep["n_apply"],
+             "relres": rep["relres"], "err_vs_oracle": err_vs_oracle(U, U_or)}
+    chosen = measure_assembled(P, torch, hm, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32, U_or)
+    P.vie_destroy(hm)
+    return {"plain": plain, "chosen": chosen,
+            "rel_diff_vs_m3_solution": err_vs_oracle(U_miii, err_ref(U)) if U_miii is not None else None,
+            "oracle_U": "tests/golden/bench_U_2d_128_mii.npy (FP64 oracle, rtol 1e-11)"
+            if U_or is not None else None}
+
+
+def err_ref(U):
+    return U.detach().cpu().numpy() if hasattr(U, "detach") else np.asarray(U)
 
 
 def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
@@ -348,8 +389,11 @@ def measure_learned(P, torch, local, seeds=(9004, 9005)):
         f = torch.as_tensor(m.f, dtype=torch.float64, device=f"cuda:{local}")
         U = torch.empty_like(f)
         row = {"seed": sd, "assemble_ms": asm}
-        for name, pre in (("gmres", None), ("fgmres_learned", net)):
-            P.vie_set_preconditioner(h, pre, 5.0)
+        for name, pre in (("gmres", None), ("fgmres_learned", net), ("fgmres_fft", "fft")):
+            if pre == "fft":
+                P.vie_set_fft_preconditioner(h)
+            else:
+                P.vie_set_preconditioner(h, pre, 5.0)
             P.vie_solve_gmres(h, f, U, rtol=RTOL, restart=128)
             torch.cuda.synchronize()
             a.record()
@@ -358,11 +402,52 @@ def measure_learned(P, torch, local, seeds=(9004, 9005)):
             torch.cuda.synchronize()
             row[name] = {"iters": rep["iters"], "ms": a.elapsed_time(b), "relres": rep["relres"],
                          "fell_back": rep["fell_back"]}
-        P.vie_set_preconditioner(h, None)
+        P.vie_set_fft_preconditioner(h, False)
         P.vie_destroy(h)
         rows.append(row)
     return {"grid": "256x256 (65536 unknowns), strongly scattering bump media, held out",
             "operator": "assembled BF16 hi/lo (17.2 GB)", "media": rows}
+
+
+def measure_fft_preconditioner(P, torch, local):
+    """The FFT preconditioner (Section 4.4, Eqs. EQ: FFT and EQ:SOL FFT) in the
+    setting of the paper's Experiment VI on a 128^2 grid: constant mu_a = 0.2
+    and mu_s = 10, 20, 40, 80, a Gaussian source at the centre.  GMRES(64) and
+    FGMRES(64) with the preconditioner, on the fast FP32 path to 1e-6 and on
+    FP64 pairs with the closed-form tau to 1e-10 (the FP32 tiles' rounding
+    floors the residual near 1e-7); solve times by CUDA events after one
+    warm-up solve, the symbol's setup reported apart."""
+    n = 128
+    xs = V.cell_centres(2, n)
+    f = torch.as_tensor(np.exp(-np.sum((xs - 0.5) ** 2, axis=1) / (2 * 0.1 ** 2)), dtype=torch.float64,
+                        device=f"cuda:{local}")
+    U = torch.empty_like(f)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for path, kw, rtol in (("fp32_march", {}, RTOL),
+                           ("fp64_closed", {"tau_mode": P.VIE_TAU_CLOSED, "precision": P.VIE_PREC_FP64}, 1e-10)):
+        for mu_s in (10.0, 20.0, 40.0, 80.0):
+            st, ss = np.full(n * n, mu_s + 0.2), np.full(n * n, mu_s)
+            h = P.vie_create(2, n, st, ss, device=local, **kw)
+            row = {"path": path, "mu_s": mu_s, "rtol": rtol}
+            for name in ("gmres", "fgmres_fft"):
+                if name == "fgmres_fft":
+                    t0 = time.perf_counter()
+                    P.vie_set_fft_preconditioner(h)
+                    row["fft_setup_ms"] = (time.perf_counter() - t0) * 1e3
+                P.vie_solve_gmres(h, f, U, rtol=rtol, maxit=3000)
+                torch.cuda.synchronize()
+                a.record()
+                rep = P.vie_solve_gmres(h, f, U, rtol=rtol, maxit=3000)
+                b.record()
+                torch.cuda.synchronize()
+                row[name] = {"iters": rep["iters"], "ms": a.elapsed_time(b), "relres": rep["relres"],
+                             "fell_back": rep["fell_back"]}
+            P.vie_destroy(h)
+            rows.append(row)
+    return {"grid": "128x128, constant mu_a = 0.2 and mu_s (Experiment VI of the paper at h = 1/128)",
+            "paper": "Table TAB:EXP VI (h = 1/512, FMM operator, tol 1e-12): FGMRES 9/11/13/15 vs GMRES "
+                     "21/34/78/110 iterations for mu_s = 10/20/40/80", "rows": rows}
 
 
 def measure_other_configs(P, torch, local, reps=3):
@@ -506,10 +591,14 @@ def run_ours(args):
     learned_128 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32,
                                     U_or, net=net)
     P.vie_unet_destroy(net)
+    chosen_fft = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32, U_or,
+                                   fft=True)
+    mii = measure_mii(P, torch, m, f_dev, flush, stream, args, local, rank, U_or)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
     batch = measure_batch(P, torch, stream, local)
     others = measure_other_configs(P, torch, local)
     learned = measure_learned(P, torch, local)
+    fftpre = measure_fft_preconditioner(P, torch, local)
 
     # end to end through the C ABI from host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -548,11 +637,14 @@ def run_ours(args):
                       "solve_ms_chosen": chosen["solve_ms"], "chosen": chosen,
                       "assembled_bf16x3": asm_bf16, "assembled_pairs32": asm_pairs, "assembled_fp32": asm_fp32,
                       "chosen_learned": learned_128,
+                      "chosen_fft": chosen_fft,
+                      "m_ii": mii,
                       "oracle_U": "tests/golden/bench_U_2d_128.npy (FP64 oracle, rtol 1e-11)"
                       if U_or is not None else None},
             "bf16x3_product": product,
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
+            "fft_preconditioner": fftpre,
             "other_workloads": others,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
@@ -571,7 +663,8 @@ def run_apply_only(args):
     import paper_1610_00835_gb300 as P
 
     m = V.heterogeneous_2d(n=args.n) if args.dim == 2 else V.heterogeneous_3d(n=args.n)
-    h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS)
+    h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS,
+                     disc=P.VIE_DISC_MII if args.disc == "m2" else P.VIE_DISC_MIII)
     mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32, "bf16x3": P.VIE_OPERATOR_BF16X3,
             "pairs32": P.VIE_OPERATOR_PAIRS32, "sym32": P.VIE_OPERATOR_SYM32}[args.operator]
     P.vie_assemble(h, mode)
@@ -589,7 +682,7 @@ def run_apply_only(args):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
-    print(json.dumps({"mode": "apply-only", "operator": args.operator, "nrhs": nrhs,
+    print(json.dumps({"mode": "apply-only", "operator": args.operator, "disc": args.disc, "nrhs": nrhs,
                       "dim": args.dim, "n": m.n, "N": m.N, "ms_per_apply": ms,
                       "gpair_per_s": float(m.N) * m.N * nrhs / ms / 1e6}), flush=True)
     P.vie_destroy(h)
@@ -603,6 +696,8 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32"], default="otf")
+    ap.add_argument("--disc", choices=["m3", "m2"], default="m3",
+                    help="apply-only: discretisation M-iii (default) or M-ii (2D)")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
