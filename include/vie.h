@@ -344,8 +344,8 @@ vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
  * W~ the homogeneous medium's A (of the handle's discretisation) as a
  * function of the displacement.  The symbol is computed once here on the
  * host in FP64 (synchronous); applies run three FP32 FFT launches on the
- * device.  It replaces a learned preconditioner set on the handle, and
- * vie_set_preconditioner replaces it.  2D handles, n <= 2048.
+ * device.  It replaces any other preconditioner set on the handle (learned
+ * or diffusion), and setting one of those replaces it.  2D handles, n <= 2048.
  * Errors: INVALID_ARG (3D; mean sigma_s >= mean sigma_t leaves the periodic
  * operator singular), UNSUPPORTED (n > 2048), OOM, CUDA. */
 vie_status vie_set_fft_preconditioner(vie_handle *h, int enable, void *stream);
@@ -353,6 +353,28 @@ vie_status vie_set_fft_preconditioner(vie_handle *h, int enable, void *stream);
 /* z = M v with the FFT preconditioner alone (v, z FP64 [N], host or device,
  * not overlapping).  Errors: INVALID_ARG (none set), CUDA. */
 vie_status vie_fft_precondition(vie_handle *h, const double *v, double *z, void *stream);
+
+/* The diffusion preconditioner of Section 4.4 (Eq. EQ:DA) as the right
+ * preconditioner of vie_solve_gmres (flexible GMRES, same stall fallback);
+ * enable = 0 removes it.  D is the second-order finite-volume form of
+ *   -div(1/(d mu) grad U) + mu_a U,  U + (2/(d mu)) dU/dn = 0 on the boundary,
+ * mu = sigma_t, mu_a = sigma_t - sigma_s per cell (harmonic-mean face
+ * coefficients; the Robin condition eliminated at boundary faces), and the
+ * preconditioner is the diffusion-synthetic form on U,
+ *   z = v + D^{-1}(sigma_s v),
+ * D^{-1} one geometric-multigrid V-cycle from zero (levels n, n/2, ... while
+ * even and above 8; red-black Gauss-Seidel 2 + 2; mean restriction; bilinear
+ * prolongation; 200 sweeps on the coarsest grid), FP64, replayed from a CUDA
+ * graph.  It works where the diffusion approximation holds and the cells are
+ * optically thin (sigma_t h well below 1); on thick cells the correction can
+ * overshoot and the stall fallback takes over.  It replaces any other
+ * preconditioner set on the handle.  2D handles; sigma_t > 0 in every cell.
+ * Errors: INVALID_ARG (3D, sigma_t = 0 somewhere), OOM, CUDA. */
+vie_status vie_set_diffusion_preconditioner(vie_handle *h, int enable, void *stream);
+
+/* z = M v with the diffusion preconditioner alone (v, z FP64 [N], host or
+ * device, not overlapping).  Errors: INVALID_ARG (none set), CUDA. */
+vie_status vie_diffusion_precondition(vie_handle *h, const double *v, double *z, void *stream);
 
 /* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
 vie_status vie_get_kernel(vie_handle *h, int *kernel);

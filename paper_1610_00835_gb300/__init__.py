@@ -6,7 +6,7 @@ is its ctypes binding.  See ``include/vie.h`` for the C ABI.
 """
 from .vie import (VIE_DISC_MII, VIE_DISC_MIII, VIE_KERNEL_AUTO, VIE_KERNEL_DISPLACEMENT,
                   VIE_KERNEL_GENERAL, VIE_KERNEL_SYMMETRIC)
-from .vie import (VieUnet, vie_fft_precondition, vie_set_fft_preconditioner, vie_set_preconditioner, vie_unet_create, vie_unet_destroy,
+from .vie import (VieUnet, vie_diffusion_precondition, vie_set_diffusion_preconditioner, vie_fft_precondition, vie_set_fft_preconditioner, vie_set_preconditioner, vie_unet_create, vie_unet_destroy,
                   vie_unet_forward, vie_unet_get_params, vie_unet_load, vie_unet_loss_grad,
                   vie_unet_num_params, vie_unet_save, vie_unet_set_params, vie_unet_train_step)
 from .vie import (VieBatch, vie_batch_apply, vie_batch_autotune, vie_batch_config,
@@ -17,7 +17,8 @@ from .vie import (VIE_OPERATOR_BF16X3, VIE_OPERATOR_FP32, VIE_OPERATOR_PAIRS32, 
                   vie_kernel_launches, vie_solve_gmres, vie_version)
 
 __all__ = ["VIE_DISC_MII", "VIE_DISC_MIII", "VIE_KERNEL_AUTO", "VIE_KERNEL_DISPLACEMENT", "VIE_KERNEL_GENERAL",
-           "VIE_KERNEL_SYMMETRIC", "VieUnet", "vie_fft_precondition", "vie_set_fft_preconditioner",
+           "VIE_KERNEL_SYMMETRIC", "VieUnet", "vie_diffusion_precondition", "vie_set_diffusion_preconditioner",
+           "vie_fft_precondition", "vie_set_fft_preconditioner",
            "vie_set_preconditioner", "vie_unet_create", "vie_unet_destroy",
            "vie_unet_forward", "vie_unet_get_params", "vie_unet_load", "vie_unet_loss_grad",
            "vie_unet_num_params", "vie_unet_save", "vie_unet_set_params", "vie_unet_train_step",

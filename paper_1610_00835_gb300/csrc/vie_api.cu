@@ -120,6 +120,7 @@ struct vie_handle {
   DispPlan disp{};                            // displacement-major kernel, when usable
   DispPlan3 disp3{};                          // its 3D form, when usable
   FftPre fft{};                               // FFT preconditioner (Section 4.4), when set
+  DiffPre diff{};                             // diffusion preconditioner (Section 4.4), when set
   int use_kernel = VIE_KERNEL_GENERAL;        // pair kernel chosen for applies
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
@@ -210,6 +211,7 @@ void free_all(vie_handle *h) {
   sym_release(&h->sym);
   disp_release(&h->disp);
   fft_release(&h->fft);
+  diffusion_release(&h->diff);
   disp3_release(&h->disp3);
   free_gmres(h);
   for (auto &ev : h->events)
@@ -758,6 +760,7 @@ vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref) {
   h->precond = unet_impl(u);
   h->precond_inv_ref = 1.0 / s_ref;
   fft_release(&h->fft);  // one preconditioner at a time
+  diffusion_release(&h->diff);
   return VIE_OK;
 }
 
@@ -787,6 +790,60 @@ vie_status vie_set_fft_preconditioner(vie_handle *h, int enable, void *stream) {
   vie_status s = fft_prepare(&h->fft, h->n, mu, mu_s, h->opts.disc == VIE_DISC_MII, st);
   if (s != VIE_OK) return s;
   h->precond = nullptr;  // one preconditioner at a time
+  diffusion_release(&h->diff);
+  return VIE_OK;
+}
+
+vie_status vie_set_diffusion_preconditioner(vie_handle *h, int enable, void *stream) {
+  if (!h) return invalid("vie_set_diffusion_preconditioner: NULL handle");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (!enable) {
+    diffusion_release(&h->diff);
+    return VIE_OK;
+  }
+  if (h->dim != 2) return invalid("vie_set_diffusion_preconditioner: 2D handles only");
+  std::vector<double> t((size_t)h->N), ss((size_t)h->N);
+  VIE_CUDA(cudaMemcpy(t.data(), h->sig_t, sizeof(double) * h->N, cudaMemcpyDeviceToHost));
+  VIE_CUDA(cudaMemcpy(ss.data(), h->sig_s, sizeof(double) * h->N, cudaMemcpyDeviceToHost));
+  vie_status s = diffusion_prepare(&h->diff, h->n, t.data(), ss.data(), h->sig_s, st);
+  if (s != VIE_OK) {
+    diffusion_release(&h->diff);
+    return s;
+  }
+  h->precond = nullptr;  // one preconditioner at a time
+  fft_release(&h->fft);
+  return VIE_OK;
+}
+
+vie_status vie_diffusion_precondition(vie_handle *h, const double *v, double *z, void *stream) {
+  if (!h || !v || !z) return invalid("vie_diffusion_precondition: NULL argument");
+  if (!h->diff.on)
+    return invalid("vie_diffusion_precondition: no diffusion preconditioner (vie_set_diffusion_preconditioner)");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long N = h->N;
+  const bool vd = is_device_ptr(v), zd = is_device_ptr(z);
+  const double *vv = v;
+  double *zz = z;
+  vie_status s;
+  if (!vd) {
+    if ((s = h->stage_a.reserve(N)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, v, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    vv = h->stage_a.ptr;
+  }
+  if (!zd) {
+    if ((s = h->stage_b.reserve(N)) != VIE_OK) return s;
+    zz = h->stage_b.ptr;
+  }
+  if ((s = diffusion_precondition(h->diff, vv, zz, st)) != VIE_OK) return s;
+  if (!zd) {
+    VIE_CUDA(cudaMemcpyAsync(z, zz, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
   return VIE_OK;
 }
 
@@ -834,7 +891,7 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
   const int m = opt.restart;
   vie_status s;
   if ((s = ensure_gmres(h, m)) != VIE_OK) return s;
-  const bool has_precond = h->precond || h->fft.on;
+  const bool has_precond = h->precond || h->fft.on || h->diff.on;
   if (has_precond && h->z_m < m) {
     dfree(h->Z);
     if ((s = dalloc(&h->Z, (size_t)m * N)) != VIE_OK) return s;
@@ -925,6 +982,9 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
         if (h->fft.on) {
           // the FFT preconditioner (Section 4.4, Eq. EQ:SOL FFT)
           if ((s = fft_precondition(h->fft, vk, zk, st)) != VIE_OK) return s;
+        } else if (h->diff.on) {
+          // the diffusion preconditioner (Section 4.4, Eq. EQ:DA)
+          if ((s = diffusion_precondition(h->diff, vk, zk, st)) != VIE_OK) return s;
         } else {
           if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
           if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,

@@ -186,6 +186,29 @@ void fft_release(FftPre *fp);
 // z = P F^{-1}(F(P^{-1} v) / lambda); v, z FP64 device [n * n]
 vie_status fft_precondition(const FftPre &fp, const double *v, double *z, cudaStream_t st);
 
+// ---- diffusion preconditioner (k_diffpre.cu): Section 4.4, Eq. EQ:DA
+constexpr int kDiffMaxLevels = 16;
+struct DiffLevel {
+  int n = 0;
+  double *c = nullptr;  // [5][n * n]: diagonal, then the west, east, south, north couplings
+  double *f = nullptr;  // right-hand side of this level
+  double *u = nullptr;  // its V-cycle iterate (level 0: the correction D^{-1}(sigma_s r))
+};
+struct DiffPre {
+  int on = 0, n = 0, L = 0, graph_kernels = 0;
+  const double *ss = nullptr;  // sigma_s on the device (the handle's)
+  DiffLevel lv[kDiffMaxLevels];
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+// sigma_t, sigma_s: host FP64 [n * n] (sigma_t > 0); sigma_s_dev stays the caller's
+vie_status diffusion_prepare(DiffPre *dp, int n, const double *sigma_t, const double *sigma_s,
+                             const double *sigma_s_dev, cudaStream_t st);
+void diffusion_release(DiffPre *dp);
+// z = v + D^{-1}(sigma_s v) by one V-cycle; v, z FP64 device [n * n]
+vie_status diffusion_precondition(const DiffPre &dp, const double *v, double *z, cudaStream_t st);
+
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
 vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,

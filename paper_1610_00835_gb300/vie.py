@@ -99,6 +99,8 @@ SIGNATURES = {
     "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
     "vie_set_fft_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
     "vie_fft_precondition": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "vie_set_diffusion_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
+    "vie_diffusion_precondition": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vie_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
@@ -384,6 +386,16 @@ def vie_fft_precondition(h: VieHandle, v, z, stream=None) -> None:
     vp, _v = _ptr(v, np.float64)
     zp, _z = _ptr(z, np.float64)
     _check(load().vie_fft_precondition(h.ptr, vp, zp, _stream(stream)))
+
+
+def vie_set_diffusion_preconditioner(h: VieHandle, enable: bool = True, stream=None) -> None:
+    _check(load().vie_set_diffusion_preconditioner(h.ptr, int(bool(enable)), _stream(stream)))
+
+
+def vie_diffusion_precondition(h: VieHandle, v, z, stream=None) -> None:
+    vp, _v = _ptr(v, np.float64)
+    zp, _z = _ptr(z, np.float64)
+    _check(load().vie_diffusion_precondition(h.ptr, vp, zp, _stream(stream)))
 
 
 def ert_sweep(h: VieHandle, U, f, dirs, Phi, stream=None) -> None:
