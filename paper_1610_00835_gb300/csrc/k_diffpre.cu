@@ -46,14 +46,15 @@ __device__ __forceinline__ double neighbour_sum(const double *__restrict__ c, co
   return s;
 }
 
-// one colour of a red-black Gauss-Seidel sweep (red: ix + iy even)
+// one colour of a red-black Gauss-Seidel sweep (red: ix + iy even); plane 5
+// of c holds 1 / diag
 __global__ void k_dp_rbgs(int n, const double *__restrict__ c, const double *__restrict__ f, double *__restrict__ u,
                           int colour) {
   const long N = (long)n * n;
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < N; j += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(j % n), iy = (int)(j / n);
     if (((ix + iy) & 1) != colour) continue;
-    u[j] = (f[j] + neighbour_sum(c, u, n, N, ix, iy, j)) / c[j];
+    u[j] = (f[j] + neighbour_sum(c, u, n, N, ix, iy, j)) * c[5 * N + j];
   }
 }
 
@@ -103,7 +104,7 @@ __global__ void k_dp_coarse(int n, const double *__restrict__ c, const double *_
     for (int colour = 0; colour < 2; ++colour) {
       for (long j = threadIdx.x; j < N; j += blockDim.x) {
         const int ix = (int)(j % n), iy = (int)(j / n);
-        if (((ix + iy) & 1) == colour) u[j] = (f[j] + neighbour_sum(c, u, n, N, ix, iy, j)) / c[j];
+        if (((ix + iy) & 1) == colour) u[j] = (f[j] + neighbour_sum(c, u, n, N, ix, iy, j)) * c[5 * N + j];
       }
       __syncthreads();
     }
@@ -128,7 +129,7 @@ void level_coefficients(int n, const std::vector<double> &mu, const std::vector<
                         std::vector<double> &c) {
   const long N = (long)n * n;
   const double h = 1.0 / n;
-  c.assign(5 * N, 0.0);
+  c.assign(6 * N, 0.0);
   for (int iy = 0; iy < n; ++iy)
     for (int ix = 0; ix < n; ++ix) {
       const long j = (long)iy * n + ix;
@@ -146,6 +147,7 @@ void level_coefficients(int n, const std::vector<double> &mu, const std::vector<
         }
       }
       c[j] = diag;
+      c[5 * N + j] = 1.0 / diag;
     }
 }
 
@@ -164,7 +166,12 @@ cudaError_t enqueue_vcycle(const DiffPre &dp, cudaStream_t st, int *kernels) {
     k_dp_restrict<<<blocks_for(N / 4), kT, 0, st>>>(lv[l].n, lv[l].c, lv[l].f, lv[l].u, lv[l + 1].f);
     ++k;
   }
-  k_dp_coarse<<<1, 1024, 0, st>>>(lv[L - 1].n, lv[L - 1].c, lv[L - 1].f, lv[L - 1].u);
+  {
+    // one CTA just large enough for the coarsest grid: its barriers stay cheap
+    const long Nc = (long)lv[L - 1].n * lv[L - 1].n;
+    const int threads = (int)std::min(1024L, std::max(32L, (Nc + 31) / 32 * 32));
+    k_dp_coarse<<<1, threads, 0, st>>>(lv[L - 1].n, lv[L - 1].c, lv[L - 1].f, lv[L - 1].u);
+  }
   ++k;
   for (int l = L - 2; l >= 0; --l) {
     const long N = (long)lv[l].n * lv[l].n;
@@ -199,10 +206,10 @@ vie_status diffusion_prepare(DiffPre *dp, int n, const double *sigma_t, const do
     const long M = (long)ln * ln;
     DiffLevel &L = dp->lv[dp->L++];  // owned by dp from here: released on failure
     L.n = ln;
-    VIE_CUDA(cudaMalloc((void **)&L.c, sizeof(double) * 5 * M));
+    VIE_CUDA(cudaMalloc((void **)&L.c, sizeof(double) * 6 * M));
     VIE_CUDA(cudaMalloc((void **)&L.f, sizeof(double) * M));
     VIE_CUDA(cudaMalloc((void **)&L.u, sizeof(double) * M));
-    VIE_CUDA(cudaMemcpyAsync(L.c, c.data(), sizeof(double) * 5 * M, cudaMemcpyHostToDevice, st));
+    VIE_CUDA(cudaMemcpyAsync(L.c, c.data(), sizeof(double) * 6 * M, cudaMemcpyHostToDevice, st));
     VIE_CUDA(cudaStreamSynchronize(st));
     if (ln % 2 || ln <= 8 || dp->L == kDiffMaxLevels) break;
     const int nc = ln / 2;

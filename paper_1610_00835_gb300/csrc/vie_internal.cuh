@@ -190,7 +190,7 @@ vie_status fft_precondition(const FftPre &fp, const double *v, double *z, cudaSt
 constexpr int kDiffMaxLevels = 16;
 struct DiffLevel {
   int n = 0;
-  double *c = nullptr;  // [5][n * n]: diagonal, then the west, east, south, north couplings
+  double *c = nullptr;  // [6][n * n]: diagonal, the west, east, south, north couplings, 1 / diagonal
   double *f = nullptr;  // right-hand side of this level
   double *u = nullptr;  // its V-cycle iterate (level 0: the correction D^{-1}(sigma_s r))
 };

@@ -20,10 +20,11 @@ def _precondition(h, v):
     return host(z)
 
 
-@pytest.mark.parametrize("n", [1, 5, 8, 16, 24, 64, 128, 133, 200])
+@pytest.mark.parametrize("n", [1, 5, 8, 16, 24, 64, 128, 133, 200, 300])
 def test_diffusion_precondition_matches_oracle(n):
     # one level (n <= 8 or odd: the coarse solve only), up to five levels
-    # (128 -> 8); 200 stops at the odd 25
+    # (128 -> 8); 200 stops at the odd 25; up to 256 the single-CTA kernel,
+    # 300 (300 -> 150 -> 75) the graph of per-phase launches
     m = V.bump_medium(2, n, 4, 0.9, seed=5400 + n)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
     P.vie_set_diffusion_preconditioner(h)
