@@ -389,9 +389,12 @@ def measure_learned(P, torch, local, seeds=(9004, 9005)):
         f = torch.as_tensor(m.f, dtype=torch.float64, device=f"cuda:{local}")
         U = torch.empty_like(f)
         row = {"seed": sd, "assemble_ms": asm}
-        for name, pre in (("gmres", None), ("fgmres_learned", net), ("fgmres_fft", "fft")):
+        for name, pre in (("gmres", None), ("fgmres_learned", net), ("fgmres_fft", "fft"),
+                          ("fgmres_diffusion", "diffusion")):
             if pre == "fft":
                 P.vie_set_fft_preconditioner(h)
+            elif pre == "diffusion":
+                P.vie_set_diffusion_preconditioner(h)
             else:
                 P.vie_set_preconditioner(h, pre, 5.0)
             P.vie_solve_gmres(h, f, U, rtol=RTOL, restart=128)
@@ -403,20 +406,21 @@ def measure_learned(P, torch, local, seeds=(9004, 9005)):
             row[name] = {"iters": rep["iters"], "ms": a.elapsed_time(b), "relres": rep["relres"],
                          "fell_back": rep["fell_back"]}
         P.vie_set_fft_preconditioner(h, False)
+        P.vie_set_diffusion_preconditioner(h, False)
         P.vie_destroy(h)
         rows.append(row)
     return {"grid": "256x256 (65536 unknowns), strongly scattering bump media, held out",
             "operator": "assembled BF16 hi/lo (17.2 GB)", "media": rows}
 
 
-def measure_fft_preconditioner(P, torch, local):
-    """The FFT preconditioner (Section 4.4, Eqs. EQ: FFT and EQ:SOL FFT) in the
-    setting of the paper's Experiment VI on a 128^2 grid: constant mu_a = 0.2
-    and mu_s = 10, 20, 40, 80, a Gaussian source at the centre.  GMRES(64) and
-    FGMRES(64) with the preconditioner, on the fast FP32 path to 1e-6 and on
-    FP64 pairs with the closed-form tau to 1e-10 (the FP32 tiles' rounding
-    floors the residual near 1e-7); solve times by CUDA events after one
-    warm-up solve, the symbol's setup reported apart."""
+def measure_paper_preconditioners(P, torch, local):
+    """The FFT and diffusion preconditioners (Section 4.4, Eqs. EQ: FFT, EQ:SOL
+    FFT and EQ:DA) in the setting of the paper's Experiments V and VI on a
+    128^2 grid: constant mu_a = 0.2 and mu_s = 10, 20, 40, 80, a Gaussian
+    source at the centre.  GMRES(64) and FGMRES(64) with each preconditioner,
+    on the fast FP32 path to 1e-6 and on FP64 pairs with the closed-form tau
+    to 1e-10 (the FP32 tiles' rounding floors the residual near 1e-7); solve
+    times by CUDA events after one warm-up solve, setups reported apart."""
     n = 128
     xs = V.cell_centres(2, n)
     f = torch.as_tensor(np.exp(-np.sum((xs - 0.5) ** 2, axis=1) / (2 * 0.1 ** 2)), dtype=torch.float64,
@@ -430,11 +434,15 @@ def measure_fft_preconditioner(P, torch, local):
             st, ss = np.full(n * n, mu_s + 0.2), np.full(n * n, mu_s)
             h = P.vie_create(2, n, st, ss, device=local, **kw)
             row = {"path": path, "mu_s": mu_s, "rtol": rtol}
-            for name in ("gmres", "fgmres_fft"):
+            for name in ("gmres", "fgmres_fft", "fgmres_diffusion"):
                 if name == "fgmres_fft":
                     t0 = time.perf_counter()
                     P.vie_set_fft_preconditioner(h)
                     row["fft_setup_ms"] = (time.perf_counter() - t0) * 1e3
+                elif name == "fgmres_diffusion":
+                    t0 = time.perf_counter()
+                    P.vie_set_diffusion_preconditioner(h)
+                    row["diffusion_setup_ms"] = (time.perf_counter() - t0) * 1e3
                 P.vie_solve_gmres(h, f, U, rtol=rtol, maxit=3000)
                 torch.cuda.synchronize()
                 a.record()
@@ -445,9 +453,10 @@ def measure_fft_preconditioner(P, torch, local):
                              "fell_back": rep["fell_back"]}
             P.vie_destroy(h)
             rows.append(row)
-    return {"grid": "128x128, constant mu_a = 0.2 and mu_s (Experiment VI of the paper at h = 1/128)",
-            "paper": "Table TAB:EXP VI (h = 1/512, FMM operator, tol 1e-12): FGMRES 9/11/13/15 vs GMRES "
-                     "21/34/78/110 iterations for mu_s = 10/20/40/80", "rows": rows}
+    return {"grid": "128x128, constant mu_a = 0.2 and mu_s (Experiments V and VI of the paper at h = 1/128)",
+            "paper": "h = 1/512, FMM operator, tol 1e-12, mu_s = 10/20/40/80: Table TAB:EXP VI FFT-preconditioned "
+                     "9/11/13/15 vs 21/34/78/110 iterations; Table TAB:EXP V diffusion-preconditioned 36/38/42/52",
+            "rows": rows}
 
 
 def measure_other_configs(P, torch, local, reps=3):
@@ -598,7 +607,7 @@ def run_ours(args):
     batch = measure_batch(P, torch, stream, local)
     others = measure_other_configs(P, torch, local)
     learned = measure_learned(P, torch, local)
-    fftpre = measure_fft_preconditioner(P, torch, local)
+    paper_pre = measure_paper_preconditioners(P, torch, local)
 
     # end to end through the C ABI from host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -644,7 +653,7 @@ def run_ours(args):
             "bf16x3_product": product,
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
-            "fft_preconditioner": fftpre,
+            "paper_preconditioners": paper_pre,
             "other_workloads": others,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
