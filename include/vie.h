@@ -147,9 +147,12 @@ enum {
   VIE_OPERATOR_PAIRS32 = 3,      /* A_jk of every unordered pair once, FP32,
                                     displacement-major (2D handles that use the
                                     displacement kernel): applies stream it */
-  VIE_OPERATOR_SYM32 = 4         /* A (symmetric) in FP32 blocks, one per pair of
+  VIE_OPERATOR_SYM32 = 4,        /* A (symmetric) in FP32 blocks, one per pair of
                                     grid rows yj <= yk (same handles): applies
                                     read each block once, y = A (sigma_s g) */
+  VIE_OPERATOR_FMM = 5           /* the interpolation-based FMM of Section 3.3
+                                    with cached near-field and M2L blocks
+                                    (vie_assemble_fmm; Chebyshev order 6 here) */
 };
 
 /* VIE_OPERATOR_SYM32: A_jk = A_kj (Section 2, Eq. EQ:Kernel; M-iii of
@@ -186,6 +189,27 @@ enum {
  * S = 64 (else VIE_ERR_UNSUPPORTED).  Asynchronous on `stream`.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 vie_status vie_assemble(vie_handle *h, int mode, void *stream);
+
+/* VIE_OPERATOR_FMM with Chebyshev order `order` per axis (2..12; the paper
+ * uses 4, 6 and 9).  Section 3.3, Eqs. EQ: CHEB, EQ:Kernel Approx, EQ:
+ * SUMMATION, EQ: M2L, EQ: L2L (Fong-Darve), 2D: the grid as a quadtree with
+ * leaves of b x b cells, n = 2^L b, b >= 8 and L >= 2 (L as large as the
+ * factors of two allow); the near field (a leaf and its 3 x 3 neighbourhood)
+ * from the M-iii entries A_jk (self cell on the diagonal), the far field from
+ * the kernel h^2 e^{-tau} / (2 pi r) at the order^2 first-kind Chebyshev
+ * nodes of each box: P2M, M2M, M2L over the 27-box interaction lists from
+ * level 2 down, L2L, L2P.  Every near entry and every M2L kernel value is
+ * computed once here on the device (FP32, the handle's tau: the S-step march
+ * with sample points clamped to the hull of the cell centres, or the closed
+ * form) and stored: 4 b^4 9 4^L + 4 * 27 order^4 sum_{l=2..L} 4^l bytes
+ * (0.09 GB at 128^2, 1.4 GB at 512^2 with order 6).  Applies (any vie_op; phi
+ * = A f directly) are 2 L + 2 launches that read the cached blocks once.
+ * The far field is an approximation: relative error ~1e-6 (order 6) on
+ * homogeneous media, 1e-5 .. 1e-4 on heterogeneous ones (tau of a bilinear
+ * sigma_t is only piecewise smooth).  Needs a 2D grid, FP32 tiles and M-iii.
+ * Errors: INVALID_ARG (order), UNSUPPORTED (grid without a far field, 3D,
+ * FP64, M-ii), OOM, CUDA. */
+vie_status vie_assemble_fmm(vie_handle *h, int order, void *stream);
 
 typedef struct {
   double rtol;  /* stop when ||phi - (I-K)U||_2 / ||phi||_2 <= rtol (FP64)   */

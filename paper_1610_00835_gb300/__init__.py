@@ -11,6 +11,7 @@ from .vie import (VieUnet, vie_diffusion_precondition, vie_set_diffusion_precond
                   vie_unet_num_params, vie_unet_save, vie_unet_set_params, vie_unet_train_step)
 from .vie import (VieBatch, vie_batch_apply, vie_batch_autotune, vie_batch_config,
                   vie_batch_create, vie_batch_destroy)
+from .vie import (VIE_OPERATOR_FMM, vie_assemble_fmm)
 from .vie import (VIE_OPERATOR_BF16X3, VIE_OPERATOR_FP32, VIE_OPERATOR_PAIRS32, VIE_OPERATOR_SYM32, VIE_OPERATOR_OTF, VIE_OP_A_RAW, VIE_OP_I_MINUS_K, VIE_OP_K_SIGMA_S, VIE_PREC_FP32,
                   VIE_PREC_FP64, VIE_TAU_CLOSED, VIE_TAU_MARCH, VieError, VieHandle, ert_sweep,
                   load, vie_apply, vie_apply_noalloc, vie_get_kernel, vie_get_kernel_work, vie_assemble, vie_create, vie_destroy, vie_get_diagonal, vie_last_error,
@@ -24,7 +25,7 @@ __all__ = ["VIE_DISC_MII", "VIE_DISC_MIII", "VIE_KERNEL_AUTO", "VIE_KERNEL_DISPL
            "vie_unet_num_params", "vie_unet_save", "vie_unet_set_params", "vie_unet_train_step",
            "VieBatch", "vie_batch_apply", "vie_batch_autotune", "vie_batch_config",
            "vie_batch_create", "vie_batch_destroy",
-           "VIE_OPERATOR_BF16X3", "VIE_OPERATOR_FP32", "VIE_OPERATOR_PAIRS32", "VIE_OPERATOR_SYM32", "VIE_OPERATOR_OTF", "VIE_OP_A_RAW", "VIE_OP_I_MINUS_K", "VIE_OP_K_SIGMA_S", "VIE_PREC_FP32",
+           "VIE_OPERATOR_FMM", "vie_assemble_fmm", "VIE_OPERATOR_BF16X3", "VIE_OPERATOR_FP32", "VIE_OPERATOR_PAIRS32", "VIE_OPERATOR_SYM32", "VIE_OPERATOR_OTF", "VIE_OP_A_RAW", "VIE_OP_I_MINUS_K", "VIE_OP_K_SIGMA_S", "VIE_PREC_FP32",
            "VIE_PREC_FP64", "VIE_TAU_CLOSED", "VIE_TAU_MARCH", "VieError", "VieHandle",
            "ert_sweep", "load", "vie_apply", "vie_apply_noalloc", "vie_get_kernel", "vie_get_kernel_work", "vie_assemble", "vie_create", "vie_destroy", "vie_get_diagonal",
            "vie_kernel_launches", "vie_last_error", "vie_solve_gmres", "vie_version"]

@@ -121,6 +121,7 @@ struct vie_handle {
   DispPlan3 disp3{};                          // its 3D form, when usable
   FftPre fft{};                               // FFT preconditioner (Section 4.4), when set
   DiffPre diff{};                             // diffusion preconditioner (Section 4.4), when set
+  FmmPlan fmm{};                              // FMM operator (Section 3.3), when assembled
   int use_kernel = VIE_KERNEL_GENERAL;        // pair kernel chosen for applies
   void *src = nullptr;                        // per-source values [N]
   double *partial = nullptr;                  // [plan.splits][N]
@@ -212,6 +213,7 @@ void free_all(vie_handle *h) {
   disp_release(&h->disp);
   fft_release(&h->fft);
   diffusion_release(&h->diff);
+  fmm_release(&h->fmm);
   disp3_release(&h->disp3);
   free_gmres(h);
   for (auto &ev : h->events)
@@ -283,6 +285,19 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   const int prec = h->opts.precision;
   const int closed = h->opts.tau_mode == VIE_TAU_CLOSED;
   const bool raw_via_k = op == VIE_OP_A_RAW && h->sig_s_positive;
+  if (h->asm_mode == VIE_OPERATOR_FMM) {
+    vie_status s = launch_source_prep(h->N, op, h->sig_s, g, VIE_PREC_FP32, h->src, st);
+    if (s != VIE_OK) return s;
+    if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
+    if ((s = fmm_apply(h->fmm, op, (const float *)h->src, g, y, st)) != VIE_OK) return s;
+    if (timed) {
+      VIE_CUDA(cudaEventRecord(ev->e[2], st));
+      VIE_CUDA(cudaEventRecord(ev->e[3], st));
+      ev->pending = true;
+    }
+    h->n_apply++;
+    return VIE_OK;
+  }
   if (h->asm_mode == VIE_OPERATOR_SYM32) {
     if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
     vie_status s = symv_apply(h->n, op, h->sig_s, g, (const float *)h->kmat, (float *)h->src, h->sym_partial, y,
@@ -638,23 +653,39 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
   return VIE_OK;
 }
 
-vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
+static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream) {
   if (!h) return invalid("vie_assemble: NULL handle");
   if (mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FP32 && mode != VIE_OPERATOR_BF16X3 &&
-      mode != VIE_OPERATOR_PAIRS32 && mode != VIE_OPERATOR_SYM32)
+      mode != VIE_OPERATOR_PAIRS32 && mode != VIE_OPERATOR_SYM32 && mode != VIE_OPERATOR_FMM)
     return invalid("vie_assemble: unknown mode");
   DeviceGuard dg(h->device);
   if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  const bool reuse = mode != VIE_OPERATOR_OTF && mode == h->asm_mode && h->kmat;
+  const bool reuse = mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FMM && mode == h->asm_mode && h->kmat;
   if (!reuse) {
-    if (h->kmat || h->kmat_lo) VIE_CUDA(cudaStreamSynchronize(st));
+    if (h->kmat || h->kmat_lo || h->fmm.on) VIE_CUDA(cudaStreamSynchronize(st));
     if (h->kmat) cudaFree(h->kmat);
     if (h->kmat_lo) cudaFree(h->kmat_lo);
     h->kmat = h->kmat_lo = nullptr;
+    fmm_release(&h->fmm);
     h->asm_mode = VIE_OPERATOR_OTF;
   }
   if (mode == VIE_OPERATOR_OTF) return VIE_OK;
+  if (mode == VIE_OPERATOR_FMM) {
+    // the interpolation-based FMM of Section 3.3 with cached kernel values
+    if (h->dim != 2 || h->opts.precision != VIE_PREC_FP32 || h->opts.disc != VIE_DISC_MIII) {
+      set_error("vie_assemble: VIE_OPERATOR_FMM needs a 2D grid, FP32 tiles and M-iii");
+      return VIE_ERR_UNSUPPORTED;
+    }
+    vie_status s = fmm_prepare(&h->fmm, h->n, order, h->sig32, h->diag, h->opts.steps,
+                               h->opts.tau_mode == VIE_TAU_CLOSED, h->med.sigma_c, st);
+    if (s != VIE_OK) {
+      fmm_release(&h->fmm);
+      return s;
+    }
+    h->asm_mode = mode;
+    return VIE_OK;
+  }
   if (mode == VIE_OPERATOR_SYM32) {
     // A in the symmetric blocks of grid-row pairs: the pair weights, expanded
     if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2 || !disp_expand_fits(h->n, h->device) ||
@@ -744,6 +775,12 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream) {
   if (s != VIE_OK) return s;
   h->asm_mode = mode;
   return VIE_OK;
+}
+
+vie_status vie_assemble(vie_handle *h, int mode, void *stream) { return assemble_impl(h, mode, 6, stream); }
+
+vie_status vie_assemble_fmm(vie_handle *h, int order, void *stream) {
+  return assemble_impl(h, VIE_OPERATOR_FMM, order, stream);
 }
 
 vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref) {

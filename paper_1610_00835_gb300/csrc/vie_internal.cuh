@@ -209,6 +209,26 @@ void diffusion_release(DiffPre *dp);
 // z = v + D^{-1}(sigma_s v) by one V-cycle; v, z FP64 device [n * n]
 vie_status diffusion_precondition(const DiffPre &dp, const double *v, double *z, cudaStream_t st);
 
+// ---- interpolation-based FMM operator (k_fmm.cu): Section 3.3, 2D
+struct FmmPlan {
+  int on = 0, n = 0, p = 0, L = 0, b = 0;
+  long node_off[32] = {};      // per level: first node value of W and Lc
+  long m2l_off[32] = {};       // per level: first float of its M2L blocks
+  long near_floats = 0, m2l_floats = 0;
+  float *near = nullptr;       // [leaf][9][b^2][b^2] (source-major) near blocks
+  float *m2l = nullptr;        // per level [box][27][p^2][p^2] (source-major)
+  float *W = nullptr, *Lc = nullptr;  // multipole and local node values, per level
+  float *Pm = nullptr;         // [p^2][b^2] leaf interpolation
+  float *Cq = nullptr;         // [4][p^2][p^2] child-to-parent interpolation
+  float *z = nullptr;          // [p] Chebyshev points
+};
+void fmm_leaf_levels(int n, int *L, int *b);
+vie_status fmm_prepare(FmmPlan *fp, int n, int p, const float *sig32, const double *diag, int steps, int closed,
+                       double sigma_c, cudaStream_t st);
+void fmm_release(FmmPlan *fp);
+// y = A s (op A_RAW, K_SIGMA_S: s already multiplied by sigma_s) or g - A s (I_MINUS_K)
+vie_status fmm_apply(const FmmPlan &fp, int op, const float *s, const double *g, double *y, cudaStream_t st);
+
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
 vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,

@@ -26,6 +26,7 @@ VIE_PREC_FP32, VIE_PREC_FP64 = 0, 1
 VIE_DISC_MIII, VIE_DISC_MII = 0, 1
 VIE_OP_K_SIGMA_S, VIE_OP_I_MINUS_K, VIE_OP_A_RAW = 0, 1, 2
 VIE_OPERATOR_OTF, VIE_OPERATOR_FP32, VIE_OPERATOR_BF16X3, VIE_OPERATOR_PAIRS32, VIE_OPERATOR_SYM32 = 0, 1, 2, 3, 4
+VIE_OPERATOR_FMM = 5
 VIE_KERNEL_AUTO, VIE_KERNEL_SYMMETRIC, VIE_KERNEL_DISPLACEMENT, VIE_KERNEL_GENERAL = 0, 1, 2, 3
 
 
@@ -78,6 +79,7 @@ SIGNATURES = {
     "vie_version": (C.c_char_p, []),
     "vie_kernel_launches": (C.c_ulonglong, []),
     "vie_assemble": (C.c_int, [_vp, C.c_int, _vp]),
+    "vie_assemble_fmm": (C.c_int, [_vp, C.c_int, _vp]),
     "vie_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(vie_grid),
                                    C.POINTER(_vp), C.POINTER(_vp), C.POINTER(vie_opts)]),
     "vie_batch_destroy": (C.c_int, [_vp]),
@@ -211,6 +213,10 @@ def vie_apply(h: VieHandle, op: int, g, y, nrhs: int = 1, stream=None) -> None:
 
 def vie_assemble(h: VieHandle, mode: int, stream=None) -> None:
     _check(load().vie_assemble(h.ptr, mode, _stream(stream)))
+
+
+def vie_assemble_fmm(h: VieHandle, order: int = 6, stream=None) -> None:
+    _check(load().vie_assemble_fmm(h.ptr, order, _stream(stream)))
 
 
 def vie_solve_gmres(h: VieHandle, f, U, rtol: float = 1e-6, restart: int = 64, maxit: int = 1000,
