@@ -257,7 +257,8 @@ def measure_assembled(P, torch, h, f_dev, U, flush, stream, args, operator, U_or
     name = {P.VIE_OPERATOR_BF16X3: "assembled BF16 hi/lo operator (row-major, 1.07 GB)",
             P.VIE_OPERATOR_FP32: "assembled FP32 operator (row-major, 1.07 GB)",
             P.VIE_OPERATOR_PAIRS32: "assembled FP32 pair weights (displacement-major, each unordered pair once, 0.54 GB)",
-            P.VIE_OPERATOR_SYM32: "assembled FP32 A in symmetric grid-row blocks (each unordered pair of rows once, 0.54 GB)"}
+            P.VIE_OPERATOR_SYM32: "assembled FP32 A in symmetric grid-row blocks (each unordered pair of rows once, 0.54 GB)",
+            P.VIE_OPERATOR_FMM: "FMM of Section 3.3, Chebyshev order 6, cached near-field and M2L blocks (0.09 GB)"}
     return {"solver": name[operator] + (" + FGMRES(64), learned U-Net preconditioner" if net is not None
                                         else " + FGMRES(64), FFT preconditioner" if fft
                                         else " + FP64 GMRES(64)"),
@@ -459,6 +460,66 @@ def measure_paper_preconditioners(P, torch, local):
             "rows": rows}
 
 
+def measure_paper_fmm_tables(P, torch, local):
+    """The paper's Experiments I and II (Tables TAB:Con Coeff and TAB:Var Coeff)
+    with the FMM operator (Section 3.3): homogeneous mu_s = 2.0, mu_a = 0.2 with
+    the closed-form tau (the paper evaluates E analytically there), and the
+    medium of Eq. EQ:Coeff (mu_a = 0.2, mu_s = 3 + 2 exp(-|x - (1/2, 1/2)|^2 / 4))
+    with the 64-step march; N = 32^2 .. 512^2, Chebyshev orders 4, 6, 9.  The
+    paper's ring source exists only as a figure; a ring of radius 0.25 and
+    width 0.05 about the centre stands in.  Per case: assembly (the paper's
+    T^fmm: every kernel value computed and cached), the GMRES(64) solve to 1e-6
+    and its time per operator apply (T_g^fmm), and E_l2 = ||U_fmm - U_dir|| /
+    ||U_dir|| against the on-the-fly direct solve up to 256^2 (the paper's
+    direct path stopped at 128^2)."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for medium in ("homogeneous", "eq_coeff"):
+        for n in (32, 64, 128, 256, 512):
+            xs = V.cell_centres(2, n)
+            r = np.sqrt(np.sum((xs - 0.5) ** 2, axis=1))
+            f = torch.as_tensor(np.exp(-(r - 0.25) ** 2 / (2 * 0.05 ** 2)), dtype=torch.float64,
+                                device=f"cuda:{local}")
+            if medium == "homogeneous":
+                ss = np.full(n * n, 2.0)
+                kw = {"tau_mode": P.VIE_TAU_CLOSED}
+            else:
+                ss = 3.0 + 2.0 * np.exp(-r ** 2 / 4.0)
+                kw = {}
+            st = ss + 0.2
+            h = P.vie_create(2, n, st, ss, device=local, **kw)
+            U = torch.empty_like(f)
+            U_dir = None
+            if n <= 256:
+                P.vie_solve_gmres(h, f, U, rtol=RTOL)
+                U_dir = U.clone()
+            for order in (4, 6, 9):
+                torch.cuda.synchronize()
+                a.record()
+                P.vie_assemble_fmm(h, order)
+                b.record()
+                torch.cuda.synchronize()
+                asm = a.elapsed_time(b)
+                P.vie_solve_gmres(h, f, U, rtol=RTOL)
+                torch.cuda.synchronize()
+                a.record()
+                rep = P.vie_solve_gmres(h, f, U, rtol=RTOL)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                row = {"medium": medium, "N": n * n, "order": order, "assemble_ms": asm, "solve_ms": ms,
+                       "iters": rep["iters"], "ms_per_apply": ms / max(1, rep["n_apply"])}
+                if U_dir is not None:
+                    row["E_l2_vs_direct"] = float(torch.linalg.norm(U - U_dir) / torch.linalg.norm(U_dir))
+                out.append(row)
+            P.vie_destroy(h)
+    return {"rtol": RTOL, "source": "ring stand-in (radius 0.25, width 0.05)",
+            "paper": "MATLAB on one i7-6560U core, tol 1e-12: order 6, N = 262144: T^fmm 13.9 s (homogeneous) / "
+                     "T_g^fmm 0.27 s per iteration; order 4 heterogeneous T^fmm 114 s; E_l2 1.3e-6 (homogeneous, "
+                     "order 6), 2.0e-4 .. 3.5e-4 (heterogeneous, order 4)",
+            "rows": out}
+
+
 def measure_other_configs(P, torch, local, reps=3):
     """The two other single-GPU workloads of the method: the homogeneous 32^2
     medium in FP64 with the closed-form tau (GMRES to 1e-10), and the 32^3
@@ -602,12 +663,14 @@ def run_ours(args):
     P.vie_unet_destroy(net)
     chosen_fft = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32, U_or,
                                    fft=True)
+    chosen_fmm = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_FMM, U_or)
     mii = measure_mii(P, torch, m, f_dev, flush, stream, args, local, rank, U_or)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
     batch = measure_batch(P, torch, stream, local)
     others = measure_other_configs(P, torch, local)
     learned = measure_learned(P, torch, local)
     paper_pre = measure_paper_preconditioners(P, torch, local)
+    paper_fmm = measure_paper_fmm_tables(P, torch, local)
 
     # end to end through the C ABI from host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -647,6 +710,7 @@ def run_ours(args):
                       "assembled_bf16x3": asm_bf16, "assembled_pairs32": asm_pairs, "assembled_fp32": asm_fp32,
                       "chosen_learned": learned_128,
                       "chosen_fft": chosen_fft,
+                      "chosen_fmm": chosen_fmm,
                       "m_ii": mii,
                       "oracle_U": "tests/golden/bench_U_2d_128.npy (FP64 oracle, rtol 1e-11)"
                       if U_or is not None else None},
@@ -654,6 +718,7 @@ def run_ours(args):
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
             "paper_preconditioners": paper_pre,
+            "paper_fmm_tables": paper_fmm,
             "other_workloads": others,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches),
@@ -675,7 +740,7 @@ def run_apply_only(args):
     h = P.vie_create(args.dim, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS,
                      disc=P.VIE_DISC_MII if args.disc == "m2" else P.VIE_DISC_MIII)
     mode = {"otf": P.VIE_OPERATOR_OTF, "fp32": P.VIE_OPERATOR_FP32, "bf16x3": P.VIE_OPERATOR_BF16X3,
-            "pairs32": P.VIE_OPERATOR_PAIRS32, "sym32": P.VIE_OPERATOR_SYM32}[args.operator]
+            "pairs32": P.VIE_OPERATOR_PAIRS32, "sym32": P.VIE_OPERATOR_SYM32, "fmm": P.VIE_OPERATOR_FMM}[args.operator]
     P.vie_assemble(h, mode)
     nrhs = args.nrhs
     G = V.bump_sources(args.dim, m.n, nrhs, seed=V.seed_for(4)) if nrhs > 1 else m.f[None, :]
@@ -704,7 +769,7 @@ def main(argv=None):
                     help="time operator applies only (profiling driver)")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32"], default="otf")
+    ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32", "fmm"], default="otf")
     ap.add_argument("--disc", choices=["m3", "m2"], default="m3",
                     help="apply-only: discretisation M-iii (default) or M-ii (2D)")
     ap.add_argument("--nrhs", type=int, default=1)
