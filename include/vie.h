@@ -203,7 +203,7 @@ vie_status vie_assemble(vie_handle *h, int mode, void *stream);
  * with sample points clamped to the hull of the cell centres, or the closed
  * form) and stored: 4 b^4 9 4^L + 4 * 27 order^4 sum_{l=2..L} 4^l bytes
  * (0.09 GB at 128^2, 1.4 GB at 512^2 with order 6).  Applies (any vie_op; phi
- * = A f directly) are 2 L + 2 launches that read the cached blocks once.
+ * = A f directly) are 2 L launches that read the cached blocks once.
  * The far field is an approximation: relative error ~1e-6 (order 6) on
  * homogeneous media, 1e-5 .. 1e-4 on heterogeneous ones (tau of a bilinear
  * sigma_t is only piecewise smooth).  Needs a 2D grid, FP32 tiles and M-iii.

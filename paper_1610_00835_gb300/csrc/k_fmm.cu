@@ -22,8 +22,8 @@
 // S-step midpoint march of the bilinear sigma_t with the sample points
 // clamped to the hull of the cell centres (nodes near the boundary lie
 // outside it).  Setup fills the near blocks and the M2L blocks on the device
-// (FP32); an apply is 2 L + 1 launches of small dense products that read the
-// cached blocks once.
+// (FP32); an apply is 2 L - 1 launches of small dense products that read the
+// cached blocks once (M2L of all levels in one of them).
 #include <math.h>
 
 #include <algorithm>
@@ -190,12 +190,29 @@ __global__ void k_fmm_m2m(int level, int P2, const float *__restrict__ Cq, const
   }
 }
 
-// M2L of one level: Lc[B] = sum over the interaction list of K_BC W_C
-__global__ void k_fmm_m2l(int level, int P2, const float *__restrict__ m2l, const float *__restrict__ W,
-                          float *__restrict__ Lc) {
+// M2L of every level in one launch (the levels do not depend on each other):
+// CTA t takes box t - first[l] of the level l with first[l] <= t < first[l + 1],
+// the small coarse levels first, so that their latency hides behind the
+// streaming of the large fine level.  Lc[B] = sum over the interaction list of
+// K_BC W_C.
+struct M2LArgs {
+  int L;
+  long first[32];     // first CTA of each level
+  long node_off[32];  // W and Lc offsets of each level
+  long m2l_off[32];   // M2L block offsets of each level
+};
+
+__global__ void k_fmm_m2l(M2LArgs a, int P2, const float *__restrict__ m2l_all, const float *__restrict__ W_all,
+                          float *__restrict__ Lc_all) {
   extern __shared__ float sh[];
+  int level = 2;
+  while (level < a.L && (long)blockIdx.x >= a.first[level + 1]) ++level;
+  const long box = (long)blockIdx.x - a.first[level];
+  const float *m2l = m2l_all + a.m2l_off[level];
+  const float *W = W_all + a.node_off[level];
+  float *Lc = Lc_all + a.node_off[level];
   const int nb = 1 << level;
-  const int bx = blockIdx.x % nb, by = blockIdx.x / nb;
+  const int bx = (int)(box % nb), by = (int)(box / nb);
   for (int i = threadIdx.x; i < kIL * P2; i += blockDim.x) {
     const int slot = i / P2, mp = i % P2;
     int ox, oy;
@@ -205,18 +222,28 @@ __global__ void k_fmm_m2l(int level, int P2, const float *__restrict__ m2l, cons
   }
   __syncthreads();
   // blockDim / P2 groups of P2 threads each take every parts-th source node
-  const float *blk = m2l + (long)blockIdx.x * kIL * P2 * P2;
+  const float *blk = m2l + box * kIL * P2 * P2;
   float *red = sh + kIL * P2;
   const int parts = blockDim.x / P2, m = threadIdx.x % P2, part = threadIdx.x / P2;
-  float acc = 0.f;
-  if (part < parts)
-    for (int i = part; i < kIL * P2; i += parts) acc = fmaf(blk[(long)i * P2 + m], sh[i], acc);
-  red[threadIdx.x] = acc;
+  // four independent chains keep four streaming loads in flight per thread
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  if (part < parts) {
+    const int I = kIL * P2;
+    int i = part;
+    for (; i + 3 * parts < I; i += 4 * parts) {
+      a0 = fmaf(__ldcs(blk + (long)i * P2 + m), sh[i], a0);
+      a1 = fmaf(__ldcs(blk + (long)(i + parts) * P2 + m), sh[i + parts], a1);
+      a2 = fmaf(__ldcs(blk + (long)(i + 2 * parts) * P2 + m), sh[i + 2 * parts], a2);
+      a3 = fmaf(__ldcs(blk + (long)(i + 3 * parts) * P2 + m), sh[i + 3 * parts], a3);
+    }
+    for (; i < I; i += parts) a0 = fmaf(__ldcs(blk + (long)i * P2 + m), sh[i], a0);
+  }
+  red[threadIdx.x] = (a0 + a1) + (a2 + a3);
   __syncthreads();
   if (threadIdx.x < P2) {
     float t = 0.f;
     for (int q = 0; q < parts; ++q) t += red[q * P2 + threadIdx.x];
-    Lc[(long)blockIdx.x * P2 + threadIdx.x] = t;
+    Lc[box * P2 + threadIdx.x] = t;
   }
 }
 
@@ -256,13 +283,21 @@ __global__ void k_fmm_leaf(int n, int L, int b, int P2, const float *__restrict_
   const float *blk = near + (long)blockIdx.x * 9 * bb * bb;
   float *red = sh + 9 * bb + P2;
   const int parts = blockDim.x / bb, j = threadIdx.x % bb, part = threadIdx.x / bb;
-  float acc = 0.f;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
   if (part < parts) {
-    for (int i = part; i < 9 * bb; i += parts) acc = fmaf(blk[(long)i * bb + j], sh[i], acc);
+    const int I = 9 * bb;
+    int i = part;
+    for (; i + 3 * parts < I; i += 4 * parts) {
+      a0 = fmaf(__ldcs(blk + (long)i * bb + j), sh[i], a0);
+      a1 = fmaf(__ldcs(blk + (long)(i + parts) * bb + j), sh[i + parts], a1);
+      a2 = fmaf(__ldcs(blk + (long)(i + 2 * parts) * bb + j), sh[i + 2 * parts], a2);
+      a3 = fmaf(__ldcs(blk + (long)(i + 3 * parts) * bb + j), sh[i + 3 * parts], a3);
+    }
+    for (; i < I; i += parts) a0 = fmaf(__ldcs(blk + (long)i * bb + j), sh[i], a0);
     if (part == 0)
-      for (int m = 0; m < P2; ++m) acc = fmaf(Pm[m * bb + j], sh[9 * bb + m], acc);
+      for (int m = 0; m < P2; ++m) a1 = fmaf(Pm[m * bb + j], sh[9 * bb + m], a1);
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = (a0 + a1) + (a2 + a3);
   __syncthreads();
   if (threadIdx.x < bb) {
     double v = 0.0;
@@ -388,10 +423,19 @@ vie_status fmm_apply(const FmmPlan &fp, int op, const float *s, const double *g,
                                                               fp.W + fp.node_off[l]);
     VIE_CHECK_LAUNCH("k_fmm_m2m");
   }
-  // interactions, then the downward pass
-  for (int l = 2; l <= L; ++l) {
-    k_fmm_m2l<<<1 << (2 * l), tm, sizeof(float) * (kIL * P2 + tm), st>>>(l, P2, fp.m2l + fp.m2l_off[l],
-                                                                 fp.W + fp.node_off[l], fp.Lc + fp.node_off[l]);
+  // interactions (all levels in one launch), then the downward pass
+  {
+    M2LArgs a;
+    a.L = L;
+    long first = 0;
+    for (int l = 2; l <= L; ++l) {
+      a.first[l] = first;
+      a.node_off[l] = fp.node_off[l];
+      a.m2l_off[l] = fp.m2l_off[l];
+      first += 1L << (2 * l);
+    }
+    a.first[L + 1] = first;
+    k_fmm_m2l<<<(unsigned)first, tm, sizeof(float) * (kIL * P2 + tm), st>>>(a, P2, fp.m2l, fp.W, fp.Lc);
     VIE_CHECK_LAUNCH("k_fmm_m2l");
   }
   for (int l = 2; l < L; ++l) {
