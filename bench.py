@@ -342,30 +342,41 @@ def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
 
 
 def measure_batch(P, torch, stream, local, reps=3):
-    """16 uneven 2D grids n = 64 ... 256 (Sum N^2 = 1.94e10 pairs) in one
-    persistent launch replayed from a CUDA graph, configuration autotuned."""
+    """16 uneven 2D grids n = 64 ... 256 (Sum N^2 = 1.94e10 pairs) replayed from
+    one CUDA graph, the persistent tile-pair launch's configuration autotuned:
+    with the automatic kernel choice (the displacement kernel for n <= 226, one
+    launch each, the persistent launch for the rest) and with every grid in the
+    one persistent launch."""
     media = V.uneven_media()
     ns = [m.n for m in media]
-    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media], device=local)
-    t0 = time.perf_counter()
-    cfg = P.vie_batch_autotune(b)
-    tune_s = time.perf_counter() - t0
     g = torch.as_tensor(np.concatenate([m.f for m in media]), dtype=torch.float64,
                         device=f"cuda:{local}")
     y = torch.empty_like(g)
-    P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(reps):
-        P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
-    e.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(e) / reps
     pairs = float(sum(m.N * m.N for m in media))
-    P.vie_batch_destroy(b)
-    return {"grids": ns, "pairs": pairs, "ms": ms, "gpair_per_s": pairs / (ms * 1e-3) / 1e9,
-            "config": {"groups_per_cta": cfg[0], "smem_policy": cfg[1]}, "autotune_s": tune_s}
+    out = {"grids": ns, "pairs": pairs}
+    for name, kernel in (("auto", P.VIE_KERNEL_AUTO), ("persistent_only", P.VIE_KERNEL_SYMMETRIC)):
+        b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media], device=local,
+                               kernel=kernel)
+        t0 = time.perf_counter()
+        cfg = P.vie_batch_autotune(b)
+        tune_s = time.perf_counter() - t0
+        P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / reps
+        P.vie_batch_destroy(b)
+        row = {"ms": ms, "gpair_per_s": pairs / (ms * 1e-3) / 1e9,
+               "config": {"groups_per_cta": cfg[0], "smem_policy": cfg[1]}, "autotune_s": tune_s}
+        if name == "auto":
+            out.update(row)
+        else:
+            out[name] = row
+    return out
 
 
 def measure_learned(P, torch, local, seeds=(9004, 9005)):

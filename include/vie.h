@@ -290,8 +290,13 @@ typedef struct vie_batch vie_batch;
 
 /* Create a batch of `count` 2D media (grids[i].dim == 2), each with its own
  * n and host FP64 coefficients sigma_t[i], sigma_s[i] (copied).  Options must
- * be FP32 tiles with the S = 64 march and M-iii.  Vectors of the batch are packed:
- * medium i occupies cells [offsets[i], offsets[i+1]) (vie_batch_layout).
+ * be FP32 tiles with the S = 64 march and M-iii.  o->kernel selects how the
+ * grids run: VIE_KERNEL_SYMMETRIC puts every grid's tile pairs into one
+ * persistent launch; VIE_KERNEL_AUTO (and DISPLACEMENT) give each grid that
+ * the displacement kernel takes (2 <= n <= 226) a launch of that kernel and
+ * put only the others into the persistent launch; all of them are replayed
+ * from one CUDA graph.  Vectors of the batch are packed: medium i occupies
+ * cells [offsets[i], offsets[i+1]) (vie_batch_layout).
  * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
 vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
                             const double *const *sigma_t, const double *const *sigma_s,

@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "vie_internal.cuh"
@@ -402,8 +403,7 @@ vie_status plan_pairs(const Medium &m, int steps, int tau_closed, int precision,
     p.smem_sigma = (!tau_closed && want <= (size_t)prop.sharedMemPerBlockOptin) ? 1 : 0;
     p.smem_bytes = p.smem_sigma ? want : stage;
     const void *k = pair_kernel(m.dim, kernel_mode(p, tau_closed), steps);
-    VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p.smem_bytes));
+    VIE_TRY(raise_smem_limit(k, (size_t)((int)p.smem_bytes)));
     VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kPairThreads, p.smem_bytes));
   }
   bps = std::max(1, bps);
@@ -468,6 +468,16 @@ vie_status launch_pairs(const Medium &m, const PairPlan &plan, int steps, int ta
   void *args[] = {&a};
   VIE_CUDA(cudaLaunchKernel(k, dim3(plan.grid), dim3(kPairThreads), args, plan.smem_bytes, st));
   count_launch();
+  return VIE_OK;
+}
+
+vie_status raise_smem_limit(const void *k, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes at;
+  VIE_CUDA(cudaFuncGetAttributes(&at, k));
+  if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return VIE_OK;
+  VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return VIE_OK;
 }
 

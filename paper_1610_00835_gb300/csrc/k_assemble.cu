@@ -217,8 +217,7 @@ vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const doub
   }
   const size_t smem = per_group * groups + lat_bytes + 64;
   AsmKernel k = pick_asm(dim, sp.ldp, sp.plane, sp.global_lattice);
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kG * groups, smem));
   if (bps < 1) {

@@ -11,6 +11,9 @@
 // memory through L1 instead.  The last CTA to finish resets the counter, so
 // the launch can be replayed from a CUDA graph.  Per-grid partial sums
 // [T][N] are reduced by the single-grid reduce kernel, one launch per grid.
+// With the automatic kernel choice, every grid that the displacement kernel
+// takes (k_pairs_disp.cu: 2 <= n <= 226) runs it instead, one launch of its
+// own in the same graph, and only the others go to the persistent launch.
 #include <math.h>
 #include <stdio.h>
 
@@ -201,7 +204,7 @@ struct BatchPlanImpl {
 };
 
 vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *cell_off,
-                      const long *lat_off, const long *part_off, int groups, int smem_policy,
+                      const long *lat_off, const long *part_off, const int *skip, int groups, int smem_policy,
                       int device) {
   cudaDeviceProp prop;
   VIE_CUDA(cudaGetDeviceProperties(&prop, device));
@@ -223,15 +226,20 @@ vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *c
     G.n_items = G.T * (G.T + 1) / 2;
     G.lat_elems = (long)(n + 1) * (n + 1);
     G.smem = (G.lat_elems <= lat_limit_smem && G.lat_elems <= lat_limit_policy) ? 1 : 0;
-    if (G.smem) max_lat = std::max(max_lat, G.lat_elems);
+    if (G.smem && !skip[i]) max_lat = std::max(max_lat, G.lat_elems);
     G.lat_off = lat_off[i];
     G.cell_off = cell_off[i];
     G.part_off = part_off[i];
     G.item_off = (long)items.size();
     G.batch_begin = nb;
-    nb += (G.n_items + groups - 1) / groups;
-    for (int a = 0; a < G.T; ++a)
-      for (int b = a; b < G.T; ++b) items.push_back(make_int2(a, b));
+    if (skip[i]) {
+      G.n_items = 0;  // this grid runs the displacement kernel instead
+      G.smem = 0;
+    } else {
+      nb += (G.n_items + groups - 1) / groups;
+      for (int a = 0; a < G.T; ++a)
+        for (int b = a; b < G.T; ++b) items.push_back(make_int2(a, b));
+    }
     const double h = 1.0 / n;
     G.tau_scale2 = (float)(h / kS * 1.4426950408889634);
     G.wcoef = (float)(h / (2.0 * kPi));
@@ -244,18 +252,19 @@ vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *c
   bp->items = nullptr;
   VIE_CUDA(cudaMalloc((void **)&bp->grids, sizeof(BatchGrid) * count));
   VIE_CUDA(cudaMemcpy(bp->grids, bp->host.data(), sizeof(BatchGrid) * count, cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&bp->items, sizeof(int2) * items.size()));
-  VIE_CUDA(cudaMemcpy(bp->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(cudaMalloc((void **)&bp->items, sizeof(int2) * std::max<size_t>(1, items.size())));
+  if (!items.empty())
+    VIE_CUDA(cudaMemcpy(bp->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   bp->smem = batch_smem(groups, max_lat);
   const void *k = batch_kernel(groups);
-  VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp->smem));
+  VIE_TRY(raise_smem_limit(k, (size_t)((int)bp->smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kG * groups, bp->smem));
   if (bps < 1) {
     set_error("batch: kernel does not fit on an SM");
     return VIE_ERR_UNSUPPORTED;
   }
-  bp->grid = (int)std::min<long>((long)bps * prop.multiProcessorCount, nb);
+  bp->grid = (int)std::min<long>((long)bps * prop.multiProcessorCount, nb);  // 0: nothing to launch
   return VIE_OK;
 }
 
@@ -275,6 +284,7 @@ vie_status batch_pad_lattice(int n, const double *sig, float *out, cudaStream_t 
 
 vie_status batch_launch(const BatchPlanImpl &bp, const float *lattice, const float *src,
                         double *partial, int *counter, cudaStream_t st) {
+  if (bp.grid < 1) return VIE_OK;  // every grid runs the displacement kernel
   BatchArgs a;
   a.grids = bp.grids;
   a.count = (int)bp.host.size();
@@ -315,6 +325,8 @@ struct vie_batch {
   const void *key_y = nullptr;
   int graph_kernels = 0;
   double *stage_g = nullptr, *stage_y = nullptr;
+  std::vector<DispPlan> disp;  // per grid: the displacement kernel, when it takes the grid
+  std::vector<int> use_disp;
 };
 
 namespace {
@@ -328,6 +340,7 @@ void batch_free(vie_batch *b) {
                   (void *)b->stage_y})
     if (p) cudaFree(p);
   batch_plan_free(&b->plan);
+  for (auto &d : b->disp) disp_release(&d);
 }
 
 bool dev_ptr(const void *p) {
@@ -351,22 +364,38 @@ vie_status replan(vie_batch *b, int groups, int policy) {
   b->graph = nullptr;
   b->key_op = -1;
   return batch_plan(&b->plan, b->count, b->ns.data(), b->cell_off.data(), b->lat_off.data(),
-                    b->part_off.data(), groups, policy, b->device);
+                    b->part_off.data(), b->use_disp.data(), groups, policy, b->device);
 }
 
-// Queue one batched apply on stream st (also used under graph capture).
-vie_status enqueue(vie_batch *b, int op, const double *g, double *y, cudaStream_t st) {
+// Queue one batched apply on stream st (also used under graph capture);
+// *kernels = the launches queued.
+vie_status enqueue(vie_batch *b, int op, const double *g, double *y, cudaStream_t st, int *kernels) {
   const long total = b->cell_off[b->count];
   vie_status s = launch_source_prep(total, op, b->sig_s, g, VIE_PREC_FP32, b->src, st);
   if (s != VIE_OK) return s;
+  int k = 1;
   if ((s = batch_launch(b->plan, b->lattice, b->src, b->partial, b->counter, st)) != VIE_OK) return s;
+  if (b->plan.grid > 0) ++k;
   for (int i = 0; i < b->count; ++i) {
     const long off = b->cell_off[i];
     const BatchGrid &G = b->plan.host[i];
-    if ((s = launch_reduce(G.N, G.T, op, b->partial + b->part_off[i], b->diag + off,
-                           b->sig_s + off, g + off, y + off, st)) != VIE_OK)
-      return s;
+    if (b->use_disp[i]) {
+      const DispPlan &dp = b->disp[i];
+      const double h = 1.0 / G.n;
+      if ((s = disp_source(dp, G.N, op, b->sig_s + off, g + off, b->src + off, st)) != VIE_OK) return s;
+      if ((s = disp_launch(dp, G.n, (float)(h / kS * 1.4426950408889634), (float)(h / (2.0 * kPi)), b->src + off,
+                           st)) != VIE_OK)
+        return s;
+      if ((s = disp_reduce(dp, G.N, op, b->diag + off, b->sig_s + off, g + off, y + off, st)) != VIE_OK) return s;
+      k += 3;
+    } else {
+      if ((s = launch_reduce(G.N, G.T, op, b->partial + b->part_off[i], b->diag + off, b->sig_s + off, g + off,
+                             y + off, st)) != VIE_OK)
+        return s;
+      ++k;
+    }
   }
+  *kernels = k;
   return VIE_OK;
 }
 
@@ -386,6 +415,9 @@ vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
   if (opts.steps != 64 || opts.tau_mode != VIE_TAU_MARCH || opts.precision != VIE_PREC_FP32 ||
       opts.disc != VIE_DISC_MIII)
     return bad("vie_batch_create: the batch supports FP32 tiles with the S = 64 march and M-iii");
+  if (opts.kernel != VIE_KERNEL_AUTO && opts.kernel != VIE_KERNEL_SYMMETRIC &&
+      opts.kernel != VIE_KERNEL_DISPLACEMENT)
+    return bad("vie_batch_create: kernel must be AUTO, SYMMETRIC or DISPLACEMENT");
   for (int i = 0; i < count; ++i) {
     if (grids[i].dim != 2 || grids[i].n < 1 || grids[i].n > 4096)
       return bad("vie_batch_create: 2D grids with 1 <= n <= 4096");
@@ -447,6 +479,16 @@ vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
     if ((s = launch_selfcell(2, b->ns[i], b->sig_t + b->cell_off[i], b->diag + b->cell_off[i], 0)) != VIE_OK)
       return fail(s);
   }
+  b->disp.assign(count, DispPlan{});
+  b->use_disp.assign(count, 0);
+  if (opts.kernel != VIE_KERNEL_SYMMETRIC) {
+    BTRY(cudaDeviceSynchronize());
+    for (int i = 0; i < count; ++i) {
+      if ((s = disp_prepare(&b->disp[i], b->ns[i], b->lattice + b->lat_off[i], opts.device, 0)) != VIE_OK)
+        return fail(s);
+      b->use_disp[i] = b->disp[i].usable;
+    }
+  }
   if ((s = replan(b, 8, 0)) != VIE_OK) return fail(s);
   BTRY(cudaDeviceSynchronize());
 #undef BTRY
@@ -502,11 +544,13 @@ vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, 
     b->exec = nullptr;
     b->graph = nullptr;
     VIE_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    vie_status s = enqueue(b, op, gg, yy, b->cap);
+    int kernels = 0;
+    vie_status s = enqueue(b, op, gg, yy, b->cap, &kernels);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (s != VIE_OK) {
       if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();  // the invalidated capture's error is reported through s
       return s;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -515,7 +559,7 @@ vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, 
     b->key_op = op;
     b->key_g = gg;
     b->key_y = yy;
-    b->graph_kernels = 2 + b->count;
+    b->graph_kernels = kernels;
   }
   VIE_CUDA(cudaGraphLaunch(b->exec, st));
   for (int i = 0; i < b->graph_kernels; ++i) count_launch();

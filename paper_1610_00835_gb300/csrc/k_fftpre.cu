@@ -211,11 +211,9 @@ vie_status fft_prepare(FftPre *fp, int n, double mu, double mu_s, int mii, cudaS
   VIE_CUDA(cudaStreamSynchronize(st));
   const size_t smem = sizeof(float2) * (size_t)m;
   if (smem > 48 * 1024) {
-    VIE_CUDA(cudaFuncSetAttribute((const void *)k_fft_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    VIE_CUDA(cudaFuncSetAttribute((const void *)k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    VIE_CUDA(cudaFuncSetAttribute((const void *)k_fft_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    VIE_TRY(raise_smem_limit((const void *)k_fft_rows_fwd, (size_t)((int)smem)));
+    VIE_TRY(raise_smem_limit((const void *)k_fft_cols, (size_t)((int)smem)));
+    VIE_TRY(raise_smem_limit((const void *)k_fft_rows_inv, (size_t)((int)smem)));
   }
   fp->n = n;
   fp->m = m;

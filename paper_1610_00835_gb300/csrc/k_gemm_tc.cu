@@ -502,8 +502,7 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
     return VIE_ERR_UNSUPPORTED;
   }
   const size_t smem = 1024 + a.stages * stage_bytes + 256;
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k_gemm_bf16x3,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k_gemm_bf16x3, (size_t)((int)smem)));
   dim3 grid((unsigned)((N + BM - 1) / BM), (unsigned)splits);
   k_gemm_bf16x3<<<grid, 128, smem, st>>>(mkhi, mklo, mghi, mglo, a);
   VIE_CHECK_LAUNCH("k_gemm_bf16x3");

@@ -875,7 +875,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
   const int ldp = disp_ldp(n), rows = n + 1 + kPad;
   DispKernel k = pick_disp(ldp);
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads, smem));
   if (bps < 1) return VIE_OK;
@@ -884,9 +884,8 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   const size_t smem_store = sizeof(float) * (size_t)rows * ldp + 16;
   const size_t smem_stream = 16;
   DispKernel ks = pick_store(ldp);
-  VIE_CUDA(cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_store));
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k_stream_disp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_stream));
+  VIE_TRY(raise_smem_limit((const void *)ks, (size_t)((int)smem_store)));
+  VIE_TRY(raise_smem_limit((const void *)k_stream_disp, (size_t)((int)smem_stream)));
   int bps_store = 0, bps_stream = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_store, ks, kThreads, smem_store));
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_stream, k_stream_disp, kThreads, smem_stream));
@@ -994,7 +993,7 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
   const void *kx = out == kSymBlocks  ? (const void *)k_expand_pairs<kSymBlocks>
                    : out == kDenseF32 ? (const void *)k_expand_pairs<kDenseF32>
                                       : (const void *)k_expand_pairs<kDenseBF16>;
-  VIE_CUDA(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_TRY(raise_smem_limit(kx, (size_t)((int)smem)));
   k_to_f32<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, sigma_s, dp.ss32);
   VIE_CHECK_LAUNCH("k_to_f32");
   const int grid = prop.multiProcessorCount;

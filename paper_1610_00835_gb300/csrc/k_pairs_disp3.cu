@@ -493,7 +493,7 @@ vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int devi
   const size_t smem = disp3_smem_bytes(n);
   if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
   Disp3Kernel k = pick_disp3(n);
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads3, smem));
   if (bps < 1) return VIE_OK;

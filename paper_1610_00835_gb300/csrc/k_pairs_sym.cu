@@ -244,8 +244,7 @@ vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_pad
     smem = sym_group_bytes();
     sp->global_lattice = 1;
   }
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kCtaThreads, smem));
   if (bps < 1) return VIE_OK;
@@ -332,8 +331,7 @@ vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *s
   const size_t smem = sym_smem_bytes(dim, n, nullptr, nullptr);
   sp->usable = 0;
   if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
-  VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kCtaThreads, smem));
   if (bps < 1) return VIE_OK;

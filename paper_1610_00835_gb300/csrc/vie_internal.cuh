@@ -28,6 +28,16 @@ void count_launch();
     if (_e != cudaSuccess) return ::vie::cuda_fail(_e, #call); \
   } while (0)
 
+#define VIE_TRY(call)                                      \
+  do {                                                     \
+    vie_status _s = (call);                                \
+    if (_s != VIE_OK) return _s;                           \
+  } while (0)
+
+// Raise kernel k's dynamic shared-memory limit to at least `bytes`, never
+// lower it: a kernel instance is shared by handles of different sizes.
+vie_status raise_smem_limit(const void *k, size_t bytes);
+
 #define VIE_CHECK_LAUNCH(what)                             \
   do {                                                     \
     cudaError_t _e = cudaGetLastError();                   \

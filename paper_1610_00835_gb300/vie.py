@@ -260,7 +260,7 @@ class VieBatch:
             pass
 
 
-def vie_batch_create(ns, sigma_t_list, sigma_s_list, device: int = 0) -> VieBatch:
+def vie_batch_create(ns, sigma_t_list, sigma_s_list, device: int = 0, kernel: int = VIE_KERNEL_AUTO) -> VieBatch:
     L = load()
     count = len(ns)
     grids = (vie_grid * count)(*[vie_grid(2, int(n)) for n in ns])
@@ -268,7 +268,7 @@ def vie_batch_create(ns, sigma_t_list, sigma_s_list, device: int = 0) -> VieBatc
     ss = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in sigma_s_list]
     pst = (_vp * count)(*[a.ctypes.data for a in st])
     pss = (_vp * count)(*[a.ctypes.data for a in ss])
-    o = vie_opts(64, VIE_TAU_MARCH, VIE_PREC_FP32, device, VIE_KERNEL_AUTO)
+    o = vie_opts(64, VIE_TAU_MARCH, VIE_PREC_FP32, device, kernel)
     b = C.c_void_p()
     _check(L.vie_batch_create(C.byref(b), count, grids, pst, pss, C.byref(o)))
     total = C.c_longlong()

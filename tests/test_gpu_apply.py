@@ -235,3 +235,17 @@ def test_symmetric_kernel_every_lattice_stride(n):
     rows = _sampled_rows(m.N, 16, n)
     want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
     assert rel_l2(got[rows], want) < FP32_TOL
+
+
+def test_handles_of_different_sizes_share_kernel_instances():
+    # grids 40 and 23 run the same displacement-kernel instance with different
+    # shared-memory sizes; creating the smaller one must not break the larger
+    media = {n: V.bump_medium(2, n, 3, 0.9, seed=4950 + n) for n in (40, 23, 100)}
+    handles = {n: P.vie_create(2, n, m.sigma_t, m.sigma_s) for n, m in media.items()}
+    for n, h in handles.items():
+        assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
+        m = media[n]
+        g = m.f + 0.05 * rng_vec(m.N, n)
+        rows = _sampled_rows(m.N, 6, n)
+        want = O.apply(2, m.sigma_t, m.sigma_s, g, rows=rows)
+        assert rel_l2(gpu_apply(h, P.VIE_OP_K_SIGMA_S, g)[rows], want) < FP32_TOL

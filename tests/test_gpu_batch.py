@@ -16,9 +16,9 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def make_batch(ns, seed0=300):
+def make_batch(ns, seed0=300, kernel=P.VIE_KERNEL_AUTO):
     media = [V.bump_medium(2, n, 4, 0.9, seed=seed0 + i) for i, n in enumerate(ns)]
-    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media])
+    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media], kernel=kernel)
     return b, media
 
 
@@ -26,9 +26,10 @@ def packed(b, media, rng):
     return np.concatenate([m.f + 0.1 * rng.standard_normal(m.N) for m in media])
 
 
-def test_small_uneven_batch_all_rows_and_single_grid_equality():
+@pytest.mark.parametrize("kernel", [P.VIE_KERNEL_AUTO, P.VIE_KERNEL_SYMMETRIC])
+def test_small_uneven_batch_all_rows_and_single_grid_equality(kernel):
     ns = [1, 5, 17, 40, 23]
-    b, media = make_batch(ns)
+    b, media = make_batch(ns, kernel=kernel)
     g = packed(b, media, np.random.default_rng(0))
     y = torch.empty(b.total, dtype=torch.float64, device="cuda:0")
     P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, dev(g), y)
@@ -37,12 +38,16 @@ def test_small_uneven_batch_all_rows_and_single_grid_equality():
         sl = slice(b.offsets[i], b.offsets[i + 1])
         want = O.apply(2, m.sigma_t, m.sigma_s, g[sl])
         assert rel_l2(y[sl], want) < TOL, ns[i]
-        # the batch runs the tile-pair kernel: same arithmetic as a single-grid
-        # handle forced to it
-        h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
+        # each grid runs the kernel a single-grid handle with the same choice
+        # takes (the displacement kernel for n = 5 .. 40 under AUTO, the
+        # tile-pair kernel otherwise): the same arithmetic
+        h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, kernel=kernel)
         y1 = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
         P.vie_apply(h, P.VIE_OP_K_SIGMA_S, dev(g[sl]), y1)
-        np.testing.assert_allclose(y[sl], host(y1), rtol=1e-12, atol=0)
+        if P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT:
+            np.testing.assert_array_equal(y[sl], host(y1))      # exact fixed-point sums
+        else:
+            np.testing.assert_allclose(y[sl], host(y1), rtol=1e-12, atol=0)
 
 
 def test_ops_graph_recapture_and_host_pointers():
@@ -84,16 +89,19 @@ def test_autotune_and_cache(tmp_path):
         assert rel_l2(y[sl], O.apply(2, m.sigma_t, m.sigma_s, g[sl])) < TOL
 
 
-def test_sixteen_uneven_grids_64_to_256_sampled_rows():
+@pytest.mark.parametrize("kernel", [P.VIE_KERNEL_AUTO, P.VIE_KERNEL_SYMMETRIC])
+def test_sixteen_uneven_grids_64_to_256_sampled_rows(kernel):
     ns = V.uneven_grid_sizes()
     media = V.uneven_media()
-    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media])
+    b = P.vie_batch_create(ns, [m.sigma_t for m in media], [m.sigma_s for m in media], kernel=kernel)
     g = np.concatenate([m.f for m in media])
     y = torch.empty(b.total, dtype=torch.float64, device="cuda:0")
     P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, dev(g), y)
     y = host(y)
     rng = np.random.default_rng(3)
-    for i in (0, 7, 12, 13, 15):   # 64, 154, 218 (largest in shared memory), 230 and 256 (global)
+    # 64, 154, 218 (the displacement kernel under AUTO; the largest lattice in
+    # shared memory for the tile pairs), 230 and 256 (tile pairs, lattice from global)
+    for i in (0, 7, 12, 13, 15):
         m = media[i]
         sl = slice(b.offsets[i], b.offsets[i + 1])
         rows = np.unique(np.concatenate([rng.choice(m.N, 6, replace=False), [0, m.N - 1]]))
