@@ -662,6 +662,17 @@ def run_ours(args):
                 "gpair_per_s_apply": float(N) * N / (kern_ms * 1e-3) / 1e9}
     if clocks["sm_mhz"]:
         roofline["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    # the per-pair work of the per-sample march (about 13 S + 12 FP32 issues per
+    # ordered pair at S = 64: 844), against the FP32 issue rate of the part: the
+    # stencil form does far fewer issues per pair, so this reads above 1
+    per_pair = 13 * S_STEPS + 12
+    issue_rate = sms * 128 * max_mhz * 1e6
+    roofline["per_sample_march_basis"] = {
+        "fp32_issues_per_pair": per_pair,
+        "pair_bound_gpair_per_s": issue_rate / per_pair / 1e9,
+        "frac": float(N) * N / (kern_ms * 1e-3) / (issue_rate / per_pair),
+        "note": "ordered pairs N^2 per apply; above 1 because the stencil march groups the samples "
+                "by lattice cell (about 142 multiply-adds per pair at 128^2, symmetric pairs once)"}
 
     chosen = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_SYM32, U_or)
     asm_bf16 = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_BF16X3, U_or)
