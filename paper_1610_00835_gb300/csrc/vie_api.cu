@@ -410,7 +410,7 @@ extern "C" {
 
 const char *vie_last_error(void) { return g_last_error.c_str(); }
 
-const char *vie_version(void) { return "vie-gb300 0.1 (sm_103a)"; }
+const char *vie_version(void) { return "vie-gb300 0.2 (sm_103a; M-iii/M-ii, FMM, FFT/diffusion/learned preconditioners)"; }
 
 unsigned long long vie_kernel_launches(void) { return g_launches.load(); }
 
