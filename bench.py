@@ -753,6 +753,50 @@ def run_ours(args):
     return 0
 
 
+def run_only(args):
+    """One workload alone, repeated (a small driver for profilers): the step-two
+    sweep of the 32^3 medium on 128 directions, the 16-grid batched apply, or the
+    learned preconditioner's forward pass at 256^2."""
+    import torch
+    import paper_1610_00835_gb300 as P
+
+    dev = "cuda:0"
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.only == "sweep":
+        m = V.heterogeneous_3d(n=32)
+        h = P.vie_create(3, 32, m.sigma_t, m.sigma_s)
+        f = torch.as_tensor(m.f, dtype=torch.float64, device=dev)
+        U = torch.empty_like(f)
+        P.vie_solve_gmres(h, f, U, rtol=RTOL)
+        dirs = torch.as_tensor(V.fibonacci_directions(128).astype(np.float32), device=dev)
+        Phi = torch.empty(128 * m.N, dtype=torch.float32, device=dev)
+        run = lambda: P.ert_sweep(h, U, f, dirs, Phi)  # noqa: E731
+    elif args.only == "batch":
+        media = [m for m in V.uneven_media() if m.n <= args.n]   # --n: the largest grid taken
+        b = P.vie_batch_create([m.n for m in media], [m.sigma_t for m in media], [m.sigma_s for m in media],
+                               kernel=P.VIE_KERNEL_SYMMETRIC)
+        g = torch.as_tensor(np.concatenate([m.f for m in media]), dtype=torch.float64, device=dev)
+        y = torch.empty_like(g)
+        run = lambda: P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)  # noqa: E731
+    else:
+        net = P.vie_unet_create(4, 32)
+        P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
+        n = 256
+        x = torch.randn(3 * n * n, dtype=torch.float32, device=dev)
+        o = torch.empty(n * n, dtype=torch.float32, device=dev)
+        run = lambda: P.vie_unet_forward(net, x, o, 1, n, use_bf16=True)  # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        run()
+    e.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "only", "workload": args.only, "ms": a.elapsed_time(e) / args.steps}), flush=True)
+    return 0
+
+
 def run_apply_only(args):
     """K operator applies on the bench medium (a small driver for profilers)."""
     import torch
@@ -792,6 +836,8 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32", "fmm"], default="otf")
+    ap.add_argument("--only", choices=["sweep", "batch", "unet"], default=None,
+                    help="run one workload alone, for profilers")
     ap.add_argument("--disc", choices=["m3", "m2"], default="m3",
                     help="apply-only: discretisation M-iii (default) or M-ii (2D)")
     ap.add_argument("--nrhs", type=int, default=1)
@@ -804,6 +850,8 @@ def main(argv=None):
         return run_reference(args)
     if args.apply_only:
         return run_apply_only(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 
