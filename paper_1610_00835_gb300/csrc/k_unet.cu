@@ -27,67 +27,90 @@ namespace vie {
 
 namespace {
 
-constexpr int TX = 32, TY = 16;   // output tile of the 3x3 convolution kernels
+constexpr int TX = 32;            // output tile width of the 3x3 convolution kernels
 constexpr int CIB = 8;            // input channels staged per step
-constexpr int COB = 32;           // output channels per CTA
+constexpr int COB = 32;           // output channels per CTA of the weight-gradient kernel
 
 // ------------------------------------------------------------ kernels
 
-// 3x3 convolution, zero padding 1, + bias (+ relu).  Thread (tx, ty) owns the
-// pixels (x0 + tx, y0 + ty) and (x0 + tx, y0 + ty + 8) for all COB outputs.
-template <bool RELU, typename WT>
+// 3x3 convolution, zero padding 1, + bias (+ relu).  A CTA computes a TX x TY
+// pixel tile for COBC output channels; thread (tx, ty), ty in 0..7, owns the
+// pixels (x0 + tx, y0 + ty + 8 k), k < TY / 8, for all COBC outputs.  Every
+// output sums its input channels and taps in the same order whatever TY and
+// COBC are, so the tile shape changes no result bit.
+template <bool RELU, typename WT, int TY, int COBC>
 __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, long in_bs, int Ci,
                                                const WT *__restrict__ w, const float *__restrict__ bias,
                                                float *__restrict__ out, long out_bs, int Co, int H,
                                                int W, int co_blocks) {
+  static_assert(TY % 8 == 0 && COBC % 4 == 0, "tile shape");
+  constexpr int PY = TY / 8;
   __shared__ float in_s[CIB][TY + 2][TX + 2];
-  __shared__ __align__(16) float w_s[CIB][9][COB];
+  __shared__ __align__(16) float w_s[CIB][9][COBC];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;  // ty in 0..7
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int b = blockIdx.z / co_blocks, cb = blockIdx.z % co_blocks;
-  const int co0 = cb * COB;
-  float acc0[COB], acc1[COB];
+  const int co0 = cb * COBC;
+  float acc[PY][COBC];
 #pragma unroll
-  for (int c = 0; c < COB; ++c) acc0[c] = acc1[c] = 0.f;
+  for (int k = 0; k < PY; ++k)
+#pragma unroll
+    for (int c = 0; c < COBC; ++c) acc[k][c] = 0.f;
   const float *inb = in + b * in_bs;
   const long plane = (long)H * W;
+  // Each step stages CIB input channels: the padded pixel tile through
+  // asynchronous 4-byte copies (zero-filled outside the image), the weights
+  // through registers, all loads in flight together.  Flat index i of a
+  // staging array is its shared-memory offset.
+  constexpr int IN_N = CIB * (TY + 2) * (TX + 2);
+  constexpr int W_N = CIB * 9 * COBC, W_K = (W_N + 255) / 256;
+  const unsigned in_s0 = (unsigned)__cvta_generic_to_shared(&in_s[0][0][0]);
   for (int ci0 = 0; ci0 < Ci; ci0 += CIB) {
     __syncthreads();
-    for (int i = threadIdx.x; i < CIB * (TY + 2) * (TX + 2); i += 256) {
+    for (int i = threadIdx.x; i < IN_N; i += 256) {
       const int c = i / ((TY + 2) * (TX + 2)), r = i % ((TY + 2) * (TX + 2));
-      const int yy = r / (TX + 2), xx = r % (TX + 2);
-      const int gy = y0 - 1 + yy, gx = x0 - 1 + xx;
-      float v = 0.f;
-      if (ci0 + c < Ci && gy >= 0 && gy < H && gx >= 0 && gx < W) v = inb[(ci0 + c) * plane + (long)gy * W + gx];
-      in_s[c][yy][xx] = v;
+      const int gy = y0 - 1 + r / (TX + 2), gx = x0 - 1 + r % (TX + 2);
+      const bool ok = ci0 + c < Ci && gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const float *src = ok ? inb + (ci0 + c) * plane + (long)gy * W + gx : inb;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(in_s0 + 4u * i), "l"(src),
+                   "r"(ok ? 4 : 0)
+                   : "memory");
     }
-    for (int i = threadIdx.x; i < CIB * 9 * COB; i += 256) {
-      const int c = i / (9 * COB), r = i % (9 * COB);
-      const int tap = r / COB, co = r % COB;
-      float v = 0.f;
-      if (ci0 + c < Ci && co0 + co < Co) v = (float)w[((long)(co0 + co) * Ci + ci0 + c) * 9 + tap];
-      w_s[c][tap][co] = v;
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    float pwt[W_K];
+#pragma unroll
+    for (int k = 0; k < W_K; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const int c = i / (9 * COBC), r = i % (9 * COBC);
+      const int tap = r / COBC, co = r % COBC;
+      pwt[k] = i < W_N && ci0 + c < Ci && co0 + co < Co
+                   ? (float)w[((long)(co0 + co) * Ci + ci0 + c) * 9 + tap]
+                   : 0.f;
     }
+#pragma unroll
+    for (int k = 0; k < W_K; ++k)
+      if (threadIdx.x + 256 * k < W_N) (&w_s[0][0][0])[threadIdx.x + 256 * k] = pwt[k];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < CIB; ++c) {
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int dy = tap / 3, dx = tap % 3;
-        const float v0 = in_s[c][ty + dy][tx + dx];
-        const float v1 = in_s[c][ty + 8 + dy][tx + dx];
+        float v[PY];
+#pragma unroll
+        for (int k = 0; k < PY; ++k) v[k] = in_s[c][ty + 8 * k + dy][tx + dx];
         const float4 *wr = reinterpret_cast<const float4 *>(&w_s[c][tap][0]);
 #pragma unroll
-        for (int q = 0; q < COB / 4; ++q) {
+        for (int q = 0; q < COBC / 4; ++q) {
           const float4 wv = wr[q];
-          acc0[4 * q + 0] = fmaf(v0, wv.x, acc0[4 * q + 0]);
-          acc0[4 * q + 1] = fmaf(v0, wv.y, acc0[4 * q + 1]);
-          acc0[4 * q + 2] = fmaf(v0, wv.z, acc0[4 * q + 2]);
-          acc0[4 * q + 3] = fmaf(v0, wv.w, acc0[4 * q + 3]);
-          acc1[4 * q + 0] = fmaf(v1, wv.x, acc1[4 * q + 0]);
-          acc1[4 * q + 1] = fmaf(v1, wv.y, acc1[4 * q + 1]);
-          acc1[4 * q + 2] = fmaf(v1, wv.z, acc1[4 * q + 2]);
-          acc1[4 * q + 3] = fmaf(v1, wv.w, acc1[4 * q + 3]);
+#pragma unroll
+          for (int k = 0; k < PY; ++k) {
+            acc[k][4 * q + 0] = fmaf(v[k], wv.x, acc[k][4 * q + 0]);
+            acc[k][4 * q + 1] = fmaf(v[k], wv.y, acc[k][4 * q + 1]);
+            acc[k][4 * q + 2] = fmaf(v[k], wv.z, acc[k][4 * q + 2]);
+            acc[k][4 * q + 3] = fmaf(v[k], wv.w, acc[k][4 * q + 3]);
+          }
         }
       }
     }
@@ -95,18 +118,17 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, lon
   const int x = x0 + tx;
   float *ob = out + b * out_bs;
 #pragma unroll
-  for (int c = 0; c < COB; ++c) {
+  for (int c = 0; c < COBC; ++c) {
     const int co = co0 + c;
     if (co >= Co || x >= W) continue;
     const float bv = bias ? bias[co] : 0.f;
-    const int ya = y0 + ty, yb = y0 + ty + 8;
-    float va = acc0[c] + bv, vb = acc1[c] + bv;
-    if (RELU) {
-      va = fmaxf(va, 0.f);
-      vb = fmaxf(vb, 0.f);
+#pragma unroll
+    for (int k = 0; k < PY; ++k) {
+      const int yk = y0 + ty + 8 * k;
+      float vk = acc[k][c] + bv;
+      if (RELU) vk = fmaxf(vk, 0.f);
+      if (yk < H) ob[co * plane + (long)yk * W + x] = vk;
     }
-    if (ya < H) ob[co * plane + (long)ya * W + x] = va;
-    if (yb < H) ob[co * plane + (long)yb * W + x] = vb;
   }
 }
 
@@ -445,15 +467,44 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   return VIE_OK;
 }
 
+template <bool RELU, typename WT, int TY, int COBC>
+void launch_conv3(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
+                  int Co, int H, int W, int B, cudaStream_t st) {
+  const int cob = (Co + COBC - 1) / COBC;
+  dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B * cob);
+  k_conv3<RELU, WT, TY, COBC><<<grid, 256, 0, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, cob);
+}
+
+// Tile shapes by decreasing work per thread: (TY, COBC) = (16, 32), (16, 16),
+// (8, 16), (8, 8).  The first whose grid covers two CTAs per SM is taken, the
+// smallest otherwise: the coarse U-Net levels have too few pixels to fill the
+// GPU with 64 outputs per thread.
+template <bool RELU, typename WT>
+void conv3_shape(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
+                 int Co, int H, int W, int B, cudaStream_t st) {
+  const long tx = (W + TX - 1) / TX;
+  auto ctas = [&](int ty, int cobc) { return tx * ((H + ty - 1) / ty) * B * ((Co + cobc - 1) / cobc); };
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long want = 2L * (sms > 0 ? sms : 1);
+  if (ctas(16, 32) >= want)
+    launch_conv3<RELU, WT, 16, 32>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
+  else if (ctas(16, 16) >= want)
+    launch_conv3<RELU, WT, 16, 16>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
+  else if (ctas(8, 16) >= want)
+    launch_conv3<RELU, WT, 8, 16>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
+  else
+    launch_conv3<RELU, WT, 8, 8>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
+}
+
 template <typename WT>
 vie_status conv3(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
                  int Co, int H, int W, int B, bool relu, cudaStream_t st) {
-  const int cob = (Co + COB - 1) / COB;
-  dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B * cob);
   if (relu)
-    k_conv3<true, WT><<<grid, 256, 0, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, cob);
+    conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
   else
-    k_conv3<false, WT><<<grid, 256, 0, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, cob);
+    conv3_shape<false, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
   VIE_CHECK_LAUNCH("k_conv3");
   return VIE_OK;
 }

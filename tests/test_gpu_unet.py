@@ -54,6 +54,29 @@ def test_forward_and_gradients_match_reference(levels, channels, n, B):
     assert rel_l2(host(ob), host(o)) < 2e-2
 
 
+@pytest.mark.parametrize("B", [1, 2, 3])
+def test_forward_at_256_on_every_tile_shape(B):
+    # the convolution's tile (rows x 32 columns x output channels per CTA)
+    # follows the grid: at 256^2 B = 3 takes 16 x 32 x 32, B = 2 16 x 32 x 16,
+    # B = 1 8 x 32 x 16, and the coarse levels go down to 8 x 32 x 8.  Each
+    # output sums its channels and taps in one order whatever the tile, so a
+    # batch equals its images run one by one, bit for bit.
+    levels, channels, n = 4, 32, 256
+    u = P.vie_unet_create(levels, channels, seed=21)
+    rng = np.random.default_rng(30 + B)
+    params = P.vie_unet_get_params(u)
+    P.vie_unet_set_params(u, params + 0.02 * rng.standard_normal(params.size).astype(np.float32))
+    x = rng.standard_normal((B, 3, n, n)).astype(np.float32)
+    o = torch.empty(B * n * n, dtype=torch.float32, device="cuda:0")
+    P.vie_unet_forward(u, dev(x.ravel(), torch.float32), o, B, n)
+    o_ref, _ = R.forward(ref_params(u, levels, channels), x.astype(np.float64), levels)
+    assert rel_l2(host(o), o_ref.ravel()) < 1e-5
+    one = torch.empty(n * n, dtype=torch.float32, device="cuda:0")
+    for i in range(B):
+        P.vie_unet_forward(u, dev(x[i].ravel(), torch.float32), one, 1, n)
+        np.testing.assert_array_equal(host(one), host(o)[i * n * n:(i + 1) * n * n])
+
+
 def test_training_reduces_loss():
     u = P.vie_unet_create(3, 8, seed=3)
     rng = np.random.default_rng(5)
