@@ -344,7 +344,7 @@ def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
 def measure_batch(P, torch, stream, local, reps=3):
     """16 uneven 2D grids n = 64 ... 256 (Sum N^2 = 1.94e10 pairs) replayed from
     one CUDA graph, the persistent tile-pair launch's configuration autotuned:
-    with the automatic kernel choice (the displacement kernel for n <= 226, one
+    with the automatic kernel choice (the displacement kernel for n <= 258, one
     launch each, the persistent launch for the rest) and with every grid in the
     one persistent launch."""
     media = V.uneven_media()

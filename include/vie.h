@@ -76,7 +76,7 @@ enum { VIE_PREC_FP32 = 0, VIE_PREC_FP64 = 1 };
  * (the cell integral of |x_j - z|^{1-d} exact, Remark REM: NEW KERNEL; error
  * O(h^2 (1 + log h)) against O(h), Eq. EQ: ERROR).  M-ii is built for 2D
  * grids with FP32 tiles, the S = 64 march and the displacement kernel
- * (n <= 226); other combinations return VIE_ERR_UNSUPPORTED at create. */
+ * (n <= 258); other combinations return VIE_ERR_UNSUPPORTED at create. */
 enum { VIE_DISC_MIII = 0, VIE_DISC_MII = 1 };
 
 typedef struct {
@@ -293,7 +293,7 @@ typedef struct vie_batch vie_batch;
  * be FP32 tiles with the S = 64 march and M-iii.  o->kernel selects how the
  * grids run: VIE_KERNEL_SYMMETRIC puts every grid's tile pairs into one
  * persistent launch; VIE_KERNEL_AUTO (and DISPLACEMENT) give each grid that
- * the displacement kernel takes (2 <= n <= 226) a launch of that kernel and
+ * the displacement kernel takes (2 <= n <= 258) a launch of that kernel and
  * put only the others into the persistent launch; all of them are replayed
  * from one CUDA graph.  Vectors of the batch are packed: medium i occupies
  * cells [offsets[i], offsets[i+1]) (vie_batch_layout).

@@ -65,6 +65,34 @@ __device__ __forceinline__ void march_chunks(const float4 *__restrict__ rec, int
   }
 }
 
+// The same march with the lattice in global memory (read through L1): the
+// chunk's cells and stacked targets lie ST elements apart from base + offset.
+template <int LC, int ST>
+__device__ __forceinline__ void march_chunks_global(const float4 *__restrict__ rec, int chunks,
+                                                    const float *__restrict__ base, float (&acc)[kR]) {
+  constexpr int RS = (LC + 4) / 4;
+#pragma unroll 1
+  for (int c = 0; c < chunks; ++c, rec += RS) {
+    float w[4 * RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+      const float4 f = __ldg(rec + i);
+      w[4 * i] = f.x;
+      w[4 * i + 1] = f.y;
+      w[4 * i + 2] = f.z;
+      w[4 * i + 3] = f.w;
+    }
+    const float *p = base + __float_as_int(w[0]);
+    float v[LC + kR - 1];
+#pragma unroll
+    for (int m = 0; m < LC + kR - 1; ++m) v[m] = __ldg(p + ST * m);
+#pragma unroll
+    for (int t = 0; t < LC; ++t)
+#pragma unroll
+      for (int q = 0; q < kR; ++q) acc[q] = fmaf(w[1 + t], v[t + q], acc[q]);
+  }
+}
+
 // Integer add whose old value nobody reads: the reduction form, with no
 // value coming back to the issuing warp.  No memory clobber, so the compiler
 // may still move the (read-only) source loads around it; the sums are read
@@ -82,6 +110,18 @@ __device__ __forceinline__ void march_unit(int lc, const float4 *__restrict__ re
     case 4: march_chunks<4, ST>(rec, chunks, base, st, acc); break;
     case 6: march_chunks<6, ST>(rec, chunks, base, st, acc); break;
     default: march_chunks<8, ST>(rec, chunks, base, st, acc); break;
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void march_unit_global(int lc, const float4 *__restrict__ rec, int chunks,
+                                                  const float *__restrict__ base, float (&acc)[kR]) {
+  switch (lc) {
+    case 2: march_chunks_global<2, ST>(rec, chunks, base, acc); break;
+    case 3: march_chunks_global<3, ST>(rec, chunks, base, acc); break;
+    case 4: march_chunks_global<4, ST>(rec, chunks, base, acc); break;
+    case 6: march_chunks_global<6, ST>(rec, chunks, base, acc); break;
+    default: march_chunks_global<8, ST>(rec, chunks, base, acc); break;
   }
 }
 

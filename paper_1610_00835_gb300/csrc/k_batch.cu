@@ -12,7 +12,7 @@
 // the launch can be replayed from a CUDA graph.  Per-grid partial sums
 // [T][N] are reduced by the single-grid reduce kernel, one launch per grid.
 // With the automatic kernel choice, every grid that the displacement kernel
-// takes (k_pairs_disp.cu: 2 <= n <= 226) runs it instead, one launch of its
+// takes (k_pairs_disp.cu: 2 <= n <= 258) runs it instead, one launch of its
 // own in the same graph, and only the others go to the persistent launch.
 #include <math.h>
 #include <stdio.h>

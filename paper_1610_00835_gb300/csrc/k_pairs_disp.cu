@@ -72,12 +72,20 @@ using dmarch::kChunkLengths;
 using dmarch::kMaxChunk;
 using dmarch::kR;
 using dmarch::march_unit;
+using dmarch::march_unit_global;
 using dmarch::red_add;
 constexpr int kThreads = 1024;
 constexpr int kPad = kR - 1 + kMaxChunk - 1;  // extra lattice rows and columns
+// Grids whose lattice does not fit in shared memory read it from global
+// memory: a square lattice of pitch kGlobalLdp (odd, like the shared one, so
+// that the lane groups of a ragged block get the same stack-block strides),
+// for n + 1 + kPad <= kGlobalLdp.
+constexpr int kGlobalLdp = 273;
+constexpr int kGlobalMaxN = kGlobalLdp - 1 - kPad;  // 258
 
 struct DispArgs {
   const float *lat;            // [n + 1 + kPad][ldp] sigma_t on the cell lattice, edge repeated
+  const float *lat_t;          // global-lattice kernels: the same lattice with y fastest
   const float4 *stencil;       // run records of every W_D
   const float *src;            // s_k, FP32 [N]
   const float *src_t;          // s transposed: s at (x, y) is src_t[x n + y]
@@ -110,7 +118,11 @@ __device__ __forceinline__ int disp_index(int dx, int dy, int n) {
   return dy == 0 ? dx - 1 : (n - 1) + (dy - 1) * (2 * n - 1) + (dx + n - 1);
 }
 
-template <int LDP, int MODE>
+// GLAT: the lattice stays in global memory (read through L1).  Units whose
+// runs go along y read lat from (x, y) on, the others lat_t from (y, x) on:
+// in both the run axis has stride LDP and the lanes are consecutive elements,
+// and the records of the runs along x carry their offsets in lat_t's layout.
+template <int LDP, int MODE, bool GLAT = false>
 __device__ __forceinline__ void disp_body(const DispArgs &a) {
   extern __shared__ float4 smem4[];
   const int n = a.n;
@@ -118,7 +130,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   // shared memory: the lattice (none when streaming)
   float *lat = reinterpret_cast<float *>(smem4);
   const int tid = threadIdx.x, lane = tid & 31;
-  if constexpr (MODE != kStream) {
+  if constexpr (MODE != kStream && !GLAT) {
     const float4 *g4 = reinterpret_cast<const float4 *>(a.lat);
     float4 *l4 = reinterpret_cast<float4 *>(lat);
     const long n4 = a.lat_elems / 4;
@@ -186,10 +198,14 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
             (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
         for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
       }
-      if (along_y)
+      if constexpr (GLAT) {
+        const float *gb = along_y ? a.lat + (x + (long)LDP * y) : a.lat_t + (y + (long)LDP * x);
+        march_unit_global<LDP>(lc, a.stencil + un.x, chunks, gb, acc);
+      } else if (along_y) {
         march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
-      else
+      } else {
         march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+      }
     }
     const float r2 = (float)(dx * dx + dy * dy);
     const float inv_r = rsqrtf(r2);
@@ -287,6 +303,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_store_disp(DispArgs a) {
 
 __global__ void __launch_bounds__(kThreads, 1) k_stream_disp(DispArgs a) {
   disp_body<1, kStream>(a);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_pairs_disp_global(DispArgs a) {
+  disp_body<kGlobalLdp, kApply, true>(a);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_store_disp_global(DispArgs a) {
+  disp_body<kGlobalLdp, kStore, true>(a);
 }
 
 // bf16 bits of v rounded to nearest even (finite v), in integer arithmetic
@@ -535,13 +559,14 @@ __global__ void k_to_f32(long N, const double *__restrict__ x, float *__restrict
 }
 
 // the padded FP32 lattice (pitch P = n + 1) extended to rows x ldp, repeating
-// its last row and column
-__global__ void k_make_lattice(int n, const float *__restrict__ pad, int rows, int ldp,
+// its last row and column; transposed: element i = x ldp + y holds point (x, y)
+__global__ void k_make_lattice(int n, const float *__restrict__ pad, int rows, int ldp, int transposed,
                                float *__restrict__ out) {
   const int P = n + 1;
   const long total = (long)rows * ldp;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / ldp), x = (int)(i % ldp);
+    const int r = (int)(i / ldp), c = (int)(i % ldp);
+    const int y = transposed ? c : r, x = transposed ? r : c;
     out[i] = pad[(long)min(y, P - 1) * P + min(x, P - 1)];
   }
 }
@@ -685,7 +710,7 @@ namespace {
 // medium: they are built once per (device, n) and shared by every handle of
 // that size (kept after the last handle goes, at most kGeoKeep unused ones).
 struct Geometry {
-  int device = -1, n = 0, refs = 0;
+  int device = -1, n = 0, ldp = 0, global = 0, refs = 0;
   int4 *units = nullptr;
   float *stencil = nullptr;
   long long *doff = nullptr;  // first stored weight of each D (displacement-major storage)
@@ -719,7 +744,8 @@ void geometry_trim() {
   }
 }
 
-vie_status geometry_build(int n, int ldp, Geometry *geo) {
+// global: the lattice-in-global-memory layout (runs along x address lat_t)
+vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
   // stencils and work units, the run axis of each D chosen by estimated cost
   struct U {
     int4 u;
@@ -753,7 +779,8 @@ vie_status geometry_build(int n, int ldp, Geometry *geo) {
       const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
       for (size_t r = 0; r + 1 < runs.size(); ++r)
         for (int c0 = runs[r]; c0 < runs[r + 1]; c0 += pl.lc) {
-          const int eoff = cells[c0].cx + ldp * cells[c0].cy;
+          const int eoff = global && !along_y ? cells[c0].cy + ldp * cells[c0].cx
+                                              : cells[c0].cx + ldp * cells[c0].cy;
           float obits;
           memcpy(&obits, &eoff, sizeof obits);
           rec.push_back(obits);
@@ -793,10 +820,10 @@ vie_status geometry_build(int n, int ldp, Geometry *geo) {
   return VIE_OK;
 }
 
-vie_status geometry_acquire(int device, int n, int ldp, Geometry **out) {
+vie_status geometry_acquire(int device, int n, int ldp, bool global, Geometry **out) {
   std::lock_guard<std::mutex> lock(g_geo_mu);
   for (Geometry *g : g_geo)
-    if (g->device == device && g->n == n) {
+    if (g->device == device && g->n == n && g->ldp == ldp && g->global == (int)global) {
       ++g->refs;
       *out = g;
       return VIE_OK;
@@ -804,7 +831,9 @@ vie_status geometry_acquire(int device, int n, int ldp, Geometry **out) {
   Geometry *g = new Geometry;
   g->device = device;
   g->n = n;
-  const vie_status s = geometry_build(n, ldp, g);
+  g->ldp = ldp;
+  g->global = global;
+  const vie_status s = geometry_build(n, ldp, global, g);
   if (s != VIE_OK) {
     geometry_free(g);
     return s;
@@ -871,19 +900,28 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   if (n < 2 || n > 4096) return VIE_OK;
   cudaDeviceProp prop;
   VIE_CUDA(cudaGetDeviceProperties(&prop, device));
-  const size_t smem = disp_smem_bytes(n);
-  if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
-  const int ldp = disp_ldp(n), rows = n + 1 + kPad;
-  DispKernel k = pick_disp(ldp);
+  // the lattice in shared memory where it fits, else (n <= kGlobalMaxN) in
+  // global memory, read through L1
+  const bool global = disp_smem_bytes(n) > (size_t)prop.sharedMemPerBlockOptin;
+  if (global && n > kGlobalMaxN) return VIE_OK;
+  const int ldp = global ? kGlobalLdp : disp_ldp(n), rows = global ? kGlobalLdp : n + 1 + kPad;
+  const size_t smem = global ? 16 : disp_smem_bytes(n);
+  DispKernel k = global ? k_pairs_disp_global : pick_disp(ldp);
   VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
+  if (global) {
+    // all of the SM's unified memory it can get as L1 (a per-kernel preference)
+    VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+    VIE_CUDA(cudaFuncSetAttribute((const void *)k_store_disp_global, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  0));
+  }
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads, smem));
   if (bps < 1) return VIE_OK;
   // the store and stream kernels of the displacement-major operator
   const long N = (long)n * n;
-  const size_t smem_store = sizeof(float) * (size_t)rows * ldp + 16;
+  const size_t smem_store = global ? 16 : sizeof(float) * (size_t)rows * ldp + 16;
   const size_t smem_stream = 16;
-  DispKernel ks = pick_store(ldp);
+  DispKernel ks = global ? k_store_disp_global : pick_store(ldp);
   VIE_TRY(raise_smem_limit((const void *)ks, (size_t)((int)smem_store)));
   VIE_TRY(raise_smem_limit((const void *)k_stream_disp, (size_t)((int)smem_stream)));
   int bps_store = 0, bps_stream = 0;
@@ -891,7 +929,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_stream, k_stream_disp, kThreads, smem_stream));
   if (bps_store < 1 || bps_stream < 1) return VIE_OK;
   Geometry *geo = nullptr;
-  vie_status s = geometry_acquire(device, n, ldp, &geo);
+  vie_status s = geometry_acquire(device, n, ldp, global, &geo);
   if (s != VIE_OK) return s;
   dp->geometry = geo;
   dp->doff = geo->doff;
@@ -904,9 +942,16 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   VIE_CUDA(cudaMemset(dp->counter, 0, 2 * sizeof(int)));
   const long lat_elems = (long)rows * ldp;
   VIE_CUDA(cudaMalloc((void **)&dp->lattice, sizeof(float) * lat_elems));
-  k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp,
+  k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp, 0,
                                                                                 (float *)dp->lattice);
   VIE_CHECK_LAUNCH("k_make_lattice");
+  if (global) {
+    VIE_CUDA(cudaMalloc((void **)&dp->lattice_t, sizeof(float) * lat_elems));
+    k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp, 1,
+                                                                                  (float *)dp->lattice_t);
+    VIE_CHECK_LAUNCH("k_make_lattice");
+  }
+  dp->global = global;
   VIE_CUDA(cudaMalloc((void **)&dp->smax, sizeof(unsigned)));
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
   VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
@@ -941,6 +986,7 @@ void disp_release(DispPlan *dp) {
   if (dp->geometry) geometry_release((Geometry *)dp->geometry);
   if (dp->counter) cudaFree(dp->counter);
   if (dp->lattice) cudaFree(dp->lattice);
+  if (dp->lattice_t) cudaFree(dp->lattice_t);
   if (dp->smax) cudaFree(dp->smax);
   if (dp->scale) cudaFree(dp->scale);
   if (dp->src_t) cudaFree(dp->src_t);
@@ -959,6 +1005,8 @@ void disp_release(DispPlan *dp) {
   dp->doff = nullptr;
   dp->counter = nullptr;
   dp->lattice = nullptr;
+  dp->lattice_t = nullptr;
+  dp->global = 0;
   dp->usable = 0;
 }
 
@@ -1047,6 +1095,7 @@ namespace {
 DispArgs disp_args(const DispPlan &dp, int n, float tau_scale2, float wcoef, const float *src, float *wbuf) {
   DispArgs a;
   a.lat = (const float *)dp.lattice;
+  a.lat_t = (const float *)dp.lattice_t;
   a.stencil = (const float4 *)dp.stencil;
   a.src = src;
   a.src_t = dp.src_t;

@@ -544,7 +544,7 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
       free_all(h);
       delete h;
       set_error("vie_create: VIE_DISC_MII needs a 2D grid with FP32 tiles, the S = 64 march and the "
-                "displacement kernel (n <= 226)");
+                "displacement kernel (n <= 258)");
       return VIE_ERR_UNSUPPORTED;
     }
     double dval = 0.0;
@@ -712,7 +712,7 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
     // every unordered pair's FP32 weight, displacement-major (the displacement kernel's march)
     if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || h->dim != 2) {
       set_error("vie_assemble: VIE_OPERATOR_PAIRS32 needs the displacement kernel (2D, FP32 tiles, S = 64, "
-                "n <= 226)");
+                "n <= 258)");
       return VIE_ERR_UNSUPPORTED;
     }
     if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * (size_t)h->disp.stored));

@@ -121,6 +121,8 @@ struct DispPlan {
   size_t stencil_bytes = 0;
   int *counter = nullptr;
   void *lattice = nullptr;
+  void *lattice_t = nullptr;  // lattice with y fastest (global-lattice kernels only)
+  int global = 0;             // lattice read from global memory (grids past shared memory, n <= 258)
   unsigned *smax = nullptr;   // max |s| of the current apply (float bits)
   double *scale = nullptr;    // fixed-point scale of the current apply
   double rbound = 0.0;        // bound on every row sum of A

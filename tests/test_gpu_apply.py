@@ -112,9 +112,10 @@ def test_2d_every_pair_kernel_all_rows(kernel, n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [100, 128, 133, 226])
+@pytest.mark.parametrize("n", [100, 128, 133, 226, 227, 230, 256, 258])
 def test_displacement_kernel_full_size_sampled_rows(n):
-    # 226 is the largest grid whose lattice fits one SM's shared memory
+    # 226 is the largest grid whose lattice fits one SM's shared memory;
+    # 227 ... 258 read it from global memory (two layouts, runs along y and x)
     m = V.bump_medium(2, n, 4, 0.9, seed=4300 + n)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
     assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
@@ -127,10 +128,10 @@ def test_displacement_kernel_full_size_sampled_rows(n):
     assert rel_l2(got, gpu_apply(hs, P.VIE_OP_K_SIGMA_S, g)) < 2e-6
 
 
-def test_displacement_kernel_falls_back_beyond_shared_memory():
-    # n = 227 does not fit one SM's shared memory: the handle takes the
-    # tile-pair kernel and still matches the oracle
-    n = 227
+def test_displacement_kernel_falls_back_beyond_its_lattice():
+    # n = 259 is past the global lattice (273 x 273 with the stacked-target
+    # padding): the handle takes the tile-pair kernel and still matches the oracle
+    n = 259
     m = V.bump_medium(2, n, 4, 0.9, seed=4436)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
     assert P.vie_get_kernel(h) == P.VIE_KERNEL_SYMMETRIC

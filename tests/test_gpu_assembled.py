@@ -95,7 +95,7 @@ def test_gmres_with_assembled_operator(mode):
     np.testing.assert_array_equal(U2, U_otf)
 
 
-@pytest.mark.parametrize("n", [2, 3, 9, 37, 64, 128, 133, 226])
+@pytest.mark.parametrize("n", [2, 3, 9, 37, 64, 128, 133, 226, 227, 256])
 def test_pairs32_bitwise_equal_to_on_the_fly(n):
     # the stored weights are the on-the-fly kernel's FP32 weights and the
     # accumulation is the same exact fixed-point sum: identical results
@@ -134,8 +134,8 @@ def test_pairs32_unsupported_without_the_displacement_kernel(case, mode):
         m = V.heterogeneous_2d(n=16)
         h = P.vie_create(2, 16, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)
     else:
-        m = V.heterogeneous_2d(n=227)
-        h = P.vie_create(2, 227, m.sigma_t, m.sigma_s)
+        m = V.heterogeneous_2d(n=259)
+        h = P.vie_create(2, 259, m.sigma_t, m.sigma_s)
     with pytest.raises(P.VieError) as e:
         P.vie_assemble(h, mode)
     assert e.value.status == P.vie.VIE_ERR_UNSUPPORTED

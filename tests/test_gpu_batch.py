@@ -100,7 +100,8 @@ def test_sixteen_uneven_grids_64_to_256_sampled_rows(kernel):
     y = host(y)
     rng = np.random.default_rng(3)
     # 64, 154, 218 (the displacement kernel under AUTO; the largest lattice in
-    # shared memory for the tile pairs), 230 and 256 (tile pairs, lattice from global)
+    # shared memory for the tile pairs), 230 and 256 (under AUTO the displacement
+    # kernel with its lattice in global memory; tile pairs with sigma from global)
     for i in (0, 7, 12, 13, 15):
         m = media[i]
         sl = slice(b.offsets[i], b.offsets[i + 1])

@@ -42,7 +42,7 @@ def test_mii_apply_all_rows(n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [128, 226])
+@pytest.mark.parametrize("n", [128, 226, 256])
 def test_mii_apply_full_size_sampled_rows(n):
     m = V.bump_medium(2, n, 4, 0.9, seed=4800 + n)
     h = mii_handle(m, n)
@@ -120,14 +120,14 @@ def test_mii_beats_miii_on_the_gaussian_weight_closed_form():
     assert err[P.VIE_DISC_MII] < 7 / n ** 2
 
 
-@pytest.mark.parametrize("case", ["3d", "fp64", "symmetric", "n227", "n1", "closed_tau"])
+@pytest.mark.parametrize("case", ["3d", "fp64", "symmetric", "n259", "n1", "closed_tau"])
 def test_mii_outside_its_combination_is_unsupported(case):
     kw = {"disc": P.VIE_DISC_MII}
     if case == "3d":
         m = V.heterogeneous_3d(n=5)
         args = (3, 5, m.sigma_t, m.sigma_s)
     else:
-        n = {"n227": 227, "n1": 1}.get(case, 16)
+        n = {"n259": 259, "n1": 1}.get(case, 16)
         m = V.bump_medium(2, n, 2, 0.9, seed=4904)
         args = (2, n, m.sigma_t, m.sigma_s)
         if case == "fp64":
