@@ -306,13 +306,19 @@ vie_status vie_batch_destroy(vie_batch *b);
 /* Total cells and the count + 1 packed offsets of the media. */
 vie_status vie_batch_layout(vie_batch *b, long long *total_cells, long long *offsets);
 
-/* Apply the operator of every medium (as vie_apply, nrhs = 1) to the packed
- * FP64 vector g, writing the packed y: one persistent kernel over all media's
- * tile pairs (dynamic scheduling across media, sigma_t re-staged per medium),
- * replayed from a CUDA graph that is captured on the first call for a given
- * (op, g, y) and re-captured when they change.  Host pointers are staged and
- * the call then synchronises.  Errors: INVALID_ARG, CUDA. */
-vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, void *stream);
+/* Apply the operator of every medium (as vie_apply) to nrhs packed FP64
+ * vectors g, writing the packed y: layout [nrhs][total_cells], source r of
+ * medium i at r * total_cells + offsets[i].  Each source is one pass of the
+ * launches vie_batch_create chose (the displacement kernel per grid, one
+ * persistent kernel over the remaining media's tile pairs with dynamic
+ * scheduling across media); all nrhs passes are replayed from one CUDA graph,
+ * captured on the first call for a given (op, g, y, nrhs) and re-captured when
+ * they change.  The pairs are marched again for every source: for many sources
+ * on one medium, vie_assemble and vie_apply with nrhs amortise the march.
+ * Host pointers are staged and the call then synchronises.
+ *   nrhs : 1 <= nrhs <= 4096.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, int nrhs, void *stream);
 
 /* Time the launch configurations (CTA groups 8/4/2; shared-memory staging of
  * every lattice that fits, or only up to 128 KB) on this batch and keep the

@@ -320,11 +320,12 @@ struct vie_batch {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int key_op = -1;
+  int key_op = -1, key_nrhs = 0;
   const void *key_g = nullptr;
   const void *key_y = nullptr;
   int graph_kernels = 0;
   double *stage_g = nullptr, *stage_y = nullptr;
+  long stage_cap = 0;          // doubles in each staging buffer
   std::vector<DispPlan> disp;  // per grid: the displacement kernel, when it takes the grid
   std::vector<int> use_disp;
 };
@@ -369,7 +370,7 @@ vie_status replan(vie_batch *b, int groups, int policy) {
 
 // Queue one batched apply on stream st (also used under graph capture);
 // *kernels = the launches queued.
-vie_status enqueue(vie_batch *b, int op, const double *g, double *y, cudaStream_t st, int *kernels) {
+vie_status enqueue_one(vie_batch *b, int op, const double *g, double *y, cudaStream_t st, int *kernels) {
   const long total = b->cell_off[b->count];
   vie_status s = launch_source_prep(total, op, b->sig_s, g, VIE_PREC_FP32, b->src, st);
   if (s != VIE_OK) return s;
@@ -396,6 +397,20 @@ vie_status enqueue(vie_batch *b, int op, const double *g, double *y, cudaStream_
     }
   }
   *kernels = k;
+  return VIE_OK;
+}
+
+// nrhs sources one after the other: source r reads g + r total and writes
+// y + r total (the scratch buffers are reused in stream order)
+vie_status enqueue(vie_batch *b, int op, const double *g, double *y, int nrhs, cudaStream_t st, int *kernels) {
+  const long total = b->cell_off[b->count];
+  *kernels = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    int k = 0;
+    vie_status s = enqueue_one(b, op, g + (size_t)r * total, y + (size_t)r * total, st, &k);
+    if (s != VIE_OK) return s;
+    *kernels += k;
+  }
   return VIE_OK;
 }
 
@@ -517,35 +532,44 @@ vie_status vie_batch_layout(vie_batch *b, long long *total_cells, long long *off
   return VIE_OK;
 }
 
-vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, void *stream) {
+vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, int nrhs, void *stream) {
   if (!b || !g || !y) return bad("vie_batch_apply: NULL argument");
   if (op != VIE_OP_K_SIGMA_S && op != VIE_OP_I_MINUS_K && op != VIE_OP_A_RAW)
     return bad("vie_batch_apply: unknown op");
+  if (nrhs < 1 || nrhs > 4096) return bad("vie_batch_apply: 1 <= nrhs <= 4096");
   int prev = -1;
   cudaGetDevice(&prev);
   VIE_CUDA(cudaSetDevice(b->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const long cells = b->cell_off[b->count];
+  const long cells = b->cell_off[b->count] * (long)nrhs;
   const bool gd = dev_ptr(g), yd = dev_ptr(y);
   const double *gg = g;
   double *yy = y;
+  if ((!gd || !yd) && b->stage_cap < cells) {
+    // grow both staging buffers (a graph captured on the old ones is dropped)
+    VIE_CUDA(cudaStreamSynchronize(st));
+    if (b->stage_g) cudaFree(b->stage_g);
+    if (b->stage_y) cudaFree(b->stage_y);
+    b->stage_g = b->stage_y = nullptr;
+    b->stage_cap = 0;
+    VIE_CUDA(cudaMalloc(&b->stage_g, sizeof(double) * cells));
+    VIE_CUDA(cudaMalloc(&b->stage_y, sizeof(double) * cells));
+    b->stage_cap = cells;
+    b->key_op = -1;
+  }
   if (!gd) {
-    if (!b->stage_g) VIE_CUDA(cudaMalloc(&b->stage_g, sizeof(double) * cells));
     VIE_CUDA(cudaMemcpyAsync(b->stage_g, g, sizeof(double) * cells, cudaMemcpyHostToDevice, st));
     gg = b->stage_g;
   }
-  if (!yd) {
-    if (!b->stage_y) VIE_CUDA(cudaMalloc(&b->stage_y, sizeof(double) * cells));
-    yy = b->stage_y;
-  }
-  if (!b->exec || b->key_op != (int)op || b->key_g != gg || b->key_y != yy) {
+  if (!yd) yy = b->stage_y;
+  if (!b->exec || b->key_op != (int)op || b->key_g != gg || b->key_y != yy || b->key_nrhs != nrhs) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
     VIE_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     int kernels = 0;
-    vie_status s = enqueue(b, op, gg, yy, b->cap, &kernels);
+    vie_status s = enqueue(b, op, gg, yy, nrhs, b->cap, &kernels);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (s != VIE_OK) {
@@ -559,6 +583,7 @@ vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, 
     b->key_op = op;
     b->key_g = gg;
     b->key_y = yy;
+    b->key_nrhs = nrhs;
     b->graph_kernels = kernels;
   }
   VIE_CUDA(cudaGraphLaunch(b->exec, st));
@@ -623,9 +648,9 @@ vie_status vie_batch_autotune(vie_batch *b, const char *cache_path, void *stream
   vie_status s = VIE_OK;
   for (int c = 0; c < 4 && s == VIE_OK; ++c) {
     if ((s = replan(b, cand[c][0], cand[c][1])) != VIE_OK) break;
-    if ((s = vie_batch_apply(b, VIE_OP_K_SIGMA_S, g, y, st)) != VIE_OK) break;  // warm-up
+    if ((s = vie_batch_apply(b, VIE_OP_K_SIGMA_S, g, y, 1, st)) != VIE_OK) break;  // warm-up
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 2 && s == VIE_OK; ++r) s = vie_batch_apply(b, VIE_OP_K_SIGMA_S, g, y, st);
+    for (int r = 0; r < 2 && s == VIE_OK; ++r) s = vie_batch_apply(b, VIE_OP_K_SIGMA_S, g, y, 1, st);
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0.f;

@@ -84,7 +84,7 @@ SIGNATURES = {
                                    C.POINTER(_vp), C.POINTER(_vp), C.POINTER(vie_opts)]),
     "vie_batch_destroy": (C.c_int, [_vp]),
     "vie_batch_layout": (C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
-    "vie_batch_apply": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "vie_batch_apply": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "vie_batch_autotune": (C.c_int, [_vp, C.c_char_p, _vp]),
     "vie_batch_config": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vie_unet_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_ulonglong, C.c_int]),
@@ -283,10 +283,11 @@ def vie_batch_destroy(b: VieBatch) -> None:
         b.ptr = C.c_void_p()
 
 
-def vie_batch_apply(b: VieBatch, op: int, g, y, stream=None) -> None:
+def vie_batch_apply(b: VieBatch, op: int, g, y, nrhs: int = 1, stream=None) -> None:
+    """g, y: [nrhs][total] packed FP64 (host arrays or device tensors)."""
     gp, _g = _ptr(g, np.float64)
     yp, _y = _ptr(y, np.float64)
-    _check(load().vie_batch_apply(b.ptr, op, gp, yp, _stream(stream)))
+    _check(load().vie_batch_apply(b.ptr, op, gp, yp, nrhs, _stream(stream)))
 
 
 def vie_batch_autotune(b: VieBatch, cache_path=None, stream=None) -> tuple:

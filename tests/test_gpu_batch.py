@@ -72,6 +72,35 @@ def test_ops_graph_recapture_and_host_pointers():
         np.testing.assert_array_equal(yh, host(yB))
 
 
+@pytest.mark.parametrize("kernel", [P.VIE_KERNEL_AUTO, P.VIE_KERNEL_SYMMETRIC])
+def test_several_sources_per_medium(kernel):
+    # the R-source form: [nrhs][total] packed sources in one graph replay;
+    # each source's result equals its single-source apply (the same launches)
+    ns = [9, 24, 40]
+    b, media = make_batch(ns, seed0=450, kernel=kernel)
+    rng = np.random.default_rng(4)
+    R = 5
+    G = np.stack([packed(b, media, rng) for _ in range(R)])
+    Y = torch.empty(R * b.total, dtype=torch.float64, device="cuda:0")
+    P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, dev(G.ravel()), Y, nrhs=R)
+    Y = host(Y).reshape(R, b.total)
+    one = torch.empty(b.total, dtype=torch.float64, device="cuda:0")
+    for r in range(R):
+        P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, dev(G[r]), one)
+        np.testing.assert_array_equal(Y[r], host(one))
+        for i, m in enumerate(media):
+            sl = slice(b.offsets[i], b.offsets[i + 1])
+            assert rel_l2(Y[r][sl], O.apply(2, m.sigma_t, m.sigma_s, G[r][sl])) < TOL
+    Yh = np.empty((R, b.total))                 # host buffers: the staging grows
+    P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, np.ascontiguousarray(G), Yh, nrhs=R)
+    np.testing.assert_array_equal(Yh, Y)
+    for bad in (0, 4097):
+        with pytest.raises(P.VieError) as e:
+            P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, dev(G.ravel()), torch.empty(R * b.total, dtype=torch.float64,
+                                                                                   device="cuda:0"), nrhs=bad)
+        assert e.value.status == P.vie.VIE_ERR_INVALID_ARG
+
+
 def test_autotune_and_cache(tmp_path):
     ns = [33, 64, 20]
     b, media = make_batch(ns, seed0=500)
