@@ -16,6 +16,11 @@ Network (L levels, C channels, inputs (sigma_t, sigma_s, b) scaled):
 conv3 is a 3 x 3 convolution with zero padding 1 and a bias; avgpool2 the
 2 x 2 mean; upsample2 the nearest-neighbour copy.  Loss = mean((o - t)^2).
 
+With bf16=True the forward pass is the one the BF16 inference kernels
+compute: every weight, and the input of every 3 x 3 convolution, rounded to
+the nearest BF16 value (ties to even) before an exact product; biases and
+everything between the convolutions stay unrounded.
+
 Parameters are a flat list [w, bias] per convolution in the order
 E0.1, E0.2, E1.1, E1.2, ..., D(L-2).1, D(L-2).2, ..., D0.1, D0.2, head;
 weights have shape [Cout, Cin, k, k].
@@ -45,6 +50,15 @@ def init_params(levels: int, channels: int, seed: int = 0):
         params.append(rng.standard_normal((co, ci, k, k)) * std)
         params.append(np.zeros(co))
     return params
+
+
+def round_bf16(x):
+    """Nearest BF16 value of each FP32 value of x, ties to even: the high 16
+    bits of the FP32 pattern after adding 0x7fff plus the lowest kept bit
+    (finite values)."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def conv(x, w, b):
@@ -96,8 +110,15 @@ def upsample2_backward(g):
     return g.reshape(B, C, H // 2, 2, W // 2, 2).sum(axis=(3, 5))
 
 
-def forward(params, x, levels: int):
+def forward(params, x, levels: int, bf16: bool = False):
     """Returns (o, cache)."""
+    if bf16:
+        def conv(x, w, b):  # noqa: F811  (the BF16 inference arithmetic)
+            if w.shape[2] == 3:
+                x = round_bf16(x)
+            return globals()["conv"](x, round_bf16(w), b)
+    else:
+        conv = globals()["conv"]
     cache = {"x": x}
     idx = 0
     xl = x

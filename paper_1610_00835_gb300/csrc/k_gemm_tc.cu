@@ -25,11 +25,14 @@
 
 #include <algorithm>
 
+#include "tcgen05.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
 
 namespace {
+
+using namespace tc;
 
 // ------------------------------------------------------------------ GEMV
 
@@ -129,7 +132,6 @@ constexpr int BM = 128;          // rows of Y per CTA (MMA M)
 constexpr int BK = 64;           // K elements per stage: 128 bytes of BF16
 constexpr int MAX_STAGES = 4;
 constexpr int UMMA_K = 16;       // K per tcgen05.mma kind::f16
-constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (about 1 s)
 
 struct GemmArgs {
   int stages;        // shared-memory ring depth (2..4)
@@ -144,40 +146,6 @@ struct GemmArgs {
   int *err;          // error word (0 = ok)
 };
 
-__device__ __forceinline__ unsigned su32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on phase `parity` of an mbarrier; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort_flag) {
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitLimit) return false;
-  }
-  return true;
-}
-
 __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar,
                                             int x, int y) {
   asm volatile(
@@ -185,50 +153,6 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map
       "%4}], [%2];" ::"r"(dst),
       "l"(map), "r"(bar), "r"(x), "r"(y)
       : "memory");
-}
-
-// K-major operand, 128-byte swizzle, rows of 128 bytes, 8-row groups 1024 B apart.
-__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
-  unsigned long long d = 0;
-  d |= (unsigned long long)((addr >> 4) & 0x3FFF);        // start address
-  d |= (unsigned long long)(16 >> 4) << 16;               // leading byte offset (unused)
-  d |= (unsigned long long)(1024 >> 4) << 32;             // stride byte offset
-  d |= 1ull << 46;                                        // descriptor version
-  d |= 2ull << 61;                                        // 128-byte swizzle
-  return d;
-}
-
-// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major.
-__host__ __device__ constexpr unsigned idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b,
-                                         unsigned idesc, unsigned accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(unsigned bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
-  unsigned r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __global__ void __launch_bounds__(128, 1)

@@ -18,9 +18,11 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
+#include "tcgen05.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
@@ -129,6 +131,181 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, lon
       if (RELU) vk = fmaxf(vk, 0.f);
       if (yk < H) ob[co * plane + (long)yk * W + x] = vk;
     }
+  }
+}
+
+// The same convolution on the 5th-generation tensor cores for BF16 weights,
+// as an implicit GEMM: D[p][co] = sum_k A[p][k] B[co][k] over a CTA tile of
+// 128 consecutive pixels p (flat index y W + x), with k = 9 ci + tap, the
+// weights' own order (B[co][k] = w[co][ci][tap]), and A[p][k] the input at
+// (ci, y + tap / 3 - 1, x + tap % 3 - 1) rounded to BF16 (0 outside the image);
+// K = 9 Ci is padded with zeros to whole 64-wide blocks.  Every thread builds
+// its pixel's row of A and a share of B for one K block into a two-stage
+// shared-memory ring (K-major, 128-byte swizzle: 16-byte chunk c of row r at
+// r 128 + 16 (c ^ r % 8)); thread 0 issues the block's four MMAs (M = 128,
+// N = Co, K = 16, FP32 accumulation in tensor memory) and commits them to the
+// stage's mbarrier, which frees the stage for the block after next.  Each warp
+// then reads its 32 tensor-memory lanes (pixels) and writes bias (+ relu) in
+// FP32.  Waits are bounded; a CTA that gives up writes NaN, which the Krylov
+// driver reports.
+constexpr int kTcM = 128, kTcBK = 64;
+
+__host__ __device__ constexpr int conv_tc_tmem_cols(int co) { return co <= 32 ? 32 : co <= 64 ? 64 : co <= 128 ? 128 : 256; }
+size_t conv_tc_smem(int co) { return 1024 + 2 * (size_t)(kTcM * 128 + co * 128) + 64; }
+
+template <bool RELU>
+__global__ void __launch_bounds__(kTcM) k_conv3_tc(const float *__restrict__ in, long in_bs, int Ci,
+                                                   const __nv_bfloat16 *__restrict__ w,
+                                                   const float *__restrict__ bias, float *__restrict__ out,
+                                                   long out_bs, int Co, int H, int W) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+  const int a_bytes = kTcM * 128, stage_bytes = a_bytes + Co * 128;
+  unsigned long long *bars = (unsigned long long *)(smem + 2 * stage_bytes);  // stages 0, 1; done
+  unsigned *tmem_slot = (unsigned *)(bars + 3);
+  volatile int *never = (volatile int *)(tmem_slot + 1);  // no abort signal: waits end by their limit
+  const int tid = threadIdx.x, warp = tid / 32;
+  const long plane = (long)H * W;
+  const long p = (long)blockIdx.x * kTcM + tid;  // this thread's pixel: row tid of A and of D
+  const bool pvalid = p < plane;
+  const int py = pvalid ? (int)(p / W) : 0, px = pvalid ? (int)(p % W) : 0;
+  unsigned tmask = 0;  // bit tap: the tap's input pixel lies in the image
+  if (pvalid)
+    for (int t = 0; t < 9; ++t) {
+      const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) tmask |= 1u << t;
+    }
+  const float *inp = in + blockIdx.y * in_bs + (long)py * W + px;
+  const int K = 9 * Ci, nkb = (K + kTcBK - 1) / kTcBK;
+  const int tcols = conv_tc_tmem_cols(Co);
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(su32(bars + i), 1);
+    *never = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+  const unsigned idesc = idesc_bf16(kTcM, Co);
+  bool ok = true;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int s = kb & 1;
+    unsigned char *st = smem + s * stage_bytes;
+    // the MMAs of block kb - 2 read this stage
+    if (kb >= 2) ok = mbar_wait(su32(bars + s), ((kb - 2) >> 1) & 1, never);
+    if (ok) {
+      // A: this thread's row, 8 chunks of 8 consecutive k; all 64 loads are
+      // issued before the first conversion
+      const unsigned arow = su32(st) + (unsigned)tid * 128u;
+      float v[64];
+      {
+        const int k0 = kb * kTcBK;
+        int ci = k0 / 9, tap = k0 - 9 * ci;
+#pragma unroll
+        for (int e = 0; e < 64; ++e) {
+          const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;  // tap / 3, tap % 3 for tap < 9
+          v[e] = (ci < Ci && ((tmask >> tap) & 1u)) ? __ldg(inp + ci * plane + (long)(dy - 1) * W + (dx - 1)) : 0.f;
+          if (++tap == 9) {
+            tap = 0;
+            ++ci;
+          }
+        }
+      }
+      // B: Co rows of 8 chunks, chunk t = 8 co + c (two per thread for Co = 32)
+      constexpr int kBT = 2;
+      unsigned short hb[kBT][8];
+#pragma unroll
+      for (int j = 0; j < kBT; ++j) {
+        const int t = tid + j * kTcM, co = t >> 3, k0 = kb * kTcBK + (t & 7) * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const __nv_bfloat16 x =
+              t < Co * 8 && k0 + e < K ? w[(long)co * K + k0 + e] : __float2bfloat16_rn(0.f);
+          hb[j][e] = *reinterpret_cast<const unsigned short *>(&x);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const __nv_bfloat162 q0 = __floats2bfloat162_rn(v[8 * c], v[8 * c + 1]);
+        const __nv_bfloat162 q1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
+        const __nv_bfloat162 q2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
+        const __nv_bfloat162 q3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
+        const unsigned dst = arow + (unsigned)((c ^ (tid & 7)) << 4);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                     "r"(*reinterpret_cast<const unsigned *>(&q0)), "r"(*reinterpret_cast<const unsigned *>(&q1)),
+                     "r"(*reinterpret_cast<const unsigned *>(&q2)), "r"(*reinterpret_cast<const unsigned *>(&q3))
+                     : "memory");
+      }
+#pragma unroll
+      for (int j = 0; j < kBT; ++j) {
+        const int t = tid + j * kTcM, co = t >> 3, c = t & 7;
+        if (t < Co * 8) {
+          const unsigned dst = su32(st + a_bytes) + (unsigned)co * 128u + (unsigned)((c ^ (co & 7)) << 4);
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                       "r"(hb[j][0] | ((unsigned)hb[j][1] << 16)), "r"(hb[j][2] | ((unsigned)hb[j][3] << 16)),
+                       "r"(hb[j][4] | ((unsigned)hb[j][5] << 16)), "r"(hb[j][6] | ((unsigned)hb[j][7] << 16))
+                       : "memory");
+        }
+      }
+      // Co > 32: the remaining B chunks one at a time
+      for (int t = tid + kBT * kTcM; t < Co * 8; t += kTcM) {
+        const int co = t >> 3, c = t & 7, k0 = kb * kTcBK + c * 8;
+        unsigned short h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const __nv_bfloat16 x = k0 + e < K ? w[(long)co * K + k0 + e] : __float2bfloat16_rn(0.f);
+          h[e] = *reinterpret_cast<const unsigned short *>(&x);
+        }
+        const unsigned dst = su32(st + a_bytes) + (unsigned)co * 128u + (unsigned)((c ^ (co & 7)) << 4);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(h[0] | ((unsigned)h[1] << 16)),
+                     "r"(h[2] | ((unsigned)h[3] << 16)), "r"(h[4] | ((unsigned)h[5] << 16)),
+                     "r"(h[6] | ((unsigned)h[7] << 16))
+                     : "memory");
+      }
+    }
+    // the generic-proxy stores above become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const unsigned off = kk * 32;  // 16 BF16 along the swizzled 128-byte row
+        mma_bf16(tmem, smem_desc_sw128(su32(st) + off), smem_desc_sw128(su32(st + a_bytes) + off), idesc,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(su32(bars + s));
+    }
+  }
+  // every product issued so far, then the accumulator
+  if (tid == 0) mma_commit(su32(bars + 2));
+  bool done = mbar_wait(su32(bars + 2), 0, never);
+  ok = __syncthreads_and(ok && done) != 0;  // tcgen05.ld below must be warp-uniform
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float *ob = out + blockIdx.y * out_bs + p;
+  for (int c0 = 0; c0 < Co; c0 += 16) {
+    float v[16];
+    if (ok) tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float x = ok ? v[i] + bias[c0 + i] : __int_as_float(0x7fc00000);
+      if (RELU && ok) x = fmaxf(x, 0.f);
+      if (pvalid) ob[(long)(c0 + i) * plane] = x;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
 }
 
@@ -501,6 +678,21 @@ void conv3_shape(const float *in, long in_bs, int Ci, const WT *w, const float *
 template <typename WT>
 vie_status conv3(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
                  int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+  if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+    if (Co % 16 == 0 && Co >= 16 && Co <= 256 && bias) {
+      // BF16 weights: the tensor-core implicit GEMM
+      const size_t smem = conv_tc_smem(Co);
+      const void *k = relu ? (const void *)k_conv3_tc<true> : (const void *)k_conv3_tc<false>;
+      VIE_TRY(raise_smem_limit(k, smem));
+      const dim3 grid((unsigned)(((long)H * W + kTcM - 1) / kTcM), (unsigned)B);
+      if (relu)
+        k_conv3_tc<true><<<grid, kTcM, smem, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W);
+      else
+        k_conv3_tc<false><<<grid, kTcM, smem, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W);
+      VIE_CHECK_LAUNCH("k_conv3_tc");
+      return VIE_OK;
+    }
+  }
   if (relu)
     conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
   else

@@ -77,6 +77,54 @@ def test_forward_at_256_on_every_tile_shape(B):
         np.testing.assert_array_equal(host(one), host(o)[i * n * n:(i + 1) * n * n])
 
 
+def _bf16_case(levels, n, B, seed):
+    u = P.vie_unet_create(levels, 32, seed=seed)
+    rng = np.random.default_rng(seed + n)
+    params = P.vie_unet_get_params(u)
+    P.vie_unet_set_params(u, params + 0.02 * rng.standard_normal(params.size).astype(np.float32))
+    x = rng.standard_normal((B, 3, n, n)).astype(np.float32)
+    o = torch.empty(B * n * n, dtype=torch.float32, device="cuda:0")
+    P.vie_unet_forward(u, dev(x.ravel(), torch.float32), o, B, n, use_bf16=True)
+    pr = ref_params(u, levels, 32)
+    want, _ = R.forward(pr, x.astype(np.float64), levels, bf16=True)
+    exact, _ = R.forward(pr, x.astype(np.float64), levels)
+    return host(o), want.ravel(), exact.ravel()
+
+
+@pytest.mark.parametrize("n,B", [(8, 1), (12, 2), (40, 1), (64, 2)])
+def test_bf16_convolutions_on_tensor_cores_match_the_rounded_reference(n, B):
+    # one level, 32 channels: a 3 -> 32 convolution (K = 27, one 64-wide K
+    # block) and a 32 -> 32 one (K = 288: five blocks through the two-stage
+    # ring) on the tensor cores, in 128-pixel tiles (64, 144, 1600, 4096
+    # pixels: ragged and whole).  The first convolution's input is the same
+    # FP32 array on both sides: its products agree to FP32 accumulation.  The
+    # second's input is the first's output, FP32 here and FP64 there; where
+    # one of its ~10^4..10^5 values lies within ~1e-7 of a BF16 tie the two
+    # round it apart (a 2^-8 jump, about one case per 50k values), which moves
+    # the outputs around that pixel by ~1e-4.  Everywhere else the results
+    # agree to 1e-5.  A wrong rounding mode (~2e-3) or a lost K block (~1e-1)
+    # fails both checks.
+    got, want, _ = _bf16_case(1, n, B, seed=41)
+    assert rel_l2(got, want) < 2e-4
+    close = np.abs(got - want) <= 1e-5 * np.abs(want).max()
+    assert close.mean() >= 0.98
+
+
+@pytest.mark.parametrize("n,B", [(32, 2), (256, 1)])
+def test_bf16_forward_on_tensor_cores_deep_network(n, B):
+    # four levels (64 -> 32 decoder convolutions, K = 576, and coarse grids of
+    # 16 pixels).  Deeper in the network the FP32 activations of the GPU and
+    # the FP64 ones of the reference differ by ~1e-7, and a value that close
+    # to a BF16 tie rounds differently on the two sides: a jump of 2^-8 that
+    # the next layers spread over a patch.  So the deep forward is held to
+    # the BF16 arithmetic's own scale: against the rounded reference, and
+    # against the exact forward within the BF16 forward's own error (the
+    # bound the CUDA-core BF16-weight forward is held to as well).
+    got, want, exact = _bf16_case(4, n, B, seed=43)
+    assert rel_l2(got, want) < 1e-2
+    assert rel_l2(got, exact) < 2e-2
+
+
 def test_training_reduces_loss():
     u = P.vie_unet_create(3, 8, seed=3)
     rng = np.random.default_rng(5)

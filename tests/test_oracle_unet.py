@@ -44,3 +44,27 @@ def test_pool_and_upsample_are_adjoint_up_to_a_factor():
     b = rng.standard_normal((1, 2, 2, 2))
     # <pool(a), b> = <a, pool^T b> and pool^T = upsample / 4
     assert np.sum(R.avgpool2(a) * b) == pytest.approx(np.sum(a * R.upsample2(b)) / 4)
+
+
+def test_round_bf16_nearest_ties_to_even():
+    # BF16 keeps 7 fraction bits: the spacing above 1 is 2^-7
+    x = np.array([1.0, 1 + 2**-8, 1 + 3 * 2**-9, 1 + 2**-7 + 2**-8, -1 - 2**-8 - 2**-20, 2.0**-130, 0.0])
+    want = np.array([1.0, 1.0, 1 + 2**-7, 1 + 2**-6, -(1 + 2**-7), 2.0**-130, 0.0])
+    np.testing.assert_array_equal(R.round_bf16(x), want)
+
+
+def test_bf16_forward_rounds_weights_and_conv_inputs_only():
+    # weights and input that are BF16 values already, perturbed by less than
+    # half a BF16 spacing: the BF16 forward rounds them back and is unchanged,
+    # bit for bit, while the exact forward moves; the rounding of the
+    # intermediate activations keeps the two forwards within a few 2^-8
+    params = R.init_params(2, 4, seed=3)
+    params = [R.round_bf16(p) if i % 2 == 0 else p for i, p in enumerate(params)]
+    x = R.round_bf16(np.random.default_rng(1).standard_normal((1, 3, 8, 8)))
+    o, _ = R.forward(params, x, 2)
+    ob, _ = R.forward(params, x, 2, bf16=True)
+    assert 0 < np.linalg.norm(ob - o) / np.linalg.norm(o) < 2e-2
+    xp = x * (1 + 2.0**-12)
+    pp = [p * (1 + 2.0**-12) if i % 2 == 0 else p for i, p in enumerate(params)]
+    np.testing.assert_array_equal(R.forward(pp, xp, 2, bf16=True)[0], ob)
+    assert not np.array_equal(R.forward(pp, xp, 2)[0], o)
