@@ -336,7 +336,7 @@ vie_status vie_batch_config(vie_batch *b, int *groups, int *smem_policy);
  * (sigma_t / s_ref, sigma_s / s_ref, b / rms(b)) on an n x n grid to o, and
  * the preconditioner is M(b) = b + rms(b) o: the network supplies the smooth
  * part of (I - K)^{-1} b.  Weights are FP32 (training) with a BF16 copy for
- * inference; accumulation is FP32.  Parameter layout: for every convolution
+ * inference (tensor cores); accumulation is FP32.  Parameter layout: for every convolution
  * in the order encoder (level 0 first, two each), decoder (deepest first, two
  * each), head: weights [Co][Ci][k][k] then bias [Co]. */
 typedef struct vie_unet vie_unet;
@@ -346,7 +346,11 @@ vie_status vie_unet_num_params(vie_unet *u, long long *n);
 vie_status vie_unet_get_params(vie_unet *u, float *host_params);
 vie_status vie_unet_set_params(vie_unet *u, const float *host_params);
 /* o = Net(x): x device FP32 [B][3][n][n], o device FP32 [B][n][n]; n divisible
- * by 2^(levels-1); use_bf16 selects the BF16 weights. */
+ * by 2^(levels-1).  use_bf16 = 0: FP32 weights and activations on the CUDA
+ * cores.  use_bf16 = 1 (what the preconditioner uses): BF16 weights; every
+ * 3x3 convolution with 16 <= channels <= 256 (a multiple of 16) runs on the
+ * tensor cores (tcgen05, implicit GEMM) with its inputs rounded to BF16 and
+ * FP32 accumulation, the others on the CUDA cores with FP32 activations. */
 vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n, int use_bf16, void *stream);
 /* Mean squared error of Net(x) against t (device FP32 [B][n][n]) and, if
  * grads_host is not NULL, its gradient with respect to every parameter
