@@ -583,6 +583,19 @@ def measure_other_configs(P, torch, local, reps=3):
                                        "sweep_rays_per_s": M * m3.N / ms_sweep * 1e3}}
 
 
+def reduce_over_ranks(dist, total_ms: float, pairs: float, device) -> tuple:
+    """Whole-job aggregation over the ranks: the slowest rank's time and the
+    pairs all ranks processed (each rank solves its own medium)."""
+    if dist is None:
+        return total_ms, pairs
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([pairs], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def run_ours(args):
     import torch
     import paper_1610_00835_gb300 as P
@@ -633,13 +646,7 @@ def run_ours(args):
     err_plain = err_vs_oracle(U, U_or)
     total_ms = sum(step_ms)
     pairs = sum(r["n_apply"] for r in reps) * float(N) * N
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        p = torch.tensor([pairs], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        pairs = float(p.item())
+    total_ms, pairs = reduce_over_ranks(dist, total_ms, pairs, f"cuda:{local}")
     value = pairs / (total_ms * 1e-3) / 1e9
 
     # roofline of the pair kernel, from the per-launch CUDA events of the timed steps
