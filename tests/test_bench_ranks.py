@@ -1,6 +1,7 @@
-"""The benchmark's multi-rank host logic on CPU: two gloo ranks (replicas, one
-medium each) aggregate the slowest rank's time and the summed pairs, and the
-reference arm runs on rank 0 only."""
+"""The benchmark's host logic on CPU: two gloo ranks (replicas, one medium
+each) aggregate the slowest rank's time and the summed pairs, the reference arm
+runs on rank 0 only, and the clock sampler's summary reads the median SM clock
+and the throttle reasons seen during the timed region."""
 import os
 import socket
 import subprocess
@@ -59,3 +60,22 @@ def test_reference_arm_prints_on_rank_zero_only():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
                         "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_summary_reads_median_clock_and_throttle_reasons():
+    # nvidia-smi --query-gpu=index,clocks.sm,clocks.max.sm,power.draw,
+    # clocks_event_reasons.{active,hw_slowdown,hw_thermal_slowdown,sw_thermal_slowdown,sw_power_cap}
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1399.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1100.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line",
+               "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = ["0, 1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
