@@ -112,3 +112,43 @@ def test_bench_medium_solution_matches_oracle_solution():
         rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
         assert rep["converged"]
         assert rel_l2(host(U), U_or) < 1e-5
+
+
+def _sampled_rows(N, count, seed):
+    return np.unique(np.random.default_rng(seed).choice(N, count, replace=False))
+
+
+def _check_sampled_residual(dim, m, h, f_dev, U, rows, rtol):
+    """The oracle's own residual r_j = phi_j - (U_j - (K U)_j) of the GPU
+    solution on sampled rows, at the level rtol implies, and the GPU's
+    operator on those rows equal to the oracle's (Algorithm 1, S.2)."""
+    u = host(U)
+    phi = O.apply(dim, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW, rows=rows)
+    lhs = O.apply(dim, m.sigma_t, m.sigma_s, u, op=O.OP_I_MINUS_K, rows=rows)
+    r_or = phi - lhs
+    # sampled rows carry the global 2-norm level within a small factor
+    assert np.linalg.norm(r_or) <= 10 * rtol * np.linalg.norm(phi), \
+        (np.linalg.norm(r_or) / np.linalg.norm(phi))
+    # the GPU's own (I - K) U and A f on the same rows: FP32 tiles against FP64
+    y = torch.empty_like(U)
+    P.vie_apply(h, P.VIE_OP_I_MINUS_K, U, y)
+    ph = torch.empty_like(U)
+    P.vie_apply(h, P.VIE_OP_A_RAW, f_dev, ph)
+    scale = np.abs(u).max()
+    assert np.max(np.abs(host(y)[rows] - lhs)) <= 2e-6 * scale
+    assert np.max(np.abs(host(ph)[rows] - phi)) <= 2e-6 * np.abs(phi).max()
+
+
+def test_config3_full_size_solve_sampled_oracle_residual():
+    # 32^3 heterogeneous medium (6 bumps, sigma_s = 0.8 sigma_t), S = 64
+    # trilinear march, FP32 tiles, FP64 GMRES to 1e-6: the solution that the
+    # step-two sweep consumes, checked by the FP64 oracle on sampled rows.
+    m = V.heterogeneous_3d()
+    assert m.n == 32
+    h = P.vie_create(3, m.n, m.sigma_t, m.sigma_s)
+    f = dev(m.f)
+    U = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
+    rep = P.vie_solve_gmres(h, f, U, rtol=1e-6)
+    assert rep["converged"] and rep["relres"] <= 1e-6
+    _check_sampled_residual(3, m, h, f, U, _sampled_rows(m.N, 32, 33), 1e-6)
+    P.vie_destroy(h)
