@@ -46,12 +46,13 @@ UNIT = "Gpair/s"
 WORKLOAD = "2D heterogeneous 128x128, sigma_t = 1 + 4 seeded bumps, sigma_s = 0.9 sigma_t, S=64 march"
 S_STEPS = 64
 RTOL = 1e-6
-# Pair-kernel traffic per launch from the ncu capture of this workload
-# (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
-# the current kernel.
-PAIR_KERNEL_DRAM_BYTES = {1: 229376,     # k_pairs_sym<2,129,0>: profiles/k_pairs_sym_2d_128.md
-                          2: 58238208}   # k_pairs_disp<143>: profiles/k_pairs_disp_2d_128.md
-KERNEL_NAMES = {1: "k_pairs_sym<2,129,0>", 2: "k_pairs_disp<143>", 3: "k_pairs_f32"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one cold-cache
+# launch of each pair kernel on this workload, from one ncu capture of the
+# kernel as it is now; an entry goes back to None whenever its kernel changes,
+# until it is captured again.
+PAIR_KERNEL_DRAM_BYTES = {1: 229376,     # k_pairs_sym<2,129,0>
+                          2: 51394816}   # k_pairs_disp<137>: 51.26 MB read (the chunk records), 0.13 MB written
+KERNEL_NAMES = {1: "k_pairs_sym<2,129,0>", 2: "k_pairs_disp<137>", 3: "k_pairs_f32"}
 
 
 def nvtx_push(torch, name: str) -> None:
@@ -339,6 +340,69 @@ def measure_bf16x3_product(P, torch, m, h, stream, args, local, nrhs=64):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_gemm_bf16x3 (+ split and finish kernels)",
                          "work": "4 B per K entry (hi + lo) + FP64 G and Y"}}
+
+
+def measure_multi_source(P, torch, m, stream, local, nrhs=64):
+    """The 64 seeded bump sources on the 128^2 medium solved to 1e-6: together
+    (lockstep GMRES, one tensor-core product of all columns per Arnoldi step,
+    assembled BF16 hi/lo K), with and without the learned preconditioner
+    (one batched forward pass per step), against the same sources solved one
+    at a time (the assembled operator's GEMV, and plain on-the-fly GMRES).
+    Assembly (once per medium) is timed apart from the solves."""
+    dev = f"cuda:{local}"
+    N = m.N
+    F = V.bump_sources(2, m.n, nrhs, seed=V.seed_for(4))
+    f_all = torch.as_tensor(F.ravel(), dtype=torch.float64, device=dev)
+    U_all = torch.empty_like(f_all)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        ms, out = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms), out
+
+    h = P.vie_create(2, m.n, m.sigma_t, m.sigma_s, steps=S_STEPS, device=local)
+    asm_ms, _ = timed(lambda: P.vie_assemble(h, P.VIE_OPERATOR_BF16X3))
+    lock_ms, reps = timed(lambda: P.vie_solve_gmres(h, f_all, U_all, rtol=RTOL, nrhs=nrhs))
+    U_lock = U_all.detach().cpu().numpy().reshape(nrhs, N)
+    net = P.vie_unet_create(4, 32, device=local)
+    P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
+    P.vie_set_preconditioner(h, net, 5.0)
+    lockl_ms, repl = timed(lambda: P.vie_solve_gmres(h, f_all, U_all, rtol=RTOL, nrhs=nrhs))
+    P.vie_set_preconditioner(h, None)
+    P.vie_unet_destroy(net)
+    u1 = torch.empty(N, dtype=torch.float64, device=dev)
+
+    def one_by_one():
+        its = []
+        for r in range(nrhs):
+            its.append(P.vie_solve_gmres(h, f_all[r * N:(r + 1) * N], u1, rtol=RTOL)["iters"])
+        return its
+
+    single_ms, single_its = timed(one_by_one, reps=1)
+    P.vie_assemble(h, P.VIE_OPERATOR_OTF)
+    plain_ms, plain_its = timed(one_by_one, reps=1)
+    P.vie_destroy(h)
+    # agreement of the lockstep solutions with the plain solves (last source)
+    dif = float(np.linalg.norm(U_lock[-1] - u1.detach().cpu().numpy()) / np.linalg.norm(U_lock[-1]))
+    return {"sources": nrhs, "medium": "2D heterogeneous 128x128 (the bench medium)",
+            "assemble_bf16x3_ms": asm_ms,
+            "lockstep_bf16x3_ms": lock_ms,
+            "lockstep_bf16x3_iters_max": max(r["iters"] for r in reps),
+            "lockstep_bf16x3_relres_max": max(r["relres"] for r in reps),
+            "lockstep_learned_bf16x3_ms": lockl_ms,
+            "lockstep_learned_iters_max": max(r["iters"] for r in repl),
+            "lockstep_learned_relres_max": max(r["relres"] for r in repl),
+            "single_bf16x3_gemv_ms": single_ms, "single_iters_max": max(single_its),
+            "plain_on_the_fly_ms": plain_ms, "plain_iters_max": max(plain_its),
+            "lockstep_vs_plain_rel_diff_last_source": dif}
 
 
 def measure_batch(P, torch, stream, local, reps=3):
@@ -695,6 +759,7 @@ def run_ours(args):
     chosen_fmm = measure_assembled(P, torch, h, f_dev, U, flush, stream, args, P.VIE_OPERATOR_FMM, U_or)
     mii = measure_mii(P, torch, m, f_dev, flush, stream, args, local, rank, U_or)
     product = measure_bf16x3_product(P, torch, m, h, stream, args, local)
+    multi = measure_multi_source(P, torch, m, stream, local)
     batch = measure_batch(P, torch, stream, local)
     others = measure_other_configs(P, torch, local)
     learned = measure_learned(P, torch, local)
@@ -744,6 +809,7 @@ def run_ours(args):
                       "oracle_U": "tests/golden/bench_U_2d_128.npy (FP64 oracle, rtol 1e-11)"
                       if U_or is not None else None},
             "bf16x3_product": product,
+            "multi_source_solve": multi,
             "batch_uneven_grids": batch,
             "learned_preconditioner": learned,
             "paper_preconditioners": paper_pre,

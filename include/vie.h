@@ -133,7 +133,9 @@ typedef enum {
  *            must not overlap.
  *   nrhs   : >= 1.
  *   stream : cudaStream_t (NULL: legacy default stream).
- * Errors: INVALID_ARG, CUDA. */
+ * With host pointers the call reports VIE_ERR_TIMEOUT if a tensor-core
+ * product gave up on a bounded wait (see vie_check_device for device pointers).
+ * Errors: INVALID_ARG, CUDA, TIMEOUT. */
 vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int nrhs,
                      void *stream);
 
@@ -142,8 +144,10 @@ enum {
   VIE_OPERATOR_OTF = 0,          /* entries generated on the fly (default)        */
   VIE_OPERATOR_FP32 = 1,         /* K assembled in HBM, FP32                      */
   VIE_OPERATOR_BF16X3 = 2,       /* K assembled as BF16 hi + lo; products with
-                                    several right-hand sides on the tensor cores
-                                    as Khi Ghi + Khi Glo + Klo Ghi, FP32 accumulate */
+                                    several right-hand sides on the tensor cores,
+                                    G split exactly into BF16 hi + mid + lo, the
+                                    five products above 2^-24 kept, FP32
+                                    accumulate (split-precision correction)     */
   VIE_OPERATOR_PAIRS32 = 3,      /* A_jk of every unordered pair once, FP32,
                                     displacement-major (2D handles that use the
                                     displacement kernel): applies stream it */
@@ -184,7 +188,7 @@ enum {
  * (Eq. EQ:ERT Intgrl FMM) when sigma_s > 0 everywhere, else the on-the-fly
  * path.  One RHS
  * uses a bandwidth-bound CUDA-core product; vie_apply with nrhs >= 2 in
- * VIE_OPERATOR_BF16X3 mode uses one tensor-core product for up to 256 RHS.
+ * VIE_OPERATOR_BF16X3 mode uses one tensor-core product per 128 RHS.
  * VIE_OPERATOR_OTF frees the matrix.  Needs FP32 precision, the march and
  * S = 64 (else VIE_ERR_UNSUPPORTED).  Asynchronous on `stream`.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
@@ -218,6 +222,9 @@ typedef struct {
   int zero_x0;  /* 1: ignore U on entry and start from U = 0               */
   int rhs_is_phi; /* 1: f already holds phi; 0: phi = A f is formed here     */
   int time_apply; /* 1: record CUDA events around every operator apply      */
+  int nrhs;       /* sources solved together on this medium (1..4096; 1 by
+                     default); f and U are then [nrhs][N] and rep an array of
+                     nrhs reports (see vie_solve_gmres)                      */
 } vie_gmres_opts;
 
 void vie_default_gmres_opts(vie_gmres_opts *o);
@@ -242,11 +249,21 @@ typedef struct {
  * Givens rotations and the triangular solve run on the device in FP64; the
  * operator is applied with the handle's precision; convergence is judged
  * on the FP64 true residual.
- *   f      : FP64 [N] source f (or phi if rhs_is_phi), host or device.
- *   U      : FP64 [N] initial guess on entry (unless zero_x0), solution on exit.
- *   rep    : may be NULL.
- * The call synchronises the stream once per Arnoldi step (residual test).
- * Returns NOT_CONVERGED (U and rep valid) when maxit is reached. */
+ *   f      : FP64 [nrhs][N] sources f (or phi if rhs_is_phi), host or device.
+ *   U      : FP64 [nrhs][N] initial guesses on entry (unless zero_x0),
+ *            solutions on exit.
+ *   rep    : NULL, or nrhs reports (one per source).
+ * With nrhs > 1 the nrhs solves run in lockstep: every Arnoldi step applies
+ * the operator to the nrhs current directions at once -- with
+ * VIE_OPERATOR_BF16X3 as one tensor-core product, up to 128 columns per
+ * product -- and a learned preconditioner runs one forward pass over all of
+ * them; CGS2, the Givens steps and the updates of all solves are one launch
+ * each.  Each solve keeps its own restart cycles, residual estimate, stall
+ * fallback and FP64 true residual, and leaves the lockstep when it
+ * converges (its report counts its own steps).
+ * The call synchronises the stream once per Arnoldi step (residual test; one
+ * copy of all nrhs estimates).  Returns NOT_CONVERGED (U and rep valid) when
+ * maxit is reached (for any source). */
 vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U,
                            const vie_gmres_opts *o, vie_report *rep, void *stream);
 
@@ -277,11 +294,14 @@ vie_status ert_sweep(vie_handle *h, const double *U, const double *f, const floa
  * (S = 64 march, FP32 tiles), self-cell diagonal included, with every
  * intermediate in one fixed device array of about 17 MB that the library
  * image holds on every GPU that loads it until the process exits.  The first
- * call with a device current looks up that array's address on the device;
- * make it before any stream capture.  Calls share the array and it keeps the
- * last call's contents (the work counter is cleared on every call); calls
- * whose work overlaps on the same GPU race, so serialise them.  Asynchronous
- * on `stream`.  Errors: INVALID_ARG (sizes, non-device pointers), CUDA. */
+ * call with a device current looks up that array's address on the device
+ * and copies the self-cell quadrature rule there (synchronously); make it
+ * before any stream capture.  Calls share the array and it keeps the last
+ * call's contents (the work counter is cleared on every call); calls whose
+ * work overlaps on the same GPU race, so serialise them.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG (sizes, non-device pointers), UNSUPPORTED
+ * (the device's shared memory cannot hold the grid's lattice for the
+ * symmetric kernel; nothing is launched), CUDA. */
 vie_status vie_apply_noalloc(int dim, int n, const double *sigma_t, const double *sigma_s,
                              vie_op op, const double *g, double *y, void *stream);
 
@@ -347,10 +367,12 @@ vie_status vie_unet_get_params(vie_unet *u, float *host_params);
 vie_status vie_unet_set_params(vie_unet *u, const float *host_params);
 /* o = Net(x): x device FP32 [B][3][n][n], o device FP32 [B][n][n]; n divisible
  * by 2^(levels-1).  use_bf16 = 0: FP32 weights and activations on the CUDA
- * cores.  use_bf16 = 1 (what the preconditioner uses): BF16 weights; every
- * 3x3 convolution with 16 <= channels <= 256 (a multiple of 16) runs on the
- * tensor cores (tcgen05, implicit GEMM) with its inputs rounded to BF16 and
- * FP32 accumulation, the others on the CUDA cores with FP32 activations. */
+ * cores, asynchronous.  use_bf16 = 1 (what the preconditioner uses): BF16
+ * weights; with 16 or 32 channels every 3x3 convolution runs on the tensor
+ * cores (tcgen05, an implicit GEMM whose shifted input tiles the TMA loads)
+ * with its inputs rounded to BF16 and FP32 accumulation, other widths on the
+ * CUDA cores with FP32 activations; the call synchronises the stream and
+ * returns VIE_ERR_TIMEOUT if a convolution gave up on a bounded wait. */
 vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n, int use_bf16, void *stream);
 /* Mean squared error of Net(x) against t (device FP32 [B][n][n]) and, if
  * grads_host is not NULL, its gradient with respect to every parameter
@@ -362,8 +384,15 @@ vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B
  * weights is NULL. */
 vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, const float *weights, int B,
                                int n, float lr, double *loss, void *stream);
+/* Checkpoint: the parameters and the Adam state (step count, first and
+ * second moments), so that vie_unet_train_step resumes exactly where a saved
+ * run stopped.  vie_unet_load also reads parameter-only files of the earlier
+ * format (the optimizer state then starts from zero).  The file must match
+ * the network's levels and channels, else INVALID_ARG. */
 vie_status vie_unet_save(vie_unet *u, const char *path);
 vie_status vie_unet_load(vie_unet *u, const char *path);
+/* Adam steps taken so far (restored by vie_unet_load). */
+vie_status vie_unet_train_state(vie_unet *u, long long *step);
 /* Use `u` as the right preconditioner of vie_solve_gmres on this handle
  * (flexible GMRES); NULL restores plain GMRES.  2D handles only, n divisible
  * by 2^(levels-1); s_ref scales the coefficient channels (> 0).  If the
@@ -414,6 +443,32 @@ vie_status vie_set_diffusion_preconditioner(vie_handle *h, int enable, void *str
 /* z = M v with the diffusion preconditioner alone (v, z FP64 [N], host or
  * device, not overlapping).  Errors: INVALID_ARG (none set), CUDA. */
 vie_status vie_diffusion_precondition(vie_handle *h, const double *v, double *z, void *stream);
+
+/* ---- Failure detection of the tensor-core kernels (no paper counterpart).
+ * Every wait of the kernels that issue tcgen05.mma (the multi-RHS product of
+ * VIE_OPERATOR_BF16X3 and the BF16 convolutions of the learned
+ * preconditioner) on an mbarrier is bounded.  A CTA whose wait runs out stops
+ * issuing work, waits (bounded by the full limit) for the copies and
+ * products it already issued, frees its tensor memory, writes NaN into its
+ * outputs and sets the error word of its handle or network.  Synchronous
+ * calls report that as VIE_ERR_TIMEOUT: vie_solve_gmres (checked at every
+ * Arnoldi step), vie_apply with host pointers, vie_unet_forward with
+ * use_bf16 (which synchronises its stream) and vie_check_device; the word is
+ * cleared when reported, so the next call runs normally.
+ *
+ * vie_set_wait_limits sets the bounds for later launches, process-wide, in
+ * milliseconds (converted with the device's clock rate): limit_ms for every
+ * wait (default 1000), first_wait_ms for the first producer/consumer wait of
+ * each CTA (negative: the same as limit_ms; 0: that wait gives up at once,
+ * which lets a test exercise the failure path without a fault).
+ * Errors: INVALID_ARG (0 < limit_ms <= 60000 and first_wait_ms <= limit_ms
+ * required). */
+vie_status vie_set_wait_limits(double limit_ms, double first_wait_ms);
+
+/* Synchronise `stream` and return VIE_ERR_TIMEOUT if a tensor-core kernel of
+ * this handle (or of its learned preconditioner) gave up on a bounded wait
+ * since the last report; asynchronous vie_apply calls report this way. */
+vie_status vie_check_device(vie_handle *h, void *stream);
 
 /* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
 vie_status vie_get_kernel(vie_handle *h, int *kernel);

@@ -386,8 +386,8 @@ int kernel_mode(const PairPlan &p, int tau_closed) { return tau_closed ? 2 : (p.
 
 vie_status plan_pairs(const Medium &m, int steps, int tau_closed, int precision, int device,
                       PairPlan *plan) {
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   PairPlan p{};
   p.tiles = (int)((m.N + kPairThreads - 1) / kPairThreads);
   size_t lattice = m.dim == 2 ? (size_t)m.P * m.P : (size_t)m.P * m.P * m.P;
@@ -471,13 +471,26 @@ vie_status launch_pairs(const Medium &m, const PairPlan &plan, int steps, int ta
   return VIE_OK;
 }
 
+// The limit a kernel has been raised to, per device, is remembered, so that
+// launches on hot paths do not query the function's attributes every time.
 vie_status raise_smem_limit(const void *k, size_t bytes) {
+  struct Seen {
+    int device;
+    const void *kernel;
+    size_t bytes;
+  };
   static std::mutex mu;
+  static std::vector<Seen> seen;
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
+  for (const Seen &e : seen)
+    if (e.device == dev && e.kernel == k && e.bytes >= bytes) return VIE_OK;
   cudaFuncAttributes at;
   VIE_CUDA(cudaFuncGetAttributes(&at, k));
-  if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return VIE_OK;
-  VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if ((size_t)at.maxDynamicSharedSizeBytes < bytes)
+    VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  seen.push_back({dev, k, std::max(bytes, (size_t)at.maxDynamicSharedSizeBytes)});
   return VIE_OK;
 }
 
@@ -509,17 +522,22 @@ vie_status launch_pad_sigma(int dim, int n, const double *sig, float *out32, dou
 
 vie_status launch_selfcell(int dim, int n, const double *sigma_t, double *diag, cudaStream_t st) {
   // The rule lives in __constant__ memory, which is per device: upload it
-  // once for every device the library runs on.
+  // once for every device the library runs on (under a lock: host threads
+  // may make their first calls on a device at the same time).
+  static std::mutex rule_mu;
   static bool have_rule[256] = {};
   int dev = 0;
   VIE_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return VIE_ERR_INVALID_ARG;
-  if (!have_rule[dev]) {
-    std::vector<double> x, w;
-    gauss_legendre(kGL, x, w);
-    VIE_CUDA(cudaMemcpyToSymbol(c_gl_x, x.data(), sizeof(double) * kGL));
-    VIE_CUDA(cudaMemcpyToSymbol(c_gl_w, w.data(), sizeof(double) * kGL));
-    have_rule[dev] = true;
+  {
+    std::lock_guard<std::mutex> lock(rule_mu);
+    if (!have_rule[dev]) {
+      std::vector<double> x, w;
+      gauss_legendre(kGL, x, w);
+      VIE_CUDA(cudaMemcpyToSymbol(c_gl_x, x.data(), sizeof(double) * kGL));
+      VIE_CUDA(cudaMemcpyToSymbol(c_gl_w, w.data(), sizeof(double) * kGL));
+      have_rule[dev] = true;
+    }
   }
   long N = dim == 2 ? (long)n * n : (long)n * n * n;
   k_selfcell<<<grid_for(N, 128), 128, 0, st>>>(dim, N, 1.0 / n, sigma_t, diag);

@@ -206,8 +206,8 @@ vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const doub
     VIE_CUDA(cudaMemsetAsync(khi, 0, kbytes / 2, st));
     VIE_CUDA(cudaMemsetAsync(klo, 0, kbytes / 2, st));
   }
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   const size_t per_group = sizeof(float4) * kG + sizeof(float) * 4 * 32 * 33 + 4 * sizeof(int);
   const size_t lat_bytes = sp.global_lattice ? 0 : sizeof(float) * sp.lattice_elems;
   int groups = (int)std::min<size_t>(8, (prop.sharedMemPerBlockOptin - lat_bytes) / per_group);

@@ -206,8 +206,8 @@ struct BatchPlanImpl {
 vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *cell_off,
                       const long *lat_off, const long *part_off, const int *skip, int groups, int smem_policy,
                       int device) {
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   bp->groups = groups;
   bp->smem_policy = smem_policy;
   bp->host.assign(count, BatchGrid{});

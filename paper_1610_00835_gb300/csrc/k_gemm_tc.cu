@@ -3,20 +3,27 @@
 // * k_gemv: y = K g for one right-hand side on the CUDA cores, K in FP32 or
 //   BF16 hi/lo (4 bytes per entry either way); bandwidth bound.
 // * k_gemm_bf16x3: Y = K G for R right-hand sides on the 5th-generation
-//   tensor cores.  K = Khi + Klo and G = Ghi + Glo are BF16 splits of FP32
-//   values; the product keeps Khi Ghi + Khi Glo + Klo Ghi (the dropped
-//   Klo Glo term is below 2^-16 of |K||G|), accumulated in FP32 in tensor
-//   memory.  One CTA computes a 128-row tile of Y for all R columns over one
-//   K-range (split-K); a TMA producer thread streams 64-wide K slices of Khi,
-//   Klo, Ghi, Glo into a 4-stage shared-memory ring (128-byte swizzle), one
-//   thread issues tcgen05.mma (M = 128, N = R, K = 16 per instruction) and
-//   the four warps read the accumulators back with tcgen05.ld.
+//   tensor cores.  K = Khi + Klo is the BF16 split of the assembled FP32
+//   operator (a fixed matrix); G is split three ways, G = Ghi + Gmid + Glo,
+//   which represents its FP32 values exactly, so the product applies that
+//   fixed matrix to FP32 G: the kept terms Khi Ghi, Khi Gmid, Klo Ghi,
+//   Khi Glo and Klo Gmid leave out only Klo Glo (below 2^-24 of |K||G|).
+//   A product whose error depended on how G rounds would not be a linear
+//   operator, and GMRES could not drive its residual below that error.  The
+//   terms accumulate in FP32 in tensor memory.  One CTA computes a 128-row
+//   tile of Y for all R columns over one K-range (split-K); a TMA producer
+//   thread streams 64-wide K slices of Khi, Klo, Ghi, Gmid, Glo into a
+//   shared-memory ring of up to 4 stages (128-byte swizzle), one thread
+//   issues tcgen05.mma (M = 128, N = R, K = 16 per instruction) and the four
+//   warps read the accumulators back with tcgen05.ld.
 //   The tensor cores do not round their FP32 accumulation to nearest, so a
 //   long chain of products into one accumulator drifts low (measured: 3e-5
-//   relative after ~770 chained MMAs).  The dominant Khi Ghi product
-//   therefore rotates over up to four accumulators, the small cross terms go
-//   to a fifth, split-K keeps every chain at or below ~128 MMAs, and the
+//   relative after ~770 chained MMAs; the drift grows with the chain, about
+//   2^-25 per MMA).  The dominant Khi Ghi product therefore rotates over up
+//   to seven accumulators (as many as tensor memory holds beside the cross
+//   terms' one), split-K keeps every chain at or below kMaxChain MMAs, and the
 //   accumulators are added in FP32 in the epilogue and across splits in FP64.
+//   At most 128 right-hand sides per product (three G slices per stage).
 //   Every mbarrier wait is bounded by a clock limit; on expiry the CTA sets
 //   an error word, stops issuing work, waits for its issued copies and
 //   products (again bounded), frees its tensor memory and returns.
@@ -88,6 +95,16 @@ __global__ void k_divide(long N, const double *__restrict__ a, const double *__r
     out[i] = a[i] / b[i];
 }
 
+// out[r][i] = a[r][i] / b[i] for R columns (column r of a at r lda, of out at r ldo)
+__global__ void k_divide_cols(long N, int R, const double *__restrict__ a, long lda, const double *__restrict__ b,
+                              double *__restrict__ out, long ldo) {
+  const long total = (long)R * N;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long r = t / N, i = t - r * N;
+    out[r * ldo + i] = a[r * lda + i] / b[i];
+  }
+}
+
 // g (FP64 [nrhs][N]) -> FP32 [nrhs][ldk], zero padded
 __global__ void k_to_f32_padded(const double *__restrict__ g, long N, long ldk, int nrhs,
                                 float *__restrict__ out) {
@@ -98,31 +115,41 @@ __global__ void k_to_f32_padded(const double *__restrict__ g, long N, long ldk, 
   }
 }
 
-// G (FP64 [nrhs][N]) -> BF16 hi/lo [rpad][ldk], zero padded
-__global__ void k_split_bf16(const double *__restrict__ g, long N, long ldk, int nrhs, int rpad,
-                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+// G (FP64, column r at g + r ldg) -> FP32 -> BF16 hi + mid + lo [rpad][ldk],
+// zero padded.  hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid):
+// each remainder is exact in FP32 and has 8 fewer significant bits, so
+// hi + mid + lo = v (FP32 v in the BF16 exponent range).
+__global__ void k_split_bf16(const double *__restrict__ g, long ldg, long N, long ldk, int nrhs, int rpad,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ mid,
+                             __nv_bfloat16 *__restrict__ lo) {
   const long total = (long)rpad * ldk;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const long r = i / ldk, c = i % ldk;
-    const float v = (r < nrhs && c < N) ? (float)g[r * N + c] : 0.f;
+    const float v = (r < nrhs && c < N) ? (float)g[r * ldg + c] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     hi[i] = h;
-    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    mid[i] = m;
+    lo[i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
   }
 }
 
-// y[r][j] = sum_split part[split][r][j]  (then the operator).  A product
-// that gave up on a bounded wait (*err != 0) turns y into NaN, which the
-// Krylov driver reports as VIE_ERR_NONFINITE.
+// y[r][j] = sum_split part[split][r][j]  (then the operator); column r of g
+// and y at r ldg and r ldy.  A product that gave up on a bounded wait
+// (*err != 0) turns y into NaN, which the Krylov driver reports as
+// VIE_ERR_NONFINITE.
 __global__ void k_gemm_finish(const float *__restrict__ part, int splits, int nrhs, long N,
-                              const double *__restrict__ g, int op, const int *__restrict__ err,
-                              double *__restrict__ y) {
+                              const double *__restrict__ g, long ldg, int op, const int *__restrict__ err,
+                              double *__restrict__ y, long ldy) {
   const long total = (long)nrhs * N;
   const bool failed = *err != 0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int p = 0; p < splits; ++p) s += part[(long)p * total + i];
-    y[i] = failed ? __longlong_as_double(0x7ff8000000000000LL) : (op == VIE_OP_I_MINUS_K ? g[i] - s : s);
+    const long r = i / N, j = i - r * N;
+    y[r * ldy + j] = failed ? __longlong_as_double(0x7ff8000000000000LL)
+                            : (op == VIE_OP_I_MINUS_K ? g[r * ldg + j] - s : s);
   }
 }
 
@@ -144,27 +171,20 @@ struct GemmArgs {
   int n_main;        // accumulators that take the Khi Ghi product in turn
   float *part;       // [splits][nrhs][N]
   int *err;          // error word (0 = ok)
+  WaitLimits wl;     // bounded waits (clock cycles)
 };
 
-__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4}], [%2];" ::"r"(dst),
-      "l"(map), "r"(bar), "r"(x), "r"(y)
-      : "memory");
-}
 
 __global__ void __launch_bounds__(128, 1)
     k_gemm_bf16x3(const __grid_constant__ CUtensorMap map_khi, const __grid_constant__ CUtensorMap map_klo,
-                  const __grid_constant__ CUtensorMap map_ghi, const __grid_constant__ CUtensorMap map_glo,
-                  GemmArgs a) {
+                  const __grid_constant__ CUtensorMap map_ghi, const __grid_constant__ CUtensorMap map_gmid,
+                  const __grid_constant__ CUtensorMap map_glo, GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzle atoms
   unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
   const int a_bytes = BM * BK * 2;            // 16 KB per K operand slice
   const int b_bytes = a.rpad * BK * 2;        // rpad * 128 B per G operand slice
-  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const int stage_bytes = 2 * a_bytes + 3 * b_bytes;
   const int STAGES = a.stages;
   unsigned char *stages = smem;
   unsigned long long *bars = (unsigned long long *)(smem + STAGES * stage_bytes);
@@ -200,7 +220,8 @@ __global__ void __launch_bounds__(128, 1)
     // TMA producer
     for (int i = 0; i < nkb; ++i) {
       const int s = i % STAGES, use = i / STAGES;
-      if (use > 0 && !mbar_wait(su32(bars + STAGES + s), (use - 1) & 1, abort_flag)) {
+      if (use > 0 && !mbar_wait(su32(bars + STAGES + s), (use - 1) & 1, abort_flag,
+                                use == 1 && s == 0 ? a.wl.first : a.wl.limit)) {
         atomicExch(a.err, 1);
         *abort_flag = 1;
         break;
@@ -212,14 +233,15 @@ __global__ void __launch_bounds__(128, 1)
       tma_load_2d(su32(st), &map_khi, full, kx, tile * BM);
       tma_load_2d(su32(st + a_bytes), &map_klo, full, kx, tile * BM);
       tma_load_2d(su32(st + 2 * a_bytes), &map_ghi, full, kx, 0);
-      tma_load_2d(su32(st + 2 * a_bytes + b_bytes), &map_glo, full, kx, 0);
+      tma_load_2d(su32(st + 2 * a_bytes + b_bytes), &map_gmid, full, kx, 0);
+      tma_load_2d(su32(st + 2 * a_bytes + 2 * b_bytes), &map_glo, full, kx, 0);
       ++issued_loads;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     for (int i = 0; i < nkb; ++i) {
       const int s = i % STAGES, use = i / STAGES;
-      if (!mbar_wait(su32(bars + s), use & 1, abort_flag)) {
+      if (!mbar_wait(su32(bars + s), use & 1, abort_flag, i == 0 ? a.wl.first : a.wl.limit)) {
         atomicExch(a.err, 2);
         *abort_flag = 1;
         break;
@@ -227,7 +249,8 @@ __global__ void __launch_bounds__(128, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned char *st = stages + s * stage_bytes;
       const unsigned a_hi = su32(st), a_lo = su32(st + a_bytes);
-      const unsigned b_hi = su32(st + 2 * a_bytes), b_lo = su32(st + 2 * a_bytes + b_bytes);
+      const unsigned b_hi = su32(st + 2 * a_bytes), b_mid = su32(st + 2 * a_bytes + b_bytes);
+      const unsigned b_lo = su32(st + 2 * a_bytes + 2 * b_bytes);
       // accumulator columns: main_q at q * rpad (q < n_main), cross terms after
       const int q = i % a.n_main;
       const unsigned d_main = tmem + (unsigned)(q * a.rpad);
@@ -238,8 +261,10 @@ __global__ void __launch_bounds__(128, 1)
         const unsigned first_main = (i < a.n_main && kk == 0) ? 0u : 1u;
         const unsigned first_cross = (i == 0 && kk == 0) ? 0u : 1u;
         mma_bf16(d_main, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, first_main);
-        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, first_cross);
+        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_mid + off), idesc, first_cross);
         mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+        mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_mid + off), idesc, 1u);
       }
       mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs finish
       ++issued_mma;
@@ -249,7 +274,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncwarp();
 
   // Epilogue: every warp reads its 32 TMEM lanes (rows) x rpad columns.
-  bool ok = nkb > 0 && mbar_wait(su32(bars + 2 * STAGES), 0, abort_flag);
+  bool ok = nkb > 0 && mbar_wait(su32(bars + 2 * STAGES), 0, abort_flag, a.wl.limit);
   ok = __syncthreads_and(ok) != 0;  // tcgen05.ld below must be warp-uniform
   if (!ok && nkb > 0 && threadIdx.x == 0) {
     atomicExch(a.err, 3);
@@ -277,14 +302,23 @@ __global__ void __launch_bounds__(128, 1)
     for (int c = 0; c < a.nrhs; ++c)
       if (row < a.N) out[(long)c * a.N + row] = 0.f;
   }
-  // On an abort, wait (bounded) for the copies and products already issued so
-  // that nothing lands in shared or tensor memory after the CTA exits.
-  if (!ok && nkb > 0 && threadIdx.x == 0) {
+  // Before the CTA frees its shared and tensor memory, everything it issued
+  // has landed, whether the run was normal (every wait below then returns at
+  // once) or aborted: the producer waits for the last load of each stage (a
+  // barrier's earlier phases cannot be told apart from its later ones), the
+  // issuer for the accumulator commit that follows its last product.  Both
+  // bounded by the full limit.
+  if (warp == 0 && lane == 0) {
     const long long t0 = clock64();
-    for (int i = 0; i < issued_loads; ++i) {
-      const int s = i % STAGES, use = i / STAGES;
-      while (!mbar_test(su32(bars + s), use & 1) && clock64() - t0 < kWaitLimit) {
+    for (int s = 0; s < STAGES && s < issued_loads; ++s) {
+      const int use = (issued_loads - 1 - s) / STAGES;
+      while (!mbar_test(su32(bars + s), use & 1) && clock64() - t0 < a.wl.limit) {
       }
+    }
+  }
+  if (warp == 1 && lane == 0) {
+    const long long t0 = clock64();
+    while (!mbar_test(su32(bars + 2 * STAGES), 0) && clock64() - t0 < a.wl.limit) {
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -293,7 +327,6 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
                  : "memory");
   }
-  (void)issued_mma;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -342,6 +375,43 @@ int grid_for(long n, int threads) {
 
 }  // namespace
 
+// A BF16 tensor map of `rank` dimensions (dims[0] innermost, strides in bytes
+// for dims 1..rank-1), box `box`, 64- or 128-byte swizzle, zero fill outside.
+vie_status encode_bf16_map(CUtensorMap *m, int rank, const void *base, const unsigned long long *dims,
+                           const unsigned long long *strides, const unsigned *box, int swizzle_bytes) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return VIE_ERR_CUDA;
+  }
+  cuuint64_t d[5], st[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    e[i] = 1;
+    if (i > 0) st[i - 1] = strides[i - 1];
+  }
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base), d, st, b, e,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed");
+    return VIE_ERR_CUDA;
+  }
+  return VIE_OK;
+}
+
+vie_status launch_divide_cols(long N, int R, const double *a, long lda, const double *b, double *out, long ldo,
+                              cudaStream_t st) {
+  k_divide_cols<<<grid_for((long)R * N, 256), 256, 0, st>>>(N, R, a, lda, b, out, ldo);
+  VIE_CHECK_LAUNCH("k_divide_cols");
+  return VIE_OK;
+}
+
 vie_status launch_divide(long N, const double *a, const double *b, double *out, cudaStream_t st) {
   k_divide<<<grid_for(N, 256), 256, 0, st>>>(N, a, b, out);
   VIE_CHECK_LAUNCH("k_divide");
@@ -367,27 +437,30 @@ static size_t part_region_bytes(int splits, int nrhs, long N) {
   return ((sizeof(float) * (size_t)splits * nrhs * N) + 255) & ~(size_t)255;
 }
 
-// Main accumulators for a given width: all five (or fewer) fit in 512 columns.
-static int n_main_for(int rpad) { return std::max(1, std::min(4, 512 / rpad - 1)); }
+// Main accumulators for a given width: they and the cross terms' one fill at
+// most the 512 tensor-memory columns.
+static int n_main_for(int rpad) { return std::max(1, std::min(7, 512 / rpad - 1)); }
+// Longest chain of MMAs into one accumulator (a drift of ~1e-6 relative).
+constexpr int kMaxChain = 32;
 
 size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms) {
   const long tiles = (N + BM - 1) / BM;
   const int kblocks = (int)(ldk / BK);
   const int rpad = (nrhs + 15) / 16 * 16;
   const int nm = n_main_for(rpad);
-  // enough CTAs for two waves, and at most ~128 chained MMAs per accumulator
+  // enough CTAs for two waves, and at most kMaxChain chained MMAs per accumulator
   const long by_occupancy = (2L * sms + tiles - 1) / tiles;
-  const long by_chain = (4L * kblocks + (long)nm * 128 - 1) / ((long)nm * 128);
+  const long by_chain = (4L * kblocks + (long)nm * kMaxChain - 1) / ((long)nm * kMaxChain);
   int splits = (int)std::max(1L, std::min<long>(kblocks, std::max(by_occupancy, by_chain)));
   if (splits_out) *splits_out = splits;
-  return part_region_bytes(splits, nrhs, N) + 2 * sizeof(short) * (size_t)rpad * ldk;
+  return part_region_bytes(splits, nrhs, N) + 3 * sizeof(short) * (size_t)rpad * ldk;
 }
 
-vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g,
-                              int nrhs, int op, double *y, void *workspace, int *err,
+vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g, long ldg,
+                              int nrhs, int op, double *y, long ldy, void *workspace, int *err,
                               cudaStream_t st) {
-  if (nrhs < 1 || nrhs > 256) {
-    set_error("BF16 product: 1 <= nrhs <= 256");
+  if (nrhs < 1 || nrhs > kGemmMaxRhs) {
+    set_error("BF16 product: 1 <= nrhs <= 128");
     return VIE_ERR_INVALID_ARG;
   }
   int dev = 0, sms = 0;
@@ -398,14 +471,15 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
   const int rpad = (nrhs + 15) / 16 * 16;
   float *part = (float *)workspace;
   __nv_bfloat16 *ghi = (__nv_bfloat16 *)((unsigned char *)workspace + part_region_bytes(splits, nrhs, N));
-  __nv_bfloat16 *glo = ghi + (size_t)rpad * ldk;
-  k_split_bf16<<<grid_for((long)rpad * ldk, 256), 256, 0, st>>>(g, N, ldk, nrhs, rpad, ghi, glo);
+  __nv_bfloat16 *gmid = ghi + (size_t)rpad * ldk, *glo = gmid + (size_t)rpad * ldk;
+  k_split_bf16<<<grid_for((long)rpad * ldk, 256), 256, 0, st>>>(g, ldg, N, ldk, nrhs, rpad, ghi, gmid, glo);
   VIE_CHECK_LAUNCH("k_split_bf16");
-  CUtensorMap mkhi, mklo, mghi, mglo;
+  CUtensorMap mkhi, mklo, mghi, mgmid, mglo;
   vie_status s;
   if ((s = make_map(&mkhi, khi, ldk, N, BM)) != VIE_OK) return s;
   if ((s = make_map(&mklo, klo, ldk, N, BM)) != VIE_OK) return s;
   if ((s = make_map(&mghi, ghi, ldk, rpad, rpad)) != VIE_OK) return s;
+  if ((s = make_map(&mgmid, gmid, ldk, rpad, rpad)) != VIE_OK) return s;
   if ((s = make_map(&mglo, glo, ldk, rpad, rpad)) != VIE_OK) return s;
   GemmArgs a;
   a.rpad = rpad;
@@ -417,7 +491,8 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
   a.tmem_cols = 512;  // one CTA per SM (shared memory), so the whole TMEM is free
   a.part = part;
   a.err = err;
-  const size_t stage_bytes = (size_t)(2 * BM * BK * 2 + 2 * rpad * BK * 2);
+  a.wl = wait_limits(dev);
+  const size_t stage_bytes = (size_t)(2 * BM * BK * 2 + 3 * rpad * BK * 2);
   int optin = 0;
   VIE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   a.stages = (int)std::min<size_t>(MAX_STAGES, ((size_t)optin - 1024 - 256) / stage_bytes);
@@ -428,9 +503,9 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
   const size_t smem = 1024 + a.stages * stage_bytes + 256;
   VIE_TRY(raise_smem_limit((const void *)k_gemm_bf16x3, (size_t)((int)smem)));
   dim3 grid((unsigned)((N + BM - 1) / BM), (unsigned)splits);
-  k_gemm_bf16x3<<<grid, 128, smem, st>>>(mkhi, mklo, mghi, mglo, a);
+  k_gemm_bf16x3<<<grid, 128, smem, st>>>(mkhi, mklo, mghi, mgmid, mglo, a);
   VIE_CHECK_LAUNCH("k_gemm_bf16x3");
-  k_gemm_finish<<<grid_for((long)nrhs * N, 256), 256, 0, st>>>(part, splits, nrhs, N, g, op, err, y);
+  k_gemm_finish<<<grid_for((long)nrhs * N, 256), 256, 0, st>>>(part, splits, nrhs, N, g, ldg, op, err, y, ldy);
   VIE_CHECK_LAUNCH("k_gemm_finish");
   return VIE_OK;
 }

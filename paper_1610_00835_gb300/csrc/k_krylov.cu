@@ -174,6 +174,158 @@ int grid_for(long n, int threads) {
   return (int)(b < 1 ? 1 : (b > 2048 ? 2048 : b));
 }
 
+// ---- R solves in lockstep (blockIdx.y = right-hand side r).  Each kernel
+// does for every r with act[r] != 0 what its single-vector form above does,
+// in the same order, so a batched solve of one right-hand side reproduces
+// the single solve's arithmetic.  Vector i of r's basis sits at
+// V + r ldv_r + i N; r's small arrays at r times their length.
+
+// out1[r][v] = V_r[v] . w_r (v < nv) and/or out2[r][v] += it; with gvmode the
+// single dot (nv = 1, V = w) is ||w_r||^2 and the last block of r then takes
+// r's Givens step of column k.
+__global__ void __launch_bounds__(kDotThreads) k_bdots_last(KBatch b, const double *__restrict__ V, long ldv_r,
+                                                            int nv, const double *__restrict__ w, long ldw_r,
+                                                            double *out1, double *out2, int gvmode, int k) {
+  __shared__ double red[kDotThreads / 32];
+  __shared__ int last;
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const long N = b.N;
+  const int m = b.m;
+  const double *Vr = V + (long)r * ldv_r;
+  const double *wr = w + (long)r * ldw_r;
+  double *part = b.part + (long)r * gridDim.x * (m + 1);
+  const long stride = (long)gridDim.x * blockDim.x;
+  const long i0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  for (int v = 0; v < nv; ++v) {
+    const double *x = Vr + (long)v * N;
+    double sum = 0.0;
+    for (long i = i0; i < N; i += stride) sum += x[i] * wr[i];
+    sum = block_sum(sum, red);
+    if (threadIdx.x == 0) part[(long)blockIdx.x * nv + v] = sum;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(b.ticket + r, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double sum = 0.0;
+    for (int q = 0; q < (int)gridDim.x; ++q) sum += __ldcg(part + (long)q * nv + v);
+    if (out1) out1[(long)r * (m + 1) + v] = sum;
+    if (out2) out2[(long)r * (m + 1) + v] += sum;
+    if (gvmode && v == 0) {
+      b.scal[r * 8 + 2] = sum;
+      givens_step(b.H + (long)r * (m + 1) * m, m, k, b.hcol + (long)r * (m + 1), sum, b.cs + (long)r * m,
+                  b.sn + (long)r * m, b.gv + (long)r * (m + 1), b.bnorm[r], b.scal + r * 8 + 3);
+    }
+  }
+  if (threadIdx.x == 0) b.ticket[r] = 0;
+}
+
+// ||w_r||^2 into scal[r][slot] (no Givens step)
+__global__ void __launch_bounds__(kDotThreads) k_bnorm2(KBatch b, const double *__restrict__ w, long ldw_r,
+                                                        int slot) {
+  __shared__ double red[kDotThreads / 32];
+  __shared__ int last;
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const long N = b.N;
+  const double *wr = w + (long)r * ldw_r;
+  double *part = b.part + (long)r * gridDim.x * (b.m + 1);
+  double sum = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    sum += wr[i] * wr[i];
+  sum = block_sum(sum, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sum;
+    __threadfence();
+    last = atomicAdd(b.ticket + r, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)gridDim.x; ++q) t += __ldcg(part + q);
+    b.scal[r * 8 + slot] = t;
+    b.ticket[r] = 0;
+  }
+}
+
+// w_r -= sum_{v < nv} h_r[v] V_r[v]
+__global__ void k_borth_update(KBatch b, const double *__restrict__ V, long ldv_r, int nv,
+                               const double *__restrict__ h, double *__restrict__ w, long ldw_r) {
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const long N = b.N;
+  const double *Vr = V + (long)r * ldv_r;
+  const double *hr = h + (long)r * (b.m + 1);
+  double *wr = w + (long)r * ldw_r;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    double acc = wr[i];
+    for (int v = 0; v < nv; ++v) acc -= hr[v] * Vr[(long)v * N + i];
+    wr[i] = acc;
+  }
+}
+
+// y_r = x_r / norm_r, norm_r = sqrt(scal[r][slot]) if use_sqrt else scal[r][slot]
+__global__ void k_bscale(KBatch b, const double *__restrict__ x, long ldx_r, int slot, int use_sqrt,
+                         double *__restrict__ y, long ldy_r) {
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const double n2 = b.scal[r * 8 + slot];
+  const double nrm = use_sqrt ? sqrt(n2) : n2;
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  const double *xr = x + (long)r * ldx_r;
+  double *yr = y + (long)r * ldy_r;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.N; i += (long)gridDim.x * blockDim.x)
+    yr[i] = xr[i] * inv;
+}
+
+// z_r = a x_r + c y_r
+__global__ void k_baxpby(KBatch b, double a, const double *__restrict__ x, long ldx_r, double c,
+                         const double *__restrict__ y, long ldy_r, double *__restrict__ z, long ldz_r) {
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const double *xr = x + (long)r * ldx_r, *yr = y + (long)r * ldy_r;
+  double *zr = z + (long)r * ldz_r;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.N; i += (long)gridDim.x * blockDim.x)
+    zr[i] = a * xr[i] + c * yr[i];
+}
+
+// r's triangular solve of its kk[r] columns (one thread per r), then x_r +=
+// sum_{v < kk[r]} y_r[v] B_r[v] (B: V or the flexible directions Z)
+__global__ void k_bbacksolve(KBatch b, const int *__restrict__ kk) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= b.R || !b.act[r]) return;
+  const int m = b.m, k = kk[r];
+  const double *H = b.H + (long)r * (m + 1) * m, *gv = b.gv + (long)r * (m + 1);
+  double *y = b.yv + (long)r * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gv[i];
+    for (int q = i + 1; q < k; ++q) s -= H[(long)q * (m + 1) + i] * y[q];
+    const double d = H[(long)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+__global__ void k_blincomb_add(KBatch b, const double *__restrict__ B, long ldb_r, const int *__restrict__ kk,
+                               double *__restrict__ x, long ldx_r) {
+  const int r = blockIdx.y;
+  if (!b.act[r]) return;
+  const int k = kk[r];
+  const double *Br = B + (long)r * ldb_r, *y = b.yv + (long)r * b.m;
+  double *xr = x + (long)r * ldx_r;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.N; i += (long)gridDim.x * blockDim.x) {
+    double acc = xr[i];
+    for (int v = 0; v < k; ++v) acc += y[v] * Br[(long)v * b.N + i];
+    xr[i] = acc;
+  }
+}
+
 }  // namespace
 
 int dot_blocks(long N) {
@@ -252,6 +404,64 @@ vie_status launch_backsolve(const double *H, int m, int k, const double *gv, dou
                             cudaStream_t st) {
   k_backsolve<<<1, 32, 0, st>>>(H, m, k, gv, y);
   VIE_CHECK_LAUNCH("k_backsolve");
+  return VIE_OK;
+}
+
+// ---- lockstep batch launchers (KBatch: vie_internal.cuh)
+static dim3 bgrid(long N, int R, int threads) {
+  long gx = (N + threads - 1) / threads;
+  gx = gx < 1 ? 1 : (gx > 2048 / (R < 8 ? R : 8) ? 2048 / (R < 8 ? R : 8) : gx);
+  return dim3((unsigned)gx, (unsigned)R);
+}
+
+vie_status launch_bdots(const KBatch &b, const double *V, long ldv_r, int nv, const double *w, long ldw_r,
+                        double *out1, double *out2, cudaStream_t st) {
+  k_bdots_last<<<dim3((unsigned)b.blocks, (unsigned)b.R), kDotThreads, 0, st>>>(b, V, ldv_r, nv, w, ldw_r, out1,
+                                                                                out2, 0, 0);
+  VIE_CHECK_LAUNCH("k_bdots_last");
+  return VIE_OK;
+}
+
+vie_status launch_bnorm2_givens(const KBatch &b, const double *w, long ldw_r, int k, cudaStream_t st) {
+  k_bdots_last<<<dim3((unsigned)b.blocks, (unsigned)b.R), kDotThreads, 0, st>>>(b, w, ldw_r, 1, w, ldw_r,
+                                                                                nullptr, nullptr, 1, k);
+  VIE_CHECK_LAUNCH("k_bdots_last");
+  return VIE_OK;
+}
+
+vie_status launch_bnorm2(const KBatch &b, const double *w, long ldw_r, int slot, cudaStream_t st) {
+  k_bnorm2<<<dim3((unsigned)b.blocks, (unsigned)b.R), kDotThreads, 0, st>>>(b, w, ldw_r, slot);
+  VIE_CHECK_LAUNCH("k_bnorm2");
+  return VIE_OK;
+}
+
+vie_status launch_borth_update(const KBatch &b, const double *V, long ldv_r, int nv, const double *h, double *w,
+                               long ldw_r, cudaStream_t st) {
+  k_borth_update<<<bgrid(b.N, b.R, 256), 256, 0, st>>>(b, V, ldv_r, nv, h, w, ldw_r);
+  VIE_CHECK_LAUNCH("k_borth_update");
+  return VIE_OK;
+}
+
+vie_status launch_bscale(const KBatch &b, const double *x, long ldx_r, int slot, int use_sqrt, double *y,
+                         long ldy_r, cudaStream_t st) {
+  k_bscale<<<bgrid(b.N, b.R, 256), 256, 0, st>>>(b, x, ldx_r, slot, use_sqrt, y, ldy_r);
+  VIE_CHECK_LAUNCH("k_bscale");
+  return VIE_OK;
+}
+
+vie_status launch_baxpby(const KBatch &b, double a, const double *x, long ldx_r, double c, const double *y,
+                         long ldy_r, double *z, long ldz_r, cudaStream_t st) {
+  k_baxpby<<<bgrid(b.N, b.R, 256), 256, 0, st>>>(b, a, x, ldx_r, c, y, ldy_r, z, ldz_r);
+  VIE_CHECK_LAUNCH("k_baxpby");
+  return VIE_OK;
+}
+
+vie_status launch_bupdate(const KBatch &b, const double *B, long ldb_r, const int *kk, double *x, long ldx_r,
+                          cudaStream_t st) {
+  k_bbacksolve<<<(b.R + 31) / 32, 32, 0, st>>>(b, kk);
+  VIE_CHECK_LAUNCH("k_bbacksolve");
+  k_blincomb_add<<<bgrid(b.N, b.R, 256), 256, 0, st>>>(b, B, ldb_r, kk, x, ldx_r);
+  VIE_CHECK_LAUNCH("k_blincomb_add");
   return VIE_OK;
 }
 

@@ -16,15 +16,16 @@
 //
 // W_D is stored as runs of consecutive cells along one lattice axis (the one
 // that makes the march cheaper, normally the axis closer to D), each run cut
-// into chunks of a fixed length Lc (one of kChunkLengths, chosen per D, few
-// so that the unrolled variants stay small; the last chunk of a
-// run is padded with zero weights).  A warp takes one displacement and a
-// block of 32 x kR targets: 32 consecutive across the run axis (one per lane)
-// and kR consecutive along it, stacked in one thread.  A chunk then takes
-// Lc + kR - 1 lattice loads per thread and kR Lc multiply-adds, all unrolled
-// for the D's chunk length.  Lanes sit on consecutive x (runs along y) or
-// consecutive y with an odd row pitch (runs along x), so every load is free
-// of bank conflicts.
+// into the fewest chunks of at most kMaxChunk cells, of equal length, so no
+// chunk multiplies zero weights; a D's chunks are stored grouped by length
+// Lc behind a header of counts, and each length runs in its own loop.  A
+// warp takes one displacement and a block of 32 x kR targets: 32 consecutive
+// across the run axis (one per lane) and kR consecutive along it, stacked in
+// one thread.  A chunk then takes Lc + kR - 1 lattice loads per thread and
+// kR Lc multiply-adds, issued as packed FP32 pairs (fma.rn.f32x2, two
+// stacked targets per instruction) in code unrolled for each Lc.  Lanes sit
+// on consecutive x (runs along y) or consecutive y with an odd row pitch
+// (runs along x), so every load is free of bank conflicts.
 //
 // Work units are (D, block of the targets j with j + D inside the grid) for D
 // in a half plane (dy > 0, or dy = 0 and dx > 0): A_jk = A_kj, so each
@@ -47,9 +48,8 @@
 //
 // Targets of a block that fall outside the rectangle (ragged blocks) are
 // computed and discarded: lanes beyond it repeat the last valid target, and
-// the lattice carries kPad = (kR - 1) + (Lc - 1) extra rows and columns
-// (repeating the edge) so that stacked targets beyond it and the padding of
-// the last chunk of a run stay in bounds.
+// the lattice carries kPad = kR - 1 extra rows and columns (repeating the
+// edge) so that stacked targets beyond it stay in bounds.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -68,25 +68,33 @@ namespace {
 
 using march::kS;
 
-using dmarch::kChunkLengths;
 using dmarch::kMaxChunk;
-using dmarch::kR;
-using dmarch::march_unit;
-using dmarch::march_unit_global;
+using dmarch::march_runs;
+using dmarch::march_runs_global;
+#ifndef VIE_DISP_STACK
+#define VIE_DISP_STACK 8
+#endif
+constexpr int kR = VIE_DISP_STACK;  // targets stacked along the run axis in one thread
 using dmarch::red_add;
-constexpr int kThreads = 1024;
-constexpr int kPad = kR - 1 + kMaxChunk - 1;  // extra lattice rows and columns
+// 16 stacked targets take about 80 registers a thread: 768 threads a CTA
+#ifndef VIE_DISP_THREADS
+#define VIE_DISP_THREADS (kR >= 16 ? 768 : 1024)
+#endif
+constexpr int kThreads = VIE_DISP_THREADS;
+// extra lattice rows and columns: the stacked targets of a block that reach
+// past the rectangle of targets (chunks carry no padding)
+constexpr int kPad = kR - 1;
 // Grids whose lattice does not fit in shared memory read it from global
 // memory: a square lattice of pitch kGlobalLdp (odd, like the shared one, so
 // that the lane groups of a ragged block get the same stack-block strides),
-// for n + 1 + kPad <= kGlobalLdp.
-constexpr int kGlobalLdp = 273;
-constexpr int kGlobalMaxN = kGlobalLdp - 1 - kPad;  // 258
+// for n <= kGlobalMaxN.
+constexpr int kGlobalMaxN = 258;
+constexpr int kGlobalLdp = (kGlobalMaxN + 1 + kPad) | 1;  // 267
 
 struct DispArgs {
   const float *lat;            // [n + 1 + kPad][ldp] sigma_t on the cell lattice, edge repeated
   const float *lat_t;          // global-lattice kernels: the same lattice with y fastest
-  const float4 *stencil;       // run records of every W_D
+  const float4 *stencil;       // chunk records of every W_D
   const float *src;            // s_k, FP32 [N]
   const float *src_t;          // s transposed: s at (x, y) is src_t[x n + y]
   const float *wtab;           // M-ii: h / (2 pi) times the cell integral of 1/|z| per D
@@ -95,8 +103,9 @@ struct DispArgs {
   double *scale_out;           // fixed-point scale of this apply (for the reduce)
   double rbound;               // bound on sum_k A_jk for every j
   unsigned long long *yacc;    // [2 N] int64 sums (x fastest, then y fastest), zero between applies
-  const int4 *units;           // {first chunk, dx | dy << 16, lane block | stack block << 16,
-                               //  runs along y | Lc << 1 | chunks << 8}
+  const int4 *units;           // {the D's record header (float4 index), dx | dy << 16,
+                               //  lane block | stack block << 16,
+                               //  runs along y | lane groups << 1 | record float4s << 12}
   int *counter;                // [2]
   float *wbuf;                 // stored weights (store: written, stream: read)
   const long long *doff;       // first stored weight of each D of the half plane
@@ -163,7 +172,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     const int xlo = dx < 0 ? -dx : 0, xhi = dx > 0 ? n - dx : n;
     const int ylo = dy < 0 ? -dy : 0, yhi = dy > 0 ? n - dy : n;
     const bool along_y = (un.w & 1) != 0;
-    const int lc = (un.w >> 1) & 15, lg = (un.w >> 5) & 3, chunks = un.w >> 8;
+    const int lg = (un.w >> 1) & 3, nrec = un.w >> 12;
     // lane groups: 1, 2 or 4 groups of 32 >> lg lanes, group g on stack block
     // sb0 + s g (s = 2 for pairs, ldp mod 4 for quads: the groups then load
     // from disjoint banks); a group past the last stack block is masked off
@@ -194,17 +203,16 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
       {
         // bring this D's chunk records into L1 (one 128-byte line per lane)
         const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
-        const int lines =
-            (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
+        const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * nrec + 127) >> 7);
         for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
       }
       if constexpr (GLAT) {
         const float *gb = along_y ? a.lat + (x + (long)LDP * y) : a.lat_t + (y + (long)LDP * x);
-        march_unit_global<LDP>(lc, a.stencil + un.x, chunks, gb, acc);
+        march_runs_global<LDP, kR>(a.stencil + un.x, gb, acc);
       } else if (along_y) {
-        march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
+        march_runs<LDP, kR>(a.stencil + un.x, base, ldp, acc);
       } else {
-        march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+        march_runs<1, kR>(a.stencil + un.x, base, 1, acc);
       }
     }
     const float r2 = (float)(dx * dx + dy * dy);
@@ -605,18 +613,21 @@ __global__ void k_disp_source(long N, int n, int op, const double *__restrict__ 
 
 typedef void (*DispKernel)(DispArgs);
 
+// compile-time lattice pitches of the 64^2 and 128^2 grids
+constexpr int kLdp64 = (64 + 1 + kPad) | 1, kLdp128 = (128 + 1 + kPad) | 1;
+
 DispKernel pick_disp(int ldp) {
   switch (ldp) {
-    case 79: return k_pairs_disp<79>;
-    case 143: return k_pairs_disp<143>;
+    case kLdp64: return k_pairs_disp<kLdp64>;
+    case kLdp128: return k_pairs_disp<kLdp128>;
     default: return k_pairs_disp<0>;
   }
 }
 
 DispKernel pick_store(int ldp) {
   switch (ldp) {
-    case 79: return k_store_disp<79>;
-    case 143: return k_store_disp<143>;
+    case kLdp64: return k_store_disp<kLdp64>;
+    case kLdp128: return k_store_disp<kLdp128>;
     default: return k_store_disp<0>;
   }
 }
@@ -670,22 +681,37 @@ void stencil_runs(const std::vector<Cell> &cells, bool along_y, std::vector<int>
   starts.push_back((int)cells.size());
 }
 
-// chunk length and estimated instructions per thread of one unit when the
-// runs are cut into chunks of Lc cells: per chunk its record loads and loop,
-// Lc + kR - 1 lattice loads and kR Lc multiply-adds
+// A run of L cells is cut into ceil(L / kMaxChunk) chunks of equal length
+// (their lengths differ by at most one).  Estimated instructions per thread of
+// one unit: per chunk its record loads and loop, Lc + kR - 1 lattice loads,
+// the packed multiply-adds (kR / 2 per even tap, kR / 2 + 1 per odd one) and
+// a weight broadcast per tap; per unit the epilogue.
 struct Plan {
-  int lc;
-  long chunks, cost;
+  long chunks, recs, cost;
 };
-Plan chunk_plan(const std::vector<int> &starts) {
-  Plan best{0, 0, -1};
-  for (int lc : kChunkLengths) {
-    long ch = 0;
-    for (size_t r = 0; r + 1 < starts.size(); ++r) ch += (starts[r + 1] - starts[r] + lc - 1) / lc;
-    const long cost = ch * (6 + (lc + 4) / 4 + (lc + kR - 1) + (long)kR * lc) + 60;
-    if (best.cost < 0 || cost < best.cost) best = {lc, ch, cost};
+long chunk_cost(int lc) {
+  return 4 + (lc + 4) / 4 + (lc + kR - 1) + ((lc + 1) / 2) * (kR / 2) + (lc / 2) * (kR / 2 + 1) + lc;
+}
+template <typename F>
+void for_each_chunk(const std::vector<int> &starts, F f) {
+  for (size_t r = 0; r + 1 < starts.size(); ++r) {
+    const int L = starts[r + 1] - starts[r], nch = (L + kMaxChunk - 1) / kMaxChunk;
+    int c0 = starts[r];
+    for (int c = 0; c < nch; ++c) {
+      const int lc = L / nch + (c < L % nch ? 1 : 0);
+      f(c0, lc);
+      c0 += lc;
+    }
   }
-  return best;
+}
+Plan chunk_plan(const std::vector<int> &starts) {
+  Plan p{0, 0, 12L * kR + 40};
+  for_each_chunk(starts, [&](int, int lc) {
+    ++p.chunks;
+    p.recs += (lc + 4) / 4;
+    p.cost += chunk_cost(lc);
+  });
+  return p;
 }
 
 }  // namespace
@@ -776,20 +802,37 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
       taps += (double)cells.size() * wx * wy;
       const std::vector<int> &runs = along_y ? cy_runs : cx_runs;
       const Plan &pl = along_y ? py : px;
-      const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
-      for (size_t r = 0; r + 1 < runs.size(); ++r)
-        for (int c0 = runs[r]; c0 < runs[r + 1]; c0 += pl.lc) {
-          const int eoff = global && !along_y ? cells[c0].cy + ldp * cells[c0].cx
-                                              : cells[c0].cx + ldp * cells[c0].cy;
+      const int off = (int)(rec.size() / 4);
+      // header: chunks per length (one byte per length 1..8), then the chunks
+      // grouped by length, each group in run order
+      unsigned counts[2] = {0u, 0u};
+      for_each_chunk(runs, [&](int, int lc) { counts[(lc - 1) >> 2] += 1u << (8 * ((lc - 1) & 3)); });
+      float hbits[2];
+      memcpy(hbits, counts, sizeof hbits);
+      rec.push_back(hbits[0]);
+      rec.push_back(hbits[1]);
+      rec.push_back(0.f);
+      rec.push_back(0.f);
+      for (int len = 1; len <= kMaxChunk; ++len)
+        for_each_chunk(runs, [&](int c0, int lc) {
+          if (lc != len) return;
+          const int eoff =
+              global && !along_y ? cells[c0].cy + ldp * cells[c0].cx : cells[c0].cx + ldp * cells[c0].cy;
           float obits;
           memcpy(&obits, &eoff, sizeof obits);
           rec.push_back(obits);
-          for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < runs[r + 1] ? (float)cells[c0 + i].w : 0.f);
-          for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
-        }
+          for (int i = 0; i < lc; ++i) rec.push_back((float)cells[c0 + i].w);
+          for (int i = lc + 1; i < 4 * ((lc + 4) / 4); ++i) rec.push_back(0.f);
+        });
+      int per_len[kMaxChunk + 1] = {};
+      for_each_chunk(runs, [&](int, int lc) { ++per_len[lc]; });
+      if (*std::max_element(per_len, per_len + kMaxChunk + 1) > 255 || pl.recs + 1 > 524287) {
+        set_error("displacement kernel: stencil longer than the unit encoding allows");
+        return VIE_ERR_UNSUPPORTED;
+      }
       const int lanes = along_y ? wx : wy, stack = along_y ? wy : wx;
       const int nsb = (stack + kR - 1) / kR, full = lanes / 32, rem = lanes % 32;
-      const int w = (along_y ? 1 : 0) | (pl.lc << 1) | ((int)pl.chunks << 8);
+      const int w = (along_y ? 1 : 0) | ((int)(pl.recs + 1) << 12);
       const int dxy = (dx & 0xffff) | (dy << 16);
       for (int sb = 0; sb < nsb; ++sb)
         for (int lb = 0; lb < full; ++lb) units.push_back({make_int4(off, dxy, lb | (sb << 16), w), pl.cost});
@@ -801,7 +844,7 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
         const int span = lg == 0 ? 1 : G * sstride;
         for (int base = 0; base < nsb; base += span)
           for (int j = 0; j < (lg == 0 ? 1 : sstride) && base + j < nsb; ++j)
-            units.push_back({make_int4(off, dxy, full | ((base + j) << 16), w | (lg << 5)), pl.cost});
+            units.push_back({make_int4(off, dxy, full | ((base + j) << 16), w | (lg << 1)), pl.cost});
       }
     }
   for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
@@ -898,8 +941,8 @@ vie_status disp_mii_prepare(DispPlan *dp, int n, double *diag_value, cudaStream_
 vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device, cudaStream_t st) {
   dp->usable = 0;
   if (n < 2 || n > 4096) return VIE_OK;
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   // the lattice in shared memory where it fits, else (n <= kGlobalMaxN) in
   // global memory, read through L1
   const bool global = disp_smem_bytes(n) > (size_t)prop.sharedMemPerBlockOptin;
@@ -1030,8 +1073,8 @@ vie_status disp_expand(const DispPlan &dp, int n, const float *wbuf, const doubl
       VIE_CUDA(cudaMemset2DAsync((__nv_bfloat16 *)klo + N, ldk * esz, 0, (ldk - N) * esz, N, st));
     }
   }
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   const size_t smem = expand_smem_bytes(n);
   if (smem > (size_t)prop.sharedMemPerBlockOptin) {
     set_error("vie_assemble: grid too large for the pair-weight expansion");
@@ -1069,8 +1112,8 @@ vie_status symv_apply(int n, int op, const double *sigma_s, const double *g, con
     return VIE_ERR_UNSUPPORTED;
   }
   const long N = (long)n * n;
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   k_symv_source<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, op, sigma_s, g, s);
   VIE_CHECK_LAUNCH("k_symv_source");
   const int items = n * (n + 1) / 2;

@@ -488,8 +488,8 @@ size_t disp3_smem_bytes(int n) {
 vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int device, cudaStream_t st) {
   dp->usable = 0;
   if (n < 2 || n > kMaxN3) return VIE_OK;
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   const size_t smem = disp3_smem_bytes(n);
   if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
   Disp3Kernel k = pick_disp3(n);

@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "march.cuh"
@@ -228,8 +229,8 @@ static size_t sym_group_bytes() {
 
 vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
                        int device, cudaStream_t st) {
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
   int ldp = 0, plane = 0;
   SymKernel k = pick(dim, n + 1, &ldp, &plane);
   size_t smem = sym_smem_bytes(dim, n, nullptr, nullptr);
@@ -321,23 +322,53 @@ namespace vie {
 // (LDP (n+1) floats in 2D, PLANE (n+1) in 3D); items_mem T (T+1)/2 int2
 // (filled by the caller in the order a = 0.., b = a..T-1); counter_mem two
 // ints set to zero by the caller before the launch.
+// Resident CTAs per SM of a symmetric-kernel variant, per device: computed
+// once (occupancy query and shared-memory opt-in), then read from the cache.
+struct OccEntry {
+  int device;
+  const void *kernel;
+  size_t smem;
+  int bps;
+};
+
+vie_status sym_occupancy(int device, const void *k, size_t smem, int *bps) {
+  static std::mutex mu;
+  static std::vector<OccEntry> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const OccEntry &e : cache)
+    if (e.device == device && e.kernel == k && e.smem == smem) {
+      *bps = e.bps;
+      return VIE_OK;
+    }
+  VIE_TRY(raise_smem_limit(k, (size_t)((int)smem)));
+  int b = 0;
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kCtaThreads, smem));
+  cache.push_back({device, k, smem, b});
+  *bps = b;
+  return VIE_OK;
+}
+
 vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
                              int device, int2 *items_mem, int *counter_mem, float *lattice_mem,
-                             cudaStream_t st) {
-  cudaDeviceProp prop;
-  VIE_CUDA(cudaGetDeviceProperties(&prop, device));
+                             long max_lattice, int max_T, cudaStream_t st) {
+  int optin = 0, sms = 0;
+  VIE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   int ldp = 0, plane = 0;
   SymKernel k = pick(dim, n + 1, &ldp, &plane);
   const size_t smem = sym_smem_bytes(dim, n, nullptr, nullptr);
   sp->usable = 0;
-  if (smem > (size_t)prop.sharedMemPerBlockOptin) return VIE_OK;
-  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
-  int bps = 0;
-  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kCtaThreads, smem));
-  if (bps < 1) return VIE_OK;
+  if (smem > (size_t)optin) return VIE_OK;
   const long P = n + 1;
   const long lattice = dim == 2 ? (long)ldp * P : (long)plane * P;
-  sp->T = (int)((N + kG - 1) / kG);
+  const int T = (int)((N + kG - 1) / kG);
+  // the caller's buffers must hold the re-strided lattice and T target tiles
+  // before anything is launched into them
+  if (lattice > max_lattice || T > max_T) return VIE_OK;
+  int bps = 0;
+  VIE_TRY(sym_occupancy(device, (const void *)k, smem, &bps));
+  if (bps < 1) return VIE_OK;
+  sp->T = T;
   sp->n_items = sp->T * (sp->T + 1) / 2;
   sp->items = items_mem;
   sp->counter = counter_mem;
@@ -352,8 +383,7 @@ vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *s
   sp->ldp = ldp;
   sp->plane = plane;
   sp->smem = smem;
-  sp->grid = (int)std::min<long>((long)bps * prop.multiProcessorCount,
-                                 (sp->n_items + kGroups - 1) / kGroups);
+  sp->grid = (int)std::min<long>((long)bps * sms, (sp->n_items + kGroups - 1) / kGroups);
   sp->kernel = (const void *)k;
   sp->usable = 1;
   return VIE_OK;

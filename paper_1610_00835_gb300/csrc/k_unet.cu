@@ -13,6 +13,7 @@
 // e_l (l < L-1) is written straight into the second half of c_l's channels.
 // Training minimises mean((o - t)^2) with Adam; inference can use a BF16 copy
 // of the weights (FP32 accumulation either way).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
@@ -134,57 +135,61 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, lon
   }
 }
 
-// The same convolution on the 5th-generation tensor cores for BF16 weights,
-// as an implicit GEMM: D[p][co] = sum_k A[p][k] B[co][k] over a CTA tile of
-// 128 consecutive pixels p (flat index y W + x), with k = 9 ci + tap, the
-// weights' own order (B[co][k] = w[co][ci][tap]), and A[p][k] the input at
-// (ci, y + tap / 3 - 1, x + tap % 3 - 1) rounded to BF16 (0 outside the image);
-// K = 9 Ci is padded with zeros to whole 64-wide blocks.  Every thread builds
-// its pixel's row of A and a share of B for one K block into a two-stage
-// shared-memory ring (K-major, 128-byte swizzle: 16-byte chunk c of row r at
-// r 128 + 16 (c ^ r % 8)); thread 0 issues the block's four MMAs (M = 128,
-// N = Co, K = 16, FP32 accumulation in tensor memory) and commits them to the
-// stage's mbarrier, which frees the stage for the block after next.  Each warp
-// then reads its 32 tensor-memory lanes (pixels) and writes bias (+ relu) in
-// FP32.  Waits are bounded; a CTA that gives up writes NaN, which the Krylov
-// driver reports.
-constexpr int kTcM = 128, kTcBK = 64;
+// Tensor-core convolution tiles: 128 TMEM lanes (pixels) per CTA.
+constexpr int kTcM = 128;
 
 __host__ __device__ constexpr int conv_tc_tmem_cols(int co) { return co <= 32 ? 32 : co <= 64 ? 64 : co <= 128 ? 128 : 256; }
-size_t conv_tc_smem(int co) { return 1024 + 2 * (size_t)(kTcM * 128 + co * 128) + 64; }
+
+// The BF16 convolution as an implicit GEMM fed by the tensor memory
+// accelerator.  The input is first rounded to BF16 and laid out NHWC with its
+// channels padded to S slices of 32 (k_to_nhwc_bf16).  A CTA owns a tile of
+// 128 TMEM lanes = R rows x Wb pixels of one image (Wb = min(W, 128), R =
+// 128 / Wb); for each tap (dy, dx) and channel slice the A operand is the
+// input shifted by the tap: one TMA box (32 channels, Wb, R, 1) at (slice,
+// x0 + dx - 1, y0 + dy - 1, image), whose out-of-image part the TMA fills
+// with zeros -- exactly the zero padding of the convolution.  Its rows are
+// 64 bytes (32 BF16 along K), written with the 64-byte swizzle that the MMA's
+// K-major descriptor reads.  The B operand of the same step is the weights'
+// [Co][32] block of that tap and slice (packed by k_pack_tc_weights), also by
+// TMA.  All 9 S steps are in flight at once (one mbarrier each, so no stage
+// is reused); one thread issues two tcgen05.mma (M = 128, N = Co, K = 16) per
+// step as its operands land, accumulating in FP32 in tensor memory; each warp
+// then reads its 32 lanes, adds the bias (and relu) and writes FP32 NCHW.
+// Waits are bounded (wl; the first operand wait takes wl.first).  A CTA that
+// gives up stops issuing, waits (bounded by wl.limit) for the loads and
+// products it issued, writes NaN and sets *err.
+constexpr int kTmaSlice = 32;   // channels per K slice (64 bytes of BF16)
+
+size_t conv_tma_smem(int S, int Co) {
+  const size_t a = (size_t)9 * S * kTcM * 64, b = (size_t)9 * S * Co * 64;
+  return 1024 + a + b + 8 * (9 * S + 1) + 16;
+}
 
 template <bool RELU>
-__global__ void __launch_bounds__(kTcM) k_conv3_tc(const float *__restrict__ in, long in_bs, int Ci,
-                                                   const __nv_bfloat16 *__restrict__ w,
-                                                   const float *__restrict__ bias, float *__restrict__ out,
-                                                   long out_bs, int Co, int H, int W) {
+__global__ void __launch_bounds__(kTcM) k_conv3_tma(const __grid_constant__ CUtensorMap map_x,
+                                                    const __grid_constant__ CUtensorMap map_w,
+                                                    const float *__restrict__ bias, float *__restrict__ out,
+                                                    long out_bs, int Co, int H, int W, int S, int Wb, int R,
+                                                    int tiles_x, WaitLimits wl, int *err) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
-  const int a_bytes = kTcM * 128, stage_bytes = a_bytes + Co * 128;
-  unsigned long long *bars = (unsigned long long *)(smem + 2 * stage_bytes);  // stages 0, 1; done
-  unsigned *tmem_slot = (unsigned *)(bars + 3);
-  volatile int *never = (volatile int *)(tmem_slot + 1);  // no abort signal: waits end by their limit
-  const int tid = threadIdx.x, warp = tid / 32;
-  const long plane = (long)H * W;
-  const long p = (long)blockIdx.x * kTcM + tid;  // this thread's pixel: row tid of A and of D
-  const bool pvalid = p < plane;
-  const int py = pvalid ? (int)(p / W) : 0, px = pvalid ? (int)(p % W) : 0;
-  unsigned tmask = 0;  // bit tap: the tap's input pixel lies in the image
-  if (pvalid)
-    for (int t = 0; t < 9; ++t) {
-      const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W) tmask |= 1u << t;
-    }
-  const float *inp = in + blockIdx.y * in_bs + (long)py * W + px;
-  const int K = 9 * Ci, nkb = (K + kTcBK - 1) / kTcBK;
+  const int steps = 9 * S;
+  const int a_bytes = kTcM * 64, b_bytes = Co * 64;
+  unsigned char *As = smem, *Bs = smem + (size_t)steps * a_bytes;
+  unsigned long long *bars = (unsigned long long *)(Bs + (size_t)steps * b_bytes);  // steps, then done
+  unsigned *tmem_slot = (unsigned *)(bars + steps + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x, img = blockIdx.y;
+  const int x0 = tx * Wb, y0 = ty * R;
   const int tcols = conv_tc_tmem_cols(Co);
   if (tid == 0) {
-    for (int i = 0; i < 3; ++i) mbar_init(su32(bars + i), 1);
-    *never = 0;
+    for (int i = 0; i <= steps; ++i) mbar_init(su32(bars + i), 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                  "r"(tcols)
                  : "memory");
@@ -194,118 +199,114 @@ __global__ void __launch_bounds__(kTcM) k_conv3_tc(const float *__restrict__ in,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
-  const unsigned idesc = idesc_bf16(kTcM, Co);
-  bool ok = true;
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int s = kb & 1;
-    unsigned char *st = smem + s * stage_bytes;
-    // the MMAs of block kb - 2 read this stage
-    if (kb >= 2) ok = mbar_wait(su32(bars + s), ((kb - 2) >> 1) & 1, never);
-    if (ok) {
-      // A: this thread's row, 8 chunks of 8 consecutive k; all 64 loads are
-      // issued before the first conversion
-      const unsigned arow = su32(st) + (unsigned)tid * 128u;
-      float v[64];
-      {
-        const int k0 = kb * kTcBK;
-        int ci = k0 / 9, tap = k0 - 9 * ci;
-#pragma unroll
-        for (int e = 0; e < 64; ++e) {
-          const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;  // tap / 3, tap % 3 for tap < 9
-          v[e] = (ci < Ci && ((tmask >> tap) & 1u)) ? __ldg(inp + ci * plane + (long)(dy - 1) * W + (dx - 1)) : 0.f;
-          if (++tap == 9) {
-            tap = 0;
-            ++ci;
-          }
-        }
-      }
-      // B: Co rows of 8 chunks, chunk t = 8 co + c (two per thread for Co = 32)
-      constexpr int kBT = 2;
-      unsigned short hb[kBT][8];
-#pragma unroll
-      for (int j = 0; j < kBT; ++j) {
-        const int t = tid + j * kTcM, co = t >> 3, k0 = kb * kTcBK + (t & 7) * 8;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const __nv_bfloat16 x =
-              t < Co * 8 && k0 + e < K ? w[(long)co * K + k0 + e] : __float2bfloat16_rn(0.f);
-          hb[j][e] = *reinterpret_cast<const unsigned short *>(&x);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const __nv_bfloat162 q0 = __floats2bfloat162_rn(v[8 * c], v[8 * c + 1]);
-        const __nv_bfloat162 q1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
-        const __nv_bfloat162 q2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
-        const __nv_bfloat162 q3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
-        const unsigned dst = arow + (unsigned)((c ^ (tid & 7)) << 4);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
-                     "r"(*reinterpret_cast<const unsigned *>(&q0)), "r"(*reinterpret_cast<const unsigned *>(&q1)),
-                     "r"(*reinterpret_cast<const unsigned *>(&q2)), "r"(*reinterpret_cast<const unsigned *>(&q3))
-                     : "memory");
-      }
-#pragma unroll
-      for (int j = 0; j < kBT; ++j) {
-        const int t = tid + j * kTcM, co = t >> 3, c = t & 7;
-        if (t < Co * 8) {
-          const unsigned dst = su32(st + a_bytes) + (unsigned)co * 128u + (unsigned)((c ^ (co & 7)) << 4);
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
-                       "r"(hb[j][0] | ((unsigned)hb[j][1] << 16)), "r"(hb[j][2] | ((unsigned)hb[j][3] << 16)),
-                       "r"(hb[j][4] | ((unsigned)hb[j][5] << 16)), "r"(hb[j][6] | ((unsigned)hb[j][7] << 16))
-                       : "memory");
-        }
-      }
-      // Co > 32: the remaining B chunks one at a time
-      for (int t = tid + kBT * kTcM; t < Co * 8; t += kTcM) {
-        const int co = t >> 3, c = t & 7, k0 = kb * kTcBK + c * 8;
-        unsigned short h[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const __nv_bfloat16 x = k0 + e < K ? w[(long)co * K + k0 + e] : __float2bfloat16_rn(0.f);
-          h[e] = *reinterpret_cast<const unsigned short *>(&x);
-        }
-        const unsigned dst = su32(st + a_bytes) + (unsigned)co * 128u + (unsigned)((c ^ (co & 7)) << 4);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(h[0] | ((unsigned)h[1] << 16)),
-                     "r"(h[2] | ((unsigned)h[3] << 16)), "r"(h[4] | ((unsigned)h[5] << 16)),
-                     "r"(h[6] | ((unsigned)h[7] << 16))
-                     : "memory");
-      }
+  int issued_loads = 0, issued_mma = 0;
+  if (tid == 0) {
+    // every step's operands at once: the box of the shifted input and the weights
+    const unsigned bytes = (unsigned)(kTmaSlice * 2 * Wb * R + b_bytes);
+    for (int k = 0; k < steps; ++k) {
+      const int tap = k / S, sl = k - tap * S;
+      const unsigned bar = su32(bars + k);
+      mbar_arrive_expect_tx(bar, bytes);
+      tma_load_4d(su32(As + (size_t)k * a_bytes), &map_x, bar, sl * kTmaSlice, x0 + tap % 3 - 1,
+                  y0 + tap / 3 - 1, img);
+      tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, bar, 0, k * Co);
+      ++issued_loads;
     }
-    // the generic-proxy stores above become visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) break;
-    if (tid == 0) {
+  } else if (tid == 32) {
+    const unsigned idesc = idesc_bf16(kTcM, Co);
+    for (int k = 0; k < steps; ++k) {
+      if (!mbar_wait(su32(bars + k), 0, abort_flag, k == 0 ? wl.first : wl.limit)) {
+        atomicExch(err, 1);
+        *abort_flag = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a = su32(As + (size_t)k * a_bytes), b = su32(Bs + (size_t)k * b_bytes);
 #pragma unroll
-      for (int kk = 0; kk < kTcBK / 16; ++kk) {
-        const unsigned off = kk * 32;  // 16 BF16 along the swizzled 128-byte row
-        mma_bf16(tmem, smem_desc_sw128(su32(st) + off), smem_desc_sw128(su32(st + a_bytes) + off), idesc,
-                 (kb > 0 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(su32(bars + s));
+      for (int kk = 0; kk < 2; ++kk)
+        mma_bf16(tmem, smem_desc_sw64(a + kk * 32), smem_desc_sw64(b + kk * 32), idesc,
+                 (k > 0 || kk > 0) ? 1u : 0u);
+      ++issued_mma;
     }
+    mma_commit(su32(bars + steps));  // the accumulator (and every product issued)
   }
-  // every product issued so far, then the accumulator
-  if (tid == 0) mma_commit(su32(bars + 2));
-  bool done = mbar_wait(su32(bars + 2), 0, never);
-  ok = __syncthreads_and(ok && done) != 0;  // tcgen05.ld below must be warp-uniform
+  __syncwarp();
+  bool ok = mbar_wait(su32(bars + steps), 0, abort_flag, wl.limit);
+  ok = __syncthreads_and(ok && *abort_flag == 0) != 0;  // tcgen05.ld below must be warp-uniform
+  if (!ok && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  float *ob = out + blockIdx.y * out_bs + p;
+  const int i = warp * 32 + lane;  // this thread's TMEM lane: pixel (x0 + i % Wb, y0 + i / Wb)
+  const int px = x0 + i % Wb, py = y0 + i / Wb;
+  const bool pvalid = i < Wb * R && px < W && py < H;
+  float *ob = out + img * out_bs + (long)py * W + px;
+  const long plane = (long)H * W;
   for (int c0 = 0; c0 < Co; c0 += 16) {
     float v[16];
     if (ok) tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      float x = ok ? v[i] + bias[c0 + i] : __int_as_float(0x7fc00000);
+    for (int j = 0; j < 16; ++j) {
+      float x = ok ? v[j] + bias[c0 + j] : __int_as_float(0x7fc00000);
       if (RELU && ok) x = fmaxf(x, 0.f);
-      if (pvalid) ob[(long)(c0 + i) * plane] = x;
+      if (pvalid) ob[(long)(c0 + j) * plane] = x;
     }
   }
+  // everything issued has landed before shared and tensor memory are released
+  // (each barrier has one phase; bounded by the full limit)
+  if (tid == 0) {
+    const long long t0 = clock64();
+    for (int k = 0; k < issued_loads; ++k)
+      while (!mbar_test(su32(bars + k), 0) && clock64() - t0 < wl.limit) {
+      }
+  }
+  if (tid == 32) {
+    const long long t0 = clock64();
+    while (!mbar_test(su32(bars + steps), 0) && clock64() - t0 < wl.limit) {
+    }
+  }
+  (void)issued_mma;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
+// in: FP32 [B][Ci][plane] (image stride in_bs) -> BF16 [B][plane][Cp], rounded
+// to nearest even, channels Ci..Cp-1 zero.  One thread per (image, pixel, 8 channels).
+__global__ void k_to_nhwc_bf16(const float *__restrict__ in, long in_bs, int Ci, long plane, int Cp, int B,
+                               __nv_bfloat16 *__restrict__ out) {
+  const int groups = Cp / 8;
+  const long total = (long)B * plane * groups;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int gq = (int)(t % groups);
+    const long pq = t / groups;
+    const long p = pq % plane;
+    const int b = (int)(pq / plane);
+    const float *src = in + b * in_bs + p;
+    unsigned w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = gq * 8 + 2 * e;
+      const float lo = c < Ci ? src[(long)c * plane] : 0.f, hi = c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f;
+      const __nv_bfloat162 q = __floats2bfloat162_rn(lo, hi);
+      w[e] = *reinterpret_cast<const unsigned *>(&q);
+    }
+    *reinterpret_cast<uint4 *>(out + (pq * Cp + gq * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Weights of one 3x3 convolution, FP32 [Co][Ci][9] -> BF16 [9 S][Co][32]:
+// block k = tap S + slice holds w[co][slice 32 + c][tap] (zero past Ci).
+__global__ void k_pack_tc_weights(const float *__restrict__ w, int Co, int Ci, int S,
+                                  __nv_bfloat16 *__restrict__ out) {
+  const long total = (long)9 * S * Co * kTmaSlice;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % kTmaSlice);
+    const long r = t / kTmaSlice;
+    const int co = (int)(r % Co);
+    const int k = (int)(r / Co);
+    const int tap = k / S, ci = (k - tap * S) * kTmaSlice + c;
+    out[t] = __float2bfloat16_rn(ci < Ci ? w[((long)co * Ci + ci) * 9 + tap] : 0.f);
   }
 }
 
@@ -558,6 +559,34 @@ __global__ void k_net_output(const double *__restrict__ v, const double *__restr
 
 int gridn(long n) { return (int)std::max(1L, std::min((n + 255) / 256, 8192L)); }
 
+// The same for R vectors at once (blockIdx.y = r): v_r at v + r ldv, ||v_r||^2
+// at scal[8 r + slot], input image r at x + 3 r N, z_r at z + r ldz.
+__global__ void k_net_input_b(const double *__restrict__ st, const double *__restrict__ ss,
+                              const double *__restrict__ v, long ldv, const double *__restrict__ scal, int slot,
+                              long N, float inv_ref, float *__restrict__ x) {
+  const int r = blockIdx.y;
+  const double rms = sqrt(scal[8 * r + slot] / (double)N);
+  const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
+  const double *vr = v + (long)r * ldv;
+  float *xr = x + 3L * r * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    xr[i] = (float)st[i] * inv_ref;
+    xr[N + i] = (float)ss[i] * inv_ref;
+    xr[2 * N + i] = (float)(vr[i] * inv);
+  }
+}
+
+__global__ void k_net_output_b(const double *__restrict__ v, long ldv, const double *__restrict__ scal, int slot,
+                               const float *__restrict__ o, long N, double *__restrict__ z, long ldz) {
+  const int r = blockIdx.y;
+  const double rms = sqrt(scal[8 * r + slot] / (double)N);
+  const double *vr = v + (long)r * ldv;
+  const float *orr = o + (long)r * N;
+  double *zr = z + (long)r * ldz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    zr[i] = vr[i] + rms * (double)orr[i];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ network host
@@ -565,6 +594,14 @@ int gridn(long n) { return (int)std::max(1L, std::min((n + 255) / 256, 8192L)); 
 struct ConvLayer {
   int co, ci, k;
   long w_off, b_off;  // into the flat parameter array
+  long tc_off;        // 3x3 layers: their packed BF16 weights [9 S][co][32] in UnetImpl::ptc
+};
+
+// A cached TMA descriptor (encoding one costs host time on every launch).
+struct MapEntry {
+  const void *base;
+  unsigned long long key[4];
+  CUtensorMap map;
 };
 
 struct UnetImpl {
@@ -581,6 +618,14 @@ struct UnetImpl {
   float *o = nullptr, *go = nullptr;
   double *part = nullptr, *h_part = nullptr;
   float *xin0_owned = nullptr;
+  int *dev_err = nullptr;  // set by a tensor-core convolution whose bounded wait gave up
+  // BF16 tensor-core forward: packed weights (rebuilt when the parameters
+  // change), the NHWC BF16 copy of the current convolution's input, cached maps
+  __nv_bfloat16 *ptc = nullptr;
+  long ptc_elems = 0;
+  bool ptc_dirty = true;
+  __nv_bfloat16 *nhwc = nullptr;
+  std::vector<MapEntry> maps;
 };
 
 namespace {
@@ -597,6 +642,9 @@ void free_acts(UnetImpl *u) {
   if (u->go) cudaFree(u->go);
   if (u->part) cudaFree(u->part);
   if (u->h_part) cudaFreeHost(u->h_part);
+  if (u->nhwc) cudaFree(u->nhwc);
+  u->nhwc = nullptr;
+  u->maps.clear();
   u->o = u->go = nullptr;
   u->part = nullptr;
   u->h_part = nullptr;
@@ -639,6 +687,9 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   if ((s = al(&u->go, (long)B * n * n)) != VIE_OK) return s;
   VIE_CUDA(cudaMalloc((void **)&u->part, sizeof(double) * 1024));
   VIE_CUDA(cudaMallocHost((void **)&u->h_part, sizeof(double) * 1024));
+  // the widest convolution input: 2 C channels (a decoder's concatenation), padded to slices
+  VIE_CUDA(cudaMalloc((void **)&u->nhwc,
+                      sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
   u->B = B;
   u->n = n;
   return VIE_OK;
@@ -675,23 +726,75 @@ void conv3_shape(const float *in, long in_bs, int Ci, const WT *w, const float *
     launch_conv3<RELU, WT, 8, 8>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
 }
 
-template <typename WT>
-vie_status conv3(const float *in, long in_bs, int Ci, const WT *w, const float *bias, float *out, long out_bs,
-                 int Co, int H, int W, int B, bool relu, cudaStream_t st) {
-  if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
-    if (Co % 16 == 0 && Co >= 16 && Co <= 256 && bias) {
-      // BF16 weights: the tensor-core implicit GEMM
-      const size_t smem = conv_tc_smem(Co);
-      const void *k = relu ? (const void *)k_conv3_tc<true> : (const void *)k_conv3_tc<false>;
-      VIE_TRY(raise_smem_limit(k, smem));
-      const dim3 grid((unsigned)(((long)H * W + kTcM - 1) / kTcM), (unsigned)B);
-      if (relu)
-        k_conv3_tc<true><<<grid, kTcM, smem, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W);
-      else
-        k_conv3_tc<false><<<grid, kTcM, smem, st>>>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W);
-      VIE_CHECK_LAUNCH("k_conv3_tc");
+// the tensor map for (base, key), encoded on first use and copied out by
+// value (the cache may grow, and move its entries, on a later call)
+vie_status cached_map(UnetImpl *u, const void *base, const unsigned long long (&key)[4], int rank,
+                      const unsigned long long *dims, const unsigned long long *strides, const unsigned *box,
+                      CUtensorMap *out) {
+  for (const MapEntry &e : u->maps)
+    if (e.base == base && e.key[0] == key[0] && e.key[1] == key[1] && e.key[2] == key[2] && e.key[3] == key[3]) {
+      *out = e.map;
       return VIE_OK;
     }
+  MapEntry e{base, {key[0], key[1], key[2], key[3]}, CUtensorMap{}};
+  VIE_TRY(encode_bf16_map(&e.map, rank, base, dims, strides, box, 64));
+  if (u->maps.size() >= 256) u->maps.clear();
+  u->maps.push_back(e);
+  *out = e.map;
+  return VIE_OK;
+}
+
+// The BF16 3x3 convolution on the tensor cores (k_conv3_tma): input to BF16
+// NHWC, then the implicit GEMM.  wtc: the layer's packed weights.
+vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __nv_bfloat16 *wtc, const float *bias,
+                     float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+  const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
+  const long plane = (long)H * W;
+  k_to_nhwc_bf16<<<gridn((long)B * plane * (Cp / 8)), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
+  VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
+  const int Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
+  const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
+  CUtensorMap mx, mw;
+  {
+    const unsigned long long key[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
+                                       (unsigned long long)B};
+    const unsigned long long dims[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
+                                        (unsigned long long)B};
+    const unsigned long long strides[3] = {2ull * Cp, 2ull * Cp * W, 2ull * Cp * W * H};
+    const unsigned box[4] = {(unsigned)kTmaSlice, (unsigned)Wb, (unsigned)R, 1u};
+    VIE_TRY(cached_map(u, u->nhwc, key, 4, dims, strides, box, &mx));
+  }
+  {
+    const unsigned long long key[4] = {(unsigned long long)S, (unsigned long long)Co, 0ull, 1ull};
+    const unsigned long long dims[2] = {(unsigned long long)kTmaSlice, 9ull * S * Co};
+    const unsigned long long strides[1] = {2ull * kTmaSlice};
+    const unsigned box[2] = {(unsigned)kTmaSlice, (unsigned)Co};
+    VIE_TRY(cached_map(u, wtc, key, 2, dims, strides, box, &mw));
+  }
+  const size_t smem = conv_tma_smem(S, Co);
+  const void *k = relu ? (const void *)k_conv3_tma<true> : (const void *)k_conv3_tma<false>;
+  VIE_TRY(raise_smem_limit(k, smem));
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  const WaitLimits wl = wait_limits(dev);
+  const dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)B);
+  if (relu)
+    k_conv3_tma<true><<<grid, kTcM, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x, wl,
+                                               u->dev_err);
+  else
+    k_conv3_tma<false><<<grid, kTcM, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x, wl,
+                                                u->dev_err);
+  VIE_CHECK_LAUNCH("k_conv3_tma");
+  return VIE_OK;
+}
+
+template <typename WT>
+vie_status conv3(UnetImpl *u, const float *in, long in_bs, int Ci, const WT *w, const __nv_bfloat16 *wtc,
+                 const float *bias, float *out, long out_bs, int Co, int H, int W, int B, bool relu,
+                 cudaStream_t st) {
+  if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+    if (wtc && Co % 16 == 0 && Co >= 16 && Co <= 32 && Ci <= 2 * kTmaSlice && bias)
+      return conv3_tma(u, in, in_bs, Ci, wtc, bias, out, out_bs, Co, H, W, B, relu, st);
   }
   if (relu)
     conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
@@ -702,24 +805,41 @@ vie_status conv3(const float *in, long in_bs, int Ci, const WT *w, const float *
 }
 
 // Forward through the network; weights FP32 (pw) or BF16 (pbw).
+// the packed BF16 weights of every 3x3 layer, from the FP32 parameters
+vie_status pack_tc_weights(UnetImpl *u, cudaStream_t st) {
+  if (!u->ptc_dirty) return VIE_OK;
+  for (const ConvLayer &c : u->layers) {
+    if (c.k != 3) continue;
+    const int S = (c.ci + kTmaSlice - 1) / kTmaSlice;
+    k_pack_tc_weights<<<gridn(9L * S * c.co * kTmaSlice), 256, 0, st>>>(u->p + c.w_off, c.co, c.ci, S,
+                                                                       u->ptc + c.tc_off);
+    VIE_CHECK_LAUNCH("k_pack_tc_weights");
+  }
+  u->ptc_dirty = false;
+  return VIE_OK;
+}
+
 template <typename WT>
 vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cudaStream_t st) {
   const int L = u->L, C = u->C;
   vie_status s;
   int li = 0;
+  const bool tc = std::is_same<WT, __nv_bfloat16>::value;
+  if (tc && (s = pack_tc_weights(u, st)) != VIE_OK) return s;
+  auto wtc = [&](const ConvLayer &c) { return tc ? u->ptc + c.tc_off : nullptr; };
   const float *xl = x;
   long xl_bs = 3L * n * n;
   for (int l = 0; l < L; ++l) {
     const int H = n >> l;
     const long hw = (long)H * H;
     const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
-    if ((s = conv3(xl, xl_bs, c1.ci, pw + c1.w_off, u->p + c1.b_off, u->a[l], (long)C * hw, C, H, H, B,
-                   true, st)) != VIE_OK)
+    if ((s = conv3(u, xl, xl_bs, c1.ci, pw + c1.w_off, wtc(c1), u->p + c1.b_off, u->a[l], (long)C * hw, C, H,
+                   H, B, true, st)) != VIE_OK)
       return s;
     float *e = l < L - 1 ? u->cat[l] + (long)C * hw : u->ebot[0];
     const long e_bs = l < L - 1 ? 2L * C * hw : (long)C * hw;
-    if ((s = conv3(u->a[l], (long)C * hw, C, pw + c2.w_off, u->p + c2.b_off, e, e_bs, C, H, H, B, true,
-                   st)) != VIE_OK)
+    if ((s = conv3(u, u->a[l], (long)C * hw, C, pw + c2.w_off, wtc(c2), u->p + c2.b_off, e, e_bs, C, H, H, B,
+                   true, st)) != VIE_OK)
       return s;
     if (l < L - 1) {
       k_avgpool<<<gridn((long)B * C * hw / 4), 256, 0, st>>>(e, e_bs, u->xin[l + 1], (long)C * hw / 4, C, H,
@@ -737,11 +857,11 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
     k_upsample<<<gridn((long)B * C * hw), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
     VIE_CHECK_LAUNCH("k_upsample");
     const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
-    if ((s = conv3(u->cat[l], 2L * C * hw, 2 * C, pw + c1.w_off, u->p + c1.b_off, u->bl[l], (long)C * hw, C,
-                   H, H, B, true, st)) != VIE_OK)
+    if ((s = conv3(u, u->cat[l], 2L * C * hw, 2 * C, pw + c1.w_off, wtc(c1), u->p + c1.b_off, u->bl[l],
+                   (long)C * hw, C, H, H, B, true, st)) != VIE_OK)
       return s;
-    if ((s = conv3(u->bl[l], (long)C * hw, C, pw + c2.w_off, u->p + c2.b_off, u->dl[l], (long)C * hw, C, H,
-                   H, B, true, st)) != VIE_OK)
+    if ((s = conv3(u, u->bl[l], (long)C * hw, C, pw + c2.w_off, wtc(c2), u->p + c2.b_off, u->dl[l],
+                   (long)C * hw, C, H, H, B, true, st)) != VIE_OK)
       return s;
     d = u->dl[l];
     d_bs = (long)C * hw;
@@ -764,7 +884,8 @@ vie_status conv3_backward(UnetImpl *u, const ConvLayer &c, const float *in, long
   if (gin) {
     k_flip<<<gridn((long)c.co * c.ci * 9), 256, 0, st>>>(u->p + c.w_off, c.co, c.ci, u->wt);
     VIE_CHECK_LAUNCH("k_flip");
-    vie_status s = conv3<float>(gout, g_bs, c.co, u->wt, nullptr, gin, gin_bs, c.ci, H, H, B, false, st);
+    vie_status s = conv3<float>(u, gout, g_bs, c.co, u->wt, nullptr, nullptr, gin, gin_bs, c.ci, H, H, B, false,
+                                st);
     if (s != VIE_OK) return s;
   }
   return VIE_OK;
@@ -885,6 +1006,38 @@ vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *s
   return VIE_OK;
 }
 
+// R preconditioner applications in one forward pass of R images (the batched
+// FGMRES driver): z_r = v_r + rms(v_r) Net(sigma_t / s_ref, sigma_s / s_ref,
+// v_r / rms(v_r)), BF16 weights.
+vie_status unet_precondition_batch(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
+                                   const double *v, long ldv, const double *scal, int slot, int R, int n,
+                                   float *xbuf, double *z, long ldz, cudaStream_t st) {
+  vie_status s;
+  if ((s = ensure_acts(u, R, n)) != VIE_OK) return s;
+  const long N = (long)n * n;
+  const dim3 grid((unsigned)std::max(1L, std::min((N + 255) / 256, 1024L)), (unsigned)R);
+  k_net_input_b<<<grid, 256, 0, st>>>(sigma_t, sigma_s, v, ldv, scal, slot, N, (float)inv_ref, xbuf);
+  VIE_CHECK_LAUNCH("k_net_input_b");
+  if ((s = forward<__nv_bfloat16>(u, u->pb, xbuf, R, n, st)) != VIE_OK) return s;
+  k_net_output_b<<<grid, 256, 0, st>>>(v, ldv, scal, slot, u->o, N, z, ldz);
+  VIE_CHECK_LAUNCH("k_net_output_b");
+  return VIE_OK;
+}
+
+// VIE_ERR_TIMEOUT (and the word cleared) if a tensor-core convolution of this
+// network gave up on a bounded wait since the last check; synchronises `st`.
+vie_status unet_take_error(UnetImpl *u, cudaStream_t st) {
+  int e = 0;
+  VIE_CUDA(cudaMemcpyAsync(&e, u->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (e == 0) return VIE_OK;
+  VIE_CUDA(cudaMemsetAsync(u->dev_err, 0, sizeof(int), st));
+  set_error("a tensor-core convolution gave up on a bounded device wait (its output is NaN)");
+  return VIE_ERR_TIMEOUT;
+}
+
+int *unet_error_word(UnetImpl *u) { return u->dev_err; }
+
 }  // namespace vie
 
 using namespace vie;
@@ -915,9 +1068,11 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
   U.C = channels;
   U.device = device;
   long off = 0;
+  long tc = 0;  // packed BF16 weights of the 3x3 layers
   auto add = [&](int co, int ci, int k) {
-    ConvLayer c{co, ci, k, off, off + (long)co * ci * k * k};
+    ConvLayer c{co, ci, k, off, off + (long)co * ci * k * k, tc};
     off = c.b_off + co;
+    if (k == 3) tc += 9L * ((ci + kTmaSlice - 1) / kTmaSlice) * co * kTmaSlice;
     U.layers.push_back(c);
   };
   for (int l = 0; l < levels; ++l) {
@@ -930,6 +1085,7 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
   }
   add(1, channels, 1);
   U.nparams = off;
+  U.ptc_elems = tc;
   long max_w = 0;
   for (auto &c : U.layers) max_w = std::max(max_w, (long)c.co * c.ci * c.k * c.k);
   // He initialisation from SplitMix64 + Box-Muller, biases zero
@@ -956,6 +1112,9 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
     if (e == cudaSuccess) e = cudaMalloc((void **)q, sizeof(float) * off);
   if (e == cudaSuccess) e = cudaMalloc((void **)&U.wt, sizeof(float) * max_w);
   if (e == cudaSuccess) e = cudaMalloc((void **)&U.pb, sizeof(__nv_bfloat16) * off);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&U.dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&U.ptc, sizeof(__nv_bfloat16) * std::max(1L, U.ptc_elems));
+  if (e == cudaSuccess) e = cudaMemset(U.dev_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(U.p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(U.m, 0, sizeof(float) * off);
   if (e == cudaSuccess) e = cudaMemset(U.v, 0, sizeof(float) * off);
@@ -967,7 +1126,8 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
   }
   if (prev >= 0) cudaSetDevice(prev);
   if (s != VIE_OK) {
-    for (void *q : {(void *)U.p, (void *)U.g, (void *)U.m, (void *)U.v, (void *)U.wt, (void *)U.pb})
+    for (void *q : {(void *)U.p, (void *)U.g, (void *)U.m, (void *)U.v, (void *)U.wt, (void *)U.pb,
+                    (void *)U.dev_err, (void *)U.ptc})
       if (q) cudaFree(q);
     delete u;
     return s;
@@ -982,7 +1142,7 @@ vie_status vie_unet_destroy(vie_unet *u) {
   cudaDeviceSynchronize();
   free_acts(&u->impl);
   for (void *q : {(void *)u->impl.p, (void *)u->impl.g, (void *)u->impl.m, (void *)u->impl.v,
-                  (void *)u->impl.wt, (void *)u->impl.pb})
+                  (void *)u->impl.wt, (void *)u->impl.pb, (void *)u->impl.dev_err, (void *)u->impl.ptc})
     if (q) cudaFree(q);
   delete u;
   return VIE_OK;
@@ -1005,6 +1165,7 @@ vie_status vie_unet_set_params(vie_unet *u, const float *host) {
   if (!u || !host) return VIE_ERR_INVALID_ARG;
   VIE_CUDA(cudaSetDevice(u->impl.device));
   VIE_CUDA(cudaMemcpy(u->impl.p, host, sizeof(float) * u->impl.nparams, cudaMemcpyHostToDevice));
+  u->impl.ptc_dirty = true;
   k_to_bf16<<<gridn(u->impl.nparams), 256>>>(u->impl.p, u->impl.pb, u->impl.nparams);
   VIE_CHECK_LAUNCH("k_to_bf16");
   VIE_CUDA(cudaDeviceSynchronize());
@@ -1024,6 +1185,8 @@ vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n,
                : forward<float>(&u->impl, u->impl.p, x, B, n, st);
   if (s != VIE_OK) return s;
   VIE_CUDA(cudaMemcpyAsync(o, u->impl.o, sizeof(float) * (long)B * n * n, cudaMemcpyDeviceToDevice, st));
+  // the tensor-core convolutions report a bounded wait that gave up here
+  if (use_bf16) return unet_take_error(&u->impl, st);
   return VIE_OK;
 }
 
@@ -1058,24 +1221,36 @@ vie_status vie_unet_train_step(vie_unet *u, const float *x, const float *t, cons
   const float c1 = 1.f - powf(b1, (float)U.step), c2 = 1.f - powf(b2, (float)U.step);
   k_adam<<<gridn(U.nparams), 256, 0, st>>>(U.p, U.g, U.m, U.v, U.pb, U.nparams, lr, b1, b2, 1e-8f, c1, c2);
   VIE_CHECK_LAUNCH("k_adam");
+  U.ptc_dirty = true;
   return VIE_OK;
 }
 
+// File layout: int32 header {"UNET", version, levels, channels}, int64
+// parameter count np, np FP32 parameters; version 2 adds the Adam state
+// (int64 step, np FP32 first moments, np FP32 second moments) so that
+// training can resume where it stopped.  Version 1 files (parameters only)
+// still load, with the optimizer state reset.
 vie_status vie_unet_save(vie_unet *u, const char *path) {
   if (!u || !path) return VIE_ERR_INVALID_ARG;
-  std::vector<float> h(u->impl.nparams);
+  UnetImpl &U = u->impl;
+  const long np = U.nparams;
+  std::vector<float> h(np), hm(np), hv(np);
   vie_status s = vie_unet_get_params(u, h.data());
   if (s != VIE_OK) return s;
+  VIE_CUDA(cudaMemcpy(hm.data(), U.m, sizeof(float) * np, cudaMemcpyDeviceToHost));
+  VIE_CUDA(cudaMemcpy(hv.data(), U.v, sizeof(float) * np, cudaMemcpyDeviceToHost));
   FILE *f = fopen(path, "wb");
   if (!f) {
     set_error(std::string("vie_unet_save: cannot open ") + path);
     return VIE_ERR_INVALID_ARG;
   }
-  const int hdr[4] = {0x54454e55 /* "UNET" */, 1, u->impl.L, u->impl.C};
-  const long long np = u->impl.nparams;
-  bool ok = fwrite(hdr, sizeof hdr, 1, f) == 1 && fwrite(&np, sizeof np, 1, f) == 1 &&
-            fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
-  fclose(f);
+  const int hdr[4] = {0x54454e55 /* "UNET" */, 2, U.L, U.C};
+  const long long n64 = np, step = U.step;
+  bool ok = fwrite(hdr, sizeof hdr, 1, f) == 1 && fwrite(&n64, sizeof n64, 1, f) == 1 &&
+            fwrite(h.data(), sizeof(float), h.size(), f) == h.size() && fwrite(&step, sizeof step, 1, f) == 1 &&
+            fwrite(hm.data(), sizeof(float), hm.size(), f) == hm.size() &&
+            fwrite(hv.data(), sizeof(float), hv.size(), f) == hv.size();
+  ok = (fclose(f) == 0) && ok;
   if (!ok) {
     set_error("vie_unet_save: write failed");
     return VIE_ERR_INVALID_ARG;
@@ -1085,23 +1260,39 @@ vie_status vie_unet_save(vie_unet *u, const char *path) {
 
 vie_status vie_unet_load(vie_unet *u, const char *path) {
   if (!u || !path) return VIE_ERR_INVALID_ARG;
+  UnetImpl &U = u->impl;
   FILE *f = fopen(path, "rb");
   if (!f) {
     set_error(std::string("vie_unet_load: cannot open ") + path);
     return VIE_ERR_INVALID_ARG;
   }
   int hdr[4];
-  long long np = 0;
-  std::vector<float> h(u->impl.nparams);
+  long long np = 0, step = 0;
+  std::vector<float> h(U.nparams), hm(U.nparams, 0.f), hv(U.nparams, 0.f);
   bool ok = fread(hdr, sizeof hdr, 1, f) == 1 && fread(&np, sizeof np, 1, f) == 1 && hdr[0] == 0x54454e55 &&
-            hdr[1] == 1 && hdr[2] == u->impl.L && hdr[3] == u->impl.C && np == u->impl.nparams &&
+            (hdr[1] == 1 || hdr[1] == 2) && hdr[2] == U.L && hdr[3] == U.C && np == U.nparams &&
             fread(h.data(), sizeof(float), h.size(), f) == h.size();
+  if (ok && hdr[1] == 2)
+    ok = fread(&step, sizeof step, 1, f) == 1 && step >= 0 &&
+         fread(hm.data(), sizeof(float), hm.size(), f) == hm.size() &&
+         fread(hv.data(), sizeof(float), hv.size(), f) == hv.size();
   fclose(f);
   if (!ok) {
     set_error("vie_unet_load: file does not match this network");
     return VIE_ERR_INVALID_ARG;
   }
-  return vie_unet_set_params(u, h.data());
+  vie_status s = vie_unet_set_params(u, h.data());
+  if (s != VIE_OK) return s;
+  VIE_CUDA(cudaMemcpy(U.m, hm.data(), sizeof(float) * U.nparams, cudaMemcpyHostToDevice));
+  VIE_CUDA(cudaMemcpy(U.v, hv.data(), sizeof(float) * U.nparams, cudaMemcpyHostToDevice));
+  U.step = (long)step;
+  return VIE_OK;
+}
+
+vie_status vie_unet_train_state(vie_unet *u, long long *step) {
+  if (!u || !step) return VIE_ERR_INVALID_ARG;
+  *step = u->impl.step;
+  return VIE_OK;
 }
 
 }  // extern "C"

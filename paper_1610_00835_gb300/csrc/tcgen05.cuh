@@ -7,10 +7,12 @@
 
 #include <cuda_runtime.h>
 
+#include "vie_internal.cuh"
+
 namespace vie {
 namespace tc {
 
-constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (about 1 s)
+constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (about 1 s): the default bound
 
 __device__ __forceinline__ unsigned su32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -37,14 +39,18 @@ __device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
 }
 
 // Bounded wait on phase `parity` of an mbarrier; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort_flag) {
+// limit: clock cycles to wait; a zero limit gives up at once (no budget).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *abort_flag,
+                                          long long limit = kWaitLimit) {
+  if (limit <= 0) return false;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitLimit) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
+
 
 // K-major operand, 128-byte swizzle, rows of 128 bytes, 8-row groups 1024 B apart.
 __device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
@@ -55,6 +61,37 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
   d |= 1ull << 46;                                        // descriptor version
   d |= 2ull << 61;                                        // 128-byte swizzle
   return d;
+}
+
+// K-major operand, 64-byte swizzle: rows of 64 bytes (32 BF16 along K),
+// 8-row groups 512 B apart (the layout a TMA box with a 64-byte inner extent
+// and 64-byte swizzle writes).
+__device__ __forceinline__ unsigned long long smem_desc_sw64(unsigned addr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((addr >> 4) & 0x3FFF);        // start address
+  d |= (unsigned long long)(16 >> 4) << 16;               // leading byte offset (unused)
+  d |= (unsigned long long)(512 >> 4) << 32;              // stride byte offset
+  d |= 1ull << 46;                                        // descriptor version
+  d |= 4ull << 61;                                        // 64-byte swizzle
+  return d;
+}
+
+// Tiled TMA loads into shared memory, completing on an mbarrier (coordinates
+// innermost first; the innermost times the element size a multiple of 16 B).
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const void *map, unsigned bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const void *map, unsigned bar, int c, int x, int y,
+                                            int b) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c), "r"(x), "r"(y), "r"(b)
+      : "memory");
 }
 
 // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major.

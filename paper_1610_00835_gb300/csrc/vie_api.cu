@@ -17,6 +17,40 @@
 namespace vie {
 
 static thread_local std::string g_last_error;
+// vie_set_wait_limits: milliseconds (first < 0: the same as limit)
+static std::atomic<double> g_wait_ms{1000.0}, g_first_wait_ms{-1.0};
+
+vie_status get_dev_props(int device, DevProps *out) {
+  static std::atomic<int> sms_cache[64], optin_cache[64];
+  int sms = device >= 0 && device < 64 ? sms_cache[device].load() : 0;
+  int optin = device >= 0 && device < 64 ? optin_cache[device].load() : 0;
+  if (sms <= 0 || optin <= 0) {
+    VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    VIE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    if (device >= 0 && device < 64) {
+      sms_cache[device].store(sms);
+      optin_cache[device].store(optin);
+    }
+  }
+  out->sharedMemPerBlockOptin = (size_t)optin;
+  out->multiProcessorCount = sms;
+  return VIE_OK;
+}
+
+WaitLimits wait_limits(int device) {
+  // the clock-rate query is slow (a driver round trip): once per device
+  static std::atomic<int> khz_cache[64];
+  int khz = device >= 0 && device < 64 ? khz_cache[device].load() : 0;
+  if (khz <= 0) {
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device) != cudaSuccess || khz <= 0) khz = 2000000;
+    if (device >= 0 && device < 64) khz_cache[device].store(khz);
+  }
+  const double ms = g_wait_ms.load(), fms = g_first_wait_ms.load();
+  WaitLimits w;
+  w.limit = (long long)(ms * khz);
+  w.first = fms < 0.0 ? w.limit : (long long)(fms * khz);
+  return w;
+}
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -101,6 +135,20 @@ struct ApplyEvents {
   bool pending = false;
 };
 
+// Workspace of R GMRES(m) solves in lockstep (vie_gmres_opts.nrhs > 1):
+// the KBatch arrays plus the bases V [R][m + 1][N], the flexible directions
+// Z [R][m][N], phi, r, w [R][N], the steps per solve kk [R], pinned host
+// copies of the scalars and of gv, and the network input [R][3][N].
+struct MultiGmres {
+  int R = 0, m = 0, has_z = 0, has_net = 0;
+  KBatch kb{};
+  double *V = nullptr, *Z = nullptr, *phi = nullptr, *r = nullptr, *w = nullptr;
+  int *kk = nullptr;
+  double *h_scal = nullptr, *h_gv = nullptr;
+  int *h_act = nullptr;
+  float *net_x = nullptr;
+};
+
 }  // namespace vie
 
 using namespace vie;
@@ -158,6 +206,8 @@ struct vie_handle {
   size_t ev_next = 0;
   double t_apply_ms = 0.0, t_kernel_ms = 0.0;
   int n_apply = 0;
+  MultiGmres mg;                              // lockstep solves of several right-hand sides
+  int *h_err = nullptr;                       // pinned copies of the device error words [2]
 };
 
 namespace {
@@ -179,6 +229,19 @@ void free_gmres(vie_handle *h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   h->h_pinned = nullptr;
   h->gm_m = 0;
+}
+
+void free_multi(MultiGmres &g) {
+  KBatch &b = g.kb;
+  for (double **p : {&g.V, &g.Z, &g.phi, &g.r, &g.w, &b.H, &b.cs, &b.sn, &b.gv, &b.yv, &b.hcol, &b.htmp, &b.part,
+                     &b.scal, &b.bnorm})
+    dfree(*p);
+  for (int **p : {&b.ticket, &b.act, &g.kk}) dfree(*p);
+  dfree(g.net_x);
+  if (g.h_scal) cudaFreeHost(g.h_scal);
+  if (g.h_gv) cudaFreeHost(g.h_gv);
+  if (g.h_act) cudaFreeHost(g.h_act);
+  g = MultiGmres{};
 }
 
 void free_all(vie_handle *h) {
@@ -216,6 +279,9 @@ void free_all(vie_handle *h) {
   fmm_release(&h->fmm);
   disp3_release(&h->disp3);
   free_gmres(h);
+  free_multi(h->mg);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  h->h_err = nullptr;
   for (auto &ev : h->events)
     for (auto &e : ev.e)
       if (e) cudaEventDestroy(e);
@@ -391,17 +457,360 @@ vie_status norm2_dev(vie_handle *h, const double *x, double *out, cudaStream_t s
   return launch_dots_finish(h->part, blocks, 1, out, 0, st);
 }
 
+// Device error words of the handle's tensor-core kernels (the product's and
+// the learned preconditioner's): queue their copies to pinned memory before a
+// synchronisation, then take_errors reports VIE_ERR_TIMEOUT if a bounded
+// device wait gave up (and clears the words for the next call).
+vie_status queue_errors(vie_handle *h, cudaStream_t st) {
+  if (!h->h_err) VIE_CUDA(cudaMallocHost((void **)&h->h_err, 2 * sizeof(int)));
+  h->h_err[0] = h->h_err[1] = 0;
+  if (h->dev_err) VIE_CUDA(cudaMemcpyAsync(h->h_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (h->precond)
+    VIE_CUDA(cudaMemcpyAsync(h->h_err + 1, unet_error_word(h->precond), sizeof(int), cudaMemcpyDeviceToHost, st));
+  return VIE_OK;
+}
+
+vie_status take_errors(vie_handle *h, cudaStream_t st) {
+  if (!h->h_err || (h->h_err[0] == 0 && h->h_err[1] == 0)) return VIE_OK;
+  if (h->h_err[0] && h->dev_err) VIE_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
+  if (h->h_err[1] && h->precond) VIE_CUDA(cudaMemsetAsync(unet_error_word(h->precond), 0, sizeof(int), st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  h->h_err[0] = h->h_err[1] = 0;
+  set_error("a tensor-core kernel gave up on a bounded device wait (its output is NaN)");
+  return VIE_ERR_TIMEOUT;
+}
+
 vie_status read_scalar(vie_handle *h, const double *dev, double *val, cudaStream_t st) {
   VIE_CUDA(cudaMemcpyAsync(h->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  vie_status s = queue_errors(h, st);
+  if (s != VIE_OK) return s;
   VIE_CUDA(cudaStreamSynchronize(st));
   *val = h->h_pinned[0];
-  return VIE_OK;
+  return take_errors(h, st);
 }
 
 bool all_finite(const double *a, long n) {
   for (long i = 0; i < n; ++i)
     if (!isfinite(a[i])) return false;
   return true;
+}
+
+vie_status ensure_multi(vie_handle *h, int R, int m, bool need_z, bool need_net) {
+  MultiGmres &g = h->mg;
+  if (g.R >= R && g.m >= m && (g.has_z || !need_z) && (g.has_net || !need_net)) return VIE_OK;
+  free_multi(g);
+  const long N = h->N;
+  const int blocks = dot_blocks(N);
+  KBatch &b = g.kb;
+  vie_status s;
+  if ((s = dalloc(&g.V, (size_t)R * (m + 1) * N)) != VIE_OK) return s;
+  if (need_z && (s = dalloc(&g.Z, (size_t)R * m * N)) != VIE_OK) return s;
+  if ((s = dalloc(&g.phi, (size_t)R * N)) != VIE_OK) return s;
+  if ((s = dalloc(&g.r, (size_t)R * N)) != VIE_OK) return s;
+  if ((s = dalloc(&g.w, (size_t)R * N)) != VIE_OK) return s;
+  if ((s = dalloc(&b.H, (size_t)R * (m + 1) * m)) != VIE_OK) return s;
+  if ((s = dalloc(&b.cs, (size_t)R * m)) != VIE_OK) return s;
+  if ((s = dalloc(&b.sn, (size_t)R * m)) != VIE_OK) return s;
+  if ((s = dalloc(&b.gv, (size_t)R * (m + 1))) != VIE_OK) return s;
+  if ((s = dalloc(&b.yv, (size_t)R * m)) != VIE_OK) return s;
+  if ((s = dalloc(&b.hcol, (size_t)R * (m + 1))) != VIE_OK) return s;
+  if ((s = dalloc(&b.htmp, (size_t)R * (m + 1))) != VIE_OK) return s;
+  if ((s = dalloc(&b.part, (size_t)R * blocks * (m + 1))) != VIE_OK) return s;
+  if ((s = dalloc(&b.scal, (size_t)R * 8)) != VIE_OK) return s;
+  if ((s = dalloc(&b.bnorm, (size_t)R)) != VIE_OK) return s;
+  if ((s = dalloc(&b.ticket, (size_t)R)) != VIE_OK) return s;
+  if ((s = dalloc(&b.act, (size_t)R)) != VIE_OK) return s;
+  if ((s = dalloc(&g.kk, (size_t)R)) != VIE_OK) return s;
+  if (need_net && (s = dalloc(&g.net_x, (size_t)R * 3 * N)) != VIE_OK) return s;
+  VIE_CUDA(cudaMemset(b.ticket, 0, sizeof(int) * R));
+  VIE_CUDA(cudaMallocHost((void **)&g.h_scal, sizeof(double) * 8 * R));
+  VIE_CUDA(cudaMallocHost((void **)&g.h_gv, sizeof(double) * (size_t)R * (m + 1)));
+  VIE_CUDA(cudaMallocHost((void **)&g.h_act, sizeof(int) * 2 * R));
+  g.R = R;
+  g.m = m;
+  g.has_z = need_z;
+  g.has_net = need_net;
+  b.N = N;
+  b.m = m;
+  b.R = R;
+  b.blocks = blocks;
+  return VIE_OK;
+}
+
+// Operator applies to R vectors, column r of g at g + r ldg and of y at
+// y + r ldy.  With the assembled BF16 hi/lo operator every product of K goes
+// through the tensor cores, all columns in one product (up to 128); otherwise
+// one apply per column with act[r] != 0 (act NULL: every column).
+vie_status apply_multi(vie_handle *h, int op, const double *g, long ldg, double *y, long ldy, int R,
+                       const int *act, cudaStream_t st, bool timed) {
+  vie_status s;
+  if (h->asm_mode == VIE_OPERATOR_BF16X3 && op != VIE_OP_A_RAW) {
+    ApplyEvents *ev = nullptr;
+    if (timed) {
+      if (h->events.empty()) {
+        h->events.resize(8);
+        for (auto &e : h->events)
+          for (auto &x : e.e) VIE_CUDA(cudaEventCreate(&x));
+      }
+      ev = &h->events[h->ev_next];
+      if (ev->pending && (s = harvest_events(h)) != VIE_OK) return s;
+      h->ev_next = (h->ev_next + 1) % h->events.size();
+      VIE_CUDA(cudaEventRecord(ev->e[0], st));
+      VIE_CUDA(cudaEventRecord(ev->e[1], st));
+    }
+    int sms = 0;
+    VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    for (int r0 = 0; r0 < R; r0 += kGemmMaxRhs) {
+      const int nr = std::min(kGemmMaxRhs, R - r0);
+      if ((s = h->gemm_ws.reserve(gemm_workspace_bytes(h->N, h->ldk, nr, nullptr, sms))) != VIE_OK) return s;
+      if ((s = launch_gemm_bf16x3(h->kmat, h->kmat_lo, h->ldk, h->N, g + (size_t)r0 * ldg, ldg, nr, op,
+                                  y + (size_t)r0 * ldy, ldy, h->gemm_ws.ptr, h->dev_err, st)) != VIE_OK)
+        return s;
+    }
+    if (timed) {
+      VIE_CUDA(cudaEventRecord(ev->e[2], st));
+      VIE_CUDA(cudaEventRecord(ev->e[3], st));
+      ev->pending = true;
+    }
+    h->n_apply++;
+    return VIE_OK;
+  }
+  for (int r = 0; r < R; ++r)
+    if (!act || act[r])
+      if ((s = apply_dev(h, op, g + (size_t)r * ldg, y + (size_t)r * ldy, st, timed)) != VIE_OK) return s;
+  return VIE_OK;
+}
+
+// act[] to the device (from pageable memory: the call returns once the host
+// values are staged, so the vector may change right after)
+vie_status upload_act(vie_handle *h, const std::vector<int> &act, cudaStream_t st) {
+  VIE_CUDA(cudaMemcpyAsync(h->mg.kb.act, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, st));
+  return VIE_OK;
+}
+
+// scal[8 r + slot] of every r, after the work queued so far
+vie_status read_multi_scal(vie_handle *h, int R, cudaStream_t st) {
+  MultiGmres &g = h->mg;
+  VIE_CUDA(cudaMemcpyAsync(g.h_scal, g.kb.scal, sizeof(double) * 8 * R, cudaMemcpyDeviceToHost, st));
+  vie_status s = queue_errors(h, st);
+  if (s != VIE_OK) return s;
+  VIE_CUDA(cudaStreamSynchronize(st));
+  return take_errors(h, st);
+}
+
+// R restarted GMRES(m) / FGMRES solves of (I - K) U_r = phi_r in lockstep
+// (Algorithm 1, S.2 for several sources on one medium): every Arnoldi step
+// applies the operator to the R current directions at once (one tensor-core
+// product with the assembled BF16 hi/lo operator), runs CGS2, the norms and
+// the Givens steps of all R in one launch each, and reads the R residual
+// estimates back in one copy.  A solve leaves the step loop when its estimate
+// reaches rtol (or it stalls under a preconditioner, or maxit), the others go
+// on; restart cycles, the true FP64 residual and convergence are per solve,
+// exactly as in the single solve.
+vie_status solve_multi(vie_handle *h, const double *fdev, double *x, int R, const vie_gmres_opts &opt,
+                       vie_report *rep, cudaStream_t st, bool timed,
+                       std::chrono::steady_clock::time_point t_start) {
+  const long N = h->N;
+  const int m = opt.restart;
+  const bool has_precond = h->precond || h->fft.on || h->diff.on;
+  vie_status s;
+  if ((s = ensure_multi(h, R, m, has_precond, h->precond != nullptr)) != VIE_OK) return s;
+  MultiGmres &g = h->mg;
+  KBatch b = g.kb;
+  b.R = R;
+  b.m = m;
+  const long ldv = (long)(m + 1) * N, ldz = (long)m * N;
+  std::vector<int> act(R, 1), conv(R, 0), iters(R, 0), restarts(R, 0), napply(R, 0), pit(R, 0), fell(R, 0);
+  std::vector<int> done(R, 0);  // maxit reached and the final true residual taken
+  std::vector<int> kk(R, 0);
+  std::vector<double> bnorm(R, 0.0), relres(R, 0.0), est(R, 0.0);
+  if ((s = upload_act(h, act, st)) != VIE_OK) return s;
+  // phi_r = A f_r (Eq. EQ:ERT Intgrl FMM), unless the caller passed phi
+  if (opt.rhs_is_phi) {
+    VIE_CUDA(cudaMemcpyAsync(g.phi, fdev, sizeof(double) * R * N, cudaMemcpyDeviceToDevice, st));
+  } else if (h->asm_mode == VIE_OPERATOR_BF16X3 && h->sig_s_positive) {
+    // phi_r = K (f_r / sigma_s) for every r in one tensor-core product
+    if ((s = launch_divide_cols(N, R, fdev, N, h->sig_s, g.w, N, st)) != VIE_OK) return s;
+    if ((s = apply_multi(h, VIE_OP_K_SIGMA_S, g.w, N, g.phi, N, R, nullptr, st, timed)) != VIE_OK) return s;
+    for (int r = 0; r < R; ++r) ++napply[r];
+  } else {
+    for (int r = 0; r < R; ++r)
+      if ((s = apply_dev(h, VIE_OP_A_RAW, fdev + (size_t)r * N, g.phi + (size_t)r * N, st, timed)) != VIE_OK)
+        return s;
+    for (int r = 0; r < R; ++r) ++napply[r];
+  }
+  if ((s = launch_bnorm2(b, g.phi, N, 0, st)) != VIE_OK) return s;
+  if ((s = read_multi_scal(h, R, st)) != VIE_OK) return s;
+  for (int r = 0; r < R; ++r) {
+    const double bn2 = g.h_scal[8 * r];
+    if (!isfinite(bn2)) {
+      set_error("vie_solve_gmres: non-finite right-hand side");
+      return VIE_ERR_NONFINITE;
+    }
+    bnorm[r] = sqrt(bn2);
+    if (bnorm[r] == 0.0) {
+      VIE_CUDA(cudaMemsetAsync(x + (size_t)r * N, 0, sizeof(double) * N, st));
+      conv[r] = 1;
+    }
+  }
+  VIE_CUDA(cudaMemcpyAsync(b.bnorm, bnorm.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  bool x_is_zero = opt.zero_x0 != 0;
+  for (;;) {
+    for (int r = 0; r < R; ++r) act[r] = !conv[r] && !done[r];
+    if (std::none_of(act.begin(), act.end(), [](int a) { return a != 0; })) break;
+    if ((s = upload_act(h, act, st)) != VIE_OK) return s;
+    // true residuals r = phi - (I - K) x
+    if (x_is_zero) {
+      VIE_CUDA(cudaMemcpyAsync(g.r, g.phi, sizeof(double) * R * N, cudaMemcpyDeviceToDevice, st));
+    } else {
+      if ((s = apply_multi(h, VIE_OP_I_MINUS_K, x, N, g.w, N, R, act.data(), st, timed)) != VIE_OK) return s;
+      for (int r = 0; r < R; ++r) napply[r] += act[r];
+      if ((s = launch_baxpby(b, 1.0, g.phi, N, -1.0, g.w, N, g.r, N, st)) != VIE_OK) return s;
+    }
+    x_is_zero = false;
+    if ((s = launch_bnorm2(b, g.r, N, 1, st)) != VIE_OK) return s;
+    if ((s = read_multi_scal(h, R, st)) != VIE_OK) return s;
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      const double rn2 = g.h_scal[8 * r + 1];
+      if (!isfinite(rn2)) {
+        set_error("vie_solve_gmres: non-finite residual");
+        return VIE_ERR_NONFINITE;
+      }
+      relres[r] = sqrt(rn2) / bnorm[r];
+      if (relres[r] <= opt.rtol) conv[r] = 1;
+      if (!conv[r] && iters[r] >= opt.maxit) done[r] = 1;
+      if (conv[r] || done[r]) act[r] = 0;
+    }
+    if (std::none_of(act.begin(), act.end(), [](int a) { return a != 0; })) break;
+    if ((s = upload_act(h, act, st)) != VIE_OK) return s;
+    // V_r0 = r_r / beta_r, gv_r = beta_r e_1
+    if ((s = launch_bscale(b, g.r, N, 1, 1, g.V, ldv, st)) != VIE_OK) return s;
+    for (int r = 0; r < R; ++r) {
+      double *gv = g.h_gv + (size_t)r * (m + 1);
+      for (int i = 0; i <= m; ++i) gv[i] = 0.0;
+      gv[0] = act[r] ? sqrt(g.h_scal[8 * r + 1]) : 0.0;
+    }
+    VIE_CUDA(cudaMemcpyAsync(b.gv, g.h_gv, sizeof(double) * R * (m + 1), cudaMemcpyHostToDevice, st));
+    const std::vector<int> cycle = act;  // the solves that take part in this cycle
+    std::fill(kk.begin(), kk.end(), 0);
+    std::vector<double> est_prev(R, 1e300), est_prev2(R, 1e300);
+    std::vector<int> stall(R, 0);
+    const bool flexible = has_precond;
+    for (int k = 0; k < m; ++k) {
+      if (std::none_of(act.begin(), act.end(), [](int a) { return a != 0; })) break;
+      const double *op_in = g.V + (size_t)k * N;
+      long ld_in = ldv;
+      if (flexible) {
+        // z_r,k = M(v_r,k) (right preconditioning, flexible GMRES); a solve
+        // whose preconditioned iteration stalled goes on with M = I
+        double *zk = g.Z + (size_t)k * N;
+        if (h->precond) {
+          if ((s = launch_bnorm2(b, g.V + (size_t)k * N, ldv, 4, st)) != VIE_OK) return s;
+          if ((s = unet_precondition_batch(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, g.V + (size_t)k * N,
+                                           ldv, b.scal, 4, R, h->n, g.net_x, zk, ldz, st)) != VIE_OK)
+            return s;
+        } else {
+          for (int r = 0; r < R; ++r) {
+            if (!act[r] || fell[r]) continue;
+            const double *vr = g.V + (size_t)r * ldv + (size_t)k * N;
+            double *zr = zk + (size_t)r * ldz;
+            if (h->fft.on)
+              s = fft_precondition(h->fft, vr, zr, st);
+            else
+              s = diffusion_precondition(h->diff, vr, zr, st);
+            if (s != VIE_OK) return s;
+          }
+        }
+        for (int r = 0; r < R; ++r) {
+          if (act[r] && fell[r])
+            VIE_CUDA(cudaMemcpyAsync(zk + (size_t)r * ldz, g.V + (size_t)r * ldv + (size_t)k * N,
+                                     sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+          if (act[r] && !fell[r]) ++pit[r];
+        }
+        op_in = zk;
+        ld_in = ldz;
+      }
+      double *vk1 = g.V + (size_t)(k + 1) * N;
+      if ((s = apply_multi(h, VIE_OP_I_MINUS_K, op_in, ld_in, vk1, ldv, R, act.data(), st, timed)) != VIE_OK)
+        return s;
+      for (int r = 0; r < R; ++r) napply[r] += act[r];
+      // CGS2 (two passes of h = V^T w, w -= V h), the norm and the Givens step
+      if ((s = launch_bdots(b, g.V, ldv, k + 1, vk1, ldv, b.hcol, nullptr, st)) != VIE_OK) return s;
+      if ((s = launch_borth_update(b, g.V, ldv, k + 1, b.hcol, vk1, ldv, st)) != VIE_OK) return s;
+      if ((s = launch_bdots(b, g.V, ldv, k + 1, vk1, ldv, b.htmp, b.hcol, st)) != VIE_OK) return s;
+      if ((s = launch_borth_update(b, g.V, ldv, k + 1, b.htmp, vk1, ldv, st)) != VIE_OK) return s;
+      if ((s = launch_bnorm2_givens(b, vk1, ldv, k, st)) != VIE_OK) return s;
+      if ((s = launch_bscale(b, vk1, ldv, 2, 1, vk1, ldv, st)) != VIE_OK) return s;
+      if ((s = read_multi_scal(h, R, st)) != VIE_OK) return s;
+      if (timed && (s = harvest_events(h)) != VIE_OK) return s;
+      bool changed = false;
+      for (int r = 0; r < R; ++r) {
+        if (!act[r]) continue;
+        const double e = g.h_scal[8 * r + 3];
+        ++iters[r];
+        kk[r] = k + 1;
+        est[r] = e;
+        if (!isfinite(e)) {
+          if (!flexible || fell[r]) {
+            set_error("vie_solve_gmres: non-finite Arnoldi step");
+            return VIE_ERR_NONFINITE;
+          }
+          --kk[r];  // the preconditioner produced a non-finite direction: drop this step
+          stall[r] = 1;
+        } else if (flexible && !fell[r] && k >= 1 && e > 0.8 * est_prev[r] && est_prev[r] > 0.8 * est_prev2[r]) {
+          stall[r] = 1;
+        }
+        if (stall[r] || e <= opt.rtol || iters[r] >= opt.maxit) {
+          act[r] = 0;
+          changed = true;
+        }
+        est_prev2[r] = est_prev[r];
+        est_prev[r] = e;
+      }
+      if (changed && (s = upload_act(h, act, st)) != VIE_OK) return s;
+    }
+    // x_r += V_r y_r (or Z_r y_r) for every solve of the cycle with steps
+    std::vector<int> upd(R, 0);
+    for (int r = 0; r < R; ++r) upd[r] = cycle[r] && kk[r] > 0;
+    if ((s = upload_act(h, upd, st)) != VIE_OK) return s;
+    VIE_CUDA(cudaMemcpyAsync(g.kk, kk.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+    if ((s = launch_bupdate(b, flexible ? g.Z : g.V, flexible ? ldz : ldv, g.kk, x, N, st)) != VIE_OK) return s;
+    // the cycle's host vectors must outlive the copies above
+    VIE_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) {
+      if (!cycle[r]) continue;
+      ++restarts[r];
+      if (stall[r]) fell[r] = 1;
+    }
+  }
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (timed && (s = harvest_events(h)) != VIE_OK) return s;
+  const double t_total =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  bool all_conv = true;
+  for (int r = 0; r < R; ++r) {
+    all_conv = all_conv && conv[r];
+    if (!rep) continue;
+    vie_report &Q = rep[r];
+    Q = vie_report{};
+    Q.iters = iters[r];
+    Q.restarts = restarts[r];
+    Q.converged = conv[r];
+    Q.n_apply = napply[r];
+    Q.relres = relres[r];
+    Q.relres_est = est[r];
+    Q.t_total_ms = t_total;
+    Q.t_apply_ms = h->t_apply_ms;
+    Q.t_apply_kernel_ms = h->t_kernel_ms;
+    Q.precond_iters = pit[r];
+    Q.fell_back = fell[r];
+  }
+  if (!all_conv) {
+    set_error("vie_solve_gmres: maxit reached before rtol for some right-hand sides");
+    return VIE_ERR_NOT_CONVERGED;
+  }
+  return VIE_OK;
 }
 
 }  // namespace
@@ -432,6 +841,7 @@ void vie_default_gmres_opts(vie_gmres_opts *o) {
   o->zero_x0 = 1;
   o->rhs_is_phi = 0;
   o->time_apply = 0;
+  o->nrhs = 1;
 }
 
 vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t,
@@ -632,12 +1042,12 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
   if (h->asm_mode == VIE_OPERATOR_BF16X3 && op != VIE_OP_A_RAW && nrhs >= 2) {
     int sms = 0;
     VIE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    for (int r0 = 0; r0 < nrhs; r0 += 256) {
-      const int nr = std::min(256, nrhs - r0);
+    for (int r0 = 0; r0 < nrhs; r0 += kGemmMaxRhs) {
+      const int nr = std::min(kGemmMaxRhs, nrhs - r0);
       if ((s = h->gemm_ws.reserve(gemm_workspace_bytes(N, h->ldk, nr, nullptr, sms))) != VIE_OK)
         return s;
-      if ((s = launch_gemm_bf16x3(h->kmat, h->kmat_lo, h->ldk, N, gg + (size_t)r0 * N, nr, op,
-                                  yy + (size_t)r0 * N, h->gemm_ws.ptr, h->dev_err, st)) != VIE_OK)
+      if ((s = launch_gemm_bf16x3(h->kmat, h->kmat_lo, h->ldk, N, gg + (size_t)r0 * N, N, nr, op,
+                                  yy + (size_t)r0 * N, N, h->gemm_ws.ptr, h->dev_err, st)) != VIE_OK)
         return s;
       h->n_apply += nr;
     }
@@ -648,8 +1058,29 @@ vie_status vie_apply(vie_handle *h, vie_op op, const double *g, double *y, int n
   }
   if (!yd) {
     VIE_CUDA(cudaMemcpyAsync(y, yy, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+    if ((s = queue_errors(h, st)) != VIE_OK) return s;
     VIE_CUDA(cudaStreamSynchronize(st));
+    return take_errors(h, st);
   }
+  return VIE_OK;
+}
+
+vie_status vie_check_device(vie_handle *h, void *stream) {
+  if (!h) return invalid("vie_check_device: NULL handle");
+  DeviceGuard dg(h->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  vie_status s = queue_errors(h, st);
+  if (s != VIE_OK) return s;
+  VIE_CUDA(cudaStreamSynchronize(st));
+  return take_errors(h, st);
+}
+
+vie_status vie_set_wait_limits(double limit_ms, double first_wait_ms) {
+  if (!(limit_ms > 0.0) || limit_ms > 60000.0 || !(first_wait_ms <= limit_ms))
+    return invalid("vie_set_wait_limits: 0 < limit_ms <= 60000 and first_wait_ms <= limit_ms required");
+  g_wait_ms = limit_ms;
+  g_first_wait_ms = first_wait_ms < 0.0 ? -1.0 : first_wait_ms;
   return VIE_OK;
 }
 
@@ -920,6 +1351,7 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
   if (o) opt = *o;
   if (!(opt.rtol > 0.0) || opt.restart < 1 || opt.restart > 256 || opt.maxit < 1)
     return invalid("vie_solve_gmres: rtol > 0, 1 <= restart <= 256, maxit >= 1 required");
+  if (opt.nrhs < 1 || opt.nrhs > 4096) return invalid("vie_solve_gmres: 1 <= nrhs <= 4096 required");
   DeviceGuard dg(h->device);
   if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
   auto t_start = std::chrono::steady_clock::now();
@@ -927,6 +1359,34 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
   const long N = h->N;
   const int m = opt.restart;
   vie_status s;
+  if (opt.nrhs > 1) {
+    // several sources on this medium: lockstep solves
+    const int R = opt.nrhs;
+    const size_t total = (size_t)R * N;
+    h->t_apply_ms = h->t_kernel_ms = 0.0;
+    h->n_apply = 0;
+    const bool fd = is_device_ptr(f), ud = is_device_ptr(U);
+    const double *fdev = f;
+    double *x = U;
+    if (!fd) {
+      if ((s = h->stage_a.reserve(total)) != VIE_OK) return s;
+      VIE_CUDA(cudaMemcpyAsync(h->stage_a.ptr, f, sizeof(double) * total, cudaMemcpyHostToDevice, st));
+      fdev = h->stage_a.ptr;
+    }
+    if (!ud) {
+      if ((s = h->stage_b.reserve(total)) != VIE_OK) return s;
+      x = h->stage_b.ptr;
+      if (!opt.zero_x0) VIE_CUDA(cudaMemcpyAsync(x, U, sizeof(double) * total, cudaMemcpyHostToDevice, st));
+    }
+    if (opt.zero_x0) VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * total, st));
+    s = solve_multi(h, fdev, x, R, opt, rep, st, opt.time_apply != 0, t_start);
+    if (s != VIE_OK && s != VIE_ERR_NOT_CONVERGED) return s;
+    if (!ud) {
+      VIE_CUDA(cudaMemcpyAsync(U, x, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+      VIE_CUDA(cudaStreamSynchronize(st));
+    }
+    return s;
+  }
   if ((s = ensure_gmres(h, m)) != VIE_OK) return s;
   const bool has_precond = h->precond || h->fft.on || h->diff.on;
   if (has_precond && h->z_m < m) {

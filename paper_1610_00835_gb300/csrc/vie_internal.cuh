@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +16,25 @@ constexpr int kPairThreads = 256;  // targets per pair-kernel CTA
 
 // Thread-local message behind vie_last_error().
 void set_error(const std::string &msg);
+
+// Bounds of the device-side waits of the tensor-core kernels, in clock
+// cycles: `limit` for every wait, except the first producer/consumer wait of
+// each CTA, which takes `first` (a shorter value lets a test make that wait
+// run out); draining already issued copies and products after an abort
+// always takes `limit`.  wait_limits(device) converts the process-wide
+// setting of vie_set_wait_limits with the device's clock rate.
+struct WaitLimits {
+  long long limit, first;
+};
+WaitLimits wait_limits(int device);
+
+// The two device properties the launch planners read, queried once per device
+// (cudaGetDeviceProperties is a slow driver round trip, too slow per apply).
+struct DevProps {
+  size_t sharedMemPerBlockOptin;
+  int multiProcessorCount;
+};
+vie_status get_dev_props(int device, DevProps *out);
 
 // Map a CUDA error to VIE_ERR_CUDA with a message naming the call site.
 vie_status cuda_fail(cudaError_t e, const char *what);
@@ -99,9 +119,12 @@ size_t sym_smem_bytes(int dim, int n, int *ldp, int *plane);
 vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_padded, int device,
                        cudaStream_t st);
 void sym_release(SymPlan *sp);
+// the symmetric plan on caller-owned buffers (lattice_mem: max_lattice floats,
+// items for max_T target tiles); unusable (sp->usable = 0, nothing launched)
+// when the grid needs more
 vie_status sym_plan_external(SymPlan *sp, int dim, int n, long N, const float *sig_padded,
                              int device, int2 *items_mem, int *counter_mem, float *lattice_mem,
-                             cudaStream_t st);
+                             long max_lattice, int max_T, cudaStream_t st);
 vie_status sym_launch(const SymPlan &sp, int dim, int n, long N, float tau_scale2, float wcoef,
                       const float *src, double *partial, cudaStream_t st);
 
@@ -241,6 +264,32 @@ void fmm_release(FmmPlan *fp);
 // y = A s (op A_RAW, K_SIGMA_S: s already multiplied by sigma_s) or g - A s (I_MINUS_K)
 vie_status fmm_apply(const FmmPlan &fp, int op, const float *s, const double *g, double *y, cudaStream_t st);
 
+// ---- R GMRES solves in lockstep (k_krylov.cu).  Per right-hand side r:
+// basis vector i at V + r ldv_r + i N, Hessenberg H + r (m + 1) m
+// (column-major), rotations cs/sn + r m, residual vector gv + r (m + 1), the
+// triangular solution yv + r m, the dot columns hcol/htmp + r (m + 1), dot
+// partials part + r blocks (m + 1), block ticket ticket[r] (0 between
+// launches), scalars scal + 8 r (slot 2: ||w||^2, 3: the Givens residual
+// estimate), bnorm[r] = ||phi_r||, act[r] != 0 while r takes part.
+struct KBatch {
+  double *H, *cs, *sn, *gv, *yv, *hcol, *htmp, *part, *scal, *bnorm;
+  int *ticket, *act;
+  long N;
+  int m, R, blocks;
+};
+vie_status launch_bdots(const KBatch &b, const double *V, long ldv_r, int nv, const double *w, long ldw_r,
+                        double *out1, double *out2, cudaStream_t st);
+vie_status launch_bnorm2_givens(const KBatch &b, const double *w, long ldw_r, int k, cudaStream_t st);
+vie_status launch_bnorm2(const KBatch &b, const double *w, long ldw_r, int slot, cudaStream_t st);
+vie_status launch_borth_update(const KBatch &b, const double *V, long ldv_r, int nv, const double *h, double *w,
+                               long ldw_r, cudaStream_t st);
+vie_status launch_bscale(const KBatch &b, const double *x, long ldx_r, int slot, int use_sqrt, double *y,
+                         long ldy_r, cudaStream_t st);
+vie_status launch_baxpby(const KBatch &b, double a, const double *x, long ldx_r, double c, const double *y,
+                         long ldy_r, double *z, long ldz_r, cudaStream_t st);
+vie_status launch_bupdate(const KBatch &b, const double *B, long ldb_r, const int *kk, double *x, long ldx_r,
+                          cudaStream_t st);
+
 // ---- assembled operator (k_assemble.cu, k_gemm_tc.cu)
 long assembled_ldk(long N);
 vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const double *sigma_s,
@@ -249,15 +298,32 @@ vie_status launch_assemble(const SymPlan &sp, int dim, int n, long N, const doub
 vie_status launch_gemv(const void *k, const void *klo, int bf16, long ldk, long N, const double *g,
                        float *g32, int op, double *y, cudaStream_t st);
 vie_status launch_divide(long N, const double *a, const double *b, double *out, cudaStream_t st);
+vie_status launch_divide_cols(long N, int R, const double *a, long lda, const double *b, double *out, long ldo,
+                              cudaStream_t st);
 size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms);
-vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g,
-                              int nrhs, int op, double *y, void *workspace, int *err,
+// A BF16 TMA descriptor: rank dims innermost first, byte strides of dims
+// 1..rank-1, box, 64- or 128-byte swizzle, zero fill outside the tensor.
+vie_status encode_bf16_map(CUtensorMap *m, int rank, const void *base, const unsigned long long *dims,
+                           const unsigned long long *strides, const unsigned *box, int swizzle_bytes);
+// Y = K G (op K_SIGMA_S) or G - K G (I_MINUS_K) for nrhs <= kGemmMaxRhs
+// columns, column r of G at g + r ldg and of Y at y + r ldy (FP64), on the
+// tensor cores.
+constexpr int kGemmMaxRhs = 128;
+vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N, const double *g, long ldg,
+                              int nrhs, int op, double *y, long ldy, void *workspace, int *err,
                               cudaStream_t st);
 
 // ---- learned preconditioner (k_unet.cu)
 struct UnetImpl;
 UnetImpl *unet_impl(vie_unet *u);
 int unet_levels(vie_unet *u);
+// the network's device error word (set by a tensor-core convolution whose
+// bounded wait gave up), and its synchronous check-and-clear
+int *unet_error_word(UnetImpl *u);
+vie_status unet_take_error(UnetImpl *u, cudaStream_t st);
+vie_status unet_precondition_batch(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
+                                   const double *v, long ldv, const double *scal, int slot, int R, int n,
+                                   float *xbuf, double *z, long ldz, cudaStream_t st);
 vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
                              const double *v, const double *vnorm2, int n, float *xbuf, double *z,
                              cudaStream_t st);

@@ -12,7 +12,9 @@
 // The array is part of the library image: every GPU on which the library is
 // loaded holds it until the process exits.  Its device address is looked up
 // once per device (cudaGetSymbolAddress) on the first call made with that
-// device current, so that first call should come before any stream capture.
+// device current, and that first call also copies the self-cell quadrature
+// rule to the device's constant memory (a synchronous copy), so the first
+// call on each device should come before any stream capture.
 // All calls on a device share its copy of the array, which keeps the last
 // call's contents; the work counter is cleared on every call and nothing else
 // needs to start at zero (every partial-sum slot is written before it is
@@ -127,9 +129,10 @@ extern "C" vie_status vie_apply_noalloc(int dim, int n, const double *sigma_t, c
   vie_status s;
   if ((s = launch_pad_sigma(dim, n, sigma_t, pad32, pad64, st)) != VIE_OK) return s;
   SymPlan sp;
-  if ((s = sym_plan_external(&sp, dim, n, N, pad32, dev, items, counter, lattice, st)) != VIE_OK)
+  if ((s = sym_plan_external(&sp, dim, n, N, pad32, dev, items, counter, lattice, kMaxLattice, (int)kMaxT, st)) !=
+      VIE_OK)
     return s;
-  if (!sp.usable || sp.lattice_elems > kMaxLattice || sp.T > kMaxT) {
+  if (!sp.usable) {
     set_error("vie_apply_noalloc: grid not supported by the shared-memory kernel");
     return VIE_ERR_UNSUPPORTED;
   }

@@ -116,6 +116,12 @@ def main(argv=None):
     ap.add_argument("--family", choices=sorted(FAMILIES), default="diffusive")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--checkpoint", default=None,
+                    help="after every epoch, save the network with its optimizer state here (and the "
+                         "epoch and the shuffling generator's state beside it, PATH.json)")
+    ap.add_argument("--resume", action="store_true",
+                    help="continue from --checkpoint: the data are drawn again from their seeds, the "
+                         "network, Adam state, epoch and shuffling resume where the checkpoint stopped")
     args = ap.parse_args(argv)
     import torch
     import paper_1610_00835_gb300 as P
@@ -149,8 +155,20 @@ def main(argv=None):
     steps_per_epoch = ntrain // args.batch
     total = steps_per_epoch * args.epochs
     step = 0
+    first_epoch = 0
+    if args.resume:
+        if not args.checkpoint:
+            raise SystemExit("--resume needs --checkpoint")
+        P.vie_unet_load(net, args.checkpoint)
+        with open(args.checkpoint + ".json") as fh:
+            side = json.load(fh)
+        first_epoch = side["epoch"] + 1
+        step = side["step"]
+        rng.bit_generator.state = side["rng"]
+        if P.vie_unet_train_state(net) != step:
+            raise SystemExit("checkpoint and its side file disagree on the step count")
     t1 = time.perf_counter()
-    for ep in range(args.epochs):
+    for ep in range(first_epoch, args.epochs):
         perm = torch.as_tensor(rng.permutation(ntrain), device=dev)
         losses = []
         for s in range(steps_per_epoch):
@@ -167,6 +185,11 @@ def main(argv=None):
         tvar = float(torch.mean(T[ntrain:] ** 2))  # unweighted validation error
         print(json.dumps({"phase": "train", "epoch": ep, "loss": float(np.mean(losses)),
                           "val_loss": vloss, "val_rel": math.sqrt(vloss / tvar)}), flush=True)
+        if args.checkpoint:
+            os.makedirs(os.path.dirname(os.path.abspath(args.checkpoint)), exist_ok=True)
+            P.vie_unet_save(net, args.checkpoint)
+            with open(args.checkpoint + ".json", "w") as fh:
+                json.dump({"epoch": ep, "step": step, "rng": rng.bit_generator.state}, fh)
     train_s = time.perf_counter() - t1
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)

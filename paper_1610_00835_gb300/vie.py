@@ -47,7 +47,8 @@ class vie_opts(C.Structure):
 
 class vie_gmres_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("zero_x0", C.c_int), ("rhs_is_phi", C.c_int), ("time_apply", C.c_int)]
+                ("zero_x0", C.c_int), ("rhs_is_phi", C.c_int), ("time_apply", C.c_int),
+                ("nrhs", C.c_int)]
 
 
 class vie_report(C.Structure):
@@ -98,6 +99,9 @@ SIGNATURES = {
                                       C.POINTER(C.c_double), _vp]),
     "vie_unet_save": (C.c_int, [_vp, C.c_char_p]),
     "vie_unet_load": (C.c_int, [_vp, C.c_char_p]),
+    "vie_unet_train_state": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
+    "vie_set_wait_limits": (C.c_int, [C.c_double, C.c_double]),
+    "vie_check_device": (C.c_int, [_vp, _vp]),
     "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
     "vie_set_fft_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
     "vie_fft_precondition": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -221,16 +225,19 @@ def vie_assemble_fmm(h: VieHandle, order: int = 6, stream=None) -> None:
 
 def vie_solve_gmres(h: VieHandle, f, U, rtol: float = 1e-6, restart: int = 64, maxit: int = 1000,
                     zero_x0: bool = True, rhs_is_phi: bool = False, time_apply: bool = False,
-                    stream=None, raise_on_nonconvergence: bool = True) -> dict:
+                    stream=None, raise_on_nonconvergence: bool = True, nrhs: int = 1):
+    """One solve (returns its report as a dict), or nrhs > 1 solves in
+    lockstep with f and U of nrhs * N values (returns a list of reports)."""
     fp, _f = _ptr(f, np.float64)
     up, _u = _ptr(U, np.float64)
-    o = vie_gmres_opts(rtol, restart, maxit, int(zero_x0), int(rhs_is_phi), int(time_apply))
-    rep = vie_report()
-    s = load().vie_solve_gmres(h.ptr, fp, up, C.byref(o), C.byref(rep), _stream(stream))
+    o = vie_gmres_opts(rtol, restart, maxit, int(zero_x0), int(rhs_is_phi), int(time_apply), int(nrhs))
+    reps = (vie_report * max(1, int(nrhs)))()
+    s = load().vie_solve_gmres(h.ptr, fp, up, C.byref(o), reps, _stream(stream))
+    out = [r.as_dict() for r in reps] if nrhs > 1 else reps[0].as_dict()
     if s == VIE_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
-        return rep.as_dict()
+        return out
     _check(s)
-    return rep.as_dict()
+    return out
 
 
 def vie_apply_noalloc(dim: int, n: int, sigma_t, sigma_s, op: int, g, y, stream=None) -> None:
@@ -379,6 +386,23 @@ def vie_unet_save(u: VieUnet, path: str) -> None:
 
 def vie_unet_load(u: VieUnet, path: str) -> None:
     _check(load().vie_unet_load(u.ptr, path.encode()))
+
+
+def vie_set_wait_limits(limit_ms: float = 1000.0, first_wait_ms: float = -1.0) -> None:
+    """Bounds of the tensor-core kernels' device waits (process-wide)."""
+    _check(load().vie_set_wait_limits(float(limit_ms), float(first_wait_ms)))
+
+
+def vie_check_device(h: VieHandle, stream=None) -> None:
+    """Synchronise and raise VieError(VIE_ERR_TIMEOUT) if a bounded wait gave up."""
+    _check(load().vie_check_device(h.ptr, _stream(stream)))
+
+
+def vie_unet_train_state(u: VieUnet) -> int:
+    """Adam steps taken so far (a checkpoint restores it)."""
+    st = C.c_longlong(0)
+    _check(load().vie_unet_train_state(u.ptr, C.byref(st)))
+    return st.value
 
 
 def vie_set_preconditioner(h: VieHandle, u, s_ref: float = 5.0) -> None:

@@ -112,10 +112,11 @@ def test_2d_every_pair_kernel_all_rows(kernel, n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [100, 128, 133, 226, 227, 230, 256, 258])
+@pytest.mark.parametrize("n", [100, 128, 133, 226, 233, 234, 256, 258])
 def test_displacement_kernel_full_size_sampled_rows(n):
-    # 226 is the largest grid whose lattice fits one SM's shared memory;
-    # 227 ... 258 read it from global memory (two layouts, runs along y and x)
+    # 233 is the largest grid whose lattice ((n + 8) rows of an odd pitch) fits
+    # one SM's shared memory; 234 ... 258 read it from global memory (two
+    # layouts, runs along y and x)
     m = V.bump_medium(2, n, 4, 0.9, seed=4300 + n)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_DISPLACEMENT)
     assert P.vie_get_kernel(h) == P.VIE_KERNEL_DISPLACEMENT
@@ -129,7 +130,7 @@ def test_displacement_kernel_full_size_sampled_rows(n):
 
 
 def test_displacement_kernel_falls_back_beyond_its_lattice():
-    # n = 259 is past the global lattice (273 x 273 with the stacked-target
+    # n = 259 is past the global lattice (267 x 267 with the stacked-target
     # padding): the handle takes the tile-pair kernel and still matches the oracle
     n = 259
     m = V.bump_medium(2, n, 4, 0.9, seed=4436)

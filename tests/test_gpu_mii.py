@@ -42,7 +42,7 @@ def test_mii_apply_all_rows(n):
         assert rel_l2(gpu_apply(h, op, g), want) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [128, 226, 256])
+@pytest.mark.parametrize("n", [128, 233, 256])
 def test_mii_apply_full_size_sampled_rows(n):
     m = V.bump_medium(2, n, 4, 0.9, seed=4800 + n)
     h = mii_handle(m, n)
@@ -72,7 +72,9 @@ def test_mii_gmres_matches_oracle_lu():
     m = V.bump_medium(2, n, 4, 0.9, seed=4902)
     h = mii_handle(m, n)
     U = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
-    rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-9)
+    # 1e-8, as for M-iii: the FP32 rounding of the sources puts the residual
+    # an FP32-tile operator can reach near 1e-9
+    rep = P.vie_solve_gmres(h, dev(m.f), U, rtol=1e-8)
     assert rep["converged"]
     phi = O.apply(2, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW, mode=MII)
     U_lu = O.lu_solve(2, m.sigma_t, m.sigma_s, phi, mode=MII)

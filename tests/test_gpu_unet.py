@@ -166,3 +166,36 @@ def test_fgmres_converges_with_any_network(scale):
     U2 = np.zeros(m.N)
     rep2 = P.vie_solve_gmres(h, m.f, U2, rtol=1e-8)
     assert rep2["precond_iters"] == 0
+
+
+def test_checkpoint_resumes_adam_where_it_stopped(tmp_path):
+    # three Adam steps, save, three more; a second network loaded from the
+    # checkpoint takes the same three steps: both end with the same
+    # parameters.  A restart from zero moments would take the fourth step with
+    # a different effective rate (|update| ~ lr for every parameter).
+    n, B = 16, 2
+    rng = np.random.default_rng(17)
+    x = dev(rng.standard_normal((B, 3, n, n)).ravel(), torch.float32)
+    t = dev(rng.standard_normal((B, n, n)).ravel(), torch.float32)
+    a = P.vie_unet_create(3, 8, seed=5)
+    for _ in range(3):
+        P.vie_unet_train_step(a, x, t, B, n, 1e-3)
+    path = str(tmp_path / "ckpt.bin")
+    P.vie_unet_save(a, path)
+    assert P.vie_unet_train_state(a) == 3
+    b = P.vie_unet_create(3, 8, seed=99)
+    P.vie_unet_load(b, path)
+    assert P.vie_unet_train_state(b) == 3
+    np.testing.assert_array_equal(P.vie_unet_get_params(a), P.vie_unet_get_params(b))
+    for _ in range(3):
+        P.vie_unet_train_step(a, x, t, B, n, 1e-3)
+        P.vie_unet_train_step(b, x, t, B, n, 1e-3)
+    pa, pb = P.vie_unet_get_params(a), P.vie_unet_get_params(b)
+    moved = np.abs(pa - P.vie_unet_get_params(P.vie_unet_create(3, 8, seed=5))).max()
+    assert np.abs(pa - pb).max() <= 1e-4 * moved
+    # a parameter-only start (moments and step reset) ends elsewhere
+    c = P.vie_unet_create(3, 8, seed=99)
+    P.vie_unet_set_params(c, P.vie_unet_get_params(b) * 0 + np.fromfile(path, dtype=np.float32)[6:6 + pa.size])
+    for _ in range(3):
+        P.vie_unet_train_step(c, x, t, B, n, 1e-3)
+    assert np.abs(P.vie_unet_get_params(c) - pa).max() > 10 * np.abs(pa - pb).max()

@@ -7,6 +7,7 @@ beyond its fixed scratch.  This file is collected last on purpose.
 import numpy as np
 import pytest
 
+import oracle as O
 import vie_synth as V
 
 torch = pytest.importorskip("torch")
@@ -38,7 +39,35 @@ def test_noalloc_matches_vie_apply_twice(dim, n, op):
         P.vie_apply_noalloc(dim, n, st, ss, op, g, y)
         torch.cuda.synchronize()
         assert _rel(y, y_ref) < TOL, f"call {call}"
+        # and what the FP64 oracle computes, on sampled rows
+        rows = np.unique(np.random.default_rng(call).choice(m.N, 16, replace=False))
+        want = O.apply(dim, m.sigma_t, m.sigma_s, g.cpu().numpy(), op=op, rows=rows)
+        got = y.cpu().numpy()[rows]
+        assert np.linalg.norm(got - want) < TOL * np.linalg.norm(want), f"call {call}"
         P.vie_destroy(h)
+
+
+def test_noalloc_on_a_side_stream_allocates_nothing():
+    # a caller that cannot allocate runs it on its own stream: the result is
+    # the same, and the device's free memory does not move across the call
+    dev = "cuda:0"
+    n = 100
+    m = V.bump_medium(2, n, 4, 0.9, seed=6100)
+    st = torch.as_tensor(m.sigma_t, device=dev)
+    ss = torch.as_tensor(m.sigma_s, device=dev)
+    g = torch.as_tensor(m.f, device=dev)
+    y0 = torch.empty_like(g)
+    y1 = torch.full_like(g, float("nan"))
+    P.vie_apply_noalloc(2, n, st, ss, P.VIE_OP_K_SIGMA_S, g, y0)   # first call on the device
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    free0 = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(side):
+        P.vie_apply_noalloc(2, n, st, ss, P.VIE_OP_K_SIGMA_S, g, y1, stream=side)
+    side.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    torch.testing.assert_close(y1, y0, rtol=0, atol=0)
 
 
 def test_noalloc_rejects_oversize_and_host_pointers():
