@@ -71,16 +71,11 @@ using march::kS;
 using dmarch::kMaxChunk;
 using dmarch::march_runs;
 using dmarch::march_runs_global;
-#ifndef VIE_DISP_STACK
-#define VIE_DISP_STACK 8
-#endif
-constexpr int kR = VIE_DISP_STACK;  // targets stacked along the run axis in one thread
+// targets stacked along the run axis in one thread (16 measured slower at
+// 128^2: 1.47 against 1.41 ms, fewer warps and more ragged blocks)
+constexpr int kR = 8;
 using dmarch::red_add;
-// 16 stacked targets take about 80 registers a thread: 768 threads a CTA
-#ifndef VIE_DISP_THREADS
-#define VIE_DISP_THREADS (kR >= 16 ? 768 : 1024)
-#endif
-constexpr int kThreads = VIE_DISP_THREADS;
+constexpr int kThreads = 1024;
 // extra lattice rows and columns: the stacked targets of a block that reach
 // past the rectangle of targets (chunks carry no padding)
 constexpr int kPad = kR - 1;
