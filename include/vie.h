@@ -374,6 +374,14 @@ vie_status vie_unet_set_params(vie_unet *u, const float *host_params);
  * CUDA cores with FP32 activations; the call synchronises the stream and
  * returns VIE_ERR_TIMEOUT if a convolution gave up on a bounded wait. */
 vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n, int use_bf16, void *stream);
+/* Diagnostics (no paper counterpart): copy the input and the output of
+ * convolution `layer` (parameter order: encoder, decoder, head) as the most
+ * recent vie_unet_forward computed them, FP32 [B][ci][H][H] and
+ * [B][co][H][H] (H = n / 2^level), into `in` and `out` (host or device;
+ * `in` may be NULL, and layer 0's input, the caller's x, is not copied).
+ * Synchronous.  Errors: INVALID_ARG (no forward yet, layer out of range). */
+vie_status vie_unet_layer_io(vie_unet *u, int layer, float *in, float *out, void *stream);
+
 /* Mean squared error of Net(x) against t (device FP32 [B][n][n]) and, if
  * grads_host is not NULL, its gradient with respect to every parameter
  * (host FP32 [num_params]). Synchronous. */

@@ -171,17 +171,17 @@ __device__ __forceinline__ void taps2(const float *w, const float *v, Acc2<R> &s
 }
 
 
-// A D's chunk records, grouped by chunk length: one header float4 whose
-// first two words hold the number of chunks of each length lc = 1..8 (one
-// byte per length, lengths 1..4 in .x and 5..8 in .y), then the chunks of
-// length 1, those of length 2, and so on.  A chunk of length LC is
+// A D's chunk records, grouped by chunk length: one header float4 whose four
+// words hold the number of chunks of each length lc = 1..8 (16 bits per
+// length: lengths 1, 2 in .x, 3, 4 in .y, 5, 6 in .z, 7, 8 in .w), then the
+// chunks of length 1, those of length 2, and so on.  A chunk of length LC is
 // (LC + 4) / 4 float4s: the offset of its first cell from the target in
 // lattice elements (int bits), then its LC weights.  Each length runs in its
 // own loop, unrolled for that length: no per-chunk dispatch.
 template <int LC>
 __device__ __forceinline__ int chunk_count(const float4 &hdr) {
-  const unsigned word = __float_as_uint(LC <= 4 ? hdr.x : hdr.y);
-  return (int)((word >> (8 * ((LC - 1) & 3))) & 255u);
+  const float f = LC <= 2 ? hdr.x : LC <= 4 ? hdr.y : LC <= 6 ? hdr.z : hdr.w;
+  return (int)((__float_as_uint(f) >> (16 * ((LC - 1) & 1))) & 0xffffu);
 }
 
 template <int LC>

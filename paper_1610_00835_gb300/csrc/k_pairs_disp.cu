@@ -798,16 +798,13 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
       const std::vector<int> &runs = along_y ? cy_runs : cx_runs;
       const Plan &pl = along_y ? py : px;
       const int off = (int)(rec.size() / 4);
-      // header: chunks per length (one byte per length 1..8), then the chunks
+      // header: chunks per length (16 bits per length 1..8), then the chunks
       // grouped by length, each group in run order
-      unsigned counts[2] = {0u, 0u};
-      for_each_chunk(runs, [&](int, int lc) { counts[(lc - 1) >> 2] += 1u << (8 * ((lc - 1) & 3)); });
-      float hbits[2];
+      unsigned counts[4] = {0u, 0u, 0u, 0u};
+      for_each_chunk(runs, [&](int, int lc) { counts[(lc - 1) >> 1] += 1u << (16 * ((lc - 1) & 1)); });
+      float hbits[4];
       memcpy(hbits, counts, sizeof hbits);
-      rec.push_back(hbits[0]);
-      rec.push_back(hbits[1]);
-      rec.push_back(0.f);
-      rec.push_back(0.f);
+      for (float f : hbits) rec.push_back(f);
       for (int len = 1; len <= kMaxChunk; ++len)
         for_each_chunk(runs, [&](int c0, int lc) {
           if (lc != len) return;
@@ -821,7 +818,7 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
         });
       int per_len[kMaxChunk + 1] = {};
       for_each_chunk(runs, [&](int, int lc) { ++per_len[lc]; });
-      if (*std::max_element(per_len, per_len + kMaxChunk + 1) > 255 || pl.recs + 1 > 524287) {
+      if (*std::max_element(per_len, per_len + kMaxChunk + 1) > 65535 || pl.recs + 1 > 524287) {
         set_error("displacement kernel: stencil longer than the unit encoding allows");
         return VIE_ERR_UNSUPPORTED;
       }

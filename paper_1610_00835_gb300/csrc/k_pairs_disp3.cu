@@ -7,8 +7,9 @@
 // so their trilinear weights, summed per lattice cell, give a stencil W_D with
 // sum_i sigma(u_j + (i + 1/2) D / S) = sum_c W_D(c) sigma[j + c] for every j.
 //
-// W_D is stored as runs along one axis, cut into chunks of Lc cells (the same
-// records and unrolled march as in 2D, disp_march.cuh).  Three orientations,
+// W_D is stored as runs along one axis, each cut into the fewest chunks of at
+// most 8 cells, of equal length, grouped by length behind a per-D header (the
+// same records and packed-pair march as in 2D, disp_march.cuh).  Three orientations,
 // chosen per D by estimated cost: runs along z with lanes on x (units fix a y),
 // runs along y with lanes on x (units fix a z), runs along x with lanes on y
 // (units fix a z).  A thread stacks kR targets along the run axis.  When the
@@ -17,9 +18,9 @@
 // with the odd pitches n + 1 and (n + 1)^2 the groups fall in distinct banks.
 //
 // The lattice is the padded (n + 1)^3 sigma_t array, linear (x fastest), with
-// kPad3 zero planes appended: reads of discarded stacked targets and of the
-// zero-weight tail of a chunk only run forward along the run axis, by at most
-// kPad3 strides, so every read stays in shared memory.  The weights of valid
+// kPad3 zero planes appended: reads of discarded stacked targets only run
+// forward along the run axis, by at most kPad3 strides, so every read stays in
+// shared memory.  The weights of valid
 // targets only touch the (n + 1)^3 part.
 //
 // Only D in a half space is marched (A_jk = A_kj); each pair adds w s_k to y_j
@@ -44,15 +45,14 @@ namespace vie {
 
 namespace {
 
-using dmarch::kChunkLengths;
 using dmarch::kMaxChunk;
 using dmarch::kR;
-using dmarch::march_unit;
+using dmarch::march_runs;
 using dmarch::red_add;
 using march::kS;
 
 constexpr int kThreads3 = 1024;
-constexpr int kPad3 = kR - 1 + kMaxChunk - 1;  // zero planes after the lattice
+constexpr int kPad3 = kR - 1;  // zero planes after the lattice
 constexpr int kMaxN3 = 32;                     // one lane block per unit
 
 struct Disp3Args {
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     const int dz = (signed char)((un.y >> 16) & 0xff);
     const int orient = (un.y >> 24) & 3, lg = (un.y >> 26) & 7;
     const int sb = un.z & 0xff, c3 = (un.z >> 8) & 0xff;
-    const int lc = un.w & 15, chunks = un.w >> 4;
+    const int nrec = un.w;
     const int xlo = max(0, -dx), xhi = n - max(0, dx);
     const int ylo = max(0, -dy), yhi = n - max(0, dy);
     const int zlo = max(0, -dz), zhi = n - max(0, dz);
@@ -135,18 +135,18 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     {
       // bring this D's chunk records into L1 (one 128-byte line per lane)
       const char *r0 = reinterpret_cast<const char *>(a.stencil + un.x);
-      const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * chunks * ((lc + 4) / 4) + 127) >> 7);
+      const int lines = (int)(((reinterpret_cast<size_t>(r0) & 127) + 16L * nrec + 127) >> 7);
       for (int l = lane; l < lines; l += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(r0 + 128L * l));
     }
     float acc[kR];
 #pragma unroll
     for (int q = 0; q < kR; ++q) acc[q] = 0.f;
     if (orient == 0)
-      march_unit<PLANE>(lc, a.stencil + un.x, chunks, base, plane, acc);
+      march_runs<PLANE, kR>(a.stencil + un.x, base, plane, acc);
     else if (orient == 1)
-      march_unit<LDP>(lc, a.stencil + un.x, chunks, base, ldp, acc);
+      march_runs<LDP, kR>(a.stencil + un.x, base, ldp, acc);
     else
-      march_unit<1>(lc, a.stencil + un.x, chunks, base, 1, acc);
+      march_runs<1, kR>(a.stencil + un.x, base, 1, acc);
     const float r2 = (float)(dx * dx + dy * dy + dz * dz);
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
@@ -283,20 +283,36 @@ void box_runs(const std::vector<double> &box, int ox, int oy, int oz, int bx, in
     }
 }
 
+// A run of L cells is cut into ceil(L / kMaxChunk) chunks of equal length
+// (lengths differ by at most one); f(first cell, length) per chunk.
+template <typename F>
+void for_each_chunk3(const std::vector<Run3> &runs, F f) {
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int L = runs[r].len, nch = (L + kMaxChunk - 1) / kMaxChunk;
+    int c0 = 0;
+    for (int c = 0; c < nch; ++c) {
+      const int lc = L / nch + (c < L % nch ? 1 : 0);
+      f(r, c0, lc);
+      c0 += lc;
+    }
+  }
+}
+
+// Estimated instructions per thread of one unit (as in 2D): per chunk its
+// record loads and loop, Lc + kR - 1 lattice loads, the packed multiply-adds
+// and a weight broadcast per tap; per unit the epilogue.
 struct Plan3 {
-  int lc;
-  long chunks, cost;
+  long chunks, recs, cost;
 };
 
 Plan3 chunk_plan3(const std::vector<Run3> &runs) {
-  Plan3 best{0, 0, -1};
-  for (int lc : kChunkLengths) {
-    long ch = 0;
-    for (const Run3 &r : runs) ch += (r.len + lc - 1) / lc;
-    const long cost = ch * (6 + (lc + 4) / 4 + (lc + kR - 1) + (long)kR * lc) + 60;
-    if (best.cost < 0 || cost < best.cost) best = {lc, ch, cost};
-  }
-  return best;
+  Plan3 p{0, 1, 12L * kR + 40};
+  for_each_chunk3(runs, [&](size_t, int, int lc) {
+    ++p.chunks;
+    p.recs += (lc + 4) / 4;
+    p.cost += 4 + (lc + 4) / 4 + (lc + kR - 1) + ((lc + 1) / 2) * (kR / 2) + (lc / 2) * (kR / 2 + 1) + lc;
+  });
+  return p;
 }
 
 int pow2ceil(int v) {
@@ -382,9 +398,18 @@ void build_plane3(int n, int dz, Plane3 &out) {
         }
       }
       const Plan3 &pl = plans[best];
-      const int off = (int)(rec.size() / 4), rs = (pl.lc + 4) / 4;
-      for (const Run3 &r : runs[best]) {
-        for (int c0 = 0; c0 < r.len; c0 += pl.lc) {
+      const int off = (int)(rec.size() / 4);
+      // header: chunks per length (16 bits per length 1..8), then the chunks
+      // grouped by length, each group in run order
+      unsigned counts[4] = {0u, 0u, 0u, 0u};
+      for_each_chunk3(runs[best], [&](size_t, int, int lc) { counts[(lc - 1) >> 1] += 1u << (16 * ((lc - 1) & 1)); });
+      float hbits[4];
+      memcpy(hbits, counts, sizeof hbits);
+      for (float f : hbits) rec.push_back(f);
+      for (int len = 1; len <= kMaxChunk; ++len)
+        for_each_chunk3(runs[best], [&](size_t ri, int c0, int lc) {
+          if (lc != len) return;
+          const Run3 &r = runs[best][ri];
           int cx = r.cx, cy = r.cy, cz = r.cz;
           if (run_axis[best] == 0) cx += c0;
           if (run_axis[best] == 1) cy += c0;
@@ -393,25 +418,25 @@ void build_plane3(int n, int dz, Plane3 &out) {
           float obits;
           memcpy(&obits, &eoff, sizeof obits);
           rec.push_back(obits);
-          for (int i = 0; i < pl.lc; ++i) rec.push_back(c0 + i < r.len ? (float)wts[best][r.woff + c0 + i] : 0.f);
-          for (int i = pl.lc + 1; i < 4 * rs; ++i) rec.push_back(0.f);
-        }
-      }
+          for (int i = 0; i < lc; ++i) rec.push_back((float)wts[best][r.woff + c0 + i]);
+          for (int i = lc + 1; i < 4 * ((lc + 4) / 4); ++i) rec.push_back(0.f);
+        });
       const int lanes = lanes_of[best], third = third_of[best];
       const int gw = pow2ceil(lanes), lg = 5 - __builtin_ctz(gw);  // 32 / gw lane groups
       const int tlo = best == 0 ? std::max(0, -dy) : 0;           // third axis y (orientation 0) or z
       const int nsb = (stack_of[best] + kR - 1) / kR;
       const int dxyz = (dx & 0xff) | ((dy & 0xff) << 8) | ((dz & 0xff) << 16) | (best << 24) | (lg << 26);
-      const int w = pl.lc | ((int)pl.chunks << 4);
+      const int w = (int)pl.recs;  // the D's record float4s (header included)
       for (int sb = 0; sb < nsb; ++sb)
         for (int j = 0; j < gw && j < third; ++j)
           units.push_back({make_int4(off, dxyz, sb | ((tlo + j) << 8), w), pl.cost});
     }
 }
 
-// Units (int4): x = first chunk record (float4 index); y = dx | dy << 8 | dz << 16
-// (8-bit two's complement) | orientation << 24 | log2(lane groups) << 26;
-// z = stack block | first third-axis coordinate << 8; w = Lc | chunks << 4.
+// Units (int4): x = the D's record header (float4 index); y = dx | dy << 8 |
+// dz << 16 (8-bit two's complement) | orientation << 24 | log2(lane groups)
+// << 26; z = stack block | first third-axis coordinate << 8; w = the D's
+// record float4s.
 // The planes dz are built on host threads and joined in dz order.
 vie_status geometry3_build(int n, Geometry3 *geo) {
   std::vector<Plane3> planes(n);

@@ -1190,6 +1190,66 @@ vie_status vie_unet_forward(vie_unet *u, const float *x, float *o, int B, int n,
   return VIE_OK;
 }
 
+vie_status vie_unet_layer_io(vie_unet *u, int layer, float *in, float *out, void *stream) {
+  if (!u || !out || layer < 0 || layer >= (int)u->impl.layers.size() || u->impl.B < 1) {
+    set_error("vie_unet_layer_io: no forward yet, or layer out of range");
+    return VIE_ERR_INVALID_ARG;
+  }
+  UnetImpl &U = u->impl;
+  VIE_CUDA(cudaSetDevice(U.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = U.L, C = U.C, B = U.B, n = U.n;
+  const ConvLayer &c = U.layers[layer];
+  // where the most recent forward keeps this layer's input and output
+  const float *src_in = nullptr, *src_out = nullptr;
+  long in_bs = 0, out_bs = 0;
+  int H = n;
+  if (layer < 2 * L) {  // encoder level l: a_l = conv(x_l), e_l = conv(a_l)
+    const int l = layer / 2;
+    H = n >> l;
+    const long hw = (long)H * H;
+    if (layer % 2 == 0) {
+      src_in = l == 0 ? nullptr : U.xin[l];
+      in_bs = (long)c.ci * hw;
+      src_out = U.a[l];
+      out_bs = (long)C * hw;
+    } else {
+      src_in = U.a[l];
+      in_bs = (long)C * hw;
+      src_out = l < L - 1 ? U.cat[l] + (long)C * hw : U.ebot[0];
+      out_bs = l < L - 1 ? 2L * C * hw : (long)C * hw;
+    }
+  } else if (layer < 2 * L + 2 * (L - 1)) {  // decoder, deepest level first
+    const int k = layer - 2 * L, l = L - 2 - k / 2;
+    H = n >> l;
+    const long hw = (long)H * H;
+    if (k % 2 == 0) {
+      src_in = U.cat[l];
+      in_bs = 2L * C * hw;
+      src_out = U.bl[l];
+    } else {
+      src_in = U.bl[l];
+      in_bs = (long)C * hw;
+      src_out = U.dl[l];
+    }
+    out_bs = (long)C * hw;
+  } else {  // head
+    const long hw = (long)n * n;
+    src_in = L > 1 ? U.dl[0] : U.ebot[0];
+    in_bs = (long)C * hw;
+    src_out = U.o;
+    out_bs = hw;
+  }
+  const long hw = (long)H * H;
+  if (in && src_in)
+    VIE_CUDA(cudaMemcpy2DAsync(in, sizeof(float) * c.ci * hw, src_in, sizeof(float) * in_bs, sizeof(float) * c.ci * hw,
+                               B, cudaMemcpyDefault, st));
+  VIE_CUDA(cudaMemcpy2DAsync(out, sizeof(float) * c.co * hw, src_out, sizeof(float) * out_bs,
+                             sizeof(float) * c.co * hw, B, cudaMemcpyDefault, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  return VIE_OK;
+}
+
 vie_status vie_unet_loss_grad(vie_unet *u, const float *x, const float *t, int B, int n, float *grads_host,
                               double *loss, void *stream) {
   if (!u || !x || !t || !loss || B < 1 || (n % (1 << (u->impl.L - 1))) != 0) {

@@ -101,6 +101,7 @@ SIGNATURES = {
     "vie_unet_load": (C.c_int, [_vp, C.c_char_p]),
     "vie_unet_train_state": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
     "vie_set_wait_limits": (C.c_int, [C.c_double, C.c_double]),
+    "vie_unet_layer_io": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "vie_check_device": (C.c_int, [_vp, _vp]),
     "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
     "vie_set_fft_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
@@ -396,6 +397,13 @@ def vie_set_wait_limits(limit_ms: float = 1000.0, first_wait_ms: float = -1.0) -
 def vie_check_device(h: VieHandle, stream=None) -> None:
     """Synchronise and raise VieError(VIE_ERR_TIMEOUT) if a bounded wait gave up."""
     _check(load().vie_check_device(h.ptr, _stream(stream)))
+
+
+def vie_unet_layer_io(u: VieUnet, layer: int, inp, out, stream=None) -> None:
+    """Input (unless None) and output of one convolution from the latest forward."""
+    ip, _i = _ptr(inp, np.float32) if inp is not None else (None, None)
+    op, _o = _ptr(out, np.float32)
+    _check(load().vie_unet_layer_io(u.ptr, int(layer), ip, op, _stream(stream)))
 
 
 def vie_unet_train_state(u: VieUnet) -> int:

@@ -199,3 +199,39 @@ def test_checkpoint_resumes_adam_where_it_stopped(tmp_path):
     for _ in range(3):
         P.vie_unet_train_step(c, x, t, B, n, 1e-3)
     assert np.abs(P.vie_unet_get_params(c) - pa).max() > 10 * np.abs(pa - pb).max()
+
+
+@pytest.mark.parametrize("n,B", [(32, 2), (256, 1)])
+def test_bf16_forward_every_layer_matches_the_rounded_reference(n, B):
+    # the 4-level BF16 forward layer by layer: each convolution's output from
+    # the tensor cores against the FP64 convolution of the same FP32 input with
+    # the BF16 inference rounding (input and weights rounded to BF16, relu after
+    # every 3x3 layer, the 1x1 head on FP32 activations).  Both sides round the
+    # same input, so only the FP32 accumulation differs: every layer, the
+    # encoder's 3 -> 32 and 32 -> 32, the decoder's 64 -> 32 (K = 576) at every
+    # resolution down to the coarsest and the head, is held to 1e-5.
+    levels, C = 4, 32
+    u = P.vie_unet_create(levels, C, seed=51)
+    rng = np.random.default_rng(n + B)
+    params = P.vie_unet_get_params(u)
+    P.vie_unet_set_params(u, params + 0.02 * rng.standard_normal(params.size).astype(np.float32))
+    x = rng.standard_normal((B, 3, n, n)).astype(np.float32)
+    o = torch.empty(B * n * n, dtype=torch.float32, device="cuda:0")
+    P.vie_unet_forward(u, dev(x.ravel(), torch.float32), o, B, n, use_bf16=True)
+    pr = ref_params(u, levels, C)
+    shapes = R.layer_shapes(levels, C)
+    res = [n >> l for l in range(levels) for _ in range(2)] + \
+          [n >> l for l in range(levels - 2, -1, -1) for _ in range(2)] + [n]
+    assert len(res) == len(shapes)
+    for i, ((co, ci, k), H) in enumerate(zip(shapes, res)):
+        inp = np.empty((B, ci, H, H), dtype=np.float32)
+        out = np.empty((B, co, H, H), dtype=np.float32)
+        P.vie_unet_layer_io(u, i, None if i == 0 else inp, out)
+        if i == 0:
+            inp = x
+        w, b = pr[2 * i], pr[2 * i + 1]
+        xi = inp.astype(np.float64)
+        want = R.conv(R.round_bf16(xi) if k == 3 else xi, R.round_bf16(w), b)
+        if k == 3:
+            want = np.maximum(want, 0)
+        assert rel_l2(out.ravel(), want.ravel()) < 1e-5, (i, co, ci, H)
