@@ -410,6 +410,16 @@ vie_status vie_unet_train_state(vie_unet *u, long long *step);
  * fell_back = 1.  The network must outlive its use by the handle. */
 vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref);
 
+/* The learned network as a correction of the diffusion preconditioner (below):
+ *   M(v) = D(v) + rms(v) Net(sigma_t / s_ref, sigma_s / s_ref, v / rms(v)),
+ * D the diffusion preconditioner's z = v + D^{-1}(sigma_s v); the network is
+ * trained on the part of (I - K)^{-1} v that D misses (train_unet.py --base
+ * diffusion).  Builds the diffusion hierarchy (synchronous), replaces any other
+ * preconditioner; NULL u removes both.  Same conditions and stall fallback as
+ * vie_set_preconditioner and vie_set_diffusion_preconditioner.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+vie_status vie_set_preconditioner_on_diffusion(vie_handle *h, vie_unet *u, double s_ref, void *stream);
+
 /* The FFT preconditioner of Section 4.4 (Eqs. EQ: FFT and EQ:SOL FFT) as the
  * right preconditioner of vie_solve_gmres (flexible GMRES, with the same
  * stall fallback as above); enable = 0 removes it.  It replaces sigma_t and

@@ -549,12 +549,12 @@ __global__ void k_net_input(const double *__restrict__ st, const double *__restr
   }
 }
 
-// z = v + rms(v) o
-__global__ void k_net_output(const double *__restrict__ v, const double *__restrict__ vnorm2,
+// z = base + rms(v) o (base: v itself, or another preconditioner's z_0 = M_0 v)
+__global__ void k_net_output(const double *__restrict__ base, const double *__restrict__ vnorm2,
                              const float *__restrict__ o, long N, double *__restrict__ z) {
   const double rms = sqrt(*vnorm2 / (double)N);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
-    z[i] = v[i] + rms * (double)o[i];
+    z[i] = base[i] + rms * (double)o[i];
 }
 
 int gridn(long n) { return (int)std::max(1L, std::min((n + 255) / 256, 8192L)); }
@@ -576,15 +576,15 @@ __global__ void k_net_input_b(const double *__restrict__ st, const double *__res
   }
 }
 
-__global__ void k_net_output_b(const double *__restrict__ v, long ldv, const double *__restrict__ scal, int slot,
+__global__ void k_net_output_b(const double *__restrict__ base, long ldb, const double *__restrict__ scal, int slot,
                                const float *__restrict__ o, long N, double *__restrict__ z, long ldz) {
   const int r = blockIdx.y;
   const double rms = sqrt(scal[8 * r + slot] / (double)N);
-  const double *vr = v + (long)r * ldv;
+  const double *br = base + (long)r * ldb;
   const float *orr = o + (long)r * N;
   double *zr = z + (long)r * ldz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
-    zr[i] = vr[i] + rms * (double)orr[i];
+    zr[i] = br[i] + rms * (double)orr[i];
 }
 
 }  // namespace
@@ -993,25 +993,26 @@ vie_status loss_grad(UnetImpl *u, const float *x, const float *t, const float *w
 
 // ---- used by the FGMRES driver (vie_api.cu)
 vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
-                             const double *v, const double *vnorm2, int n, float *xbuf, double *z,
-                             cudaStream_t st) {
+                             const double *v, const double *vnorm2, int n, float *xbuf, const double *base,
+                             double *z, cudaStream_t st) {
   vie_status s;
   if ((s = ensure_acts(u, 1, n)) != VIE_OK) return s;
   const long N = (long)n * n;
   k_net_input<<<gridn(N), 256, 0, st>>>(sigma_t, sigma_s, v, vnorm2, N, (float)inv_ref, xbuf);
   VIE_CHECK_LAUNCH("k_net_input");
   if ((s = forward<__nv_bfloat16>(u, u->pb, xbuf, 1, n, st)) != VIE_OK) return s;
-  k_net_output<<<gridn(N), 256, 0, st>>>(v, vnorm2, u->o, N, z);
+  k_net_output<<<gridn(N), 256, 0, st>>>(base ? base : v, vnorm2, u->o, N, z);
   VIE_CHECK_LAUNCH("k_net_output");
   return VIE_OK;
 }
 
 // R preconditioner applications in one forward pass of R images (the batched
-// FGMRES driver): z_r = v_r + rms(v_r) Net(sigma_t / s_ref, sigma_s / s_ref,
-// v_r / rms(v_r)), BF16 weights.
+// FGMRES driver): z_r = base_r + rms(v_r) Net(sigma_t / s_ref, sigma_s / s_ref,
+// v_r / rms(v_r)), BF16 weights; base_r = v_r, or (base non-null) another
+// preconditioner's result that the network corrects.
 vie_status unet_precondition_batch(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
                                    const double *v, long ldv, const double *scal, int slot, int R, int n,
-                                   float *xbuf, double *z, long ldz, cudaStream_t st) {
+                                   float *xbuf, const double *base, long ldb, double *z, long ldz, cudaStream_t st) {
   vie_status s;
   if ((s = ensure_acts(u, R, n)) != VIE_OK) return s;
   const long N = (long)n * n;
@@ -1019,7 +1020,7 @@ vie_status unet_precondition_batch(UnetImpl *u, const double *sigma_t, const dou
   k_net_input_b<<<grid, 256, 0, st>>>(sigma_t, sigma_s, v, ldv, scal, slot, N, (float)inv_ref, xbuf);
   VIE_CHECK_LAUNCH("k_net_input_b");
   if ((s = forward<__nv_bfloat16>(u, u->pb, xbuf, R, n, st)) != VIE_OK) return s;
-  k_net_output_b<<<grid, 256, 0, st>>>(v, ldv, scal, slot, u->o, N, z, ldz);
+  k_net_output_b<<<grid, 256, 0, st>>>(base ? base : v, base ? ldb : ldv, scal, slot, u->o, N, z, ldz);
   VIE_CHECK_LAUNCH("k_net_output_b");
   return VIE_OK;
 }

@@ -198,6 +198,7 @@ struct vie_handle {
   bool sig_s_positive = false;                // phi = K (f / sigma_s) is available
   UnetImpl *precond = nullptr;                // learned right preconditioner
   double precond_inv_ref = 0.2;
+  bool precond_on_diff = false;               // the network corrects the diffusion preconditioner's z
   double *Z = nullptr;                        // FGMRES: preconditioned basis [m][N]
   int z_m = 0;
   float *net_x = nullptr;                     // network input [3][N]
@@ -706,9 +707,16 @@ vie_status solve_multi(vie_handle *h, const double *fdev, double *x, int R, cons
         // whose preconditioned iteration stalled goes on with M = I
         double *zk = g.Z + (size_t)k * N;
         if (h->precond) {
+          if (h->precond_on_diff)  // the diffusion preconditioner first; the network corrects it
+            for (int r = 0; r < R; ++r)
+              if (act[r] && !fell[r] &&
+                  (s = diffusion_precondition(h->diff, g.V + (size_t)r * ldv + (size_t)k * N, zk + (size_t)r * ldz,
+                                              st)) != VIE_OK)
+                return s;
           if ((s = launch_bnorm2(b, g.V + (size_t)k * N, ldv, 4, st)) != VIE_OK) return s;
           if ((s = unet_precondition_batch(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, g.V + (size_t)k * N,
-                                           ldv, b.scal, 4, R, h->n, g.net_x, zk, ldz, st)) != VIE_OK)
+                                           ldv, b.scal, 4, R, h->n, g.net_x, h->precond_on_diff ? zk : nullptr,
+                                           ldz, zk, ldz, st)) != VIE_OK)
             return s;
         } else {
           for (int r = 0; r < R; ++r) {
@@ -1227,8 +1235,28 @@ vie_status vie_set_preconditioner(vie_handle *h, vie_unet *u, double s_ref) {
     return invalid("vie_set_preconditioner: n must be divisible by 2^(levels-1)");
   h->precond = unet_impl(u);
   h->precond_inv_ref = 1.0 / s_ref;
+  h->precond_on_diff = false;
   fft_release(&h->fft);  // one preconditioner at a time
   diffusion_release(&h->diff);
+  return VIE_OK;
+}
+
+vie_status vie_set_preconditioner_on_diffusion(vie_handle *h, vie_unet *u, double s_ref, void *stream) {
+  if (!h) return invalid("vie_set_preconditioner_on_diffusion: NULL handle");
+  if (!u) {
+    h->precond = nullptr;
+    h->precond_on_diff = false;
+    diffusion_release(&h->diff);
+    return VIE_OK;
+  }
+  vie_status s = vie_set_preconditioner(h, u, s_ref);
+  if (s != VIE_OK) return s;
+  UnetImpl *net = h->precond;
+  const double inv = h->precond_inv_ref;
+  if ((s = vie_set_diffusion_preconditioner(h, 1, stream)) != VIE_OK) return s;  // clears the network
+  h->precond = net;
+  h->precond_inv_ref = inv;
+  h->precond_on_diff = true;
   return VIE_OK;
 }
 
@@ -1282,6 +1310,7 @@ vie_status vie_set_diffusion_preconditioner(vie_handle *h, int enable, void *str
     return s;
   }
   h->precond = nullptr;  // one preconditioner at a time
+  h->precond_on_diff = false;
   fft_release(&h->fft);
   return VIE_OK;
 }
@@ -1479,13 +1508,20 @@ vie_status vie_solve_gmres(vie_handle *h, const double *f, double *U, const vie_
         if (h->fft.on) {
           // the FFT preconditioner (Section 4.4, Eq. EQ:SOL FFT)
           if ((s = fft_precondition(h->fft, vk, zk, st)) != VIE_OK) return s;
+        } else if (h->precond && h->precond_on_diff) {
+          // the diffusion preconditioner, then the network's correction of it
+          if ((s = diffusion_precondition(h->diff, vk, zk, st)) != VIE_OK) return s;
+          if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
+          if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,
+                                     h->n, h->net_x, zk, zk, st)) != VIE_OK)
+            return s;
         } else if (h->diff.on) {
           // the diffusion preconditioner (Section 4.4, Eq. EQ:DA)
           if ((s = diffusion_precondition(h->diff, vk, zk, st)) != VIE_OK) return s;
         } else {
           if ((s = norm2_dev(h, vk, h->scal + 4, st)) != VIE_OK) return s;
           if ((s = unet_precondition(h->precond, h->sig_t, h->sig_s, h->precond_inv_ref, vk, h->scal + 4,
-                                     h->n, h->net_x, zk, st)) != VIE_OK)
+                                     h->n, h->net_x, nullptr, zk, st)) != VIE_OK)
             return s;
         }
         op_in = zk;

@@ -321,12 +321,13 @@ int unet_levels(vie_unet *u);
 // bounded wait gave up), and its synchronous check-and-clear
 int *unet_error_word(UnetImpl *u);
 vie_status unet_take_error(UnetImpl *u, cudaStream_t st);
+// z = base + rms(v) Net(...) with base = v when null (one vector, or R at a time)
 vie_status unet_precondition_batch(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
                                    const double *v, long ldv, const double *scal, int slot, int R, int n,
-                                   float *xbuf, double *z, long ldz, cudaStream_t st);
+                                   float *xbuf, const double *base, long ldb, double *z, long ldz, cudaStream_t st);
 vie_status unet_precondition(UnetImpl *u, const double *sigma_t, const double *sigma_s, double inv_ref,
-                             const double *v, const double *vnorm2, int n, float *xbuf, double *z,
-                             cudaStream_t st);
+                             const double *v, const double *vnorm2, int n, float *xbuf, const double *base,
+                             double *z, cudaStream_t st);
 
 // ---- Krylov kernels (k_krylov.cu)
 int dot_blocks(long N);

@@ -41,11 +41,13 @@ S_REF = 5.0
 FAMILIES = {"thin": V.random_training_medium, "diffusive": V.diffusive_training_medium}
 
 
-def make_sample(P, torch, i, n, dev, family="diffusive"):
+def make_sample(P, torch, i, n, dev, family="diffusive", base="identity"):
     """Sample i: kind i % 3 = 0 a physical solve (b = phi = A f, U by GMRES to
     1e-6); 1 and 2 a manufactured pair (U = w a random smooth / rough field,
     b = (I - K) w by one apply), which covers the residual-like vectors a
-    Krylov method feeds to its preconditioner."""
+    Krylov method feeds to its preconditioner.  The target is (U - z0) / rms(b)
+    with z0 = b (base "identity": M(b) = b + rms(b) Net) or z0 the diffusion
+    preconditioner's D(b) (base "diffusion": M(b) = D(b) + rms(b) Net)."""
     m = FAMILIES[family](n, 5000 + i)
     h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
     kind = i % 3
@@ -64,17 +66,22 @@ def make_sample(P, torch, i, n, dev, family="diffusive"):
                             device=dev)
         b = torch.empty_like(U)
         P.vie_apply(h, P.VIE_OP_I_MINUS_K, U, b)
+    z0 = b
+    if base == "diffusion" and rep["converged"]:
+        P.vie_set_diffusion_preconditioner(h)
+        z0 = torch.empty_like(b)
+        P.vie_diffusion_precondition(h, b, z0)
     P.vie_destroy(h)
     if not rep["converged"]:
         return None, None, rep["iters"]
     rms = torch.sqrt(torch.mean(b * b))
     x = torch.stack([torch.as_tensor(m.sigma_t, device=dev) / S_REF,
                      torch.as_tensor(m.sigma_s, device=dev) / S_REF, b / rms]).float()
-    t = ((U - b) / rms).float()
+    t = ((U - z0) / rms).float()
     return x.reshape(-1), t, rep["iters"]
 
 
-def evaluate(P, torch, net, n, count, dev, rtol=1e-6, family="diffusive"):
+def evaluate(P, torch, net, n, count, dev, rtol=1e-6, family="diffusive", base="identity"):
     rows = []
     for i in range(count):
         m = FAMILIES[family](n, 9000 + i)
@@ -82,8 +89,16 @@ def evaluate(P, torch, net, n, count, dev, rtol=1e-6, family="diffusive"):
         P.vie_assemble(h, P.VIE_OPERATOR_BF16X3)
         f = torch.as_tensor(m.f, dtype=torch.float64, device=dev)
         res = {}
-        for name, pre in (("plain", None), ("learned", net)):
-            P.vie_set_preconditioner(h, pre, S_REF) if pre is not None else P.vie_set_preconditioner(h, None)
+        cases = (("plain", None), ("learned", net)) if base == "identity" else \
+            (("plain", None), ("diffusion", "diffusion"), ("learned", net))
+        for name, pre in cases:
+            P.vie_set_preconditioner(h, None)
+            if pre == "diffusion":
+                P.vie_set_diffusion_preconditioner(h)
+            elif pre is not None and base == "diffusion":
+                P.vie_set_preconditioner_on_diffusion(h, pre, S_REF)
+            elif pre is not None:
+                P.vie_set_preconditioner(h, pre, S_REF)
             U = torch.empty_like(f)
             P.vie_solve_gmres(h, f, U, rtol=rtol, restart=128, maxit=3000,
                               raise_on_nonconvergence=False)          # warm-up (allocations)
@@ -96,6 +111,7 @@ def evaluate(P, torch, net, n, count, dev, rtol=1e-6, family="diffusive"):
                          "relres": rep["relres"], "fell_back": rep["fell_back"],
                          "converged": rep["converged"]}
         P.vie_set_preconditioner(h, None)
+        P.vie_set_diffusion_preconditioner(h, False)
         P.vie_destroy(h)
         rows.append(res)
     return rows
@@ -114,6 +130,9 @@ def main(argv=None):
     ap.add_argument("--eval-n", type=int, default=256)
     ap.add_argument("--eval-count", type=int, default=8)
     ap.add_argument("--family", choices=sorted(FAMILIES), default="diffusive")
+    ap.add_argument("--base", choices=["identity", "diffusion"], default="identity",
+                    help="what the network corrects: the identity (M(b) = b + rms(b) Net) or the "
+                         "diffusion preconditioner (M(b) = D(b) + rms(b) Net)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     ap.add_argument("--checkpoint", default=None,
@@ -133,7 +152,7 @@ def main(argv=None):
     T = torch.empty(args.samples, args.n * args.n, dtype=torch.float32, device=dev)
     iters, kept, i = [], 0, 0
     while kept < args.samples and i < 2 * args.samples:
-        x, t, it = make_sample(P, torch, i, args.n, dev, args.family)
+        x, t, it = make_sample(P, torch, i, args.n, dev, args.family, args.base)
         i += 1
         iters.append(it)
         if x is None:
@@ -194,13 +213,15 @@ def main(argv=None):
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
         P.vie_unet_save(net, args.out)
-    rows = (evaluate(P, torch, net, args.eval_n, args.eval_count, dev, family=args.family)
+    rows = (evaluate(P, torch, net, args.eval_n, args.eval_count, dev, family=args.family, base=args.base)
             if args.eval_count else [])
     summary = {"phase": "eval", "n": args.eval_n, "train_seconds": train_s, "data_seconds": gen_s,
                "plain_iters": [r["plain"]["iters"] for r in rows],
                "learned_iters": [r["learned"]["iters"] for r in rows],
                "plain_ms": [r["plain"]["ms"] for r in rows],
                "learned_ms": [r["learned"]["ms"] for r in rows],
+               "diffusion_iters": [r["diffusion"]["iters"] for r in rows if "diffusion" in r],
+               "diffusion_ms": [r["diffusion"]["ms"] for r in rows if "diffusion" in r],
                "fell_back": [r["learned"]["fell_back"] for r in rows],
                "converged": [[r["plain"]["converged"], r["learned"]["converged"]] for r in rows]}
     print(json.dumps(summary), flush=True)

@@ -104,6 +104,7 @@ SIGNATURES = {
     "vie_unet_layer_io": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "vie_check_device": (C.c_int, [_vp, _vp]),
     "vie_set_preconditioner": (C.c_int, [_vp, _vp, C.c_double]),
+    "vie_set_preconditioner_on_diffusion": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "vie_set_fft_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
     "vie_fft_precondition": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vie_set_diffusion_preconditioner": (C.c_int, [_vp, C.c_int, _vp]),
@@ -411,6 +412,12 @@ def vie_unet_train_state(u: VieUnet) -> int:
     st = C.c_longlong(0)
     _check(load().vie_unet_train_state(u.ptr, C.byref(st)))
     return st.value
+
+
+def vie_set_preconditioner_on_diffusion(h: VieHandle, u, s_ref: float = 5.0, stream=None) -> None:
+    """The network as a correction of the diffusion preconditioner (None removes both)."""
+    _check(load().vie_set_preconditioner_on_diffusion(h.ptr, u.ptr if u is not None else None, float(s_ref),
+                                                      _stream(stream)))
 
 
 def vie_set_preconditioner(h: VieHandle, u, s_ref: float = 5.0) -> None:

@@ -235,3 +235,31 @@ def test_bf16_forward_every_layer_matches_the_rounded_reference(n, B):
         if k == 3:
             want = np.maximum(want, 0)
         assert rel_l2(out.ravel(), want.ravel()) < 1e-5, (i, co, ci, H)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_network_on_diffusion_converges_with_any_network(nrhs):
+    # the network as a correction of the diffusion preconditioner: with an
+    # untrained network (or a zero one, M = D) FGMRES still reaches the
+    # tolerance, one source or several in lockstep, and matches the LU solution
+    # (optically thin cells, where the diffusion approximation holds)
+    n = 32
+    m = V.heterogeneous_2d(n=n, seed=8600)
+    h = P.vie_create(2, n, m.sigma_t, m.sigma_s)
+    F = V.bump_sources(2, n, nrhs, seed=81)
+    phi = [O.apply(2, m.sigma_t, m.sigma_s, f, op=O.OP_A_RAW) for f in F]
+    K = O.k_matrix(2, m.sigma_t, m.sigma_s)
+    want = [np.linalg.solve(np.eye(m.N) - K, p) for p in phi]
+    for scale in (0.0, 1.0):
+        u = P.vie_unet_create(4, 8, seed=7)
+        P.vie_unet_set_params(u, P.vie_unet_get_params(u) * scale)
+        P.vie_set_preconditioner_on_diffusion(h, u)
+        U = np.zeros(nrhs * m.N)
+        reps = P.vie_solve_gmres(h, F.ravel(), U, rtol=1e-8, nrhs=nrhs)
+        reps = reps if nrhs > 1 else [reps]
+        for r in range(nrhs):
+            assert reps[r]["converged"] and reps[r]["precond_iters"] >= 1
+            assert rel_l2(U[r * m.N:(r + 1) * m.N], want[r]) < 1e-5
+    P.vie_set_preconditioner_on_diffusion(h, None)
+    U = np.zeros(m.N)
+    assert P.vie_solve_gmres(h, F[0], U, rtol=1e-8)["precond_iters"] == 0

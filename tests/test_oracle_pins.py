@@ -442,3 +442,20 @@ def test_discrete_ordinates_brute_force_matches_vie():
         U_vie = O.lu_solve(2, st, ss, phi)
         gaps.append(np.linalg.norm(U_do - U_vie) / np.linalg.norm(U_vie))
     assert gaps[1] < gaps[0] and gaps[1] < 0.08
+
+
+def test_gmres_dense_branch_equals_matrix_free_and_lu():
+    # or_gmres with the dense (I - K) (its `dense` argument) against the
+    # matrix-free branch and numpy's LU: one Krylov iteration, two operators
+    m = V.heterogeneous_2d(n=12)
+    phi = O.apply(2, m.sigma_t, m.sigma_s, m.f, op=O.OP_A_RAW)
+    IK = np.eye(m.N) - O.k_matrix(2, m.sigma_t, m.sigma_s)
+    Ud, itd, rrd, okd = O.gmres(2, m.sigma_t, m.sigma_s, phi, rtol=1e-12, dense=IK)
+    Um, itm, rrm, okm = O.gmres(2, m.sigma_t, m.sigma_s, phi, rtol=1e-12)
+    assert okd and okm and rrd <= 1e-12 and itd == itm
+    U_lu = np.linalg.solve(IK, phi)
+    assert np.linalg.norm(Ud - U_lu) <= 1e-11 * np.linalg.norm(U_lu)
+    assert np.linalg.norm(Ud - Um) <= 1e-11 * np.linalg.norm(U_lu)
+    # a different dense operator gives its own solution (the argument is used)
+    Ud2, _, _, ok2 = O.gmres(2, m.sigma_t, m.sigma_s, phi, rtol=1e-12, dense=2.0 * IK)
+    assert ok2 and np.linalg.norm(Ud2 - 0.5 * U_lu) <= 1e-11 * np.linalg.norm(U_lu)
