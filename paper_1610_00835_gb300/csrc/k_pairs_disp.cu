@@ -19,10 +19,10 @@
 // into the fewest chunks of at most kMaxChunk cells, of equal length, so no
 // chunk multiplies zero weights; a D's chunks are stored grouped by length
 // Lc behind a header of counts, and each length runs in its own loop.  A
-// warp takes one displacement and a block of 32 x kR targets: 32 consecutive
-// across the run axis (one per lane) and kR consecutive along it, stacked in
-// one thread.  A chunk then takes Lc + kR - 1 lattice loads per thread and
-// kR Lc multiply-adds, issued as packed FP32 pairs (fma.rn.f32x2, two
+// warp takes one displacement and a block of 32 x R targets: 32 consecutive
+// across the run axis (one per lane) and R consecutive along it, stacked in
+// one thread.  A chunk then takes Lc + R - 1 lattice loads per thread and
+// R Lc multiply-adds, issued as packed FP32 pairs (fma.rn.f32x2, two
 // stacked targets per instruction) in code unrolled for each Lc.  Lanes sit
 // on consecutive x (runs along y) or consecutive y with an odd row pitch
 // (runs along x), so every load is free of bank conflicts.
@@ -48,7 +48,7 @@
 //
 // Targets of a block that fall outside the rectangle (ragged blocks) are
 // computed and discarded: lanes beyond it repeat the last valid target, and
-// the lattice carries kPad = kR - 1 extra rows and columns (repeating the
+// the lattice carries R - 1 extra rows and columns (repeating the
 // edge) so that stacked targets beyond it stay in bounds.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -71,23 +71,31 @@ using march::kS;
 using dmarch::kMaxChunk;
 using dmarch::march_runs;
 using dmarch::march_runs_global;
-// targets stacked along the run axis in one thread (16 measured slower at
-// 128^2: 1.47 against 1.41 ms, fewer warps and more ragged blocks)
-constexpr int kR = 8;
+// R, the targets stacked along the run axis in one thread: 12 on grids of
+// 96 and more, 8 below (measured per apply: 8 / 12 took 0.100 / 0.107 ms at
+// 64^2, 0.550 / 0.519 at 100^2, 1.41 / 1.38 at 128^2, 42.9 / 38.3 at 256^2;
+// 16 took 1.47 at 128^2, with fewer warps resident; a last block of 4 or 8
+// for the rest of a rectangle, as its own code path, 1.62).  The lattice
+// carries R - 1 extra rows and columns: the stacked targets of a block that
+// reach past the rectangle of targets (chunks carry no padding).
 using dmarch::red_add;
 constexpr int kThreads = 1024;
-// extra lattice rows and columns: the stacked targets of a block that reach
-// past the rectangle of targets (chunks carry no padding)
-constexpr int kPad = kR - 1;
+__host__ __device__ constexpr int disp_depth(int n) { return n >= 96 ? 12 : 8; }
+// lattice pitch: room for R - 1 stacked targets past the grid, odd so that
+// 32 consecutive rows of one column fall in 32 different banks
+__host__ __device__ constexpr int disp_pitch(int n, int R) { return (n + R) | 1; }
+// Lane groups of a ragged lane block sit s blocks apart along the stack, s R
+// rows of an odd pitch: s R = 16 (mod 32) for pairs and 8 or 24 for quads,
+// so the groups load from disjoint banks.
+__host__ __device__ constexpr int group_stride(int R, int lg) { return lg == 1 ? (R == 8 ? 2 : 4) : (R == 8 ? 1 : 2); }
 // Grids whose lattice does not fit in shared memory read it from global
-// memory: a square lattice of pitch kGlobalLdp (odd, like the shared one, so
-// that the lane groups of a ragged block get the same stack-block strides),
-// for n <= kGlobalMaxN.
+// memory: a square lattice of pitch disp_pitch(kGlobalMaxN, R) (odd, like the
+// shared one, so that the lane groups of a ragged block get the same
+// strides), for n <= kGlobalMaxN.
 constexpr int kGlobalMaxN = 258;
-constexpr int kGlobalLdp = (kGlobalMaxN + 1 + kPad) | 1;  // 267
 
 struct DispArgs {
-  const float *lat;            // [n + 1 + kPad][ldp] sigma_t on the cell lattice, edge repeated
+  const float *lat;            // [n + R][ldp] sigma_t on the cell lattice, edge repeated
   const float *lat_t;          // global-lattice kernels: the same lattice with y fastest
   const float4 *stencil;       // chunk records of every W_D
   const float *src;            // s_k, FP32 [N]
@@ -126,7 +134,7 @@ __device__ __forceinline__ int disp_index(int dx, int dy, int n) {
 // runs go along y read lat from (x, y) on, the others lat_t from (y, x) on:
 // in both the run axis has stride LDP and the lanes are consecutive elements,
 // and the records of the runs along x carry their offsets in lat_t's layout.
-template <int LDP, int MODE, bool GLAT = false>
+template <int LDP, int MODE, bool GLAT, int R>
 __device__ __forceinline__ void disp_body(const DispArgs &a) {
   extern __shared__ float4 smem4[];
   const int n = a.n;
@@ -162,37 +170,37 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
       u_end = min(got + 4, a.n_units);
     }
     const int4 un = a.units[u0++];
+    {
     const int dx = (short)(un.y & 0xffff), dy = un.y >> 16;
-    const int lb = un.z & 0xffff, sb0 = un.z >> 16;
+    const int lb = un.z & 0xffff, row0 = un.z >> 16;
     const int xlo = dx < 0 ? -dx : 0, xhi = dx > 0 ? n - dx : n;
     const int ylo = dy < 0 ? -dy : 0, yhi = dy > 0 ? n - dy : n;
     const bool along_y = (un.w & 1) != 0;
     const int lg = (un.w >> 1) & 3, nrec = un.w >> 12;
-    // lane groups: 1, 2 or 4 groups of 32 >> lg lanes, group g on stack block
-    // sb0 + s g (s = 2 for pairs, ldp mod 4 for quads: the groups then load
-    // from disjoint banks); a group past the last stack block is masked off
+    // lane groups: 1, 2 or 4 groups of 32 >> lg lanes, group g on the block
+    // starting R s g rows after row0 (s = group_stride); a group past the
+    // last block is masked off
     const int gw = 32 >> lg, g = lane >> (5 - lg), lig = lane & (gw - 1);
-    const int sstride = lg == 1 ? 2 : (a.ldp & 3);  // the lattice pitch, also in the stream kernel
-    const int nsb = ((along_y ? yhi - ylo : xhi - xlo) + kR - 1) / kR;
-    int sb = sb0 + sstride * g;
-    bool lvalid = sb < nsb;
-    if (!lvalid) sb = sb0;
+    const int stack = along_y ? yhi - ylo : xhi - xlo;
+    int row = row0 + R * group_stride(R, lg) * g;
+    bool lvalid = row < stack;
+    if (!lvalid) row = row0;
     // lane coordinate (clamped to the rectangle) and the first stacked target
     int x, y;
     if (along_y) {
       const int xr = xlo + 32 * lb + lig;
       lvalid = lvalid && xr < xhi;
       x = xr < xhi ? xr : xhi - 1;
-      y = ylo + kR * sb;
+      y = ylo + row;
     } else {
       const int yr = ylo + 32 * lb + lig;
       lvalid = lvalid && yr < yhi;
       y = yr < yhi ? yr : yhi - 1;
-      x = xlo + kR * sb;
+      x = xlo + row;
     }
-    float acc[kR];
+    float acc[R];
 #pragma unroll
-    for (int q = 0; q < kR; ++q) acc[q] = 0.f;
+    for (int q = 0; q < R; ++q) acc[q] = 0.f;
     if constexpr (MODE != kStream) {
       const unsigned base = lat_base + 4u * (unsigned)(x + ldp * y);
       {
@@ -203,11 +211,11 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
       }
       if constexpr (GLAT) {
         const float *gb = along_y ? a.lat + (x + (long)LDP * y) : a.lat_t + (y + (long)LDP * x);
-        march_runs_global<LDP, kR>(a.stencil + un.x, gb, acc);
+        march_runs_global<LDP, R>(a.stencil + un.x, gb, acc);
       } else if (along_y) {
-        march_runs<LDP, kR>(a.stencil + un.x, base, ldp, acc);
+        march_runs<LDP, R>(a.stencil + un.x, base, ldp, acc);
       } else {
-        march_runs<1, kR>(a.stencil + un.x, base, 1, acc);
+        march_runs<1, R>(a.stencil + un.x, base, 1, acc);
       }
     }
     const float r2 = (float)(dx * dx + dy * dy);
@@ -217,7 +225,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     // integral of |x_j - z|^{-1} over T_k (Remark REM: NEW KERNEL), per D
     const float wk = a.wtab ? __ldg(a.wtab + disp_index(dx, dy, n)) : a.wcoef * inv_r;
     // stored weights of D: its rectangle of targets, row-major (lanes along x
-    // write 128 contiguous bytes; lanes along y each write their 8 targets)
+    // write 128 contiguous bytes; lanes along y each write their R targets)
     long woff = 0;
     if constexpr (MODE != kApply) woff = a.doff[disp_index(dx, dy, n)];
     const int wx = xhi - xlo;
@@ -232,7 +240,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
     if constexpr (MODE == kStream) {
       // four targets at a time: their global loads are issued before their atomics
 #pragma unroll
-      for (int q0 = 0; q0 < kR; q0 += 4) {
+      for (int q0 = 0; q0 < R; q0 += 4) {
         float wv[4], sjv[4], skv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -260,7 +268,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < kR; ++q) {
+      for (int q = 0; q < R; ++q) {
         const int xq = along_y ? x : x + q, yq = along_y ? y + q : y;
         if (lvalid && (along_y ? yq < yhi : xq < xhi)) {
           const float wq = wk * exp2f(tscale * acc[q]);
@@ -275,6 +283,7 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
           }
         }
       }
+    }
     }
   }
   // every warp of this CTA is past its last unit before the CTA counts as done
@@ -294,26 +303,29 @@ __device__ __forceinline__ void disp_body(const DispArgs &a) {
   }
 }
 
-template <int LDP>
+template <int LDP, int R>
 __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp(DispArgs a) {
-  disp_body<LDP, kApply>(a);
+  disp_body<LDP, kApply, false, R>(a);
 }
 
-template <int LDP>
+template <int LDP, int R>
 __global__ void __launch_bounds__(kThreads, 1) k_store_disp(DispArgs a) {
-  disp_body<LDP, kStore>(a);
+  disp_body<LDP, kStore, false, R>(a);
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads, 1) k_stream_disp(DispArgs a) {
-  disp_body<1, kStream>(a);
+  disp_body<1, kStream, false, R>(a);
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads, 1) k_pairs_disp_global(DispArgs a) {
-  disp_body<kGlobalLdp, kApply, true>(a);
+  disp_body<disp_pitch(kGlobalMaxN, R), kApply, true, R>(a);
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads, 1) k_store_disp_global(DispArgs a) {
-  disp_body<kGlobalLdp, kStore, true>(a);
+  disp_body<disp_pitch(kGlobalMaxN, R), kStore, true, R>(a);
 }
 
 // bf16 bits of v rounded to nearest even (finite v), in integer arithmetic
@@ -608,31 +620,20 @@ __global__ void k_disp_source(long N, int n, int op, const double *__restrict__ 
 
 typedef void (*DispKernel)(DispArgs);
 
-// compile-time lattice pitches of the 64^2 and 128^2 grids
-constexpr int kLdp64 = (64 + 1 + kPad) | 1, kLdp128 = (128 + 1 + kPad) | 1;
+// compile-time lattice pitches of the 64^2 and 128^2 grids (stack depths
+// disp_depth(64) = 8 and disp_depth(128) = 12)
+constexpr int kLdp64 = disp_pitch(64, disp_depth(64)), kLdp128 = disp_pitch(128, disp_depth(128));
 
-DispKernel pick_disp(int ldp) {
-  switch (ldp) {
-    case kLdp64: return k_pairs_disp<kLdp64>;
-    case kLdp128: return k_pairs_disp<kLdp128>;
-    default: return k_pairs_disp<0>;
+// the shared-lattice apply (store) kernel of lattice pitch ldp, depth R
+DispKernel pick_disp(int ldp, int R, bool store) {
+  if (R == 8) {
+    if (ldp == kLdp64) return store ? k_store_disp<kLdp64, 8> : k_pairs_disp<kLdp64, 8>;
+    return store ? k_store_disp<0, 8> : k_pairs_disp<0, 8>;
   }
+  if (ldp == kLdp128) return store ? k_store_disp<kLdp128, 12> : k_pairs_disp<kLdp128, 12>;
+  return store ? k_store_disp<0, 12> : k_pairs_disp<0, 12>;
 }
 
-DispKernel pick_store(int ldp) {
-  switch (ldp) {
-    case kLdp64: return k_store_disp<kLdp64>;
-    case kLdp128: return k_store_disp<kLdp128>;
-    default: return k_store_disp<0>;
-  }
-}
-
-// lattice pitch: room for kPad stacked targets past the grid, odd so that 32
-// consecutive rows of one column fall in 32 different banks
-int disp_ldp(int n) {
-  const int p = n + 1 + kPad;
-  return p | 1;
-}
 
 struct Cell {
   int cx, cy;
@@ -678,14 +679,18 @@ void stencil_runs(const std::vector<Cell> &cells, bool along_y, std::vector<int>
 
 // A run of L cells is cut into ceil(L / kMaxChunk) chunks of equal length
 // (their lengths differ by at most one).  Estimated instructions per thread of
-// one unit: per chunk its record loads and loop, Lc + kR - 1 lattice loads,
-// the packed multiply-adds (kR / 2 per even tap, kR / 2 + 1 per odd one) and
-// a weight broadcast per tap; per unit the epilogue.
+// one unit of stack depth R: per chunk its record loads and loop, Lc + R - 1
+// lattice loads, the packed multiply-adds (R / 2 per even tap, R / 2 + 1 per
+// odd one) and a weight broadcast per tap; per unit the epilogue.
 struct Plan {
   long chunks, recs, cost;
 };
-long chunk_cost(int lc) {
-  return 4 + (lc + 4) / 4 + (lc + kR - 1) + ((lc + 1) / 2) * (kR / 2) + (lc / 2) * (kR / 2 + 1) + lc;
+long chunk_cost(int lc, int R) {
+  return 4 + (lc + 4) / 4 + (lc + R - 1) + ((lc + 1) / 2) * (R / 2) + (lc / 2) * (R / 2 + 1) + lc;
+}
+// estimated cost of all units of one D for stack `stack` across `lanes` lanes
+long axis_cost(const Plan &p, int lanes, int stack, int R) {
+  return (long)((lanes + 31) / 32) * ((stack + R - 1) / R) * p.cost;
 }
 template <typename F>
 void for_each_chunk(const std::vector<int> &starts, F f) {
@@ -699,12 +704,12 @@ void for_each_chunk(const std::vector<int> &starts, F f) {
     }
   }
 }
-Plan chunk_plan(const std::vector<int> &starts) {
-  Plan p{0, 0, 12L * kR + 40};
+Plan chunk_plan(const std::vector<int> &starts, int R) {
+  Plan p{0, 0, 12L * R + 40};
   for_each_chunk(starts, [&](int, int lc) {
     ++p.chunks;
     p.recs += (lc + 4) / 4;
-    p.cost += chunk_cost(lc);
+    p.cost += chunk_cost(lc, R);
   });
   return p;
 }
@@ -720,9 +725,9 @@ bool disp_expand_fits(int n, int device) {
   return expand_smem_bytes(n) <= (size_t)optin;
 }
 
-size_t disp_smem_bytes(int n) {
-  const long rows = n + 1 + kPad;
-  return sizeof(float) * (size_t)rows * disp_ldp(n) + 16;
+size_t disp_smem_bytes(int n, int R) {
+  const long rows = n + R;
+  return sizeof(float) * (size_t)rows * disp_pitch(n, R) + 16;
 }
 
 namespace {
@@ -731,7 +736,7 @@ namespace {
 // medium: they are built once per (device, n) and shared by every handle of
 // that size (kept after the last handle goes, at most kGeoKeep unused ones).
 struct Geometry {
-  int device = -1, n = 0, ldp = 0, global = 0, refs = 0;
+  int device = -1, n = 0, ldp = 0, global = 0, depth = 0, refs = 0;
   int4 *units = nullptr;
   float *stencil = nullptr;
   long long *doff = nullptr;  // first stored weight of each D (displacement-major storage)
@@ -766,7 +771,7 @@ void geometry_trim() {
 }
 
 // global: the lattice-in-global-memory layout (runs along x address lat_t)
-vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
+vie_status geometry_build(int n, int ldp, bool global, int R, Geometry *geo) {
   // stencils and work units, the run axis of each D chosen by estimated cost
   struct U {
     int4 u;
@@ -789,10 +794,8 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
       stencil_runs(cy_cells, true, cy_runs);
       stencil_cells(dx, dy, false, cx_cells);
       stencil_runs(cx_cells, false, cx_runs);
-      const long uy = (long)((wx + 31) / 32) * ((wy + kR - 1) / kR);
-      const long ux = (long)((wy + 31) / 32) * ((wx + kR - 1) / kR);
-      const Plan py = chunk_plan(cy_runs), px = chunk_plan(cx_runs);
-      const bool along_y = uy * py.cost <= ux * px.cost;
+      const Plan py = chunk_plan(cy_runs, R), px = chunk_plan(cx_runs, R);
+      const bool along_y = axis_cost(py, wx, wy, R) <= axis_cost(px, wy, wx, R);
       const std::vector<Cell> &cells = along_y ? cy_cells : cx_cells;
       taps += (double)cells.size() * wx * wy;
       const std::vector<int> &runs = along_y ? cy_runs : cx_runs;
@@ -823,20 +826,24 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
         return VIE_ERR_UNSUPPORTED;
       }
       const int lanes = along_y ? wx : wy, stack = along_y ? wy : wx;
-      const int nsb = (stack + kR - 1) / kR, full = lanes / 32, rem = lanes % 32;
+      // blocks of R stacked targets (the last one ragged); a unit carries
+      // its first row (offset along the stack)
+      const int nfb = (stack + R - 1) / R, full = lanes / 32, rem = lanes % 32;
       const int w = (along_y ? 1 : 0) | ((int)(pl.recs + 1) << 12);
       const int dxy = (dx & 0xffff) | (dy << 16);
-      for (int sb = 0; sb < nsb; ++sb)
-        for (int lb = 0; lb < full; ++lb) units.push_back({make_int4(off, dxy, lb | (sb << 16), w), pl.cost});
+      for (int sb = 0; sb < nfb; ++sb)
+        for (int lb = 0; lb < full; ++lb)
+          units.push_back({make_int4(off, dxy, lb | ((R * sb) << 16), w), pl.cost});
       if (rem > 0) {
-        // the ragged last lane block: 2 or 4 stack blocks share a warp when it
-        // is at most 16 or 8 lanes wide (stack blocks sb, sb + s, ...)
+        // the ragged last lane block: 2 or 4 blocks share a warp when it
+        // is at most 16 or 8 lanes wide (blocks sb, sb + s, ...; s =
+        // group_stride, as the kernel reads it)
         const int lg = rem <= 8 ? 2 : rem <= 16 ? 1 : 0, G = 1 << lg;
-        const int sstride = lg == 1 ? 2 : (ldp & 3);
+        const int sstride = group_stride(R, lg);
         const int span = lg == 0 ? 1 : G * sstride;
-        for (int base = 0; base < nsb; base += span)
-          for (int j = 0; j < (lg == 0 ? 1 : sstride) && base + j < nsb; ++j)
-            units.push_back({make_int4(off, dxy, full | ((base + j) << 16), w | (lg << 1)), pl.cost});
+        for (int base = 0; base < nfb; base += span)
+          for (int j = 0; j < (lg == 0 ? 1 : sstride) && base + j < nfb; ++j)
+            units.push_back({make_int4(off, dxy, full | ((R * (base + j)) << 16), w | (lg << 1)), pl.cost});
       }
     }
   for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
@@ -855,10 +862,10 @@ vie_status geometry_build(int n, int ldp, bool global, Geometry *geo) {
   return VIE_OK;
 }
 
-vie_status geometry_acquire(int device, int n, int ldp, bool global, Geometry **out) {
+vie_status geometry_acquire(int device, int n, int ldp, bool global, int R, Geometry **out) {
   std::lock_guard<std::mutex> lock(g_geo_mu);
   for (Geometry *g : g_geo)
-    if (g->device == device && g->n == n && g->ldp == ldp && g->global == (int)global) {
+    if (g->device == device && g->n == n && g->ldp == ldp && g->global == (int)global && g->depth == R) {
       ++g->refs;
       *out = g;
       return VIE_OK;
@@ -868,7 +875,8 @@ vie_status geometry_acquire(int device, int n, int ldp, bool global, Geometry **
   g->n = n;
   g->ldp = ldp;
   g->global = global;
-  const vie_status s = geometry_build(n, ldp, global, g);
+  g->depth = R;
+  const vie_status s = geometry_build(n, ldp, global, R, g);
   if (s != VIE_OK) {
     geometry_free(g);
     return s;
@@ -935,19 +943,24 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   if (n < 2 || n > 4096) return VIE_OK;
   DevProps prop;
   VIE_TRY(get_dev_props(device, &prop));
-  // the lattice in shared memory where it fits, else (n <= kGlobalMaxN) in
-  // global memory, read through L1
-  const bool global = disp_smem_bytes(n) > (size_t)prop.sharedMemPerBlockOptin;
+  // the lattice in shared memory where it fits (with the smaller stack
+  // depth's padding, if only that fits), else (n <= kGlobalMaxN) in global
+  // memory, read through L1
+  const size_t optin = (size_t)prop.sharedMemPerBlockOptin;
+  int R = disp_depth(n);
+  if (disp_smem_bytes(n, R) > optin && disp_smem_bytes(n, 8) <= optin) R = 8;
+  const bool global = disp_smem_bytes(n, R) > optin;
   if (global && n > kGlobalMaxN) return VIE_OK;
-  const int ldp = global ? kGlobalLdp : disp_ldp(n), rows = global ? kGlobalLdp : n + 1 + kPad;
-  const size_t smem = global ? 16 : disp_smem_bytes(n);
-  DispKernel k = global ? k_pairs_disp_global : pick_disp(ldp);
+  const int ldp = disp_pitch(global ? kGlobalMaxN : n, R), rows = global ? ldp : n + R;
+  const size_t smem = global ? 16 : disp_smem_bytes(n, R);
+  DispKernel k = global ? (R == 8 ? k_pairs_disp_global<8> : k_pairs_disp_global<12>) : pick_disp(ldp, R, false);
+  DispKernel ks = global ? (R == 8 ? k_store_disp_global<8> : k_store_disp_global<12>) : pick_disp(ldp, R, true);
+  DispKernel kst = R == 8 ? k_stream_disp<8> : k_stream_disp<12>;
   VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)smem)));
   if (global) {
     // all of the SM's unified memory it can get as L1 (a per-kernel preference)
     VIE_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-    VIE_CUDA(cudaFuncSetAttribute((const void *)k_store_disp_global, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  0));
+    VIE_CUDA(cudaFuncSetAttribute((const void *)ks, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
   }
   int bps = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads, smem));
@@ -956,15 +969,14 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   const long N = (long)n * n;
   const size_t smem_store = global ? 16 : sizeof(float) * (size_t)rows * ldp + 16;
   const size_t smem_stream = 16;
-  DispKernel ks = global ? k_store_disp_global : pick_store(ldp);
   VIE_TRY(raise_smem_limit((const void *)ks, (size_t)((int)smem_store)));
-  VIE_TRY(raise_smem_limit((const void *)k_stream_disp, (size_t)((int)smem_stream)));
+  VIE_TRY(raise_smem_limit((const void *)kst, (size_t)((int)smem_stream)));
   int bps_store = 0, bps_stream = 0;
   VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_store, ks, kThreads, smem_store));
-  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_stream, k_stream_disp, kThreads, smem_stream));
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_stream, kst, kThreads, smem_stream));
   if (bps_store < 1 || bps_stream < 1) return VIE_OK;
   Geometry *geo = nullptr;
-  vie_status s = geometry_acquire(device, n, ldp, global, &geo);
+  vie_status s = geometry_acquire(device, n, ldp, global, R, &geo);
   if (s != VIE_OK) return s;
   dp->geometry = geo;
   dp->doff = geo->doff;
@@ -1009,7 +1021,7 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   dp->kernel_store = (const void *)ks;
   dp->smem_store = smem_store;
   dp->grid_store = bps_store * prop.multiProcessorCount;
-  dp->kernel_stream = (const void *)k_stream_disp;
+  dp->kernel_stream = (const void *)kst;
   dp->smem_stream = smem_stream;
   dp->grid_stream = std::min(bps_stream * prop.multiProcessorCount, dp->grid);
   dp->stored = N * (N - 1) / 2;

@@ -181,7 +181,7 @@ vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const
                        float *src, float tau_scale2, float wcoef, double *y, cudaEvent_t mid0, cudaEvent_t mid1,
                        cudaStream_t st);
 
-size_t disp_smem_bytes(int n);
+size_t disp_smem_bytes(int n, int R);  // shared lattice bytes at stack depth R
 bool disp_expand_fits(int n, int device);  // k_expand_pairs has room for the grid (n <= 169)
 vie_status disp_source(const DispPlan &dp, long N, int op, const double *sigma_s, const double *g,
                        float *src, cudaStream_t st);
