@@ -869,10 +869,10 @@ def run_only(args):
     else:
         net = P.vie_unet_create(4, 32)
         P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
-        n = 256
-        x = torch.randn(3 * n * n, dtype=torch.float32, device=dev)
-        o = torch.empty(n * n, dtype=torch.float32, device=dev)
-        run = lambda: P.vie_unet_forward(net, x, o, 1, n, use_bf16=True)  # noqa: E731
+        n, B = args.unet_n, args.batch
+        x = torch.randn(B * 3 * n * n, dtype=torch.float32, device=dev)
+        o = torch.empty(B * n * n, dtype=torch.float32, device=dev)
+        run = lambda: P.vie_unet_forward(net, x, o, B, n, use_bf16=True)  # noqa: E731
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
@@ -924,6 +924,8 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32", "fmm"], default="otf")
+    ap.add_argument("--unet-n", type=int, default=256, help="--only unet: grid of the images")
+    ap.add_argument("--batch", type=int, default=1, help="--only unet: images per forward")
     ap.add_argument("--only", choices=["sweep", "batch", "unet"], default=None,
                     help="run one workload alone, for profilers")
     ap.add_argument("--disc", choices=["m3", "m2"], default="m3",

@@ -135,63 +135,92 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, lon
   }
 }
 
-// Tensor-core convolution tiles: 128 TMEM lanes (pixels) per CTA.
+// Tensor-core convolution tiles: 128 TMEM lanes (pixels) per tile.
 constexpr int kTcM = 128;
-
-__host__ __device__ constexpr int conv_tc_tmem_cols(int co) { return co <= 32 ? 32 : co <= 64 ? 64 : co <= 128 ? 128 : 256; }
 
 // The BF16 convolution as an implicit GEMM fed by the tensor memory
 // accelerator.  The input is first rounded to BF16 and laid out NHWC with its
-// channels padded to S slices of 32 (k_to_nhwc_bf16).  A CTA owns a tile of
-// 128 TMEM lanes = R rows x Wb pixels of one image (Wb = min(W, 128), R =
-// 128 / Wb); for each tap (dy, dx) and channel slice the A operand is the
-// input shifted by the tap: one TMA box (32 channels, Wb, R, 1) at (slice,
-// x0 + dx - 1, y0 + dy - 1, image), whose out-of-image part the TMA fills
-// with zeros -- exactly the zero padding of the convolution.  Its rows are
-// 64 bytes (32 BF16 along K), written with the 64-byte swizzle that the MMA's
-// K-major descriptor reads.  The B operand of the same step is the weights'
-// [Co][32] block of that tap and slice (packed by k_pack_tc_weights), also by
-// TMA.  All 9 S steps are in flight at once (one mbarrier each, so no stage
-// is reused); one thread issues two tcgen05.mma (M = 128, N = Co, K = 16) per
-// step as its operands land, accumulating in FP32 in tensor memory; each warp
-// then reads its 32 lanes, adds the bias (and relu) and writes FP32 NCHW.
-// Waits are bounded (wl; the first operand wait takes wl.first).  A CTA that
-// gives up stops issuing, waits (bounded by wl.limit) for the loads and
-// products it issued, writes NaN and sets *err.
+// channels padded to S slices of 32 (k_to_nhwc_bf16).  A tile is 128 TMEM
+// lanes = R rows x Wb pixels of one image (Wb = min(W, 128), R = 128 / Wb);
+// for each tap (dy, dx) and channel slice the A operand is the input shifted
+// by the tap: one TMA box (32 channels, Wb, R, 1) at (slice, x0 + dx - 1,
+// y0 + dy - 1, image), whose out-of-image part the TMA fills with zeros --
+// exactly the zero padding of the convolution.  Its rows are 64 bytes (32
+// BF16 along K), written with the 64-byte swizzle that the MMA's K-major
+// descriptor reads.  The B operand of the same step is the weights' [Co][32]
+// block of that tap and slice (packed by k_pack_tc_weights).
+//
+// Two CTAs per SM (half of its shared memory each) take tiles blockIdx.x,
+// blockIdx.x + G, ... in a warp-specialised pipeline: the weights are loaded once; warp 4 streams the A
+// boxes of its tiles into a ring of nst stages (a tile of one image row
+// takes, per slice, its 3 input rows once as boxes of Wb + 2 pixels, and the
+// MMAs read the 3 taps of a row at 64-byte offsets into them: a third of the
+// TMA rows; other tiles take one box per tap and slice); warp 5 issues two
+// tcgen05.mma (M = 128, N = Co, K = 16) per tap into one of kAcc tensor-
+// memory accumulators (FP32), committing each stage back to the producer and
+// each finished tile to the epilogue; warps 0-3 read their 32 lanes of a
+// finished accumulator, hand it back, add the bias (and relu) and write FP32
+// NCHW, while the next tiles' loads and products run.  Waits are bounded (wl;
+// the first operand wait takes wl.first).  On expiry the CTA stops issuing,
+// writes NaN for the tiles it has not finished, sets *err, waits (bounded by
+// wl.limit) for the loads and products it issued and frees its tensor memory.
 constexpr int kTmaSlice = 32;   // channels per K slice (64 bytes of BF16)
+constexpr int kAcc = 4;         // tensor-memory accumulators (Co <= 32 columns each)
+constexpr int kConvThreads = 192;
 
-size_t conv_tma_smem(int S, int Co) {
-  const size_t a = (size_t)9 * S * kTcM * 64, b = (size_t)9 * S * Co * 64;
-  return 1024 + a + b + 8 * (9 * S + 1) + 16;
+// one ring stage: a tap box of 128 pixels, or a halo box of Wb + 2 (Wb = 128)
+// rounded up to 1024 bytes
+__host__ __device__ inline int conv_stage_bytes(int Wb) { return Wb == kTcM ? 9216 : kTcM * 64; }
+// ring stages of a CTA with `budget` bytes of shared memory
+int conv_stages(int S, int Co, int Wb, size_t budget) {
+  const size_t b = (size_t)9 * S * Co * 64, fixed = 1024 + b + 1024;
+  if (budget <= fixed) return 0;
+  return (int)std::min<size_t>(32, (budget - fixed) / (size_t)conv_stage_bytes(Wb));
+}
+size_t conv_tma_smem(int S, int Co, int Wb, int nst) {
+  return 1024 + (size_t)9 * S * Co * 64 + (size_t)nst * conv_stage_bytes(Wb) + 8 * (2 * nst + 2 * kAcc + 2) + 16;
 }
 
 template <bool RELU>
-__global__ void __launch_bounds__(kTcM) k_conv3_tma(const __grid_constant__ CUtensorMap map_x,
-                                                    const __grid_constant__ CUtensorMap map_w,
-                                                    const float *__restrict__ bias, float *__restrict__ out,
-                                                    long out_bs, int Co, int H, int W, int S, int Wb, int R,
-                                                    int tiles_x, WaitLimits wl, int *err) {
+__global__ void __launch_bounds__(kConvThreads, 2)
+    k_conv3_tma(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+                const float *__restrict__ bias, float *__restrict__ out, long out_bs, int Co, int H, int W, int S,
+                int Wb, int R, int tiles_x, int tiles, int nst, WaitLimits wl, int *err) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
-  const int steps = 9 * S;
-  const int a_bytes = kTcM * 64, b_bytes = Co * 64;
-  unsigned char *As = smem, *Bs = smem + (size_t)steps * a_bytes;
-  unsigned long long *bars = (unsigned long long *)(Bs + (size_t)steps * b_bytes);  // steps, then done
-  unsigned *tmem_slot = (unsigned *)(bars + steps + 1);
+  // halo: tiles of one image row take, per slice, the 3 input rows once
+  // (Wb + 2 pixels each) and the 3 taps of a row as 64-byte offsets into
+  // that box; other tiles take one box per tap and slice
+  const bool halo = R == 1;
+  const int steps = (halo ? 3 : 9) * S, taps_step = halo ? 3 : 1;
+  const int tiles_img = tiles_x * ((H + R - 1) / R);
+  const int a_bytes = conv_stage_bytes(Wb), b_bytes = Co * 64;
+  unsigned char *Bs = smem, *As = smem + (size_t)9 * S * b_bytes;
+  unsigned long long *full = (unsigned long long *)(As + (size_t)nst * a_bytes);
+  unsigned long long *empty = full + nst, *tfull = empty + nst, *tempty = tfull + kAcc;
+  unsigned long long *wbar = tempty + kAcc, *done = wbar + 1;
+  unsigned *tmem_slot = (unsigned *)(done + 1);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x, img = blockIdx.y;
-  const int x0 = tx * Wb, y0 = ty * R;
-  const int tcols = conv_tc_tmem_cols(Co);
+  const int G = gridDim.x;
   if (tid == 0) {
-    for (int i = 0; i <= steps; ++i) mbar_init(su32(bars + i), 1);
+    for (int i = 0; i < nst; ++i) {
+      mbar_init(su32(full + i), 1);
+      mbar_init(su32(empty + i), 1);
+    }
+    for (int i = 0; i < kAcc; ++i) {
+      mbar_init(su32(tfull + i), 1);
+      mbar_init(su32(tempty + i), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(su32(wbar), 1);
+    mbar_init(su32(done), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(tcols)
+                 "r"(kAcc * 32)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -199,75 +228,136 @@ __global__ void __launch_bounds__(kTcM) k_conv3_tma(const __grid_constant__ CUte
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
-  int issued_loads = 0, issued_mma = 0;
-  if (tid == 0) {
-    // every step's operands at once: the box of the shifted input and the weights
-    const unsigned bytes = (unsigned)(kTmaSlice * 2 * Wb * R + b_bytes);
-    for (int k = 0; k < steps; ++k) {
-      const int tap = k / S, sl = k - tap * S;
-      const unsigned bar = su32(bars + k);
-      mbar_arrive_expect_tx(bar, bytes);
-      tma_load_4d(su32(As + (size_t)k * a_bytes), &map_x, bar, sl * kTmaSlice, x0 + tap % 3 - 1,
-                  y0 + tap / 3 - 1, img);
-      tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, bar, 0, k * Co);
-      ++issued_loads;
+  const unsigned box_bytes = (unsigned)(kTmaSlice * 2 * (halo ? Wb + 2 : Wb * R));
+  int issued_loads = 0;
+  if (warp == 4 && lane == 0) {
+    // TMA producer: the weights once, then every step's shifted input box
+    mbar_arrive_expect_tx(su32(wbar), (unsigned)(9 * S * b_bytes));
+    for (int k = 0; k < 9 * S; ++k) tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, su32(wbar), 0, k * Co);
+    int g = 0;
+    bool go = true;
+    for (int t = blockIdx.x; t < tiles && go; t += G) {
+      const int img = t / tiles_img, r = t - img * tiles_img;
+      const int x0 = (r % tiles_x) * Wb, y0 = (r / tiles_x) * R;
+      for (int k = 0; k < steps; ++k, ++g) {
+        const int st = g % nst, use = g / nst;
+        if (use > 0 && !mbar_wait(su32(empty + st), (use - 1) & 1, abort_flag, wl.limit)) {
+          atomicExch(err, 1);
+          *abort_flag = 1;
+          go = false;
+          break;
+        }
+        // step k: slice sl of input row dy (halo) or of tap (dy, dx)
+        const int q = k / S, sl = k - q * S;
+        const int dy = halo ? q : q / 3, dx = halo ? 0 : q % 3;
+        mbar_arrive_expect_tx(su32(full + st), box_bytes);
+        tma_load_4d(su32(As + (size_t)st * a_bytes), &map_x, su32(full + st), sl * kTmaSlice, x0 + dx - 1,
+                    y0 + dy - 1, img);
+        ++issued_loads;
+      }
     }
-  } else if (tid == 32) {
+  } else if (warp == 5 && lane == 0) {
+    // MMA issuer
     const unsigned idesc = idesc_bf16(kTcM, Co);
-    for (int k = 0; k < steps; ++k) {
-      if (!mbar_wait(su32(bars + k), 0, abort_flag, k == 0 ? wl.first : wl.limit)) {
-        atomicExch(err, 1);
-        *abort_flag = 1;
+    bool go = mbar_wait(su32(wbar), 0, abort_flag, wl.first);
+    int g = 0, j = 0;
+    for (int t = blockIdx.x; t < tiles && go; t += G, ++j) {
+      const int b = j % kAcc;
+      if (j >= kAcc && !mbar_wait(su32(tempty + b), (j / kAcc - 1) & 1, abort_flag, wl.limit)) {
+        go = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned a = su32(As + (size_t)k * a_bytes), b = su32(Bs + (size_t)k * b_bytes);
+      const unsigned d = tmem + (unsigned)(b * 32);
+      for (int k = 0; k < steps; ++k, ++g) {
+        const int st = g % nst;
+        if (!mbar_wait(su32(full + st), (g / nst) & 1, abort_flag, g == 0 ? wl.first : wl.limit)) {
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int q = k / S, sl = k - q * S;
+        for (int e = 0; e < taps_step; ++e) {
+          // tap (dy, dx): its weights, and its input rows e pixels into a halo box
+          const int tap = halo ? 3 * q + e : q;
+          const unsigned a = su32(As + (size_t)st * a_bytes) + 64u * (unsigned)e;
+          const unsigned bb = su32(Bs + (size_t)(tap * S + sl) * b_bytes);
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk)
-        mma_bf16(tmem, smem_desc_sw64(a + kk * 32), smem_desc_sw64(b + kk * 32), idesc,
-                 (k > 0 || kk > 0) ? 1u : 0u);
-      ++issued_mma;
+          for (int kk = 0; kk < 2; ++kk)
+            mma_bf16(d, smem_desc_sw64(a + kk * 32), smem_desc_sw64(bb + kk * 32), idesc,
+                     (k > 0 || e > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(su32(empty + st));  // the stage is free once these products finish
+      }
+      if (!go) break;
+      mma_commit(su32(tfull + b));     // the tile's accumulator is complete
     }
-    mma_commit(su32(bars + steps));  // the accumulator (and every product issued)
+    if (!go) {
+      atomicExch(err, 1);
+      *abort_flag = 1;
+    }
+    mma_commit(su32(done));            // every product this thread issued
+  } else if (warp < 4) {
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31
+    const int i = warp * 32 + lane;  // this thread's lane: pixel (x0 + i % Wb, y0 + i / Wb) of the tile
+    const long plane = (long)H * W;
+    float bv[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) bv[c] = c < Co ? bias[c] : 0.f;
+    int j = 0;
+    for (int t = blockIdx.x; t < tiles; t += G, ++j) {
+      const int b = j % kAcc;
+      const int img = t / tiles_img, r = t - img * tiles_img;
+      const int px = (r % tiles_x) * Wb + i % Wb, py = (r / tiles_x) * R + i / Wb;
+      const bool pvalid = i < Wb * R && px < W && py < H;
+      bool ok = *abort_flag == 0 && mbar_wait(su32(tfull + b), (j / kAcc) & 1, abort_flag, wl.limit);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+      float v[32];
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * 32);
+        tmem_ld16(ta, v);
+        if (Co > 16) tmem_ld16(ta + 16, v + 16);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(su32(tempty + b));  // the accumulator may be overwritten
+      } else if (lane == 0) {
+        atomicExch(err, 1);
+        *abort_flag = 1;
+      }
+      float *ob = out + img * out_bs + (long)py * W + px;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c >= Co) break;
+        float x = ok ? v[c] + bv[c] : __int_as_float(0x7fc00000);
+        if (RELU && ok) x = fmaxf(x, 0.f);
+        if (pvalid) ob[(long)c * plane] = x;
+      }
+    }
   }
   __syncwarp();
-  bool ok = mbar_wait(su32(bars + steps), 0, abort_flag, wl.limit);
-  ok = __syncthreads_and(ok && *abort_flag == 0) != 0;  // tcgen05.ld below must be warp-uniform
-  if (!ok && tid == 0) atomicExch(err, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int i = warp * 32 + lane;  // this thread's TMEM lane: pixel (x0 + i % Wb, y0 + i / Wb)
-  const int px = x0 + i % Wb, py = y0 + i / Wb;
-  const bool pvalid = i < Wb * R && px < W && py < H;
-  float *ob = out + img * out_bs + (long)py * W + px;
-  const long plane = (long)H * W;
-  for (int c0 = 0; c0 < Co; c0 += 16) {
-    float v[16];
-    if (ok) tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float x = ok ? v[j] + bias[c0 + j] : __int_as_float(0x7fc00000);
-      if (RELU && ok) x = fmaxf(x, 0.f);
-      if (pvalid) ob[(long)(c0 + j) * plane] = x;
-    }
-  }
   // everything issued has landed before shared and tensor memory are released
-  // (each barrier has one phase; bounded by the full limit)
-  if (tid == 0) {
+  // (bounded by the full limit): the producer waits for the weights and for
+  // the last load into each stage, the issuer for its last commit
+  if (warp == 4 && lane == 0) {
     const long long t0 = clock64();
-    for (int k = 0; k < issued_loads; ++k)
-      while (!mbar_test(su32(bars + k), 0) && clock64() - t0 < wl.limit) {
+    while (!mbar_test(su32(wbar), 0) && clock64() - t0 < wl.limit) {
+    }
+    for (int s = 0; s < nst && s < issued_loads; ++s) {
+      const int use = (issued_loads - 1 - s) / nst;
+      while (!mbar_test(su32(full + s), use & 1) && clock64() - t0 < wl.limit) {
       }
-  }
-  if (tid == 32) {
-    const long long t0 = clock64();
-    while (!mbar_test(su32(bars + steps), 0) && clock64() - t0 < wl.limit) {
     }
   }
-  (void)issued_mma;
+  if (warp == 5 && lane == 0) {
+    const long long t0 = clock64();
+    while (!mbar_test(su32(done), 0) && clock64() - t0 < wl.limit) {
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  if (warp == 5) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * 32) : "memory");
   }
 }
 
@@ -756,12 +846,14 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
   const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
   CUtensorMap mx, mw;
   {
-    const unsigned long long key[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
-                                       (unsigned long long)B};
+    // tiles of one row load halo boxes of Wb + 2 pixels (the kernel's halo mode)
+    const unsigned bw = R == 1 ? (unsigned)Wb + 2 : (unsigned)Wb;
+    const unsigned long long key[4] = {(unsigned long long)Cp | ((unsigned long long)bw << 32), (unsigned long long)W,
+                                       (unsigned long long)H, (unsigned long long)B};
     const unsigned long long dims[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
                                         (unsigned long long)B};
     const unsigned long long strides[3] = {2ull * Cp, 2ull * Cp * W, 2ull * Cp * W * H};
-    const unsigned box[4] = {(unsigned)kTmaSlice, (unsigned)Wb, (unsigned)R, 1u};
+    const unsigned box[4] = {(unsigned)kTmaSlice, bw, (unsigned)R, 1u};
     VIE_TRY(cached_map(u, u->nhwc, key, 4, dims, strides, box, &mx));
   }
   {
@@ -771,19 +863,42 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
     const unsigned box[2] = {(unsigned)kTmaSlice, (unsigned)Co};
     VIE_TRY(cached_map(u, wtc, key, 2, dims, strides, box, &mw));
   }
-  const size_t smem = conv_tma_smem(S, Co);
-  const void *k = relu ? (const void *)k_conv3_tma<true> : (const void *)k_conv3_tma<false>;
-  VIE_TRY(raise_smem_limit(k, smem));
   int dev = 0;
   VIE_CUDA(cudaGetDevice(&dev));
+  DevProps prop;
+  VIE_TRY(get_dev_props(dev, &prop));
+  // two CTAs per SM (two epilogues and issuers in flight), each with half of
+  // the SM's shared memory less the per-CTA reserve, where three stages fit;
+  // else one with all of it.  Measured with 64 images at 128^2: one CTA per
+  // SM 1.69 ms per forward, two 1.25, three 1.42, four 1.45.  (The occupancy
+  // query reports one CTA per SM for this kernel at any shared-memory size;
+  // two run side by side all the same, and a grid they could not share would
+  // only run in two waves, each CTA taking every G-th tile.)
+  const size_t optin = (size_t)prop.sharedMemPerBlockOptin;
+  int per_sm = 2, nst = conv_stages(S, Co, Wb, (optin + 1024) / 2 - 1024);
+  if (nst < 3) {
+    per_sm = 1;
+    nst = conv_stages(S, Co, Wb, optin);
+  }
+  if (nst < 2) {
+    set_error("BF16 convolution: not enough shared memory for two stages");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const size_t smem = conv_tma_smem(S, Co, Wb, nst);
+  const void *k = relu ? (const void *)k_conv3_tma<true> : (const void *)k_conv3_tma<false>;
+  VIE_TRY(raise_smem_limit(k, smem));
+  // all of the SM's unified memory as shared memory, so that two CTAs fit
+  VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const WaitLimits wl = wait_limits(dev);
-  const dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)B);
+  // per_sm CTAs per SM, each taking every G-th tile
+  const int tiles = tiles_x * tiles_y * B;
+  const int grid = std::min(tiles, per_sm * prop.multiProcessorCount);
   if (relu)
-    k_conv3_tma<true><<<grid, kTcM, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x, wl,
-                                               u->dev_err);
+    k_conv3_tma<true><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
+                                                        tiles, nst, wl, u->dev_err);
   else
-    k_conv3_tma<false><<<grid, kTcM, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x, wl,
-                                                u->dev_err);
+    k_conv3_tma<false><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
+                                                         tiles, nst, wl, u->dev_err);
   VIE_CHECK_LAUNCH("k_conv3_tma");
   return VIE_OK;
 }
