@@ -362,26 +362,27 @@ __global__ void __launch_bounds__(kConvThreads, 2)
 }
 
 // in: FP32 [B][Ci][plane] (image stride in_bs) -> BF16 [B][plane][Cp], rounded
-// to nearest even, channels Ci..Cp-1 zero.  One thread per (image, pixel, 8 channels).
+// to nearest even, channels Ci..Cp-1 zero.  One thread per (image, pixel):
+// a warp reads 32 consecutive pixels of a channel plane at a time and writes
+// its pixels' Cp channels as 16-byte groups.
 __global__ void k_to_nhwc_bf16(const float *__restrict__ in, long in_bs, int Ci, long plane, int Cp, int B,
                                __nv_bfloat16 *__restrict__ out) {
-  const int groups = Cp / 8;
-  const long total = (long)B * plane * groups;
+  const long total = (long)B * plane;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-    const int gq = (int)(t % groups);
-    const long pq = t / groups;
-    const long p = pq % plane;
-    const int b = (int)(pq / plane);
+    const long b = t / plane, p = t - b * plane;
     const float *src = in + b * in_bs + p;
-    unsigned w[4];
+    uint4 *dst = reinterpret_cast<uint4 *>(out + t * Cp);
+    for (int gq = 0; gq < Cp / 8; ++gq) {
+      unsigned w[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int c = gq * 8 + 2 * e;
-      const float lo = c < Ci ? src[(long)c * plane] : 0.f, hi = c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f;
-      const __nv_bfloat162 q = __floats2bfloat162_rn(lo, hi);
-      w[e] = *reinterpret_cast<const unsigned *>(&q);
+      for (int e = 0; e < 4; ++e) {
+        const int c = gq * 8 + 2 * e;
+        const float lo = c < Ci ? src[(long)c * plane] : 0.f, hi = c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f;
+        const __nv_bfloat162 q = __floats2bfloat162_rn(lo, hi);
+        w[e] = *reinterpret_cast<const unsigned *>(&q);
+      }
+      dst[gq] = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    *reinterpret_cast<uint4 *>(out + (pq * Cp + gq * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -529,51 +530,65 @@ __global__ void k_head_bwd_w(const float *__restrict__ go, const float *__restri
   }
 }
 
+// The 2x2 pooling and upsampling kernels take one thread per coarse pixel of
+// one plane (blockIdx.y = b C + c): 32-bit pixel arithmetic, the fine pixels
+// of a row pair as float2.  H, W: the fine size (even).
+__device__ __forceinline__ bool coarse_pixel(int H, int W, int C, int &b, int &c, int &y, int &x, int &q) {
+  const int Wo = W / 2;
+  q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (H / 2) * Wo) return false;
+  b = blockIdx.y / C;
+  c = blockIdx.y - b * C;
+  y = q / Wo;
+  x = q - y * Wo;
+  return true;
+}
+dim3 coarse_grid(int H, int W, int C, int B) { return dim3((unsigned)(((H / 2) * (W / 2) + 255) / 256), (unsigned)(B * C)); }
+
 __global__ void k_avgpool(const float *__restrict__ in, long in_bs, float *__restrict__ out, long out_bs,
                           int C, int H, int W, int B) {
-  const int Ho = H / 2, Wo = W / 2;
-  const long per = (long)C * Ho * Wo;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
-    const long b = i / per, r = i % per, c = r / ((long)Ho * Wo), q = r % ((long)Ho * Wo);
-    const long y = q / Wo, x = q % Wo;
-    const float *p = in + b * in_bs + c * (long)H * W + (2 * y) * W + 2 * x;
-    out[b * out_bs + c * (long)Ho * Wo + q] = 0.25f * (p[0] + p[1] + p[W] + p[W + 1]);
-  }
+  int b, c, y, x, q;
+  if (!coarse_pixel(H, W, C, b, c, y, x, q)) return;
+  const float *p = in + b * in_bs + (long)c * H * W + (long)(2 * y) * W + 2 * x;
+  const float2 r0 = *reinterpret_cast<const float2 *>(p), r1 = *reinterpret_cast<const float2 *>(p + W);
+  out[b * out_bs + (long)c * (H / 2) * (W / 2) + q] = 0.25f * (r0.x + r0.y + r1.x + r1.y);
 }
 
 // grad of avgpool: g_in (+)= g_out / 4 on each 2x2 block
 __global__ void k_avgpool_bwd(const float *__restrict__ go, long go_bs, float *__restrict__ gi, long gi_bs,
                               int C, int H, int W, int B, int accumulate) {
-  const long per = (long)C * H * W;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
-    const long b = i / per, r = i % per, c = r / ((long)H * W), q = r % ((long)H * W);
-    const long y = q / W, x = q % W;
-    const float v = 0.25f * go[b * go_bs + c * (long)(H / 2) * (W / 2) + (y / 2) * (W / 2) + x / 2];
-    float *dst = gi + b * gi_bs + c * (long)H * W + q;
-    *dst = accumulate ? *dst + v : v;
+  int b, c, y, x, q;
+  if (!coarse_pixel(H, W, C, b, c, y, x, q)) return;
+  const float v = 0.25f * go[b * go_bs + (long)c * (H / 2) * (W / 2) + q];
+  float2 *d0 = reinterpret_cast<float2 *>(gi + b * gi_bs + (long)c * H * W + (long)(2 * y) * W + 2 * x);
+  float2 *d1 = reinterpret_cast<float2 *>(reinterpret_cast<float *>(d0) + W);
+  if (accumulate) {
+    const float2 a0 = *d0, a1 = *d1;
+    *d0 = make_float2(a0.x + v, a0.y + v);
+    *d1 = make_float2(a1.x + v, a1.y + v);
+  } else {
+    *d0 = make_float2(v, v);
+    *d1 = make_float2(v, v);
   }
 }
 
 __global__ void k_upsample(const float *__restrict__ in, long in_bs, float *__restrict__ out, long out_bs,
                            int C, int H, int W, int B) {  // H, W: output size
-  const long per = (long)C * H * W;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
-    const long b = i / per, r = i % per, c = r / ((long)H * W), q = r % ((long)H * W);
-    const long y = q / W, x = q % W;
-    out[b * out_bs + c * (long)H * W + q] = in[b * in_bs + c * (long)(H / 2) * (W / 2) + (y / 2) * (W / 2) + x / 2];
-  }
+  int b, c, y, x, q;
+  if (!coarse_pixel(H, W, C, b, c, y, x, q)) return;
+  const float v = in[b * in_bs + (long)c * (H / 2) * (W / 2) + q];
+  float *o = out + b * out_bs + (long)c * H * W + (long)(2 * y) * W + 2 * x;
+  *reinterpret_cast<float2 *>(o) = make_float2(v, v);
+  *reinterpret_cast<float2 *>(o + W) = make_float2(v, v);
 }
 
 __global__ void k_upsample_bwd(const float *__restrict__ go, long go_bs, float *__restrict__ gi, long gi_bs,
                                int C, int H, int W, int B) {  // H, W: upsampled size
-  const int Hi = H / 2, Wi = W / 2;
-  const long per = (long)C * Hi * Wi;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)B * per; i += (long)gridDim.x * blockDim.x) {
-    const long b = i / per, r = i % per, c = r / ((long)Hi * Wi), q = r % ((long)Hi * Wi);
-    const long y = q / Wi, x = q % Wi;
-    const float *p = go + b * go_bs + c * (long)H * W + (2 * y) * W + 2 * x;
-    gi[b * gi_bs + c * (long)Hi * Wi + q] = p[0] + p[1] + p[W] + p[W + 1];
-  }
+  int b, c, y, x, q;
+  if (!coarse_pixel(H, W, C, b, c, y, x, q)) return;
+  const float *p = go + b * go_bs + (long)c * H * W + (long)(2 * y) * W + 2 * x;
+  const float2 r0 = *reinterpret_cast<const float2 *>(p), r1 = *reinterpret_cast<const float2 *>(p + W);
+  gi[b * gi_bs + (long)c * (H / 2) * (W / 2) + q] = r0.x + r0.y + r1.x + r1.y;
 }
 
 // g *= (a > 0): relu backward through a stored activation
@@ -840,7 +855,7 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
                      float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st) {
   const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
   const long plane = (long)H * W;
-  k_to_nhwc_bf16<<<gridn((long)B * plane * (Cp / 8)), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
+  k_to_nhwc_bf16<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
   VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
   const int Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
   const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
@@ -957,7 +972,7 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
                    true, st)) != VIE_OK)
       return s;
     if (l < L - 1) {
-      k_avgpool<<<gridn((long)B * C * hw / 4), 256, 0, st>>>(e, e_bs, u->xin[l + 1], (long)C * hw / 4, C, H,
+      k_avgpool<<<coarse_grid(H, H, C, B), 256, 0, st>>>(e, e_bs, u->xin[l + 1], (long)C * hw / 4, C, H,
                                                              H, B);
       VIE_CHECK_LAUNCH("k_avgpool");
       xl = u->xin[l + 1];
@@ -969,7 +984,7 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
   for (int l = L - 2; l >= 0; --l) {
     const int H = n >> l;
     const long hw = (long)H * H;
-    k_upsample<<<gridn((long)B * C * hw), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
+    k_upsample<<<coarse_grid(H, H, C, B), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
     VIE_CHECK_LAUNCH("k_upsample");
     const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
     if ((s = conv3(u, u->cat[l], 2L * C * hw, 2 * C, pw + c1.w_off, wtc(c1), u->p + c1.b_off, u->bl[l],
@@ -1044,7 +1059,7 @@ vie_status backward(UnetImpl *u, const float *x, int B, int n, cudaStream_t st) 
       return s;
     // upsample part of the concat -> gradient of d_{l+1}
     float *gnext = (l + 1 <= L - 2) ? u->gdl[l + 1] : u->gebot[0];
-    k_upsample_bwd<<<gridn((long)B * C * hw / 4), 256, 0, st>>>(u->gcat[l], 2L * C * hw, gnext, (long)C * hw / 4,
+    k_upsample_bwd<<<coarse_grid(H, H, C, B), 256, 0, st>>>(u->gcat[l], 2L * C * hw, gnext, (long)C * hw / 4,
                                                                  C, H, H, B);
     VIE_CHECK_LAUNCH("k_upsample_bwd");
   }
@@ -1063,7 +1078,7 @@ vie_status backward(UnetImpl *u, const float *x, int B, int n, cudaStream_t st) 
       e = u->cat[l] + (long)C * hw;
       e_bs = 2L * C * hw;
       // + pool path from level l+1's input gradient
-      k_avgpool_bwd<<<gridn((long)B * C * hw), 256, 0, st>>>(u->gx[l + 1], (long)C * hw / 4, ge, ge_bs, C, H, H,
+      k_avgpool_bwd<<<coarse_grid(H, H, C, B), 256, 0, st>>>(u->gx[l + 1], (long)C * hw / 4, ge, ge_bs, C, H, H,
                                                               B, 1);
       VIE_CHECK_LAUNCH("k_avgpool_bwd");
     } else {
