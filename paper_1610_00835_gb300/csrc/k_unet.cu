@@ -185,7 +185,8 @@ template <bool RELU>
 __global__ void __launch_bounds__(kConvThreads, 2)
     k_conv3_tma(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
                 const float *__restrict__ bias, float *__restrict__ out, long out_bs, int Co, int H, int W, int S,
-                int Wb, int R, int tiles_x, int tiles, int nst, WaitLimits wl, int *err) {
+                int Wb, int R, int tiles_x, int tiles, int nst, WaitLimits wl, int *err,
+                __nv_bfloat16 *__restrict__ out_h, long oh_bs, int oh_cp, int oh_c0) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
@@ -328,10 +329,26 @@ __global__ void __launch_bounds__(kConvThreads, 2)
       float *ob = out + img * out_bs + (long)py * W + px;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        if (c >= Co) break;
         float x = ok ? v[c] + bv[c] : __int_as_float(0x7fc00000);
         if (RELU && ok) x = fmaxf(x, 0.f);
-        if (pvalid) ob[(long)c * plane] = x;
+        v[c] = x;
+        if (c < Co && pvalid) ob[(long)c * plane] = x;
+      }
+      if (out_h && pvalid) {
+        // the same values in BF16 for the next convolution's NHWC input:
+        // channels oh_c0 .. oh_c0 + Co of this pixel, 16 bytes at a time
+        uint4 *hp = reinterpret_cast<uint4 *>(out_h + img * oh_bs + ((long)py * W + px) * oh_cp + oh_c0);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          if (8 * g8 >= Co) break;
+          unsigned w4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 q2 = __floats2bfloat162_rn(v[8 * g8 + 2 * e], v[8 * g8 + 2 * e + 1]);
+            w4[e] = *reinterpret_cast<const unsigned *>(&q2);
+          }
+          hp[g8] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
       }
     }
   }
@@ -591,6 +608,38 @@ __global__ void k_upsample_bwd(const float *__restrict__ go, long go_bs, float *
   gi[b * gi_bs + (long)c * (H / 2) * (W / 2) + q] = r0.x + r0.y + r1.x + r1.y;
 }
 
+// The decoder's upsampled half straight into its BF16 NHWC concatenation:
+// coarse FP32 planes (image stride in_bs) -> channels 0 .. C (C a multiple of
+// 8) of the 4 fine pixels of each coarse pixel, pixels o_cp channels apart.
+// One thread per (image, coarse pixel, group of 8 channels), the groups
+// fastest, so a warp's stores cover whole 16-byte runs of each fine pixel.
+// H, W: the fine size.
+__global__ void k_upsample_nhwc(const float *__restrict__ in, long in_bs, int C, int H, int W, int B,
+                                __nv_bfloat16 *__restrict__ out, long o_bs, int o_cp) {
+  const int Wc = W / 2, G8 = C / 8;
+  const long per = (long)(H / 2) * Wc;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)B * per * G8;
+       t += (long)gridDim.x * blockDim.x) {
+    const long pq = t / G8;
+    const int g8 = (int)(t - pq * G8);
+    const long b = pq / per;
+    const int q = (int)(pq - b * per), y = q / Wc, x = q - y * Wc;
+    const float *src = in + b * in_bs + (long)(8 * g8) * per + q;
+    unsigned w4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 q2 = __floats2bfloat162_rn(src[(long)(2 * e) * per], src[(long)(2 * e + 1) * per]);
+      w4[e] = *reinterpret_cast<const unsigned *>(&q2);
+    }
+    const uint4 v = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    __nv_bfloat16 *o = out + b * o_bs + ((long)(2 * y) * W + 2 * x) * o_cp + 8 * g8;
+    *reinterpret_cast<uint4 *>(o) = v;
+    *reinterpret_cast<uint4 *>(o + o_cp) = v;
+    *reinterpret_cast<uint4 *>(o + (long)W * o_cp) = v;
+    *reinterpret_cast<uint4 *>(o + (long)(W + 1) * o_cp) = v;
+  }
+}
+
 // g *= (a > 0): relu backward through a stored activation
 __global__ void k_relu_mask(float *__restrict__ g, long g_bs, const float *__restrict__ a, long a_bs,
                             long per, int B) {
@@ -730,6 +779,11 @@ struct UnetImpl {
   long ptc_elems = 0;
   bool ptc_dirty = true;
   __nv_bfloat16 *nhwc = nullptr;
+  // BF16 NHWC inputs written by the convolutions themselves: hx, a level's
+  // second convolution's input (C channels padded to slices); hcat[l], the
+  // decoder's concatenation at level l (the upsampled half, then the skip)
+  __nv_bfloat16 *hx = nullptr;
+  std::vector<__nv_bfloat16 *> hcat;
   std::vector<MapEntry> maps;
 };
 
@@ -749,6 +803,11 @@ void free_acts(UnetImpl *u) {
   if (u->h_part) cudaFreeHost(u->h_part);
   if (u->nhwc) cudaFree(u->nhwc);
   u->nhwc = nullptr;
+  if (u->hx) cudaFree(u->hx);
+  u->hx = nullptr;
+  for (__nv_bfloat16 *q : u->hcat)
+    if (q) cudaFree(q);
+  u->hcat.clear();
   u->maps.clear();
   u->o = u->go = nullptr;
   u->part = nullptr;
@@ -795,6 +854,16 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   // the widest convolution input: 2 C channels (a decoder's concatenation), padded to slices
   VIE_CUDA(cudaMalloc((void **)&u->nhwc,
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
+  // the hand-off buffers, zeroed once: their padding channels are never written
+  const size_t cp1 = (size_t)((C + 31) / 32) * 32, cp2 = (size_t)((2 * C + 31) / 32) * 32;
+  VIE_CUDA(cudaMalloc((void **)&u->hx, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
+  VIE_CUDA(cudaMemset(u->hx, 0, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
+  u->hcat.assign(L, nullptr);
+  for (int l = 0; l < L - 1; ++l) {
+    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)B * (n >> l) * (n >> l) * cp2;
+    VIE_CUDA(cudaMalloc((void **)&u->hcat[l], bytes));
+    VIE_CUDA(cudaMemset(u->hcat[l], 0, bytes));
+  }
   u->B = B;
   u->n = n;
   return VIE_OK;
@@ -849,14 +918,34 @@ vie_status cached_map(UnetImpl *u, const void *base, const unsigned long long (&
   return VIE_OK;
 }
 
+// the BF16 convolutions the tensor-core kernel takes
+bool conv_on_tensor_cores(const void *wtc, int Ci, int Co, const float *bias) {
+  return wtc && Co % 16 == 0 && Co >= 16 && Co <= 32 && Ci <= 2 * kTmaSlice && bias;
+}
+
 // The BF16 3x3 convolution on the tensor cores (k_conv3_tma): input to BF16
 // NHWC, then the implicit GEMM.  wtc: the layer's packed weights.
+// Fused NHWC hand-off between convolutions (all optional): in_h, the input
+// already in BF16 NHWC with S 32-channel slices (else `in` is converted);
+// out_h, a second output in BF16 NHWC at channel oh_c0 of pixels oh_cp
+// channels apart (image stride oh_bs elements).
+struct NhwcIo {
+  const __nv_bfloat16 *in_h = nullptr;
+  __nv_bfloat16 *out_h = nullptr;
+  long oh_bs = 0;
+  int oh_cp = 0, oh_c0 = 0;
+  bool wrote = false;  // set when out_h was written
+};
+
 vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __nv_bfloat16 *wtc, const float *bias,
-                     float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+                     float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st, NhwcIo *io) {
   const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
   const long plane = (long)H * W;
-  k_to_nhwc_bf16<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
-  VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
+  const __nv_bfloat16 *src = io && io->in_h ? io->in_h : u->nhwc;
+  if (src == u->nhwc) {
+    k_to_nhwc_bf16<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
+    VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
+  }
   const int Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
   const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
   CUtensorMap mx, mw;
@@ -869,7 +958,7 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
                                         (unsigned long long)B};
     const unsigned long long strides[3] = {2ull * Cp, 2ull * Cp * W, 2ull * Cp * W * H};
     const unsigned box[4] = {(unsigned)kTmaSlice, bw, (unsigned)R, 1u};
-    VIE_TRY(cached_map(u, u->nhwc, key, 4, dims, strides, box, &mx));
+    VIE_TRY(cached_map(u, src, key, 4, dims, strides, box, &mx));
   }
   {
     const unsigned long long key[4] = {(unsigned long long)S, (unsigned long long)Co, 0ull, 1ull};
@@ -908,23 +997,29 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
   // per_sm CTAs per SM, each taking every G-th tile
   const int tiles = tiles_x * tiles_y * B;
   const int grid = std::min(tiles, per_sm * prop.multiProcessorCount);
+  __nv_bfloat16 *oh = io ? io->out_h : nullptr;
+  const long oh_bs = io ? io->oh_bs : 0;
+  const int oh_cp = io ? io->oh_cp : 0, oh_c0 = io ? io->oh_c0 : 0;
   if (relu)
     k_conv3_tma<true><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
-                                                        tiles, nst, wl, u->dev_err);
+                                                        tiles, nst, wl, u->dev_err, oh, oh_bs, oh_cp, oh_c0);
   else
     k_conv3_tma<false><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
-                                                         tiles, nst, wl, u->dev_err);
+                                                         tiles, nst, wl, u->dev_err, oh, oh_bs, oh_cp, oh_c0);
+  if (io) io->wrote = oh != nullptr;
   VIE_CHECK_LAUNCH("k_conv3_tma");
   return VIE_OK;
 }
 
+// io (tensor-core path only; ignored, with io->wrote false, on the CUDA cores)
 template <typename WT>
 vie_status conv3(UnetImpl *u, const float *in, long in_bs, int Ci, const WT *w, const __nv_bfloat16 *wtc,
                  const float *bias, float *out, long out_bs, int Co, int H, int W, int B, bool relu,
-                 cudaStream_t st) {
+                 cudaStream_t st, NhwcIo *io = nullptr) {
+  if (io) io->wrote = false;
   if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
-    if (wtc && Co % 16 == 0 && Co >= 16 && Co <= 32 && Ci <= 2 * kTmaSlice && bias)
-      return conv3_tma(u, in, in_bs, Ci, wtc, bias, out, out_bs, Co, H, W, B, relu, st);
+    if (conv_on_tensor_cores(wtc, Ci, Co, bias))
+      return conv3_tma(u, in, in_bs, Ci, wtc, bias, out, out_bs, Co, H, W, B, relu, st, io);
   }
   if (relu)
     conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
@@ -959,18 +1054,39 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
   auto wtc = [&](const ConvLayer &c) { return tc ? u->ptc + c.tc_off : nullptr; };
   const float *xl = x;
   long xl_bs = 3L * n * n;
+  // BF16 NHWC hand-off (tensor-core path): each convolution also writes the
+  // next one's input, and the encoder's second convolution its skip into the
+  // decoder's concatenation
+  const int cp1 = ((C + 31) / 32) * 32, cp2 = ((2 * C + 31) / 32) * 32;
+  const bool handoff = tc && C % 8 == 0;
+  std::vector<char> skip_h(L, 0);
   for (int l = 0; l < L; ++l) {
     const int H = n >> l;
     const long hw = (long)H * H;
     const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
+    NhwcIo io1;
+    if (handoff) {
+      io1.out_h = u->hx;
+      io1.oh_bs = hw * cp1;
+      io1.oh_cp = cp1;
+    }
     if ((s = conv3(u, xl, xl_bs, c1.ci, pw + c1.w_off, wtc(c1), u->p + c1.b_off, u->a[l], (long)C * hw, C, H,
-                   H, B, true, st)) != VIE_OK)
+                   H, B, true, st, &io1)) != VIE_OK)
       return s;
     float *e = l < L - 1 ? u->cat[l] + (long)C * hw : u->ebot[0];
     const long e_bs = l < L - 1 ? 2L * C * hw : (long)C * hw;
+    NhwcIo io2;
+    io2.in_h = io1.wrote ? u->hx : nullptr;
+    if (handoff && l < L - 1) {
+      io2.out_h = u->hcat[l];
+      io2.oh_bs = hw * cp2;
+      io2.oh_cp = cp2;
+      io2.oh_c0 = C;
+    }
     if ((s = conv3(u, u->a[l], (long)C * hw, C, pw + c2.w_off, wtc(c2), u->p + c2.b_off, e, e_bs, C, H, H, B,
-                   true, st)) != VIE_OK)
+                   true, st, &io2)) != VIE_OK)
       return s;
+    skip_h[l] = io2.wrote;
     if (l < L - 1) {
       k_avgpool<<<coarse_grid(H, H, C, B), 256, 0, st>>>(e, e_bs, u->xin[l + 1], (long)C * hw / 4, C, H,
                                                              H, B);
@@ -984,14 +1100,31 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
   for (int l = L - 2; l >= 0; --l) {
     const int H = n >> l;
     const long hw = (long)H * H;
-    k_upsample<<<coarse_grid(H, H, C, B), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
-    VIE_CHECK_LAUNCH("k_upsample");
     const ConvLayer &c1 = u->layers[li++], &c2 = u->layers[li++];
+    NhwcIo io1, io2;
+    if (skip_h[l] && conv_on_tensor_cores(wtc(c1), c1.ci, c1.co, u->p + c1.b_off)) {
+      // the upsampled half in BF16 beside the skip the encoder wrote; the FP32
+      // concatenation's first half is not written (vie_unet_layer_io rebuilds it)
+      const long per = hw / 4;
+      k_upsample_nhwc<<<gridn((long)B * per * (C / 8)), 256, 0, st>>>(d, d_bs, C, H, H, B, u->hcat[l], hw * cp2,
+                                                                      cp2);
+      VIE_CHECK_LAUNCH("k_upsample_nhwc");
+      io1.in_h = u->hcat[l];
+    } else {
+      k_upsample<<<coarse_grid(H, H, C, B), 256, 0, st>>>(d, d_bs, u->cat[l], 2L * C * hw, C, H, H, B);
+      VIE_CHECK_LAUNCH("k_upsample");
+    }
+    if (handoff) {
+      io1.out_h = u->hx;
+      io1.oh_bs = hw * cp1;
+      io1.oh_cp = cp1;
+    }
     if ((s = conv3(u, u->cat[l], 2L * C * hw, 2 * C, pw + c1.w_off, wtc(c1), u->p + c1.b_off, u->bl[l],
-                   (long)C * hw, C, H, H, B, true, st)) != VIE_OK)
+                   (long)C * hw, C, H, H, B, true, st, &io1)) != VIE_OK)
       return s;
+    io2.in_h = io1.wrote ? u->hx : nullptr;
     if ((s = conv3(u, u->bl[l], (long)C * hw, C, pw + c2.w_off, wtc(c2), u->p + c2.b_off, u->dl[l],
-                   (long)C * hw, C, H, H, B, true, st)) != VIE_OK)
+                   (long)C * hw, C, H, H, B, true, st, &io2)) != VIE_OK)
       return s;
     d = u->dl[l];
     d_bs = (long)C * hw;
@@ -1358,6 +1491,13 @@ vie_status vie_unet_layer_io(vie_unet *u, int layer, float *in, float *out, void
       src_in = U.cat[l];
       in_bs = 2L * C * hw;
       src_out = U.bl[l];
+      if (in) {
+        // the BF16 forward hands the upsampled half to the convolution in
+        // BF16 only: rebuild its FP32 copy from the level below
+        const float *d = l == L - 2 ? U.ebot[0] : U.dl[l + 1];
+        k_upsample<<<coarse_grid(H, H, C, B), 256, 0, st>>>(d, (long)C * hw / 4, U.cat[l], 2L * C * hw, C, H, H, B);
+        VIE_CHECK_LAUNCH("k_upsample");
+      }
     } else {
       src_in = U.bl[l];
       in_bs = (long)C * hw;
