@@ -866,6 +866,13 @@ def run_only(args):
         g = torch.as_tensor(np.concatenate([m.f for m in media]), dtype=torch.float64, device=dev)
         y = torch.empty_like(g)
         run = lambda: P.vie_batch_apply(b, P.VIE_OP_K_SIGMA_S, g, y)  # noqa: E731
+    elif args.only == "train":
+        # one training step of the U-Net (FP32 forward, backward, Adam) on random images
+        net = P.vie_unet_create(4, 32)
+        n, B = args.unet_n, args.batch
+        x = torch.randn(B * 3 * n * n, dtype=torch.float32, device=dev)
+        t = torch.randn(B * n * n, dtype=torch.float32, device=dev)
+        run = lambda: P.vie_unet_train_step(net, x, t, B, n, 1e-4)  # noqa: E731
     else:
         net = P.vie_unet_create(4, 32)
         P.vie_unet_load(net, os.path.join(ROOT, "paper_1610_00835_gb300", "data", "unet_l4_c32.bin"))
@@ -924,9 +931,9 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--operator", choices=["otf", "fp32", "bf16x3", "pairs32", "sym32", "fmm"], default="otf")
-    ap.add_argument("--unet-n", type=int, default=256, help="--only unet: grid of the images")
-    ap.add_argument("--batch", type=int, default=1, help="--only unet: images per forward")
-    ap.add_argument("--only", choices=["sweep", "batch", "unet"], default=None,
+    ap.add_argument("--unet-n", type=int, default=256, help="--only unet / train: grid of the images")
+    ap.add_argument("--batch", type=int, default=1, help="--only unet / train: images per forward")
+    ap.add_argument("--only", choices=["sweep", "batch", "unet", "train"], default=None,
                     help="run one workload alone, for profilers")
     ap.add_argument("--disc", choices=["m3", "m2"], default="m3",
                     help="apply-only: discretisation M-iii (default) or M-ii (2D)")

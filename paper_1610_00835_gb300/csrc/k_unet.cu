@@ -172,18 +172,25 @@ constexpr int kConvThreads = 192;
 // rounded up to 1024 bytes
 __host__ __device__ inline int conv_stage_bytes(int Wb) { return Wb == kTcM ? 9216 : kTcM * 64; }
 // ring stages of a CTA with `budget` bytes of shared memory
-int conv_stages(int S, int Co, int Wb, size_t budget) {
-  const size_t b = (size_t)9 * S * Co * 64, fixed = 1024 + b + 1024;
+// (np = 2: split precision, operands in two parts)
+int conv_stages(int S, int Co, int Wb, size_t budget, int np = 1) {
+  const size_t b = (size_t)np * 9 * S * Co * 64, fixed = 1024 + b + 1024;
   if (budget <= fixed) return 0;
-  return (int)std::min<size_t>(32, (budget - fixed) / (size_t)conv_stage_bytes(Wb));
+  return (int)std::min<size_t>(32, (budget - fixed) / ((size_t)np * conv_stage_bytes(Wb)));
 }
-size_t conv_tma_smem(int S, int Co, int Wb, int nst) {
-  return 1024 + (size_t)9 * S * Co * 64 + (size_t)nst * conv_stage_bytes(Wb) + 8 * (2 * nst + 2 * kAcc + 2) + 16;
+size_t conv_tma_smem(int S, int Co, int Wb, int nst, int np = 1) {
+  return 1024 + (size_t)np * 9 * S * Co * 64 + (size_t)nst * np * conv_stage_bytes(Wb) + 8 * (2 * nst + 2 * kAcc + 2) +
+         16;
 }
 
-template <bool RELU>
+// SPLIT: the FP32 convolution of training in split precision: input and
+// weights each as BF16 hi + lo (map_xl, map_wl the lo halves), every tap
+// three products hi hi + hi lo + lo hi into the FP32 accumulator (lo lo, below
+// 2^-16 of the terms, left out); a stage holds the hi box, then the lo box.
+template <bool RELU, bool SPLIT>
 __global__ void __launch_bounds__(kConvThreads, 2)
     k_conv3_tma(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+                const __grid_constant__ CUtensorMap map_xl, const __grid_constant__ CUtensorMap map_wl,
                 const float *__restrict__ bias, float *__restrict__ out, long out_bs, int Co, int H, int W, int S,
                 int Wb, int R, int tiles_x, int tiles, int nst, WaitLimits wl, int *err,
                 __nv_bfloat16 *__restrict__ out_h, long oh_bs, int oh_cp, int oh_c0) {
@@ -196,8 +203,10 @@ __global__ void __launch_bounds__(kConvThreads, 2)
   const bool halo = R == 1;
   const int steps = (halo ? 3 : 9) * S, taps_step = halo ? 3 : 1;
   const int tiles_img = tiles_x * ((H + R - 1) / R);
-  const int a_bytes = conv_stage_bytes(Wb), b_bytes = Co * 64;
-  unsigned char *Bs = smem, *As = smem + (size_t)9 * S * b_bytes;
+  constexpr int NP = SPLIT ? 2 : 1;  // operand parts
+  const int a_part = conv_stage_bytes(Wb), a_bytes = NP * a_part, b_bytes = Co * 64;
+  unsigned char *Bs = smem, *Bl = smem + (size_t)9 * S * b_bytes;
+  unsigned char *As = smem + (size_t)NP * 9 * S * b_bytes;
   unsigned long long *full = (unsigned long long *)(As + (size_t)nst * a_bytes);
   unsigned long long *empty = full + nst, *tfull = empty + nst, *tempty = tfull + kAcc;
   unsigned long long *wbar = tempty + kAcc, *done = wbar + 1;
@@ -233,8 +242,11 @@ __global__ void __launch_bounds__(kConvThreads, 2)
   int issued_loads = 0;
   if (warp == 4 && lane == 0) {
     // TMA producer: the weights once, then every step's shifted input box
-    mbar_arrive_expect_tx(su32(wbar), (unsigned)(9 * S * b_bytes));
-    for (int k = 0; k < 9 * S; ++k) tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, su32(wbar), 0, k * Co);
+    mbar_arrive_expect_tx(su32(wbar), (unsigned)(NP * 9 * S * b_bytes));
+    for (int k = 0; k < 9 * S; ++k) {
+      tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, su32(wbar), 0, k * Co);
+      if (SPLIT) tma_load_2d(su32(Bl + (size_t)k * b_bytes), &map_wl, su32(wbar), 0, k * Co);
+    }
     int g = 0;
     bool go = true;
     for (int t = blockIdx.x; t < tiles && go; t += G) {
@@ -251,9 +263,12 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         // step k: slice sl of input row dy (halo) or of tap (dy, dx)
         const int q = k / S, sl = k - q * S;
         const int dy = halo ? q : q / 3, dx = halo ? 0 : q % 3;
-        mbar_arrive_expect_tx(su32(full + st), box_bytes);
+        mbar_arrive_expect_tx(su32(full + st), NP * box_bytes);
         tma_load_4d(su32(As + (size_t)st * a_bytes), &map_x, su32(full + st), sl * kTmaSlice, x0 + dx - 1,
                     y0 + dy - 1, img);
+        if (SPLIT)
+          tma_load_4d(su32(As + (size_t)st * a_bytes + a_part), &map_xl, su32(full + st), sl * kTmaSlice,
+                      x0 + dx - 1, y0 + dy - 1, img);
         ++issued_loads;
       }
     }
@@ -284,9 +299,15 @@ __global__ void __launch_bounds__(kConvThreads, 2)
           const unsigned a = su32(As + (size_t)st * a_bytes) + 64u * (unsigned)e;
           const unsigned bb = su32(Bs + (size_t)(tap * S + sl) * b_bytes);
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
+          for (int kk = 0; kk < 2; ++kk) {
             mma_bf16(d, smem_desc_sw64(a + kk * 32), smem_desc_sw64(bb + kk * 32), idesc,
                      (k > 0 || e > 0 || kk > 0) ? 1u : 0u);
+            if (SPLIT) {
+              const unsigned al = a + (unsigned)a_part, bl = su32(Bl + (size_t)(tap * S + sl) * b_bytes);
+              mma_bf16(d, smem_desc_sw64(a + kk * 32), smem_desc_sw64(bl + kk * 32), idesc, 1u);
+              mma_bf16(d, smem_desc_sw64(al + kk * 32), smem_desc_sw64(bb + kk * 32), idesc, 1u);
+            }
+          }
         }
         mma_commit(su32(empty + st));  // the stage is free once these products finish
       }
@@ -304,7 +325,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const long plane = (long)H * W;
     float bv[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) bv[c] = c < Co ? bias[c] : 0.f;
+    for (int c = 0; c < 32; ++c) bv[c] = bias && c < Co ? bias[c] : 0.f;
     int j = 0;
     for (int t = blockIdx.x; t < tiles; t += G, ++j) {
       const int b = j % kAcc;
@@ -418,16 +439,63 @@ __global__ void k_pack_tc_weights(const float *__restrict__ w, int Co, int Ci, i
   }
 }
 
+// The split-precision operands of training: v = hi + lo, hi = bf16(v),
+// lo = bf16(v - hi) (v - hi is exact in FP32), 16 significant bits in all.
+// Input: FP32 [B][Ci][plane] -> hi, lo BF16 [B][plane][Cp], one thread per
+// (image, pixel) as in k_to_nhwc_bf16.
+__global__ void k_to_nhwc_split(const float *__restrict__ in, long in_bs, int Ci, long plane, int Cp, int B,
+                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+  const long total = (long)B * plane;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / plane, p = t - b * plane;
+    const float *src = in + b * in_bs + p;
+    uint4 *dh = reinterpret_cast<uint4 *>(hi + t * Cp), *dl = reinterpret_cast<uint4 *>(lo + t * Cp);
+    for (int gq = 0; gq < Cp / 8; ++gq) {
+      unsigned wh[4], wl[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = gq * 8 + 2 * e;
+        const float v0 = c < Ci ? src[(long)c * plane] : 0.f, v1 = c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        wh[e] = *reinterpret_cast<const unsigned *>(&h2);
+        wl[e] = *reinterpret_cast<const unsigned *>(&l2);
+      }
+      dh[gq] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+      dl[gq] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    }
+  }
+}
+
+// Weights FP32 [Co][Ci][9], output channels co0 .. co0 + cb -> hi, lo BF16
+// [9 S][cb][32] in k_pack_tc_weights's block order.
+__global__ void k_pack_split_weights(const float *__restrict__ w, int Co, int Ci, int S, int co0, int cb,
+                                     __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+  const long total = (long)9 * S * cb * kTmaSlice;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % kTmaSlice);
+    const long r = t / kTmaSlice;
+    const int co = co0 + (int)(r % cb);
+    const int k = (int)(r / cb);
+    const int tap = k / S, ci = (k - tap * S) * kTmaSlice + c;
+    const float v = ci < Ci && co < Co ? w[((long)co * Ci + ci) * 9 + tap] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[t] = h;
+    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 // Gradient of a 3x3 convolution's weights and bias over one 32 x 8 pixel tile
-// of one image and 8 input channels; thread (co, ci) keeps its 9 taps and
-// accumulates them into dw with atomics.  A 3 x 3 window of the input slides
-// along x in registers.
+// of images b0 .. b1 and 8 input channels; thread (co, ci) keeps its 9 taps
+// over those images and adds them into dw with atomics once.  A 3 x 3 window
+// of the input slides along x in registers.
 constexpr int WY = 8;
 __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, long x_bs, int Ci,
                                                   const float *__restrict__ gy, long g_bs, int Co,
                                                   int H, int W, float *__restrict__ dw,
                                                   float *__restrict__ db, int ci_blocks,
-                                                  int co_blocks) {
+                                                  int co_blocks, int B, int b_splits) {
   __shared__ float g_s[COB][WY * TX + 1];
   __shared__ float x_s[CIB][WY + 2][TX + 2];
   const int co_l = threadIdx.x % 32, ci_l = threadIdx.x / 32;
@@ -436,9 +504,16 @@ __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, l
   const int cib = z % ci_blocks;
   z /= ci_blocks;
   const int cob = z % co_blocks;
-  const int b = z / co_blocks;
+  const int bs = z / co_blocks;
   const int ci0 = cib * CIB, co0 = cob * COB;
   const long plane = (long)H * W;
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  float bsum = 0.f;
+  const int b_lo = (int)((long)B * bs / b_splits), b_hi = (int)((long)B * (bs + 1) / b_splits);
+  for (int b = b_lo; b < b_hi; ++b) {
+  if (b > b_lo) __syncthreads();  // the previous image's tiles are consumed
   for (int i = threadIdx.x; i < COB * WY * TX; i += 256) {
     const int c = i / (WY * TX), p = i % (WY * TX);
     const int yy = p / TX, xx = p % TX;
@@ -457,10 +532,6 @@ __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, l
     x_s[c][yy][xx] = v;
   }
   __syncthreads();
-  float acc[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
-  float bsum = 0.f;
   for (int yy = 0; yy < WY; ++yy) {
     float win[3][3];
 #pragma unroll
@@ -483,6 +554,7 @@ __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, l
         win[r][1] = win[r][2];
       }
     }
+  }
   }
   const int co = co0 + co_l, ci = ci0 + ci_l;
   if (co < Co && ci < Ci) {
@@ -523,14 +595,18 @@ __global__ void k_head_bwd_data(const float *__restrict__ go, int C, const float
   }
 }
 
+// Gradient of the 1x1 head's weights and bias in two passes, deterministic:
+// block (c, k) sums channel c's products (c == C: the bias) over the k-th of
+// gridDim.y slices of the B planes into part[c][k]; k_head_bwd_w_finish adds
+// each channel's slices in order.
 __global__ void k_head_bwd_w(const float *__restrict__ go, const float *__restrict__ d, long d_bs, int C,
-                             long plane, int B, float *__restrict__ dw, float *__restrict__ db) {
-  // one block per channel (+ one for the bias)
-  __shared__ float red[256];
-  const int c = blockIdx.x;
-  float s = 0.f;
-  for (long i = threadIdx.x; i < (long)B * plane; i += blockDim.x) {
-    const long b = i / plane, p = i % plane;
+                             long plane, int B, double *__restrict__ part) {
+  __shared__ double red[256];
+  const int c = blockIdx.x, k = blockIdx.y, K = gridDim.y;
+  const long total = (long)B * plane, i0 = total * k / K, i1 = total * (k + 1) / K;
+  float s = 0.f;  // a few dozen terms per thread in FP32; the block's sum in FP64
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const long b = i / plane, p = i - b * plane;
     s += go[i] * (c < C ? d[b * d_bs + c * plane + p] : 1.f);
   }
   red[threadIdx.x] = s;
@@ -539,12 +615,19 @@ __global__ void k_head_bwd_w(const float *__restrict__ go, const float *__restri
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (c < C)
-      dw[c] += red[0];
-    else
-      db[0] += red[0];
-  }
+  if (threadIdx.x == 0) part[c * K + k] = red[0];
+}
+
+__global__ void k_head_bwd_w_finish(const double *__restrict__ part, int C, int K, float *__restrict__ dw,
+                                    float *__restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > C) return;
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += part[c * K + k];
+  if (c < C)
+    dw[c] += (float)s;
+  else
+    db[0] += (float)s;
 }
 
 // The 2x2 pooling and upsampling kernels take one thread per coarse pixel of
@@ -784,6 +867,11 @@ struct UnetImpl {
   // decoder's concatenation at level l (the upsampled half, then the skip)
   __nv_bfloat16 *hx = nullptr;
   std::vector<__nv_bfloat16 *> hcat;
+  // the input-gradient convolutions of training on the tensor cores (split
+  // precision): the lo half of the converted input, the split weights of
+  // one 32-channel output block
+  bool train_tc = false;
+  __nv_bfloat16 *nhwc_lo = nullptr, *wsp_hi = nullptr, *wsp_lo = nullptr;
   std::vector<MapEntry> maps;
 };
 
@@ -805,6 +893,10 @@ void free_acts(UnetImpl *u) {
   u->nhwc = nullptr;
   if (u->hx) cudaFree(u->hx);
   u->hx = nullptr;
+  if (u->nhwc_lo) cudaFree(u->nhwc_lo);
+  if (u->wsp_hi) cudaFree(u->wsp_hi);
+  if (u->wsp_lo) cudaFree(u->wsp_lo);
+  u->nhwc_lo = u->wsp_hi = u->wsp_lo = nullptr;
   for (__nv_bfloat16 *q : u->hcat)
     if (q) cudaFree(q);
   u->hcat.clear();
@@ -854,6 +946,13 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   // the widest convolution input: 2 C channels (a decoder's concatenation), padded to slices
   VIE_CUDA(cudaMalloc((void **)&u->nhwc,
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
+  VIE_CUDA(cudaMalloc((void **)&u->nhwc_lo,
+                      sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
+  {
+    const size_t wsp = (size_t)9 * ((2 * C + 31) / 32) * 32 * 32;  // 9 S blocks of [32][32]
+    VIE_CUDA(cudaMalloc((void **)&u->wsp_hi, sizeof(__nv_bfloat16) * wsp));
+    VIE_CUDA(cudaMalloc((void **)&u->wsp_lo, sizeof(__nv_bfloat16) * wsp));
+  }
   // the hand-off buffers, zeroed once: their padding channels are never written
   const size_t cp1 = (size_t)((C + 31) / 32) * 32, cp2 = (size_t)((2 * C + 31) / 32) * 32;
   VIE_CUDA(cudaMalloc((void **)&u->hx, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
@@ -937,36 +1036,36 @@ struct NhwcIo {
   bool wrote = false;  // set when out_h was written
 };
 
-vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __nv_bfloat16 *wtc, const float *bias,
-                     float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st, NhwcIo *io) {
-  const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
-  const long plane = (long)H * W;
-  const __nv_bfloat16 *src = io && io->in_h ? io->in_h : u->nhwc;
-  if (src == u->nhwc) {
-    k_to_nhwc_bf16<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
-    VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
-  }
+// the input's tensor map: NHWC BF16 at src, S slices; tiles of one row load
+// halo boxes of Wb + 2 pixels (the kernel's halo mode)
+vie_status conv_input_map(UnetImpl *u, const __nv_bfloat16 *src, int S, int H, int W, int B, CUtensorMap *mx) {
+  const int Cp = S * kTmaSlice, Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
+  const unsigned bw = R == 1 ? (unsigned)Wb + 2 : (unsigned)Wb;
+  const unsigned long long key[4] = {(unsigned long long)Cp | ((unsigned long long)bw << 32), (unsigned long long)W,
+                                     (unsigned long long)H, (unsigned long long)B};
+  const unsigned long long dims[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
+                                      (unsigned long long)B};
+  const unsigned long long strides[3] = {2ull * Cp, 2ull * Cp * W, 2ull * Cp * W * H};
+  const unsigned box[4] = {(unsigned)kTmaSlice, bw, (unsigned)R, 1u};
+  return cached_map(u, src, key, 4, dims, strides, box, mx);
+}
+
+// packed weights [9 S][Co][32] at wtc
+vie_status conv_weight_map(UnetImpl *u, const __nv_bfloat16 *wtc, int S, int Co, CUtensorMap *mw) {
+  const unsigned long long key[4] = {(unsigned long long)S, (unsigned long long)Co, 0ull, 1ull};
+  const unsigned long long dims[2] = {(unsigned long long)kTmaSlice, 9ull * S * Co};
+  const unsigned long long strides[1] = {2ull * kTmaSlice};
+  const unsigned box[2] = {(unsigned)kTmaSlice, (unsigned)Co};
+  return cached_map(u, wtc, key, 2, dims, strides, box, mw);
+}
+
+// Launch k_conv3_tma (split: the split-precision form, mxl / mwl its lo maps).
+vie_status launch_conv_tma(UnetImpl *u, const CUtensorMap &mx, const CUtensorMap &mw, const CUtensorMap &mxl,
+                           const CUtensorMap &mwl, bool split, const float *bias, float *out, long out_bs, int Co,
+                           int H, int W, int S, int B, bool relu, cudaStream_t st, NhwcIo *io) {
   const int Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
   const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
-  CUtensorMap mx, mw;
-  {
-    // tiles of one row load halo boxes of Wb + 2 pixels (the kernel's halo mode)
-    const unsigned bw = R == 1 ? (unsigned)Wb + 2 : (unsigned)Wb;
-    const unsigned long long key[4] = {(unsigned long long)Cp | ((unsigned long long)bw << 32), (unsigned long long)W,
-                                       (unsigned long long)H, (unsigned long long)B};
-    const unsigned long long dims[4] = {(unsigned long long)Cp, (unsigned long long)W, (unsigned long long)H,
-                                        (unsigned long long)B};
-    const unsigned long long strides[3] = {2ull * Cp, 2ull * Cp * W, 2ull * Cp * W * H};
-    const unsigned box[4] = {(unsigned)kTmaSlice, bw, (unsigned)R, 1u};
-    VIE_TRY(cached_map(u, src, key, 4, dims, strides, box, &mx));
-  }
-  {
-    const unsigned long long key[4] = {(unsigned long long)S, (unsigned long long)Co, 0ull, 1ull};
-    const unsigned long long dims[2] = {(unsigned long long)kTmaSlice, 9ull * S * Co};
-    const unsigned long long strides[1] = {2ull * kTmaSlice};
-    const unsigned box[2] = {(unsigned)kTmaSlice, (unsigned)Co};
-    VIE_TRY(cached_map(u, wtc, key, 2, dims, strides, box, &mw));
-  }
+  const int np = split ? 2 : 1;
   int dev = 0;
   VIE_CUDA(cudaGetDevice(&dev));
   DevProps prop;
@@ -979,35 +1078,78 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
   // two run side by side all the same, and a grid they could not share would
   // only run in two waves, each CTA taking every G-th tile.)
   const size_t optin = (size_t)prop.sharedMemPerBlockOptin;
-  int per_sm = 2, nst = conv_stages(S, Co, Wb, (optin + 1024) / 2 - 1024);
+  int per_sm = 2, nst = conv_stages(S, Co, Wb, (optin + 1024) / 2 - 1024, np);
   if (nst < 3) {
     per_sm = 1;
-    nst = conv_stages(S, Co, Wb, optin);
+    nst = conv_stages(S, Co, Wb, optin, np);
   }
   if (nst < 2) {
     set_error("BF16 convolution: not enough shared memory for two stages");
     return VIE_ERR_UNSUPPORTED;
   }
-  const size_t smem = conv_tma_smem(S, Co, Wb, nst);
-  const void *k = relu ? (const void *)k_conv3_tma<true> : (const void *)k_conv3_tma<false>;
+  const size_t smem = conv_tma_smem(S, Co, Wb, nst, np);
+  const void *k = split ? (relu ? (const void *)k_conv3_tma<true, true> : (const void *)k_conv3_tma<false, true>)
+                        : (relu ? (const void *)k_conv3_tma<true, false> : (const void *)k_conv3_tma<false, false>);
   VIE_TRY(raise_smem_limit(k, smem));
   // all of the SM's unified memory as shared memory, so that two CTAs fit
   VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  const WaitLimits wl = wait_limits(dev);
+  WaitLimits wl = wait_limits(dev);
   // per_sm CTAs per SM, each taking every G-th tile
-  const int tiles = tiles_x * tiles_y * B;
+  int tiles = tiles_x * tiles_y * B;
   const int grid = std::min(tiles, per_sm * prop.multiProcessorCount);
   __nv_bfloat16 *oh = io ? io->out_h : nullptr;
-  const long oh_bs = io ? io->oh_bs : 0;
-  const int oh_cp = io ? io->oh_cp : 0, oh_c0 = io ? io->oh_c0 : 0;
-  if (relu)
-    k_conv3_tma<true><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
-                                                        tiles, nst, wl, u->dev_err, oh, oh_bs, oh_cp, oh_c0);
-  else
-    k_conv3_tma<false><<<grid, kConvThreads, smem, st>>>(mx, mw, bias, out, out_bs, Co, H, W, S, Wb, R, tiles_x,
-                                                         tiles, nst, wl, u->dev_err, oh, oh_bs, oh_cp, oh_c0);
+  long oh_bs = io ? io->oh_bs : 0;
+  int oh_cp = io ? io->oh_cp : 0, oh_c0 = io ? io->oh_c0 : 0;
+  int nst_i = nst, S_i = S, Co_i = Co, H_i = H, W_i = W, Wb_i = Wb, R_i = R, tx_i = tiles_x;
+  int *err = u->dev_err;
+  void *args[] = {(void *)&mx, (void *)&mw, (void *)&mxl, (void *)&mwl, (void *)&bias, (void *)&out,
+                  (void *)&out_bs, (void *)&Co_i, (void *)&H_i, (void *)&W_i, (void *)&S_i, (void *)&Wb_i,
+                  (void *)&R_i, (void *)&tx_i, (void *)&tiles, (void *)&nst_i, (void *)&wl, (void *)&err,
+                  (void *)&oh, (void *)&oh_bs, (void *)&oh_cp, (void *)&oh_c0};
+  VIE_CUDA(cudaLaunchKernel(k, dim3((unsigned)grid), dim3(kConvThreads), args, smem, st));
   if (io) io->wrote = oh != nullptr;
   VIE_CHECK_LAUNCH("k_conv3_tma");
+  return VIE_OK;
+}
+
+vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __nv_bfloat16 *wtc, const float *bias,
+                     float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st, NhwcIo *io) {
+  const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
+  const long plane = (long)H * W;
+  const __nv_bfloat16 *src = io && io->in_h ? io->in_h : u->nhwc;
+  if (src == u->nhwc) {
+    k_to_nhwc_bf16<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc);
+    VIE_CHECK_LAUNCH("k_to_nhwc_bf16");
+  }
+  CUtensorMap mx, mw;
+  VIE_TRY(conv_input_map(u, src, S, H, W, B, &mx));
+  VIE_TRY(conv_weight_map(u, wtc, S, Co, &mw));
+  return launch_conv_tma(u, mx, mw, mx, mw, false, bias, out, out_bs, Co, H, W, S, B, relu, st, io);
+}
+
+// The FP32 convolution of training on the tensor cores in split precision:
+// the input split into BF16 hi + lo NHWC, the FP32 weights [Co][Ci][9] split
+// and packed per block of 32 output channels, one launch per block.
+bool conv_split_ok(int Ci, int Co) { return Ci <= 2 * kTmaSlice && Co % 32 == 0 && Co <= 64; }
+
+vie_status conv3_split(UnetImpl *u, const float *in, long in_bs, int Ci, const float *w, const float *bias,
+                       float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+  const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
+  const long plane = (long)H * W;
+  k_to_nhwc_split<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc, u->nhwc_lo);
+  VIE_CHECK_LAUNCH("k_to_nhwc_split");
+  CUtensorMap mx, mxl, mw, mwl;
+  VIE_TRY(conv_input_map(u, u->nhwc, S, H, W, B, &mx));
+  VIE_TRY(conv_input_map(u, u->nhwc_lo, S, H, W, B, &mxl));
+  VIE_TRY(conv_weight_map(u, u->wsp_hi, S, 32, &mw));
+  VIE_TRY(conv_weight_map(u, u->wsp_lo, S, 32, &mwl));
+  for (int co0 = 0; co0 < Co; co0 += 32) {
+    k_pack_split_weights<<<gridn(9L * S * 32 * kTmaSlice), 256, 0, st>>>(w, Co, Ci, S, co0, 32, u->wsp_hi,
+                                                                         u->wsp_lo);
+    VIE_CHECK_LAUNCH("k_pack_split_weights");
+    VIE_TRY(launch_conv_tma(u, mx, mw, mxl, mwl, true, bias ? bias + co0 : nullptr, out + co0 * plane, out_bs, 32,
+                            H, W, S, B, relu, st, nullptr));
+  }
   return VIE_OK;
 }
 
@@ -1020,6 +1162,9 @@ vie_status conv3(UnetImpl *u, const float *in, long in_bs, int Ci, const WT *w, 
   if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
     if (conv_on_tensor_cores(wtc, Ci, Co, bias))
       return conv3_tma(u, in, in_bs, Ci, wtc, bias, out, out_bs, Co, H, W, B, relu, st, io);
+  } else {
+    if (u->train_tc && conv_split_ok(Ci, Co))
+      return conv3_split(u, in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, relu, st);
   }
   if (relu)
     conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
@@ -1140,9 +1285,17 @@ vie_status forward(UnetImpl *u, const WT *pw, const float *x, int B, int n, cuda
 vie_status conv3_backward(UnetImpl *u, const ConvLayer &c, const float *in, long in_bs, const float *gout,
                           long g_bs, float *gin, long gin_bs, int H, int B, cudaStream_t st) {
   const int cib = (c.ci + CIB - 1) / CIB, cob = (c.co + COB - 1) / COB;
-  dim3 grid((H + TX - 1) / TX, (H + WY - 1) / WY, B * cob * cib);
+  // images per CTA: about four CTAs per SM in all, each adding its sums once
+  const long per_split = (long)((H + TX - 1) / TX) * ((H + WY - 1) / WY) * cob * cib;
+  int sms = 0, dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  DevProps prop;
+  VIE_TRY(get_dev_props(dev, &prop));
+  sms = prop.multiProcessorCount;
+  const int splits = (int)std::max(1L, std::min<long>(B, (4L * sms + per_split - 1) / per_split));
+  dim3 grid((H + TX - 1) / TX, (H + WY - 1) / WY, splits * cob * cib);
   k_conv3_dw<<<grid, 256, 0, st>>>(in, in_bs, c.ci, gout, g_bs, c.co, H, H, u->g + c.w_off, u->g + c.b_off,
-                                  cib, cob);
+                                  cib, cob, B, splits);
   VIE_CHECK_LAUNCH("k_conv3_dw");
   if (gin) {
     k_flip<<<gridn((long)c.co * c.ci * 9), 256, 0, st>>>(u->p + c.w_off, c.co, c.ci, u->wt);
@@ -1169,9 +1322,15 @@ vie_status backward(UnetImpl *u, const float *x, int B, int n, cudaStream_t st) 
   const float *d = L > 1 ? u->dl[0] : u->ebot[0];
   float *gd = L > 1 ? u->gdl[0] : u->gebot[0];
   const long plane0 = (long)n * n;
-  k_head_bwd_w<<<C + 1, 256, 0, st>>>(u->go, d, (long)C * plane0, C, plane0, B, u->g + hd.w_off,
-                                      u->g + hd.b_off);
-  VIE_CHECK_LAUNCH("k_head_bwd_w");
+  {
+    // (C + 1) x K blocks, K slices of the pixels (the partials fit u->part's 1024 doubles)
+    const int K = std::max(1, std::min(1024 / (C + 1), (int)std::min(64L, (long)B * plane0 / 4096 + 1)));
+    k_head_bwd_w<<<dim3((unsigned)(C + 1), (unsigned)K), 256, 0, st>>>(u->go, d, (long)C * plane0, C, plane0, B,
+                                                                      u->part);
+    VIE_CHECK_LAUNCH("k_head_bwd_w");
+    k_head_bwd_w_finish<<<1, ((C + 1 + 31) / 32) * 32, 0, st>>>(u->part, C, K, u->g + hd.w_off, u->g + hd.b_off);
+    VIE_CHECK_LAUNCH("k_head_bwd_w_finish");
+  }
   k_head_bwd_data<<<gridn((long)B * C * plane0), 256, 0, st>>>(u->go, C, u->p + hd.w_off, gd, (long)C * plane0,
                                                                 plane0, B);
   VIE_CHECK_LAUNCH("k_head_bwd_data");
@@ -1242,9 +1401,22 @@ vie_status loss_grad(UnetImpl *u, const float *x, const float *t, const float *w
   const int blocks = 512;
   k_mse<<<blocks, 256, 0, st>>>(u->o, t, cnt, (long)n * n, wts, u->go, u->part);
   VIE_CHECK_LAUNCH("k_mse");
-  VIE_CUDA(cudaMemsetAsync(u->g, 0, sizeof(float) * u->nparams, st));
-  if ((s = backward(u, x, B, n, st)) != VIE_OK) return s;
+  // the loss partials leave u->part before the backward pass reuses it
   VIE_CUDA(cudaMemcpyAsync(u->h_part, u->part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaMemsetAsync(u->g, 0, sizeof(float) * u->nparams, st));
+  {
+    // the input-gradient convolutions on the tensor cores in split
+    // precision.  The forward stays in FP32 on the CUDA cores: its ~1e-5
+    // relative error in split precision flips ReLU masks of pre-activations
+    // near zero, and each flip moves a gradient entry by a whole term
+    // (measured: 3.6e-3 relative against the FP64 reference, 1e-4 allowed).
+    struct TrainTc {
+      UnetImpl *u;
+      explicit TrainTc(UnetImpl *q) : u(q) { u->train_tc = true; }
+      ~TrainTc() { u->train_tc = false; }
+    } train_tc(u);
+    if ((s = backward(u, x, B, n, st)) != VIE_OK) return s;
+  }
   VIE_CUDA(cudaStreamSynchronize(st));
   double sum = 0.0;
   for (int i = 0; i < blocks; ++i) sum += u->h_part[i];
