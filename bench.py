@@ -779,7 +779,7 @@ def run_ours(args):
     paper_fmm = measure_paper_fmm_tables(P, torch, local)
 
     # end to end through the C ABI from host buffers
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 10))
     U_host = np.zeros(N)
     t_e2e = []
     for _ in range(e2e_steps):

@@ -488,6 +488,20 @@ vie_status vie_set_wait_limits(double limit_ms, double first_wait_ms);
  * since the last report; asynchronous vie_apply calls report this way. */
 vie_status vie_check_device(vie_handle *h, void *stream);
 
+/* Device memory.  The library keeps the device buffers that vie_destroy,
+ * vie_unet_destroy, vie_batch_destroy and workspace growth free, per device
+ * and size class (512-byte steps up to 1 MiB, 2 MiB steps above; at most
+ * 4 GiB in all), and hands them to later requests of the same class: a
+ * handle created per solve then costs no cudaMalloc after the first.  Its
+ * pinned host buffers (the solvers' read-back scalars) are kept likewise.  A
+ * buffer enters the cache only after the device has finished with it.  An
+ * allocation that fails releases the cache and tries again.
+ * vie_release_memory synchronises the current device and returns every
+ * cached buffer, device and pinned host, to CUDA (buffers still owned by live
+ * objects stay).
+ * Errors: none. */
+vie_status vie_release_memory(void);
+
 /* The pair kernel this handle's on-the-fly applies use (VIE_KERNEL_*). */
 vie_status vie_get_kernel(vie_handle *h, int *kernel);
 

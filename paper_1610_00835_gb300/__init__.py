@@ -10,7 +10,8 @@ from .vie import (VieUnet, vie_diffusion_precondition, vie_set_diffusion_precond
                   vie_unet_forward, vie_unet_get_params, vie_unet_load, vie_unet_loss_grad,
                   vie_unet_num_params, vie_unet_save, vie_unet_set_params, vie_unet_train_step,
                   vie_unet_train_state, vie_unet_layer_io)
-from .vie import (VIE_ERR_TIMEOUT, vie_check_device, vie_set_wait_limits, vie_set_preconditioner_on_diffusion)
+from .vie import (VIE_ERR_TIMEOUT, vie_check_device, vie_set_wait_limits, vie_set_preconditioner_on_diffusion,
+                  vie_release_memory)
 from .vie import (VieBatch, vie_batch_apply, vie_batch_autotune, vie_batch_config,
                   vie_batch_create, vie_batch_destroy)
 from .vie import (VIE_OPERATOR_FMM, vie_assemble_fmm)
@@ -26,7 +27,7 @@ __all__ = ["VIE_DISC_MII", "VIE_DISC_MIII", "VIE_KERNEL_AUTO", "VIE_KERNEL_DISPL
            "vie_unet_forward", "vie_unet_get_params", "vie_unet_load", "vie_unet_loss_grad",
            "vie_unet_num_params", "vie_unet_save", "vie_unet_set_params", "vie_unet_train_step",
            "vie_unet_train_state", "vie_unet_layer_io", "VIE_ERR_TIMEOUT", "vie_check_device", "vie_set_wait_limits",
-           "vie_set_preconditioner_on_diffusion",
+           "vie_set_preconditioner_on_diffusion", "vie_release_memory",
            "VieBatch", "vie_batch_apply", "vie_batch_autotune", "vie_batch_config",
            "vie_batch_create", "vie_batch_destroy",
            "VIE_OPERATOR_FMM", "vie_assemble_fmm", "VIE_OPERATOR_BF16X3", "VIE_OPERATOR_FP32", "VIE_OPERATOR_PAIRS32", "VIE_OPERATOR_SYM32", "VIE_OPERATOR_OTF", "VIE_OP_A_RAW", "VIE_OP_I_MINUS_K", "VIE_OP_K_SIGMA_S", "VIE_PREC_FP32",

@@ -246,13 +246,13 @@ vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *c
   }
   bp->n_batches = nb;
   bp->max_smem_lat = max_lat;
-  if (bp->grids) cudaFree(bp->grids);
-  if (bp->items) cudaFree(bp->items);
+  if (bp->grids) vie_free(bp->grids);
+  if (bp->items) vie_free(bp->items);
   bp->grids = nullptr;
   bp->items = nullptr;
-  VIE_CUDA(cudaMalloc((void **)&bp->grids, sizeof(BatchGrid) * count));
+  VIE_CUDA(vie_malloc((void **)&bp->grids, sizeof(BatchGrid) * count));
   VIE_CUDA(cudaMemcpy(bp->grids, bp->host.data(), sizeof(BatchGrid) * count, cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&bp->items, sizeof(int2) * std::max<size_t>(1, items.size())));
+  VIE_CUDA(vie_malloc((void **)&bp->items, sizeof(int2) * std::max<size_t>(1, items.size())));
   if (!items.empty())
     VIE_CUDA(cudaMemcpy(bp->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   bp->smem = batch_smem(groups, max_lat);
@@ -269,8 +269,8 @@ vie_status batch_plan(BatchPlanImpl *bp, int count, const int *ns, const long *c
 }
 
 void batch_plan_free(BatchPlanImpl *bp) {
-  if (bp->grids) cudaFree(bp->grids);
-  if (bp->items) cudaFree(bp->items);
+  if (bp->grids) vie_free(bp->grids);
+  if (bp->items) vie_free(bp->items);
   bp->grids = nullptr;
   bp->items = nullptr;
 }
@@ -339,7 +339,7 @@ void batch_free(vie_batch *b) {
   for (void *p : {(void *)b->sig_t, (void *)b->sig_s, (void *)b->diag, (void *)b->lattice,
                   (void *)b->src, (void *)b->partial, (void *)b->counter, (void *)b->stage_g,
                   (void *)b->stage_y})
-    if (p) cudaFree(p);
+    if (p) vie_free(p);
   batch_plan_free(&b->plan);
   for (auto &d : b->disp) disp_release(&d);
 }
@@ -476,13 +476,13 @@ vie_status vie_batch_create(vie_batch **out, int count, const vie_grid *grids,
     cudaError_t _e = (call);                                  \
     if (_e != cudaSuccess) return fail(cuda_fail(_e, #call)); \
   } while (0)
-  BTRY(cudaMalloc(&b->sig_t, sizeof(double) * cells));
-  BTRY(cudaMalloc(&b->sig_s, sizeof(double) * cells));
-  BTRY(cudaMalloc(&b->diag, sizeof(double) * cells));
-  BTRY(cudaMalloc(&b->src, sizeof(float) * cells));
-  BTRY(cudaMalloc(&b->lattice, sizeof(float) * b->lat_off[count]));
-  BTRY(cudaMalloc(&b->partial, sizeof(double) * b->part_off[count]));
-  BTRY(cudaMalloc(&b->counter, 2 * sizeof(int)));
+  BTRY(vie_malloc(&b->sig_t, sizeof(double) * cells));
+  BTRY(vie_malloc(&b->sig_s, sizeof(double) * cells));
+  BTRY(vie_malloc(&b->diag, sizeof(double) * cells));
+  BTRY(vie_malloc(&b->src, sizeof(float) * cells));
+  BTRY(vie_malloc(&b->lattice, sizeof(float) * b->lat_off[count]));
+  BTRY(vie_malloc(&b->partial, sizeof(double) * b->part_off[count]));
+  BTRY(vie_malloc(&b->counter, 2 * sizeof(int)));
   BTRY(cudaMemset(b->counter, 0, 2 * sizeof(int)));
   BTRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   for (int i = 0; i < count; ++i) {
@@ -548,12 +548,12 @@ vie_status vie_batch_apply(vie_batch *b, vie_op op, const double *g, double *y, 
   if ((!gd || !yd) && b->stage_cap < cells) {
     // grow both staging buffers (a graph captured on the old ones is dropped)
     VIE_CUDA(cudaStreamSynchronize(st));
-    if (b->stage_g) cudaFree(b->stage_g);
-    if (b->stage_y) cudaFree(b->stage_y);
+    if (b->stage_g) vie_free(b->stage_g);
+    if (b->stage_y) vie_free(b->stage_y);
     b->stage_g = b->stage_y = nullptr;
     b->stage_cap = 0;
-    VIE_CUDA(cudaMalloc(&b->stage_g, sizeof(double) * cells));
-    VIE_CUDA(cudaMalloc(&b->stage_y, sizeof(double) * cells));
+    VIE_CUDA(vie_malloc(&b->stage_g, sizeof(double) * cells));
+    VIE_CUDA(vie_malloc(&b->stage_y, sizeof(double) * cells));
     b->stage_cap = cells;
     b->key_op = -1;
   }
@@ -635,8 +635,8 @@ vie_status vie_batch_autotune(vie_batch *b, const char *cache_path, void *stream
   }
   const long cells = b->cell_off[b->count];
   double *g = nullptr, *y = nullptr;
-  VIE_CUDA(cudaMalloc(&g, sizeof(double) * cells));
-  VIE_CUDA(cudaMalloc(&y, sizeof(double) * cells));
+  VIE_CUDA(vie_malloc(&g, sizeof(double) * cells));
+  VIE_CUDA(vie_malloc(&y, sizeof(double) * cells));
   VIE_CUDA(cudaMemset(g, 0, sizeof(double) * cells));
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
@@ -662,8 +662,8 @@ vie_status vie_batch_autotune(vie_batch *b, const char *cache_path, void *stream
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(g);
-  cudaFree(y);
+  vie_free(g);
+  vie_free(y);
   if (s == VIE_OK) s = replan(b, cand[best_i][0], cand[best_i][1]);
   if (s == VIE_OK && cache_path) {
     FILE *fp = fopen(cache_path, "a");

@@ -206,9 +206,9 @@ vie_status diffusion_prepare(DiffPre *dp, int n, const double *sigma_t, const do
     const long M = (long)ln * ln;
     DiffLevel &L = dp->lv[dp->L++];  // owned by dp from here: released on failure
     L.n = ln;
-    VIE_CUDA(cudaMalloc((void **)&L.c, sizeof(double) * 6 * M));
-    VIE_CUDA(cudaMalloc((void **)&L.f, sizeof(double) * M));
-    VIE_CUDA(cudaMalloc((void **)&L.u, sizeof(double) * M));
+    VIE_CUDA(vie_malloc((void **)&L.c, sizeof(double) * 6 * M));
+    VIE_CUDA(vie_malloc((void **)&L.f, sizeof(double) * M));
+    VIE_CUDA(vie_malloc((void **)&L.u, sizeof(double) * M));
     VIE_CUDA(cudaMemcpyAsync(L.c, c.data(), sizeof(double) * 6 * M, cudaMemcpyHostToDevice, st));
     VIE_CUDA(cudaStreamSynchronize(st));
     if (ln % 2 || ln <= 8 || dp->L == kDiffMaxLevels) break;
@@ -249,9 +249,9 @@ void diffusion_release(DiffPre *dp) {
   if (dp->graph) cudaGraphDestroy(dp->graph);
   if (dp->cap) cudaStreamDestroy(dp->cap);
   for (int l = 0; l < dp->L; ++l) {
-    if (dp->lv[l].c) cudaFree(dp->lv[l].c);
-    if (dp->lv[l].f) cudaFree(dp->lv[l].f);
-    if (dp->lv[l].u) cudaFree(dp->lv[l].u);
+    if (dp->lv[l].c) vie_free(dp->lv[l].c);
+    if (dp->lv[l].f) vie_free(dp->lv[l].f);
+    if (dp->lv[l].u) vie_free(dp->lv[l].u);
   }
   *dp = DiffPre{};
 }

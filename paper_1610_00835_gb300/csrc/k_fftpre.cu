@@ -203,9 +203,9 @@ vie_status fft_prepare(FftPre *fp, int n, double mu, double mu_s, int mii, cudaS
   }
   std::vector<float2> tw((size_t)m / 2);
   for (int k = 0; k < m / 2; ++k) tw[k] = make_float2((float)wt[k].real(), (float)wt[k].imag());
-  VIE_CUDA(cudaMalloc((void **)&fp->inv_lambda, sizeof(float) * inv.size()));
-  VIE_CUDA(cudaMalloc((void **)&fp->tw, sizeof(float2) * tw.size()));
-  VIE_CUDA(cudaMalloc((void **)&fp->buf, sizeof(float2) * (size_t)n * m));
+  VIE_CUDA(vie_malloc((void **)&fp->inv_lambda, sizeof(float) * inv.size()));
+  VIE_CUDA(vie_malloc((void **)&fp->tw, sizeof(float2) * tw.size()));
+  VIE_CUDA(vie_malloc((void **)&fp->buf, sizeof(float2) * (size_t)n * m));
   VIE_CUDA(cudaMemcpyAsync(fp->inv_lambda, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice, st));
   VIE_CUDA(cudaMemcpyAsync(fp->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, st));
   VIE_CUDA(cudaStreamSynchronize(st));
@@ -225,9 +225,9 @@ vie_status fft_prepare(FftPre *fp, int n, double mu, double mu_s, int mii, cudaS
 }
 
 void fft_release(FftPre *fp) {
-  if (fp->inv_lambda) cudaFree(fp->inv_lambda);
-  if (fp->tw) cudaFree(fp->tw);
-  if (fp->buf) cudaFree(fp->buf);
+  if (fp->inv_lambda) vie_free(fp->inv_lambda);
+  if (fp->tw) vie_free(fp->tw);
+  if (fp->buf) vie_free(fp->buf);
   *fp = FftPre{};
 }
 

@@ -375,13 +375,13 @@ vie_status fmm_prepare(FmmPlan *fp, int n, int p, const float *sig32, const doub
     m2l_total += ((long)kIL * P2 * P2) << (2 * l);
   }
   const long near_total = (long)nl * nl * 9 * bb * bb;
-  VIE_CUDA(cudaMalloc((void **)&fp->near, sizeof(float) * near_total));
-  VIE_CUDA(cudaMalloc((void **)&fp->m2l, sizeof(float) * m2l_total));
-  VIE_CUDA(cudaMalloc((void **)&fp->W, sizeof(float) * nodes));
-  VIE_CUDA(cudaMalloc((void **)&fp->Lc, sizeof(float) * nodes));
-  VIE_CUDA(cudaMalloc((void **)&fp->Pm, sizeof(float) * Pm.size()));
-  VIE_CUDA(cudaMalloc((void **)&fp->Cq, sizeof(float) * Cq.size()));
-  VIE_CUDA(cudaMalloc((void **)&fp->z, sizeof(float) * p));
+  VIE_CUDA(vie_malloc((void **)&fp->near, sizeof(float) * near_total));
+  VIE_CUDA(vie_malloc((void **)&fp->m2l, sizeof(float) * m2l_total));
+  VIE_CUDA(vie_malloc((void **)&fp->W, sizeof(float) * nodes));
+  VIE_CUDA(vie_malloc((void **)&fp->Lc, sizeof(float) * nodes));
+  VIE_CUDA(vie_malloc((void **)&fp->Pm, sizeof(float) * Pm.size()));
+  VIE_CUDA(vie_malloc((void **)&fp->Cq, sizeof(float) * Cq.size()));
+  VIE_CUDA(vie_malloc((void **)&fp->z, sizeof(float) * p));
   VIE_CUDA(cudaMemcpyAsync(fp->Pm, Pm.data(), sizeof(float) * Pm.size(), cudaMemcpyHostToDevice, st));
   VIE_CUDA(cudaMemcpyAsync(fp->Cq, Cq.data(), sizeof(float) * Cq.size(), cudaMemcpyHostToDevice, st));
   VIE_CUDA(cudaMemcpyAsync(fp->z, zf.data(), sizeof(float) * p, cudaMemcpyHostToDevice, st));
@@ -401,13 +401,13 @@ vie_status fmm_prepare(FmmPlan *fp, int n, int p, const float *sig32, const doub
 }
 
 void fmm_release(FmmPlan *fp) {
-  if (fp->near) cudaFree(fp->near);
-  if (fp->m2l) cudaFree(fp->m2l);
-  if (fp->W) cudaFree(fp->W);
-  if (fp->Lc) cudaFree(fp->Lc);
-  if (fp->Pm) cudaFree(fp->Pm);
-  if (fp->Cq) cudaFree(fp->Cq);
-  if (fp->z) cudaFree(fp->z);
+  if (fp->near) vie_free(fp->near);
+  if (fp->m2l) vie_free(fp->m2l);
+  if (fp->W) vie_free(fp->W);
+  if (fp->Lc) vie_free(fp->Lc);
+  if (fp->Pm) vie_free(fp->Pm);
+  if (fp->Cq) vie_free(fp->Cq);
+  if (fp->z) vie_free(fp->z);
   *fp = FmmPlan{};
 }
 

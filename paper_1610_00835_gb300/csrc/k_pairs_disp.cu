@@ -743,15 +743,16 @@ struct Geometry {
   long n_units = 0;
   size_t stencil_bytes = 0;
   double taps = 0.0;
+  double inv_r_sum = 0.0;  // sum over the nonzero displacements D of 1 / |D|
 };
 std::mutex g_geo_mu;
 std::vector<Geometry *> g_geo;
 constexpr int kGeoKeep = 4;
 
 void geometry_free(Geometry *g) {
-  if (g->units) cudaFree(g->units);
-  if (g->stencil) cudaFree(g->stencil);
-  if (g->doff) cudaFree(g->doff);
+  if (g->units) vie_free(g->units);
+  if (g->stencil) vie_free(g->stencil);
+  if (g->doff) vie_free(g->doff);
   delete g;
 }
 
@@ -850,13 +851,18 @@ vie_status geometry_build(int n, int ldp, bool global, int R, Geometry *geo) {
   std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
   std::vector<int4> uv(units.size());
   for (size_t i = 0; i < units.size(); ++i) uv[i] = units[i].u;
-  VIE_CUDA(cudaMalloc((void **)&geo->units, sizeof(int4) * uv.size()));
+  VIE_CUDA(vie_malloc((void **)&geo->units, sizeof(int4) * uv.size()));
   VIE_CUDA(cudaMemcpy(geo->units, uv.data(), sizeof(int4) * uv.size(), cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&geo->stencil, sizeof(float) * rec.size()));
+  VIE_CUDA(vie_malloc((void **)&geo->stencil, sizeof(float) * rec.size()));
   VIE_CUDA(cudaMemcpy(geo->stencil, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&geo->doff, sizeof(long long) * doff.size()));
+  VIE_CUDA(vie_malloc((void **)&geo->doff, sizeof(long long) * doff.size()));
   VIE_CUDA(cudaMemcpy(geo->doff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice));
   geo->n_units = (long)uv.size();
+  double rb = 0.0;
+  for (int dy = -(n - 1); dy < n; ++dy)
+    for (int dx = -(n - 1); dx < n; ++dx)
+      if (dx || dy) rb += 1.0 / sqrt((double)dx * dx + (double)dy * dy);
+  geo->inv_r_sum = rb;
   geo->stencil_bytes = sizeof(float) * rec.size();
   geo->taps = taps;
   return VIE_OK;
@@ -927,10 +933,10 @@ vie_status disp_mii_prepare(DispPlan *dp, int n, double *diag_value, cudaStream_
     for (int dx = -(n - 1); dx < n; ++dx)
       if (dx || dy) rb += c * unit_cell_integral(dx, dy);
   *diag_value = c * unit_cell_integral(0.0, 0.0);
-  if (dp->wtab) cudaFree((void *)dp->wtab);
+  if (dp->wtab) vie_free((void *)dp->wtab);
   dp->wtab = nullptr;
   float *d = nullptr;
-  VIE_CUDA(cudaMalloc((void **)&d, sizeof(float) * tab.size()));
+  VIE_CUDA(vie_malloc((void **)&d, sizeof(float) * tab.size()));
   dp->wtab = d;
   VIE_CUDA(cudaMemcpyAsync(d, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, st));
   VIE_CUDA(cudaStreamSynchronize(st));
@@ -985,33 +991,30 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
   dp->n_units = geo->n_units;
   dp->taps = geo->taps;
   dp->stencil_bytes = geo->stencil_bytes;
-  VIE_CUDA(cudaMalloc((void **)&dp->counter, 2 * sizeof(int)));
+  VIE_CUDA(vie_malloc((void **)&dp->counter, 2 * sizeof(int)));
   VIE_CUDA(cudaMemset(dp->counter, 0, 2 * sizeof(int)));
   const long lat_elems = (long)rows * ldp;
-  VIE_CUDA(cudaMalloc((void **)&dp->lattice, sizeof(float) * lat_elems));
+  VIE_CUDA(vie_malloc((void **)&dp->lattice, sizeof(float) * lat_elems));
   k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp, 0,
                                                                                 (float *)dp->lattice);
   VIE_CHECK_LAUNCH("k_make_lattice");
   if (global) {
-    VIE_CUDA(cudaMalloc((void **)&dp->lattice_t, sizeof(float) * lat_elems));
+    VIE_CUDA(vie_malloc((void **)&dp->lattice_t, sizeof(float) * lat_elems));
     k_make_lattice<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(n, sig_padded, rows, ldp, 1,
                                                                                   (float *)dp->lattice_t);
     VIE_CHECK_LAUNCH("k_make_lattice");
   }
   dp->global = global;
-  VIE_CUDA(cudaMalloc((void **)&dp->smax, sizeof(unsigned)));
+  VIE_CUDA(vie_malloc((void **)&dp->smax, sizeof(unsigned)));
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
-  VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
-  VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
-  VIE_CUDA(cudaMalloc((void **)&dp->ss32, sizeof(float) * (size_t)n * n));
-  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)n * n));
+  VIE_CUDA(vie_malloc((void **)&dp->scale, sizeof(double)));
+  VIE_CUDA(vie_malloc((void **)&dp->src_t, sizeof(float) * (size_t)n * n));
+  VIE_CUDA(vie_malloc((void **)&dp->ss32, sizeof(float) * (size_t)n * n));
+  VIE_CUDA(vie_malloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)n * n));
   VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * 2 * (size_t)n * n));
-  // every row sum of A is below sum over all nonzero displacements of h / (2 pi r)
-  double rb = 0.0;
-  for (int dy = -(n - 1); dy < n; ++dy)
-    for (int dx = -(n - 1); dx < n; ++dx)
-      if (dx || dy) rb += 1.0 / sqrt((double)dx * dx + (double)dy * dy);
-  dp->rbound = rb / (2.0 * kPi * n);
+  // every row sum of A is below sum over all nonzero displacements of
+  // h / (2 pi r) (the sum of 1 / |D| is kept with the geometry)
+  dp->rbound = geo->inv_r_sum / (2.0 * kPi * n);
   dp->n = n;
   dp->lat_elems = lat_elems;
   dp->ldp = ldp;
@@ -1031,15 +1034,15 @@ vie_status disp_prepare(DispPlan *dp, int n, const float *sig_padded, int device
 
 void disp_release(DispPlan *dp) {
   if (dp->geometry) geometry_release((Geometry *)dp->geometry);
-  if (dp->counter) cudaFree(dp->counter);
-  if (dp->lattice) cudaFree(dp->lattice);
-  if (dp->lattice_t) cudaFree(dp->lattice_t);
-  if (dp->smax) cudaFree(dp->smax);
-  if (dp->scale) cudaFree(dp->scale);
-  if (dp->src_t) cudaFree(dp->src_t);
-  if (dp->ss32) cudaFree(dp->ss32);
-  if (dp->yacc) cudaFree(dp->yacc);
-  if (dp->wtab) cudaFree((void *)dp->wtab);
+  if (dp->counter) vie_free(dp->counter);
+  if (dp->lattice) vie_free(dp->lattice);
+  if (dp->lattice_t) vie_free(dp->lattice_t);
+  if (dp->smax) vie_free(dp->smax);
+  if (dp->scale) vie_free(dp->scale);
+  if (dp->src_t) vie_free(dp->src_t);
+  if (dp->ss32) vie_free(dp->ss32);
+  if (dp->yacc) vie_free(dp->yacc);
+  if (dp->wtab) vie_free((void *)dp->wtab);
   dp->wtab = nullptr;
   dp->yacc = nullptr;
   dp->ss32 = nullptr;

@@ -333,8 +333,8 @@ std::vector<Geometry3 *> g_geo3;
 constexpr int kGeo3Keep = 2;
 
 void geometry3_free(Geometry3 *g) {
-  if (g->units) cudaFree(g->units);
-  if (g->stencil) cudaFree(g->stencil);
+  if (g->units) vie_free(g->units);
+  if (g->stencil) vie_free(g->stencil);
   delete g;
 }
 
@@ -465,9 +465,9 @@ vie_status geometry3_build(int n, Geometry3 *geo) {
   std::stable_sort(units.begin(), units.end(), [](const Unit3 &p, const Unit3 &q) { return p.cost > q.cost; });
   std::vector<int4> uv(units.size());
   for (size_t i = 0; i < units.size(); ++i) uv[i] = units[i].u;
-  VIE_CUDA(cudaMalloc((void **)&geo->units, sizeof(int4) * uv.size()));
+  VIE_CUDA(vie_malloc((void **)&geo->units, sizeof(int4) * uv.size()));
   VIE_CUDA(cudaMemcpy(geo->units, uv.data(), sizeof(int4) * uv.size(), cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&geo->stencil, sizeof(float) * rec.size()));
+  VIE_CUDA(vie_malloc((void **)&geo->stencil, sizeof(float) * rec.size()));
   VIE_CUDA(cudaMemcpy(geo->stencil, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice));
   geo->n_units = (long)uv.size();
   geo->taps = taps;
@@ -532,17 +532,17 @@ vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int devi
   dp->taps = geo->taps;
   const long N = (long)n * n * n, p = n + 1;
   const long lat = p * p * p, lat_elems = p * p * (p + kPad3);
-  VIE_CUDA(cudaMalloc((void **)&dp->counter, 2 * sizeof(int)));
+  VIE_CUDA(vie_malloc((void **)&dp->counter, 2 * sizeof(int)));
   VIE_CUDA(cudaMemset(dp->counter, 0, 2 * sizeof(int)));
-  VIE_CUDA(cudaMalloc((void **)&dp->lattice, sizeof(float) * lat_elems));
+  VIE_CUDA(vie_malloc((void **)&dp->lattice, sizeof(float) * lat_elems));
   k_make_lattice3<<<(int)std::min((lat_elems + 255) / 256, 4096L), 256, 0, st>>>(lat, lat_elems, sig_padded,
                                                                                  (float *)dp->lattice);
   VIE_CHECK_LAUNCH("k_make_lattice3");
-  VIE_CUDA(cudaMalloc((void **)&dp->smax, sizeof(unsigned)));
+  VIE_CUDA(vie_malloc((void **)&dp->smax, sizeof(unsigned)));
   VIE_CUDA(cudaMemset(dp->smax, 0, sizeof(unsigned)));
-  VIE_CUDA(cudaMalloc((void **)&dp->scale, sizeof(double)));
-  VIE_CUDA(cudaMalloc((void **)&dp->src_t, sizeof(float) * (size_t)N));
-  VIE_CUDA(cudaMalloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)N));
+  VIE_CUDA(vie_malloc((void **)&dp->scale, sizeof(double)));
+  VIE_CUDA(vie_malloc((void **)&dp->src_t, sizeof(float) * (size_t)N));
+  VIE_CUDA(vie_malloc((void **)&dp->yacc, sizeof(unsigned long long) * 2 * (size_t)N));
   VIE_CUDA(cudaMemset(dp->yacc, 0, sizeof(unsigned long long) * 2 * (size_t)N));
   // every row sum of A is below sum over all nonzero displacements of h / (4 pi |D|^2)
   double rb = 0.0;
@@ -562,12 +562,12 @@ vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int devi
 
 void disp3_release(DispPlan3 *dp) {
   if (dp->geometry) geometry3_release((Geometry3 *)dp->geometry);
-  if (dp->counter) cudaFree(dp->counter);
-  if (dp->lattice) cudaFree(dp->lattice);
-  if (dp->smax) cudaFree(dp->smax);
-  if (dp->scale) cudaFree(dp->scale);
-  if (dp->src_t) cudaFree(dp->src_t);
-  if (dp->yacc) cudaFree(dp->yacc);
+  if (dp->counter) vie_free(dp->counter);
+  if (dp->lattice) vie_free(dp->lattice);
+  if (dp->smax) vie_free(dp->smax);
+  if (dp->scale) vie_free(dp->scale);
+  if (dp->src_t) vie_free(dp->src_t);
+  if (dp->yacc) vie_free(dp->yacc);
   *dp = DispPlan3{};
 }
 

@@ -257,11 +257,11 @@ vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_pad
   items.reserve(sp->n_items);
   for (int a = 0; a < sp->T; ++a)
     for (int b = a; b < sp->T; ++b) items.push_back(make_int2(a, b));
-  VIE_CUDA(cudaMalloc((void **)&sp->items, sizeof(int2) * items.size()));
+  VIE_CUDA(vie_malloc((void **)&sp->items, sizeof(int2) * items.size()));
   VIE_CUDA(cudaMemcpy(sp->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
-  VIE_CUDA(cudaMalloc((void **)&sp->counter, 2 * sizeof(int)));
+  VIE_CUDA(vie_malloc((void **)&sp->counter, 2 * sizeof(int)));
   VIE_CUDA(cudaMemset(sp->counter, 0, 2 * sizeof(int)));
-  VIE_CUDA(cudaMalloc((void **)&sp->lattice, sizeof(float) * lattice));
+  VIE_CUDA(vie_malloc((void **)&sp->lattice, sizeof(float) * lattice));
   {
     long b = (lattice + 255) / 256;
     k_restride<<<(int)std::min(b, 4096L), 256, 0, st>>>(dim, (int)P, ldp, plane, sig_padded,
@@ -280,9 +280,9 @@ vie_status sym_prepare(SymPlan *sp, int dim, int n, long N, const float *sig_pad
 }
 
 void sym_release(SymPlan *sp) {
-  if (sp->items) cudaFree(sp->items);
-  if (sp->counter) cudaFree(sp->counter);
-  if (sp->lattice) cudaFree(sp->lattice);
+  if (sp->items) vie_free(sp->items);
+  if (sp->counter) vie_free(sp->counter);
+  if (sp->lattice) vie_free(sp->lattice);
   sp->items = nullptr;
   sp->counter = nullptr;
   sp->lattice = nullptr;

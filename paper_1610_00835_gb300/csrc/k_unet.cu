@@ -880,25 +880,25 @@ namespace {
 void free_acts(UnetImpl *u) {
   auto fr = [](std::vector<float *> &vv) {
     for (float *&q : vv)
-      if (q) cudaFree(q);
+      if (q) vie_free(q);
     vv.clear();
   };
   fr(u->xin); fr(u->a); fr(u->cat); fr(u->bl); fr(u->dl); fr(u->ebot);
   fr(u->gx); fr(u->ga); fr(u->gcat); fr(u->gbl); fr(u->gdl); fr(u->gebot);
-  if (u->o) cudaFree(u->o);
-  if (u->go) cudaFree(u->go);
-  if (u->part) cudaFree(u->part);
-  if (u->h_part) cudaFreeHost(u->h_part);
-  if (u->nhwc) cudaFree(u->nhwc);
+  if (u->o) vie_free(u->o);
+  if (u->go) vie_free(u->go);
+  if (u->part) vie_free(u->part);
+  if (u->h_part) vie_free_host(u->h_part);
+  if (u->nhwc) vie_free(u->nhwc);
   u->nhwc = nullptr;
-  if (u->hx) cudaFree(u->hx);
+  if (u->hx) vie_free(u->hx);
   u->hx = nullptr;
-  if (u->nhwc_lo) cudaFree(u->nhwc_lo);
-  if (u->wsp_hi) cudaFree(u->wsp_hi);
-  if (u->wsp_lo) cudaFree(u->wsp_lo);
+  if (u->nhwc_lo) vie_free(u->nhwc_lo);
+  if (u->wsp_hi) vie_free(u->wsp_hi);
+  if (u->wsp_lo) vie_free(u->wsp_lo);
   u->nhwc_lo = u->wsp_hi = u->wsp_lo = nullptr;
   for (__nv_bfloat16 *q : u->hcat)
-    if (q) cudaFree(q);
+    if (q) vie_free(q);
   u->hcat.clear();
   u->maps.clear();
   u->o = u->go = nullptr;
@@ -912,7 +912,7 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   free_acts(u);
   const int L = u->L, C = u->C;
   auto al = [](float **q, long count) -> vie_status {
-    VIE_CUDA(cudaMalloc((void **)q, sizeof(float) * std::max(1L, count)));
+    VIE_CUDA(vie_malloc((void **)q, sizeof(float) * std::max(1L, count)));
     return VIE_OK;
   };
   u->xin.assign(L, nullptr); u->a.assign(L, nullptr); u->cat.assign(L, nullptr);
@@ -941,26 +941,26 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
   if ((s = al(&u->gebot[0], (long)B * C * hwb)) != VIE_OK) return s;
   if ((s = al(&u->o, (long)B * n * n)) != VIE_OK) return s;
   if ((s = al(&u->go, (long)B * n * n)) != VIE_OK) return s;
-  VIE_CUDA(cudaMalloc((void **)&u->part, sizeof(double) * 1024));
-  VIE_CUDA(cudaMallocHost((void **)&u->h_part, sizeof(double) * 1024));
+  VIE_CUDA(vie_malloc((void **)&u->part, sizeof(double) * 1024));
+  VIE_CUDA(vie_malloc_host((void **)&u->h_part, sizeof(double) * 1024));
   // the widest convolution input: 2 C channels (a decoder's concatenation), padded to slices
-  VIE_CUDA(cudaMalloc((void **)&u->nhwc,
+  VIE_CUDA(vie_malloc((void **)&u->nhwc,
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
-  VIE_CUDA(cudaMalloc((void **)&u->nhwc_lo,
+  VIE_CUDA(vie_malloc((void **)&u->nhwc_lo,
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
   {
     const size_t wsp = (size_t)9 * ((2 * C + 31) / 32) * 32 * 32;  // 9 S blocks of [32][32]
-    VIE_CUDA(cudaMalloc((void **)&u->wsp_hi, sizeof(__nv_bfloat16) * wsp));
-    VIE_CUDA(cudaMalloc((void **)&u->wsp_lo, sizeof(__nv_bfloat16) * wsp));
+    VIE_CUDA(vie_malloc((void **)&u->wsp_hi, sizeof(__nv_bfloat16) * wsp));
+    VIE_CUDA(vie_malloc((void **)&u->wsp_lo, sizeof(__nv_bfloat16) * wsp));
   }
   // the hand-off buffers, zeroed once: their padding channels are never written
   const size_t cp1 = (size_t)((C + 31) / 32) * 32, cp2 = (size_t)((2 * C + 31) / 32) * 32;
-  VIE_CUDA(cudaMalloc((void **)&u->hx, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
+  VIE_CUDA(vie_malloc((void **)&u->hx, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
   VIE_CUDA(cudaMemset(u->hx, 0, sizeof(__nv_bfloat16) * (size_t)B * n * n * cp1));
   u->hcat.assign(L, nullptr);
   for (int l = 0; l < L - 1; ++l) {
     const size_t bytes = sizeof(__nv_bfloat16) * (size_t)B * (n >> l) * (n >> l) * cp2;
-    VIE_CUDA(cudaMalloc((void **)&u->hcat[l], bytes));
+    VIE_CUDA(vie_malloc((void **)&u->hcat[l], bytes));
     VIE_CUDA(cudaMemset(u->hcat[l], 0, bytes));
   }
   u->B = B;
@@ -1545,11 +1545,11 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
   vie_status s = VIE_OK;
   cudaError_t e = cudaSuccess;
   for (float **q : {&U.p, &U.g, &U.m, &U.v})
-    if (e == cudaSuccess) e = cudaMalloc((void **)q, sizeof(float) * off);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&U.wt, sizeof(float) * max_w);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&U.pb, sizeof(__nv_bfloat16) * off);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&U.dev_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&U.ptc, sizeof(__nv_bfloat16) * std::max(1L, U.ptc_elems));
+    if (e == cudaSuccess) e = vie_malloc((void **)q, sizeof(float) * off);
+  if (e == cudaSuccess) e = vie_malloc((void **)&U.wt, sizeof(float) * max_w);
+  if (e == cudaSuccess) e = vie_malloc((void **)&U.pb, sizeof(__nv_bfloat16) * off);
+  if (e == cudaSuccess) e = vie_malloc((void **)&U.dev_err, sizeof(int));
+  if (e == cudaSuccess) e = vie_malloc((void **)&U.ptc, sizeof(__nv_bfloat16) * std::max(1L, U.ptc_elems));
   if (e == cudaSuccess) e = cudaMemset(U.dev_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(U.p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(U.m, 0, sizeof(float) * off);
@@ -1564,7 +1564,7 @@ vie_status vie_unet_create(vie_unet **out, int levels, int channels, unsigned lo
   if (s != VIE_OK) {
     for (void *q : {(void *)U.p, (void *)U.g, (void *)U.m, (void *)U.v, (void *)U.wt, (void *)U.pb,
                     (void *)U.dev_err, (void *)U.ptc})
-      if (q) cudaFree(q);
+      if (q) vie_free(q);
     delete u;
     return s;
   }
@@ -1579,7 +1579,7 @@ vie_status vie_unet_destroy(vie_unet *u) {
   free_acts(&u->impl);
   for (void *q : {(void *)u->impl.p, (void *)u->impl.g, (void *)u->impl.m, (void *)u->impl.v,
                   (void *)u->impl.wt, (void *)u->impl.pb, (void *)u->impl.dev_err, (void *)u->impl.ptc})
-    if (q) cudaFree(q);
+    if (q) vie_free(q);
   delete u;
   return VIE_OK;
 }

@@ -95,7 +95,7 @@ template <typename T>
 static vie_status dalloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) return VIE_OK;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  cudaError_t e = vie_malloc((void **)p, count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     return cuda_fail(e, "cudaMalloc");
@@ -105,7 +105,7 @@ static vie_status dalloc(T **p, size_t count) {
 
 template <typename T>
 static void dfree(T *&p) {
-  if (p) cudaFree((void *)p);
+  if (p) vie_free((void *)p);
   p = nullptr;
 }
 
@@ -227,7 +227,7 @@ void free_gmres(vie_handle *h) {
   dfree(h->htmp);
   dfree(h->part);
   dfree(h->scal);
-  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->h_pinned) vie_free_host(h->h_pinned);
   h->h_pinned = nullptr;
   h->gm_m = 0;
 }
@@ -239,9 +239,9 @@ void free_multi(MultiGmres &g) {
     dfree(*p);
   for (int **p : {&b.ticket, &b.act, &g.kk}) dfree(*p);
   dfree(g.net_x);
-  if (g.h_scal) cudaFreeHost(g.h_scal);
-  if (g.h_gv) cudaFreeHost(g.h_gv);
-  if (g.h_act) cudaFreeHost(g.h_act);
+  if (g.h_scal) vie_free_host(g.h_scal);
+  if (g.h_gv) vie_free_host(g.h_gv);
+  if (g.h_act) vie_free_host(g.h_act);
   g = MultiGmres{};
 }
 
@@ -251,11 +251,11 @@ void free_all(vie_handle *h) {
   dfree(h->sig32);
   dfree(h->sig64);
   dfree(h->diag);
-  if (h->src) cudaFree(h->src);
+  if (h->src) vie_free(h->src);
   h->src = nullptr;
-  if (h->pairs) cudaFree(h->pairs);
+  if (h->pairs) vie_free(h->pairs);
   h->pairs = nullptr;
-  if (h->sym_partial) cudaFree(h->sym_partial);
+  if (h->sym_partial) vie_free(h->sym_partial);
   h->sym_partial = nullptr;
   dfree(h->partial);
   h->stage_a.release();
@@ -266,8 +266,8 @@ void free_all(vie_handle *h) {
   dfree(h->qpad);
   dfree(h->Z);
   dfree(h->net_x);
-  if (h->kmat) cudaFree(h->kmat);
-  if (h->kmat_lo) cudaFree(h->kmat_lo);
+  if (h->kmat) vie_free(h->kmat);
+  if (h->kmat_lo) vie_free(h->kmat_lo);
   h->kmat = h->kmat_lo = nullptr;
   h->g32.release();
   h->gemm_ws.release();
@@ -281,7 +281,7 @@ void free_all(vie_handle *h) {
   disp3_release(&h->disp3);
   free_gmres(h);
   free_multi(h->mg);
-  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_err) vie_free_host(h->h_err);
   h->h_err = nullptr;
   for (auto &ev : h->events)
     for (auto &e : ev.e)
@@ -312,7 +312,7 @@ vie_status ensure_gmres(vie_handle *h, int m) {
     if ((s = dalloc(&h->ticket, 1)) != VIE_OK) return s;
     VIE_CUDA(cudaMemset(h->ticket, 0, sizeof(int)));
   }
-  VIE_CUDA(cudaMallocHost((void **)&h->h_pinned, sizeof(double) * (m + 1 + 8)));
+  VIE_CUDA(vie_malloc_host((void **)&h->h_pinned, sizeof(double) * (m + 1 + 8)));
   h->gm_m = m;
   return VIE_OK;
 }
@@ -463,7 +463,7 @@ vie_status norm2_dev(vie_handle *h, const double *x, double *out, cudaStream_t s
 // synchronisation, then take_errors reports VIE_ERR_TIMEOUT if a bounded
 // device wait gave up (and clears the words for the next call).
 vie_status queue_errors(vie_handle *h, cudaStream_t st) {
-  if (!h->h_err) VIE_CUDA(cudaMallocHost((void **)&h->h_err, 2 * sizeof(int)));
+  if (!h->h_err) VIE_CUDA(vie_malloc_host((void **)&h->h_err, 2 * sizeof(int)));
   h->h_err[0] = h->h_err[1] = 0;
   if (h->dev_err) VIE_CUDA(cudaMemcpyAsync(h->h_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (h->precond)
@@ -524,9 +524,9 @@ vie_status ensure_multi(vie_handle *h, int R, int m, bool need_z, bool need_net)
   if ((s = dalloc(&g.kk, (size_t)R)) != VIE_OK) return s;
   if (need_net && (s = dalloc(&g.net_x, (size_t)R * 3 * N)) != VIE_OK) return s;
   VIE_CUDA(cudaMemset(b.ticket, 0, sizeof(int) * R));
-  VIE_CUDA(cudaMallocHost((void **)&g.h_scal, sizeof(double) * 8 * R));
-  VIE_CUDA(cudaMallocHost((void **)&g.h_gv, sizeof(double) * (size_t)R * (m + 1)));
-  VIE_CUDA(cudaMallocHost((void **)&g.h_act, sizeof(int) * 2 * R));
+  VIE_CUDA(vie_malloc_host((void **)&g.h_scal, sizeof(double) * 8 * R));
+  VIE_CUDA(vie_malloc_host((void **)&g.h_gv, sizeof(double) * (size_t)R * (m + 1)));
+  VIE_CUDA(vie_malloc_host((void **)&g.h_act, sizeof(int) * 2 * R));
   g.R = R;
   g.m = m;
   g.has_z = need_z;
@@ -938,7 +938,7 @@ vie_status vie_create(vie_handle **out, const vie_grid *g, const double *sigma_t
                  opts.device, &h->plan));
   {
     size_t bytes = (opts.precision == VIE_PREC_FP64 ? sizeof(double) : sizeof(float)) * N;
-    cudaError_t e = cudaMalloc(&h->src, bytes);
+    cudaError_t e = vie_malloc(&h->src, bytes);
     if (e != cudaSuccess) TRY(cuda_fail(e, "cudaMalloc"));
   }
   const bool fast = opts.precision == VIE_PREC_FP32 && opts.tau_mode == VIE_TAU_MARCH && opts.steps == 64;
@@ -988,7 +988,10 @@ vie_status vie_destroy(vie_handle *h) {
   if (!h) return VIE_OK;
   DeviceGuard dg(h->device);
   cudaDeviceSynchronize();
-  free_all(h);
+  {
+    DeviceIdle idle;  // synchronised just above: the buffers go back to the cache at once
+    free_all(h);
+  }
   delete h;
   return VIE_OK;
 }
@@ -1103,8 +1106,8 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
   const bool reuse = mode != VIE_OPERATOR_OTF && mode != VIE_OPERATOR_FMM && mode == h->asm_mode && h->kmat;
   if (!reuse) {
     if (h->kmat || h->kmat_lo || h->fmm.on) VIE_CUDA(cudaStreamSynchronize(st));
-    if (h->kmat) cudaFree(h->kmat);
-    if (h->kmat_lo) cudaFree(h->kmat_lo);
+    if (h->kmat) vie_free(h->kmat);
+    if (h->kmat_lo) vie_free(h->kmat_lo);
     h->kmat = h->kmat_lo = nullptr;
     fmm_release(&h->fmm);
     h->asm_mode = VIE_OPERATOR_OTF;
@@ -1133,9 +1136,9 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
                 "block product (2D, FP32 tiles, S = 64, n <= 160)");
       return VIE_ERR_UNSUPPORTED;
     }
-    if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * symv_block_floats(h->n)));
-    if (!h->sym_partial) VIE_CUDA(cudaMalloc((void **)&h->sym_partial, sizeof(float) * symv_partial_floats(h->n)));
-    if (!h->pairs) VIE_CUDA(cudaMalloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
+    if (!reuse) VIE_CUDA(vie_malloc(&h->kmat, sizeof(float) * symv_block_floats(h->n)));
+    if (!h->sym_partial) VIE_CUDA(vie_malloc((void **)&h->sym_partial, sizeof(float) * symv_partial_floats(h->n)));
+    if (!h->pairs) VIE_CUDA(vie_malloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
     const double hh = 1.0 / h->n;
     const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
     const float wcoef = (float)(hh / (2.0 * kPi));
@@ -1154,7 +1157,7 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
                 "n <= 258)");
       return VIE_ERR_UNSUPPORTED;
     }
-    if (!reuse) VIE_CUDA(cudaMalloc(&h->kmat, sizeof(float) * (size_t)h->disp.stored));
+    if (!reuse) VIE_CUDA(vie_malloc(&h->kmat, sizeof(float) * (size_t)h->disp.stored));
     const double hh = 1.0 / h->n;
     const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
     const float wcoef = (float)(hh / (2.0 * kPi));
@@ -1184,12 +1187,12 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
   if (reuse) {
     // same storage, entries recomputed in place
   } else if (mode == VIE_OPERATOR_FP32) {
-    VIE_CUDA(cudaMalloc(&h->kmat, 2 * half));
+    VIE_CUDA(vie_malloc(&h->kmat, 2 * half));
   } else {
-    VIE_CUDA(cudaMalloc(&h->kmat, half));
-    cudaError_t e = cudaMalloc(&h->kmat_lo, half);
+    VIE_CUDA(vie_malloc(&h->kmat, half));
+    cudaError_t e = vie_malloc(&h->kmat_lo, half);
     if (e != cudaSuccess) {
-      cudaFree(h->kmat);
+      vie_free(h->kmat);
       h->kmat = nullptr;
       return cuda_fail(e, "cudaMalloc");
     }
@@ -1200,7 +1203,7 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
   void *khi = mode == VIE_OPERATOR_BF16X3 ? h->kmat : nullptr;
   if (disp2) {
     // march every unordered pair once into the pair weights, then expand them into K
-    if (!h->pairs) VIE_CUDA(cudaMalloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
+    if (!h->pairs) VIE_CUDA(vie_malloc(&h->pairs, sizeof(float) * (size_t)h->disp.stored));
     const double hh = 1.0 / h->n;
     const float tau_scale2 = (float)(hh / h->opts.steps * 1.4426950408889634);
     const float wcoef = (float)(hh / (2.0 * kPi));

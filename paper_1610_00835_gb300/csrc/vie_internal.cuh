@@ -23,6 +23,29 @@ void set_error(const std::string &msg);
 // run out); draining already issued copies and products after an abort
 // always takes `limit`.  wait_limits(device) converts the process-wide
 // setting of vie_set_wait_limits with the device's clock rate.
+// Device memory of the library (vie_mem.cu): a caching allocator in front of
+// cudaMalloc / cudaFree, same contract (vie_free synchronises the device, as
+// cudaFree does, unless a DeviceIdle is alive on the calling thread).
+cudaError_t vie_malloc(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t vie_malloc(T **p, size_t bytes) {
+  return vie_malloc(reinterpret_cast<void **>(p), bytes);
+}
+cudaError_t vie_free(void *p);
+// the same for pinned host buffers (cudaMallocHost / cudaFreeHost)
+cudaError_t vie_malloc_host(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t vie_malloc_host(T **p, size_t bytes) {
+  return vie_malloc_host(reinterpret_cast<void **>(p), bytes);
+}
+cudaError_t vie_free_host(void *p);
+void vie_release_cached_memory();
+// the caller has synchronised the device: frees need not wait for it again
+struct DeviceIdle {
+  DeviceIdle();
+  ~DeviceIdle();
+};
+
 struct WaitLimits {
   long long limit, first;
 };

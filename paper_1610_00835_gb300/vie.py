@@ -95,6 +95,7 @@ SIGNATURES = {
     "vie_unet_set_params": (C.c_int, [_vp, _vp]),
     "vie_unet_forward": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "vie_unet_loss_grad": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
+    "vie_release_memory": (C.c_int, []),
     "vie_unet_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float,
                                       C.POINTER(C.c_double), _vp]),
     "vie_unet_save": (C.c_int, [_vp, C.c_char_p]),
@@ -480,3 +481,8 @@ def vie_version() -> str:
 
 def vie_kernel_launches() -> int:
     return int(load().vie_kernel_launches())
+
+
+def vie_release_memory() -> None:
+    """Return the library's cached device buffers to CUDA (include/vie.h)."""
+    _check(load().vie_release_memory())
