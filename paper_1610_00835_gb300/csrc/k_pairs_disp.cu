@@ -56,6 +56,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "disp_march.cuh"
@@ -778,19 +779,33 @@ vie_status geometry_build(int n, int ldp, bool global, int R, Geometry *geo) {
     int4 u;
     long cost;
   };
-  std::vector<U> units;
-  std::vector<float> rec;
-  std::vector<Cell> cy_cells, cx_cells;
-  std::vector<int> cy_runs, cx_runs;
+  // first stored weight of each D, in the half plane's order
   std::vector<long long> doff;
   long long stored = 0;
-  double taps = 0.0;
   for (int dy = 0; dy < n; ++dy)
     for (int dx = -(n - 1); dx < n; ++dx) {
       if (dy == 0 && dx <= 0) continue;
-      const int wx = n - std::abs(dx), wy = n - dy;
       doff.push_back(stored);
-      stored += (long long)wx * wy;
+      stored += (long long)(n - std::abs(dx)) * (n - dy);
+    }
+  // each row dy of displacements into its own lists (record offsets local to
+  // the row), the rows spread over host threads, then joined in row order
+  struct Row {
+    std::vector<U> units;
+    std::vector<float> rec;
+    double taps = 0.0;
+    vie_status s = VIE_OK;
+  };
+  std::vector<Row> rows(n);
+  auto build_row = [&](int dy, Row &o) {
+    std::vector<U> &units = o.units;
+    std::vector<float> &rec = o.rec;
+    double &taps = o.taps;
+    std::vector<Cell> cy_cells, cx_cells;
+    std::vector<int> cy_runs, cx_runs;
+    for (int dx = -(n - 1); dx < n; ++dx) {
+      if (dy == 0 && dx <= 0) continue;
+      const int wx = n - std::abs(dx), wy = n - dy;
       stencil_cells(dx, dy, true, cy_cells);
       stencil_runs(cy_cells, true, cy_runs);
       stencil_cells(dx, dy, false, cx_cells);
@@ -823,8 +838,8 @@ vie_status geometry_build(int n, int ldp, bool global, int R, Geometry *geo) {
       int per_len[kMaxChunk + 1] = {};
       for_each_chunk(runs, [&](int, int lc) { ++per_len[lc]; });
       if (*std::max_element(per_len, per_len + kMaxChunk + 1) > 65535 || pl.recs + 1 > 524287) {
-        set_error("displacement kernel: stencil longer than the unit encoding allows");
-        return VIE_ERR_UNSUPPORTED;
+        o.s = VIE_ERR_UNSUPPORTED;
+        return;
       }
       const int lanes = along_y ? wx : wy, stack = along_y ? wy : wx;
       // blocks of R stacked targets (the last one ragged); a unit carries
@@ -847,6 +862,35 @@ vie_status geometry_build(int n, int ldp, bool global, int R, Geometry *geo) {
             units.push_back({make_int4(off, dxy, full | ((R * (base + j)) << 16), w | (lg << 1)), pl.cost});
       }
     }
+  };
+  {
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+      pool.emplace_back([&, t]() {
+        for (int dy = t; dy < n; dy += nt) build_row(dy, rows[dy]);
+      });
+    for (std::thread &th : pool) th.join();
+  }
+  std::vector<U> units;
+  std::vector<float> rec;
+  double taps = 0.0;
+  for (int dy = 0; dy < n; ++dy) {
+    Row &o = rows[dy];
+    if (o.s != VIE_OK) {
+      set_error("displacement kernel: stencil longer than the unit encoding allows");
+      return o.s;
+    }
+    const int base = (int)(rec.size() / 4);
+    for (U u : o.units) {
+      u.u.x += base;
+      units.push_back(u);
+    }
+    rec.insert(rec.end(), o.rec.begin(), o.rec.end());
+    taps += o.taps;
+    std::vector<U>().swap(o.units);
+    std::vector<float>().swap(o.rec);
+  }
   for (int i = 0; i < 32; ++i) rec.push_back(0.f);  // the L1 prefetch may reach 127 bytes past a stencil
   std::stable_sort(units.begin(), units.end(), [](const U &p, const U &q) { return p.cost > q.cost; });
   std::vector<int4> uv(units.size());
