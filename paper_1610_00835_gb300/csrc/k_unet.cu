@@ -183,14 +183,18 @@ size_t conv_tma_smem(int S, int Co, int Wb, int nst, int np = 1) {
          16;
 }
 
-// SPLIT: the FP32 convolution of training in split precision: input and
-// weights each as BF16 hi + lo (map_xl, map_wl the lo halves), every tap
-// three products hi hi + hi lo + lo hi into the FP32 accumulator (lo lo, below
-// 2^-16 of the terms, left out); a stage holds the hi box, then the lo box.
-template <bool RELU, bool SPLIT>
+// NP > 1: the FP32 convolutions of training in split precision: input and
+// weights each as NP BF16 parts (v = p0 + p1 [+ p2], each part the BF16
+// rounding of what the earlier ones leave; map_x1 / map_w1, map_x2 / map_w2
+// the later parts), every tap the products of parts i, j with i + j < NP
+// into the FP32 accumulator (the terms left out are below 2^-8 NP of the
+// kept ones: 2^-16 for two parts, 2^-24 for three); a stage holds the parts'
+// boxes one after the other.
+template <bool RELU, int NP>
 __global__ void __launch_bounds__(kConvThreads, 2)
     k_conv3_tma(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
-                const __grid_constant__ CUtensorMap map_xl, const __grid_constant__ CUtensorMap map_wl,
+                const __grid_constant__ CUtensorMap map_x1, const __grid_constant__ CUtensorMap map_w1,
+                const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_w2,
                 const float *__restrict__ bias, float *__restrict__ out, long out_bs, int Co, int H, int W, int S,
                 int Wb, int R, int tiles_x, int tiles, int nst, WaitLimits wl, int *err,
                 __nv_bfloat16 *__restrict__ out_h, long oh_bs, int oh_cp, int oh_c0) {
@@ -203,10 +207,10 @@ __global__ void __launch_bounds__(kConvThreads, 2)
   const bool halo = R == 1;
   const int steps = (halo ? 3 : 9) * S, taps_step = halo ? 3 : 1;
   const int tiles_img = tiles_x * ((H + R - 1) / R);
-  constexpr int NP = SPLIT ? 2 : 1;  // operand parts
   const int a_part = conv_stage_bytes(Wb), a_bytes = NP * a_part, b_bytes = Co * 64;
-  unsigned char *Bs = smem, *Bl = smem + (size_t)9 * S * b_bytes;
-  unsigned char *As = smem + (size_t)NP * 9 * S * b_bytes;
+  const size_t b_part = (size_t)9 * S * b_bytes;  // one part of the weights
+  unsigned char *Bs = smem;
+  unsigned char *As = smem + (size_t)NP * b_part;
   unsigned long long *full = (unsigned long long *)(As + (size_t)nst * a_bytes);
   unsigned long long *empty = full + nst, *tfull = empty + nst, *tempty = tfull + kAcc;
   unsigned long long *wbar = tempty + kAcc, *done = wbar + 1;
@@ -245,7 +249,8 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     mbar_arrive_expect_tx(su32(wbar), (unsigned)(NP * 9 * S * b_bytes));
     for (int k = 0; k < 9 * S; ++k) {
       tma_load_2d(su32(Bs + (size_t)k * b_bytes), &map_w, su32(wbar), 0, k * Co);
-      if (SPLIT) tma_load_2d(su32(Bl + (size_t)k * b_bytes), &map_wl, su32(wbar), 0, k * Co);
+      if (NP > 1) tma_load_2d(su32(Bs + b_part + (size_t)k * b_bytes), &map_w1, su32(wbar), 0, k * Co);
+      if (NP > 2) tma_load_2d(su32(Bs + 2 * b_part + (size_t)k * b_bytes), &map_w2, su32(wbar), 0, k * Co);
     }
     int g = 0;
     bool go = true;
@@ -266,8 +271,11 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         mbar_arrive_expect_tx(su32(full + st), NP * box_bytes);
         tma_load_4d(su32(As + (size_t)st * a_bytes), &map_x, su32(full + st), sl * kTmaSlice, x0 + dx - 1,
                     y0 + dy - 1, img);
-        if (SPLIT)
-          tma_load_4d(su32(As + (size_t)st * a_bytes + a_part), &map_xl, su32(full + st), sl * kTmaSlice,
+        if (NP > 1)
+          tma_load_4d(su32(As + (size_t)st * a_bytes + a_part), &map_x1, su32(full + st), sl * kTmaSlice,
+                      x0 + dx - 1, y0 + dy - 1, img);
+        if (NP > 2)
+          tma_load_4d(su32(As + (size_t)st * a_bytes + 2 * a_part), &map_x2, su32(full + st), sl * kTmaSlice,
                       x0 + dx - 1, y0 + dy - 1, img);
         ++issued_loads;
       }
@@ -300,13 +308,16 @@ __global__ void __launch_bounds__(kConvThreads, 2)
           const unsigned bb = su32(Bs + (size_t)(tap * S + sl) * b_bytes);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            mma_bf16(d, smem_desc_sw64(a + kk * 32), smem_desc_sw64(bb + kk * 32), idesc,
-                     (k > 0 || e > 0 || kk > 0) ? 1u : 0u);
-            if (SPLIT) {
-              const unsigned al = a + (unsigned)a_part, bl = su32(Bl + (size_t)(tap * S + sl) * b_bytes);
-              mma_bf16(d, smem_desc_sw64(a + kk * 32), smem_desc_sw64(bl + kk * 32), idesc, 1u);
-              mma_bf16(d, smem_desc_sw64(al + kk * 32), smem_desc_sw64(bb + kk * 32), idesc, 1u);
-            }
+            // parts i of the input and j of the weights, i + j < NP
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+#pragma unroll
+              for (int j = 0; i + j < NP; ++j) {
+                const unsigned ai = a + (unsigned)(i * a_part) + kk * 32;
+                const unsigned bj = bb + (unsigned)(j * b_part) + kk * 32;
+                mma_bf16(d, smem_desc_sw64(ai), smem_desc_sw64(bj), idesc,
+                         (k > 0 || e > 0 || kk > 0 || i > 0 || j > 0) ? 1u : 0u);
+              }
           }
         }
         mma_commit(su32(empty + st));  // the stage is free once these products finish
@@ -439,39 +450,54 @@ __global__ void k_pack_tc_weights(const float *__restrict__ w, int Co, int Ci, i
   }
 }
 
-// The split-precision operands of training: v = hi + lo, hi = bf16(v),
-// lo = bf16(v - hi) (v - hi is exact in FP32), 16 significant bits in all.
-// Input: FP32 [B][Ci][plane] -> hi, lo BF16 [B][plane][Cp], one thread per
-// (image, pixel) as in k_to_nhwc_bf16.
+// The split-precision operands of training: v = p0 + p1 [+ p2], p0 = bf16(v),
+// each later part the BF16 rounding of what the earlier ones leave (exact in
+// FP32): 16 significant bits for two parts, 24 (all of FP32's) for three.
+__device__ __forceinline__ void split_parts(float v, int np, __nv_bfloat16 (&part)[3]) {
+  float r = v;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    part[q] = __float2bfloat16_rn(q < np ? r : 0.f);
+    r -= __bfloat162float(part[q]);
+  }
+}
+
+// Input: FP32 [B][Ci][plane] -> NP BF16 parts [B][plane][Cp] (out0, out1,
+// out2), one thread per (image, pixel) as in k_to_nhwc_bf16.
+template <int NP>
 __global__ void k_to_nhwc_split(const float *__restrict__ in, long in_bs, int Ci, long plane, int Cp, int B,
-                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+                                __nv_bfloat16 *__restrict__ out0, __nv_bfloat16 *__restrict__ out1,
+                                __nv_bfloat16 *__restrict__ out2) {
   const long total = (long)B * plane;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
     const long b = t / plane, p = t - b * plane;
     const float *src = in + b * in_bs + p;
-    uint4 *dh = reinterpret_cast<uint4 *>(hi + t * Cp), *dl = reinterpret_cast<uint4 *>(lo + t * Cp);
     for (int gq = 0; gq < Cp / 8; ++gq) {
-      unsigned wh[4], wl[4];
+      unsigned w[3][4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int c = gq * 8 + 2 * e;
-        const float v0 = c < Ci ? src[(long)c * plane] : 0.f, v1 = c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f;
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-        const float2 hf = __bfloat1622float2(h2);
-        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        wh[e] = *reinterpret_cast<const unsigned *>(&h2);
-        wl[e] = *reinterpret_cast<const unsigned *>(&l2);
+        __nv_bfloat16 p0[3], p1[3];
+        split_parts(c < Ci ? src[(long)c * plane] : 0.f, NP, p0);
+        split_parts(c + 1 < Ci ? src[(long)(c + 1) * plane] : 0.f, NP, p1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const __nv_bfloat162 h2 = __halves2bfloat162(p0[q], p1[q]);
+          w[q][e] = *reinterpret_cast<const unsigned *>(&h2);
+        }
       }
-      dh[gq] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-      dl[gq] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      reinterpret_cast<uint4 *>(out0 + t * Cp)[gq] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+      if (NP > 1) reinterpret_cast<uint4 *>(out1 + t * Cp)[gq] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+      if (NP > 2) reinterpret_cast<uint4 *>(out2 + t * Cp)[gq] = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
     }
   }
 }
 
-// Weights FP32 [Co][Ci][9], output channels co0 .. co0 + cb -> hi, lo BF16
+// Weights FP32 [Co][Ci][9], output channels co0 .. co0 + cb -> np BF16 parts
 // [9 S][cb][32] in k_pack_tc_weights's block order.
-__global__ void k_pack_split_weights(const float *__restrict__ w, int Co, int Ci, int S, int co0, int cb,
-                                     __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+__global__ void k_pack_split_weights(const float *__restrict__ w, int Co, int Ci, int S, int co0, int cb, int np,
+                                     __nv_bfloat16 *__restrict__ w0, __nv_bfloat16 *__restrict__ w1,
+                                     __nv_bfloat16 *__restrict__ w2) {
   const long total = (long)9 * S * cb * kTmaSlice;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
     const int c = (int)(t % kTmaSlice);
@@ -479,10 +505,11 @@ __global__ void k_pack_split_weights(const float *__restrict__ w, int Co, int Ci
     const int co = co0 + (int)(r % cb);
     const int k = (int)(r / cb);
     const int tap = k / S, ci = (k - tap * S) * kTmaSlice + c;
-    const float v = ci < Ci && co < Co ? w[((long)co * Ci + ci) * 9 + tap] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[t] = h;
-    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    __nv_bfloat16 part[3];
+    split_parts(ci < Ci && co < Co ? w[((long)co * Ci + ci) * 9 + tap] : 0.f, np, part);
+    w0[t] = part[0];
+    if (np > 1) w1[t] = part[1];
+    if (np > 2) w2[t] = part[2];
   }
 }
 
@@ -870,8 +897,8 @@ struct UnetImpl {
   // the input-gradient convolutions of training on the tensor cores (split
   // precision): the lo half of the converted input, the split weights of
   // one 32-channel output block
-  bool train_tc = false;
-  __nv_bfloat16 *nhwc_lo = nullptr, *wsp_hi = nullptr, *wsp_lo = nullptr;
+  int train_tc = 0;  // operand parts of the training convolutions on the tensor cores (0: CUDA cores)
+  __nv_bfloat16 *nhwc_lo = nullptr, *nhwc_p2 = nullptr, *wsp_hi = nullptr, *wsp_lo = nullptr, *wsp_p2 = nullptr;
   std::vector<MapEntry> maps;
 };
 
@@ -893,10 +920,10 @@ void free_acts(UnetImpl *u) {
   u->nhwc = nullptr;
   if (u->hx) vie_free(u->hx);
   u->hx = nullptr;
-  if (u->nhwc_lo) vie_free(u->nhwc_lo);
-  if (u->wsp_hi) vie_free(u->wsp_hi);
-  if (u->wsp_lo) vie_free(u->wsp_lo);
-  u->nhwc_lo = u->wsp_hi = u->wsp_lo = nullptr;
+  for (__nv_bfloat16 **q : {&u->nhwc_lo, &u->nhwc_p2, &u->wsp_hi, &u->wsp_lo, &u->wsp_p2}) {
+    if (*q) vie_free(*q);
+    *q = nullptr;
+  }
   for (__nv_bfloat16 *q : u->hcat)
     if (q) vie_free(q);
   u->hcat.clear();
@@ -948,10 +975,13 @@ vie_status ensure_acts(UnetImpl *u, int B, int n) {
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
   VIE_CUDA(vie_malloc((void **)&u->nhwc_lo,
                       sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
+  VIE_CUDA(vie_malloc((void **)&u->nhwc_p2,
+                      sizeof(__nv_bfloat16) * (size_t)B * n * n * (size_t)(((2 * C + 31) / 32) * 32)));
   {
     const size_t wsp = (size_t)9 * ((2 * C + 31) / 32) * 32 * 32;  // 9 S blocks of [32][32]
     VIE_CUDA(vie_malloc((void **)&u->wsp_hi, sizeof(__nv_bfloat16) * wsp));
     VIE_CUDA(vie_malloc((void **)&u->wsp_lo, sizeof(__nv_bfloat16) * wsp));
+    VIE_CUDA(vie_malloc((void **)&u->wsp_p2, sizeof(__nv_bfloat16) * wsp));
   }
   // the hand-off buffers, zeroed once: their padding channels are never written
   const size_t cp1 = (size_t)((C + 31) / 32) * 32, cp2 = (size_t)((2 * C + 31) / 32) * 32;
@@ -1059,13 +1089,13 @@ vie_status conv_weight_map(UnetImpl *u, const __nv_bfloat16 *wtc, int S, int Co,
   return cached_map(u, wtc, key, 2, dims, strides, box, mw);
 }
 
-// Launch k_conv3_tma (split: the split-precision form, mxl / mwl its lo maps).
-vie_status launch_conv_tma(UnetImpl *u, const CUtensorMap &mx, const CUtensorMap &mw, const CUtensorMap &mxl,
-                           const CUtensorMap &mwl, bool split, const float *bias, float *out, long out_bs, int Co,
-                           int H, int W, int S, int B, bool relu, cudaStream_t st, NhwcIo *io) {
+// Launch k_conv3_tma with np operand parts (maps mx[p], mw[p]; np > 1: the
+// split-precision form).
+vie_status launch_conv_tma(UnetImpl *u, const CUtensorMap *mx, const CUtensorMap *mw, int np, const float *bias,
+                           float *out, long out_bs, int Co, int H, int W, int S, int B, bool relu, cudaStream_t st,
+                           NhwcIo *io) {
   const int Wb = std::min(W, kTcM), R = std::min(kTcM / Wb, H);
   const int tiles_x = (W + Wb - 1) / Wb, tiles_y = (H + R - 1) / R;
-  const int np = split ? 2 : 1;
   int dev = 0;
   VIE_CUDA(cudaGetDevice(&dev));
   DevProps prop;
@@ -1088,8 +1118,9 @@ vie_status launch_conv_tma(UnetImpl *u, const CUtensorMap &mx, const CUtensorMap
     return VIE_ERR_UNSUPPORTED;
   }
   const size_t smem = conv_tma_smem(S, Co, Wb, nst, np);
-  const void *k = split ? (relu ? (const void *)k_conv3_tma<true, true> : (const void *)k_conv3_tma<false, true>)
-                        : (relu ? (const void *)k_conv3_tma<true, false> : (const void *)k_conv3_tma<false, false>);
+  const void *k = np == 3   ? (relu ? (const void *)k_conv3_tma<true, 3> : (const void *)k_conv3_tma<false, 3>)
+                  : np == 2 ? (relu ? (const void *)k_conv3_tma<true, 2> : (const void *)k_conv3_tma<false, 2>)
+                            : (relu ? (const void *)k_conv3_tma<true, 1> : (const void *)k_conv3_tma<false, 1>);
   VIE_TRY(raise_smem_limit(k, smem));
   // all of the SM's unified memory as shared memory, so that two CTAs fit
   VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1102,7 +1133,10 @@ vie_status launch_conv_tma(UnetImpl *u, const CUtensorMap &mx, const CUtensorMap
   int oh_cp = io ? io->oh_cp : 0, oh_c0 = io ? io->oh_c0 : 0;
   int nst_i = nst, S_i = S, Co_i = Co, H_i = H, W_i = W, Wb_i = Wb, R_i = R, tx_i = tiles_x;
   int *err = u->dev_err;
-  void *args[] = {(void *)&mx, (void *)&mw, (void *)&mxl, (void *)&mwl, (void *)&bias, (void *)&out,
+  // maps of the parts past np: copies of part 0 (not read)
+  const CUtensorMap *x1 = np > 1 ? mx + 1 : mx, *w1 = np > 1 ? mw + 1 : mw;
+  const CUtensorMap *x2 = np > 2 ? mx + 2 : mx, *w2 = np > 2 ? mw + 2 : mw;
+  void *args[] = {(void *)mx, (void *)mw, (void *)x1, (void *)w1, (void *)x2, (void *)w2, (void *)&bias, (void *)&out,
                   (void *)&out_bs, (void *)&Co_i, (void *)&H_i, (void *)&W_i, (void *)&S_i, (void *)&Wb_i,
                   (void *)&R_i, (void *)&tx_i, (void *)&tiles, (void *)&nst_i, (void *)&wl, (void *)&err,
                   (void *)&oh, (void *)&oh_bs, (void *)&oh_cp, (void *)&oh_c0};
@@ -1124,31 +1158,35 @@ vie_status conv3_tma(UnetImpl *u, const float *in, long in_bs, int Ci, const __n
   CUtensorMap mx, mw;
   VIE_TRY(conv_input_map(u, src, S, H, W, B, &mx));
   VIE_TRY(conv_weight_map(u, wtc, S, Co, &mw));
-  return launch_conv_tma(u, mx, mw, mx, mw, false, bias, out, out_bs, Co, H, W, S, B, relu, st, io);
+  return launch_conv_tma(u, &mx, &mw, 1, bias, out, out_bs, Co, H, W, S, B, relu, st, io);
 }
 
 // The FP32 convolution of training on the tensor cores in split precision:
-// the input split into BF16 hi + lo NHWC, the FP32 weights [Co][Ci][9] split
+// the input split into np BF16 NHWC parts, the FP32 weights [Co][Ci][9] split
 // and packed per block of 32 output channels, one launch per block.
 bool conv_split_ok(int Ci, int Co) { return Ci <= 2 * kTmaSlice && Co % 32 == 0 && Co <= 64; }
 
 vie_status conv3_split(UnetImpl *u, const float *in, long in_bs, int Ci, const float *w, const float *bias,
-                       float *out, long out_bs, int Co, int H, int W, int B, bool relu, cudaStream_t st) {
+                       float *out, long out_bs, int Co, int H, int W, int B, bool relu, int np, cudaStream_t st) {
   const int S = (Ci + kTmaSlice - 1) / kTmaSlice, Cp = S * kTmaSlice;
   const long plane = (long)H * W;
-  k_to_nhwc_split<<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, u->nhwc, u->nhwc_lo);
+  __nv_bfloat16 *xin[3] = {u->nhwc, u->nhwc_lo, u->nhwc_p2}, *wsp[3] = {u->wsp_hi, u->wsp_lo, u->wsp_p2};
+  if (np == 3)
+    k_to_nhwc_split<3><<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, xin[0], xin[1], xin[2]);
+  else
+    k_to_nhwc_split<2><<<gridn((long)B * plane), 256, 0, st>>>(in, in_bs, Ci, plane, Cp, B, xin[0], xin[1], xin[2]);
   VIE_CHECK_LAUNCH("k_to_nhwc_split");
-  CUtensorMap mx, mxl, mw, mwl;
-  VIE_TRY(conv_input_map(u, u->nhwc, S, H, W, B, &mx));
-  VIE_TRY(conv_input_map(u, u->nhwc_lo, S, H, W, B, &mxl));
-  VIE_TRY(conv_weight_map(u, u->wsp_hi, S, 32, &mw));
-  VIE_TRY(conv_weight_map(u, u->wsp_lo, S, 32, &mwl));
+  CUtensorMap mx[3], mw[3];
+  for (int q = 0; q < np; ++q) {
+    VIE_TRY(conv_input_map(u, xin[q], S, H, W, B, &mx[q]));
+    VIE_TRY(conv_weight_map(u, wsp[q], S, 32, &mw[q]));
+  }
   for (int co0 = 0; co0 < Co; co0 += 32) {
-    k_pack_split_weights<<<gridn(9L * S * 32 * kTmaSlice), 256, 0, st>>>(w, Co, Ci, S, co0, 32, u->wsp_hi,
-                                                                         u->wsp_lo);
+    k_pack_split_weights<<<gridn(9L * S * 32 * kTmaSlice), 256, 0, st>>>(w, Co, Ci, S, co0, 32, np, wsp[0], wsp[1],
+                                                                         wsp[2]);
     VIE_CHECK_LAUNCH("k_pack_split_weights");
-    VIE_TRY(launch_conv_tma(u, mx, mw, mxl, mwl, true, bias ? bias + co0 : nullptr, out + co0 * plane, out_bs, 32,
-                            H, W, S, B, relu, st, nullptr));
+    VIE_TRY(launch_conv_tma(u, mx, mw, np, bias ? bias + co0 : nullptr, out + co0 * plane, out_bs, 32, H, W, S, B,
+                            relu, st, nullptr));
   }
   return VIE_OK;
 }
@@ -1163,8 +1201,8 @@ vie_status conv3(UnetImpl *u, const float *in, long in_bs, int Ci, const WT *w, 
     if (conv_on_tensor_cores(wtc, Ci, Co, bias))
       return conv3_tma(u, in, in_bs, Ci, wtc, bias, out, out_bs, Co, H, W, B, relu, st, io);
   } else {
-    if (u->train_tc && conv_split_ok(Ci, Co))
-      return conv3_split(u, in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, relu, st);
+    if (u->train_tc > 1 && conv_split_ok(Ci, Co))
+      return conv3_split(u, in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, relu, u->train_tc, st);
   }
   if (relu)
     conv3_shape<true, WT>(in, in_bs, Ci, w, bias, out, out_bs, Co, H, W, B, st);
@@ -1396,7 +1434,20 @@ vie_status loss_grad(UnetImpl *u, const float *x, const float *t, const float *w
                      cudaStream_t st) {
   vie_status s;
   if ((s = ensure_acts(u, B, n)) != VIE_OK) return s;
-  if ((s = forward<float>(u, u->p, x, B, n, st)) != VIE_OK) return s;
+  // the training convolutions on the tensor cores in split precision: the
+  // forward in three parts (24 significant bits, FP32's own: in two parts its
+  // ~1e-5 relative error flipped the ReLU masks of pre-activations near zero,
+  // each flip moving a gradient entry by a whole term, 3.6e-3 relative
+  // against the FP64 reference, 1e-4 allowed), the input gradients in two
+  struct TrainTc {
+    UnetImpl *u;
+    TrainTc(UnetImpl *q, int np) : u(q) { u->train_tc = np; }
+    ~TrainTc() { u->train_tc = 0; }
+  };
+  {
+    TrainTc tc3(u, 3);
+    if ((s = forward<float>(u, u->p, x, B, n, st)) != VIE_OK) return s;
+  }
   const long cnt = (long)B * n * n;
   const int blocks = 512;
   k_mse<<<blocks, 256, 0, st>>>(u->o, t, cnt, (long)n * n, wts, u->go, u->part);
@@ -1405,16 +1456,7 @@ vie_status loss_grad(UnetImpl *u, const float *x, const float *t, const float *w
   VIE_CUDA(cudaMemcpyAsync(u->h_part, u->part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st));
   VIE_CUDA(cudaMemsetAsync(u->g, 0, sizeof(float) * u->nparams, st));
   {
-    // the input-gradient convolutions on the tensor cores in split
-    // precision.  The forward stays in FP32 on the CUDA cores: its ~1e-5
-    // relative error in split precision flips ReLU masks of pre-activations
-    // near zero, and each flip moves a gradient entry by a whole term
-    // (measured: 3.6e-3 relative against the FP64 reference, 1e-4 allowed).
-    struct TrainTc {
-      UnetImpl *u;
-      explicit TrainTc(UnetImpl *q) : u(q) { u->train_tc = true; }
-      ~TrainTc() { u->train_tc = false; }
-    } train_tc(u);
+    TrainTc tc2(u, 2);
     if ((s = backward(u, x, B, n, st)) != VIE_OK) return s;
   }
   VIE_CUDA(cudaStreamSynchronize(st));
