@@ -518,7 +518,7 @@ __global__ void k_pack_split_weights(const float *__restrict__ w, int Co, int Ci
 // over those images and adds them into dw with atomics once.  A 3 x 3 window
 // of the input slides along x in registers.
 constexpr int WY = 8;
-__global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, long x_bs, int Ci,
+__global__ void __launch_bounds__(256, 3) k_conv3_dw(const float *__restrict__ x, long x_bs, int Ci,
                                                   const float *__restrict__ gy, long g_bs, int Co,
                                                   int H, int W, float *__restrict__ dw,
                                                   float *__restrict__ db, int ci_blocks,
@@ -566,6 +566,9 @@ __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, l
       win[r][0] = x_s[ci_l][yy + r][0];
       win[r][1] = x_s[ci_l][yy + r][1];
     }
+    // unrolled by four along the row: the window's shift is register
+    // renaming within each group
+#pragma unroll 4
     for (int xx = 0; xx < TX; ++xx) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) win[r][2] = x_s[ci_l][yy + r][xx + 2];
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(256) k_conv3_dw(const float *__restrict__ x, l
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[r * 3 + c] = fmaf(g, win[r][c], acc[r * 3 + c]);
-      bsum += g;
+      if (ci_l == 0) bsum += g;  // the bias gradient: warp 0 alone adds it
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         win[r][0] = win[r][1];
