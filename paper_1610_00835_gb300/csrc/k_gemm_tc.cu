@@ -14,15 +14,21 @@
 //   tile of Y for all R columns over one K-range (split-K); a TMA producer
 //   thread streams 64-wide K slices of Khi, Klo, Ghi, Gmid, Glo into a
 //   shared-memory ring of up to 4 stages (128-byte swizzle), one thread
-//   issues tcgen05.mma (M = 128, N = R, K = 16 per instruction) and the four
-//   warps read the accumulators back with tcgen05.ld.
+//   issues tcgen05.mma and the four warps read the accumulators back with
+//   tcgen05.ld.  Per 16-wide K step three instructions (M = 128, K = 16):
+//   Khi Ghi (N = R), and the cross terms as two N = 2R products into one
+//   block of 2R columns, Khi [Gmid; Glo] and Klo [Ghi; Gmid] (the G slices
+//   sit back to back in the stage, so each pair is one operand).  Each
+//   instruction has a fixed cost beside its math, so three wide ones take
+//   less time than five N = R ones on the same operands.
 //   The tensor cores do not round their FP32 accumulation to nearest, so a
 //   long chain of products into one accumulator drifts low (measured: 3e-5
 //   relative after ~770 chained MMAs; the drift grows with the chain, about
 //   2^-25 per MMA).  The dominant Khi Ghi product therefore rotates over up
 //   to seven accumulators (as many as tensor memory holds beside the cross
-//   terms' one), split-K keeps every chain at or below kMaxChain MMAs, and the
-//   accumulators are added in FP32 in the epilogue and across splits in FP64.
+//   block), split-K keeps every chain at or below kMaxChain MMAs, and the
+//   accumulators are added in FP32 in the epilogue, and across splits as an
+//   FP32 hi + lo pair (error-free additions) converted once to FP64.
 //   At most 128 right-hand sides per product (three G slices per stage).
 //   Every mbarrier wait is bounded by a clock limit; on expiry the CTA sets
 //   an error word, stops issuing work, waits for its issued copies and
@@ -118,25 +124,58 @@ __global__ void k_to_f32_padded(const double *__restrict__ g, long N, long ldk, 
 // G (FP64, column r at g + r ldg) -> FP32 -> BF16 hi + mid + lo [rpad][ldk],
 // zero padded.  hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid):
 // each remainder is exact in FP32 and has 8 fewer significant bits, so
-// hi + mid + lo = v (FP32 v in the BF16 exponent range).
-__global__ void k_split_bf16(const double *__restrict__ g, long ldg, long N, long ldk, int nrhs, int rpad,
+// hi + mid + lo = v (FP32 v in the BF16 exponent range).  Row r = blockIdx.y,
+// two columns per thread (ldk is a multiple of 64).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+  h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+__global__ void k_split_bf16(const double *__restrict__ g, long ldg, long N, long ldk, int nrhs,
                              __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ mid,
                              __nv_bfloat16 *__restrict__ lo) {
-  const long total = (long)rpad * ldk;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const long r = i / ldk, c = i % ldk;
-    const float v = (r < nrhs && c < N) ? (float)g[r * ldg + c] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    hi[i] = h;
-    mid[i] = m;
-    lo[i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  const int r = blockIdx.y;
+  const double *gr = g + (long)r * ldg;
+  const long row = (long)r * ldk;
+  for (long c = 2 * (blockIdx.x * (long)blockDim.x + threadIdx.x); c < ldk; c += 2L * gridDim.x * blockDim.x) {
+    const float v0 = (r < nrhs && c < N) ? (float)gr[c] : 0.f;
+    const float v1 = (r < nrhs && c + 1 < N) ? (float)gr[c + 1] : 0.f;
+    __nv_bfloat162 h, m, l;
+    split3(v0, h.x, m.x, l.x);
+    split3(v1, h.y, m.y, l.y);
+    *(__nv_bfloat162 *)(hi + row + c) = h;
+    *(__nv_bfloat162 *)(mid + row + c) = m;
+    *(__nv_bfloat162 *)(lo + row + c) = l;
   }
 }
 
+// Error-free FP32 addition (Knuth's TwoSum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// Running sum of FP32 partials as an unevaluated pair hi + lo: hi is the
+// rounded sum, lo collects the rounding errors (error ~2^-48 relative).
+struct PairSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float e;
+    two_sum(hi, v, hi, e);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // y[r][j] = sum_split part[split][r][j]  (then the operator); column r of g
-// and y at r ldg and r ldy.  A product that gave up on a bounded wait
+// and y at r ldg and r ldy.  The splits are added in split order as an FP32
+// hi + lo pair and converted once: GB300's FP64 pipe is narrow, and a
+// conversion and an FP64 add per split made this kernel FP64-bound.  Row
+// r = blockIdx.y, four columns per thread (16-byte loads of the partials
+// when N is a multiple of 4).  A product that gave up on a bounded wait
 // (*err != 0) turns y into NaN, which the Krylov driver reports as
 // VIE_ERR_NONFINITE.
 __global__ void k_gemm_finish(const float *__restrict__ part, int splits, int nrhs, long N,
@@ -144,12 +183,46 @@ __global__ void k_gemm_finish(const float *__restrict__ part, int splits, int nr
                               double *__restrict__ y, long ldy) {
   const long total = (long)nrhs * N;
   const bool failed = *err != 0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < splits; ++p) s += part[(long)p * total + i];
-    const long r = i / N, j = i - r * N;
-    y[r * ldy + j] = failed ? __longlong_as_double(0x7ff8000000000000LL)
-                            : (op == VIE_OP_I_MINUS_K ? g[r * ldg + j] - s : s);
+  const int r = blockIdx.y;
+  const float *pr = part + (long)r * N;
+  for (long j0 = 4 * (blockIdx.x * (long)blockDim.x + threadIdx.x); j0 < N; j0 += 4L * gridDim.x * blockDim.x) {
+    PairSum s[4];
+    if ((N & 3) == 0) {
+      int p = 0;
+      for (; p + 4 <= splits; p += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg((const float4 *)(pr + (long)(p + u) * total + j0));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          s[0].add(v[u].x);
+          s[1].add(v[u].y);
+          s[2].add(v[u].z);
+          s[3].add(v[u].w);
+        }
+      }
+      for (; p < splits; ++p) {
+        const float4 v = __ldg((const float4 *)(pr + (long)p * total + j0));
+        s[0].add(v.x);
+        s[1].add(v.y);
+        s[2].add(v.z);
+        s[3].add(v.w);
+      }
+    } else {
+      for (int p = 0; p < splits; ++p)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (j0 + e < N) s[e].add(pr[(long)p * total + j0 + e]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const long j = j0 + e;
+      if (j < N) {
+        const double v = s[e].value();
+        y[(long)r * ldy + j] = failed ? __longlong_as_double(0x7ff8000000000000LL)
+                                      : (op == VIE_OP_I_MINUS_K ? g[(long)r * ldg + j] - v : v);
+      }
+    }
   }
 }
 
@@ -214,6 +287,7 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
   const unsigned idesc = idesc_bf16(BM, a.rpad);
+  const unsigned idesc2 = idesc_bf16(BM, 2 * a.rpad);
 
   int issued_loads = 0, issued_mma = 0;
   if (warp == 0 && lane == 0) {
@@ -251,7 +325,8 @@ __global__ void __launch_bounds__(128, 1)
       const unsigned a_hi = su32(st), a_lo = su32(st + a_bytes);
       const unsigned b_hi = su32(st + 2 * a_bytes), b_mid = su32(st + 2 * a_bytes + b_bytes);
       const unsigned b_lo = su32(st + 2 * a_bytes + 2 * b_bytes);
-      // accumulator columns: main_q at q * rpad (q < n_main), cross terms after
+      // accumulator columns: main_q at q * rpad (q < n_main); after them the
+      // cross block of 2 rpad columns, [Khi Gmid + Klo Ghi | Khi Glo + Klo Gmid]
       const int q = i % a.n_main;
       const unsigned d_main = tmem + (unsigned)(q * a.rpad);
       const unsigned d_cross = tmem + (unsigned)(a.n_main * a.rpad);
@@ -261,10 +336,10 @@ __global__ void __launch_bounds__(128, 1)
         const unsigned first_main = (i < a.n_main && kk == 0) ? 0u : 1u;
         const unsigned first_cross = (i == 0 && kk == 0) ? 0u : 1u;
         mma_bf16(d_main, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, first_main);
-        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_mid + off), idesc, first_cross);
-        mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
-        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
-        mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_mid + off), idesc, 1u);
+        // the G slices sit back to back, so [Gmid; Glo] and [Ghi; Gmid] are
+        // operands of 2 rpad rows: one instruction each for Khi and Klo
+        mma_bf16(d_cross, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_mid + off), idesc2, first_cross);
+        mma_bf16(d_cross, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc2, 1u);
       }
       mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs finish
       ++issued_mma;
@@ -289,6 +364,9 @@ __global__ void __launch_bounds__(128, 1)
     for (int c0 = 0; c0 < a.rpad; c0 += 16) {
       float v[16], w[16];
       tmem_ld16(lane_base + (unsigned)(a.n_main * a.rpad + c0), v);
+      tmem_ld16(lane_base + (unsigned)((a.n_main + 1) * a.rpad + c0), w);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] += w[i];
       for (int q = 0; q < used; ++q) {
         tmem_ld16(lane_base + (unsigned)(q * a.rpad + c0), w);
 #pragma unroll
@@ -437,9 +515,9 @@ static size_t part_region_bytes(int splits, int nrhs, long N) {
   return ((sizeof(float) * (size_t)splits * nrhs * N) + 255) & ~(size_t)255;
 }
 
-// Main accumulators for a given width: they and the cross terms' one fill at
-// most the 512 tensor-memory columns.
-static int n_main_for(int rpad) { return std::max(1, std::min(7, 512 / rpad - 1)); }
+// Main accumulators for a given width: they and the cross block (2 rpad
+// columns) fill at most the 512 tensor-memory columns.
+static int n_main_for(int rpad) { return std::max(1, std::min(7, 512 / rpad - 2)); }
 // Longest chain of MMAs into one accumulator (a drift of ~1e-6 relative).
 constexpr int kMaxChain = 32;
 
@@ -448,10 +526,25 @@ size_t gemm_workspace_bytes(long N, long ldk, int nrhs, int *splits_out, int sms
   const int kblocks = (int)(ldk / BK);
   const int rpad = (nrhs + 15) / 16 * 16;
   const int nm = n_main_for(rpad);
-  // enough CTAs for two waves, and at most kMaxChain chained MMAs per accumulator
-  const long by_occupancy = (2L * sms + tiles - 1) / tiles;
+  // At most kMaxChain chained MMAs per accumulator; above that bound, the
+  // split count whose CTAs (one per SM) stream K in the fewest bytes-times:
+  // waves x the K slices of one split, plus the FP32 partials each split
+  // writes and the finish kernel reads back.
   const long by_chain = (4L * kblocks + (long)nm * kMaxChain - 1) / ((long)nm * kMaxChain);
-  int splits = (int)std::max(1L, std::min<long>(kblocks, std::max(by_occupancy, by_chain)));
+  const long s0 = std::max(1L, std::min<long>(kblocks, by_chain));
+  long splits_best = s0;
+  double cost_best = 0.0;
+  for (long s = s0; s <= std::min<long>(kblocks, s0 + 64); ++s) {
+    const long per = (kblocks + s - 1) / s;
+    if (s > s0 && (s - 1) * per >= kblocks) continue;  // a split would be empty
+    const double waves = (double)((tiles * s + sms - 1) / sms);
+    const double cost = waves * sms * per * (2.0 * BM * BK * 2) + s * 8.0 * nrhs * N;
+    if (s == s0 || cost < cost_best) {
+      cost_best = cost;
+      splits_best = s;
+    }
+  }
+  int splits = (int)splits_best;
   if (splits_out) *splits_out = splits;
   return part_region_bytes(splits, nrhs, N) + 3 * sizeof(short) * (size_t)rpad * ldk;
 }
@@ -472,7 +565,8 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
   float *part = (float *)workspace;
   __nv_bfloat16 *ghi = (__nv_bfloat16 *)((unsigned char *)workspace + part_region_bytes(splits, nrhs, N));
   __nv_bfloat16 *gmid = ghi + (size_t)rpad * ldk, *glo = gmid + (size_t)rpad * ldk;
-  k_split_bf16<<<grid_for((long)rpad * ldk, 256), 256, 0, st>>>(g, ldg, N, ldk, nrhs, rpad, ghi, gmid, glo);
+  k_split_bf16<<<dim3((unsigned)std::min<long>((ldk / 2 + 255) / 256, 1024L), (unsigned)rpad), 256, 0, st>>>(
+      g, ldg, N, ldk, nrhs, ghi, gmid, glo);
   VIE_CHECK_LAUNCH("k_split_bf16");
   CUtensorMap mkhi, mklo, mghi, mgmid, mglo;
   vie_status s;
@@ -505,7 +599,8 @@ vie_status launch_gemm_bf16x3(const void *khi, const void *klo, long ldk, long N
   dim3 grid((unsigned)((N + BM - 1) / BM), (unsigned)splits);
   k_gemm_bf16x3<<<grid, 128, smem, st>>>(mkhi, mklo, mghi, mgmid, mglo, a);
   VIE_CHECK_LAUNCH("k_gemm_bf16x3");
-  k_gemm_finish<<<grid_for((long)nrhs * N, 256), 256, 0, st>>>(part, splits, nrhs, N, g, ldg, op, err, y, ldy);
+  k_gemm_finish<<<dim3((unsigned)std::min<long>((N + 1023) / 1024, 1024L), (unsigned)nrhs), 256, 0, st>>>(
+      part, splits, nrhs, N, g, ldg, op, err, y, ldy);
   VIE_CHECK_LAUNCH("k_gemm_finish");
   return VIE_OK;
 }

@@ -15,15 +15,19 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
+// Block sum in a fixed order, valid in thread 0: every thread's value goes to
+// shared memory, lane l of warp 0 adds values l, l + 32, ... in turn, and a
+// shuffle tree over warp 0 finishes.  GB300's FP64 pipe is narrow, and a
+// shuffle tree in every warp cost more FP64 adds than the dot products.
 __device__ __forceinline__ double block_sum(double v, double *red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
+  __syncthreads();  // an earlier call may still be reading red
+  red[threadIdx.x] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += red[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
   return s;
 }
 
@@ -31,7 +35,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 __global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__ V, int nv, long ldv,
                                                       const double *__restrict__ w, long N,
                                                       double *__restrict__ part) {
-  __shared__ double red[kDotThreads / 32];
+  __shared__ double red[kDotThreads];
   const long stride = (long)gridDim.x * blockDim.x;
   const long i0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
   for (int v = 0; v < nv; ++v) {
@@ -75,8 +79,13 @@ __global__ void k_lincomb_add(const double *__restrict__ V, int nv, long ldv,
 // y = x / norm, norm = sqrt(*n2) if use_sqrt else *n2; a zero norm gives y = 0.
 __global__ void k_scale(const double *__restrict__ x, const double *__restrict__ n2, int use_sqrt,
                         double *__restrict__ y, long N) {
-  double nrm = use_sqrt ? sqrt(*n2) : *n2;
-  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  __shared__ double s_inv;  // one square root and divide per block, not per thread
+  if (threadIdx.x == 0) {
+    const double nrm = use_sqrt ? sqrt(*n2) : *n2;
+    s_inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  }
+  __syncthreads();
+  const double inv = s_inv;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
     y[i] = x[i] * inv;
 }
@@ -130,7 +139,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dots_last(const double *__restr
                                                            int *ticket, double *out1, double *out2, double *H,
                                                            int m, int k, const double *hcol, double *cs,
                                                            double *sn, double *gv, double bnorm, double *est) {
-  __shared__ double red[kDotThreads / 32];
+  __shared__ double red[kDotThreads];
   __shared__ int last;
   const long stride = (long)gridDim.x * blockDim.x;
   const long i0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -186,7 +195,7 @@ int grid_for(long n, int threads) {
 __global__ void __launch_bounds__(kDotThreads) k_bdots_last(KBatch b, const double *__restrict__ V, long ldv_r,
                                                             int nv, const double *__restrict__ w, long ldw_r,
                                                             double *out1, double *out2, int gvmode, int k) {
-  __shared__ double red[kDotThreads / 32];
+  __shared__ double red[kDotThreads];
   __shared__ int last;
   const int r = blockIdx.y;
   if (!b.act[r]) return;
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(kDotThreads) k_bdots_last(KBatch b, const doub
 // ||w_r||^2 into scal[r][slot] (no Givens step)
 __global__ void __launch_bounds__(kDotThreads) k_bnorm2(KBatch b, const double *__restrict__ w, long ldw_r,
                                                         int slot) {
-  __shared__ double red[kDotThreads / 32];
+  __shared__ double red[kDotThreads];
   __shared__ int last;
   const int r = blockIdx.y;
   if (!b.act[r]) return;
@@ -276,9 +285,14 @@ __global__ void k_bscale(KBatch b, const double *__restrict__ x, long ldx_r, int
                          double *__restrict__ y, long ldy_r) {
   const int r = blockIdx.y;
   if (!b.act[r]) return;
-  const double n2 = b.scal[r * 8 + slot];
-  const double nrm = use_sqrt ? sqrt(n2) : n2;
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  __shared__ double s_inv;  // one square root and divide per block, not per thread
+  if (threadIdx.x == 0) {
+    const double n2 = b.scal[r * 8 + slot];
+    const double nrm = use_sqrt ? sqrt(n2) : n2;
+    s_inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  }
+  __syncthreads();
+  const double inv = s_inv;
   const double *xr = x + (long)r * ldx_r;
   double *yr = y + (long)r * ldy_r;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.N; i += (long)gridDim.x * blockDim.x)
