@@ -599,8 +599,8 @@ def measure_other_configs(P, torch, local, reps=3):
     """The two other single-GPU workloads of the method: the homogeneous 32^2
     medium in FP64 with the closed-form tau (GMRES to 1e-10), and the 32^3
     heterogeneous medium (FP32 tiles, S = 64): one apply, the GMRES solve to
-    1e-6, and the step-two sweep on 128 Fibonacci directions (Algorithm 1,
-    S.3).  Median of `reps` runs after one warm-up, CUDA events."""
+    1e-6 (on the fly, and on K assembled from the pair weights), and the
+    step-two sweep on 128 Fibonacci directions (Algorithm 1, S.3).  Median of `reps` runs after one warm-up, CUDA events."""
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
@@ -635,6 +635,13 @@ def measure_other_configs(P, torch, local, reps=3):
     dirs = torch.as_tensor(V.fibonacci_directions(M).astype(np.float32), device=dev)  # [M, 3]
     Phi = torch.empty(M * m3.N, dtype=torch.float32, device=dev)
     ms_sweep, _ = timed(lambda: P.ert_sweep(h3, U3, f3, dirs, Phi))
+    # the chosen solver: K assembled from the 3D displacement kernel's pair
+    # weights (each unordered pair marched once), then GMRES on the GEMV
+    asm3, _ = timed(lambda: P.vie_assemble(h3, P.VIE_OPERATOR_FP32))
+    U3c = torch.empty_like(f3)
+    ms3c, rep3c = timed(lambda: P.vie_solve_gmres(h3, f3, U3c, rtol=RTOL))
+    dif3 = float(torch.linalg.norm(U3c - U3) / torch.linalg.norm(U3))
+    P.vie_assemble(h3, P.VIE_OPERATOR_OTF)
     P.vie_destroy(h3)
     return {"homogeneous_32x32_fp64": {"tau": "closed form", "rtol": 1e-10, "solve_ms": ms1,
                                        "iters": rep1["iters"], "relres": rep1["relres"]},
@@ -643,6 +650,11 @@ def measure_other_configs(P, torch, local, reps=3):
                                        "tau_multiply_adds": work3,
                                        "apply_tflops": 2.0 * work3 / ms_apply / 1e9,
                                        "solve_ms": ms3, "iters": rep3["iters"], "relres": rep3["relres"],
+                                       "chosen": {"solver": "assembled FP32 K from the 3D displacement kernel's "
+                                                            "pair weights (4.3 GB) + FP64 GMRES(64)",
+                                                  "assemble_ms": asm3, "solve_ms": ms3c,
+                                                  "total_ms": asm3 + ms3c, "iters": rep3c["iters"],
+                                                  "relres": rep3c["relres"], "rel_diff_vs_plain": dif3},
                                        "sweep_directions": M, "sweep_ms": ms_sweep,
                                        "sweep_rays_per_s": M * m3.N / ms_sweep * 1e3}}
 

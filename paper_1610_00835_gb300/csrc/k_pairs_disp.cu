@@ -329,11 +329,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_store_disp_global(DispArgs a) {
   disp_body<disp_pitch(kGlobalMaxN, R), kStore, true, R>(a);
 }
 
-// bf16 bits of v rounded to nearest even (finite v), in integer arithmetic
-__device__ __forceinline__ unsigned short bf16_bits_rn(float v) {
-  const unsigned u = __float_as_uint(v);
-  return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
-}
 
 // output forms of the expansion
 enum ExpandOut {

@@ -64,6 +64,8 @@ struct Disp3Args {
   double *scale_out;         // fixed-point scale of this apply
   double rbound;             // bound on every row sum of A
   unsigned long long *yacc;  // [2 N] int64 sums (x fastest, then y fastest), zero between applies
+  float *pairs;              // store mode: the weight of every unordered pair (displacement-major)
+  const long long *doff;     // store mode: first stored weight of each D of the half space
   const int4 *units;         // see geometry3_build
   int *counter;              // [2]
   long n_units;
@@ -72,7 +74,12 @@ struct Disp3Args {
   float tau_scale2, wcoef;
 };
 
-template <int LDP, int PLANE>
+// STORE: instead of the apply's sums, write w = h^3 e^{-tau} / (4 pi r^2) of
+// every pair (j, j + D) to pairs: per D of the half space its box of targets,
+// x fastest, then y, then z.  A warp's stores are contiguous when its lanes
+// run along x; for runs along x (lanes on y) they are strided, but the units
+// of one D run back to back and L2 gathers its box before writing it out.
+template <int LDP, int PLANE, bool STORE>
 __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
   extern __shared__ float4 smem4[];
   float *lat = reinterpret_cast<float *>(smem4);
@@ -84,9 +91,11 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     for (long i = n4 * 4 + tid; i < a.lat_elems; i += kThreads3) lat[i] = a.lat[i];
   }
   __syncthreads();
-  const float smax = __uint_as_float(*a.smax);
-  const double scale_d =
-      smax > 0.f ? ldexp(1.0, ilogb(4.611686018427387904e18 / ((double)smax * a.rbound))) : 1.0;
+  double scale_d = 1.0;
+  if constexpr (!STORE) {
+    const float smax = __uint_as_float(*a.smax);
+    if (smax > 0.f) scale_d = ldexp(1.0, ilogb(4.611686018427387904e18 / ((double)smax * a.rbound)));
+  }
   const float scale = (float)scale_d;
   const int n = a.n;
   const int ldp = LDP > 0 ? LDP : a.ldp, plane = PLANE > 0 ? PLANE : a.plane;
@@ -151,6 +160,18 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     const float inv_r = rsqrtf(r2);
     const float tscale = -a.tau_scale2 * r2 * inv_r;  // -(h/S) log2(e) r
     const float wk = a.wcoef * inv_r * inv_r;
+    if constexpr (STORE) {
+      const int m2 = 2 * n - 1;
+      const long base = __ldg(a.doff + ((long)(dz + n - 1) * m2 + (dy + n - 1)) * m2 + (dx + n - 1));
+      const long wx = xhi - xlo, wy = yhi - ylo;
+      // the unit's first target in the box, and the stride of its stacked targets
+      const long o0 = base + ((long)(z - zlo) * wy + (y - ylo)) * wx + (x - xlo);
+      const long ostep = orient == 0 ? wx * wy : orient == 1 ? wx : 1;
+#pragma unroll
+      for (int q = 0; q < kR; ++q)
+        if (lvalid && b0 + q < shi) __stcs(a.pairs + o0 + q * ostep, wk * exp2f(tscale * acc[q]));
+      continue;
+    }
     // targets and partners in the layout whose fastest axis carries the lanes:
     // x fastest (s, the first half of yacc) or, for runs along x, y fastest
     // (s_t, the second half), so the atomics of a warp hit contiguous words
@@ -173,13 +194,13 @@ __global__ void __launch_bounds__(kThreads3, 1) k_pairs_disp3(Disp3Args a) {
     }
   }
   __syncthreads();
-  if (blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
+  if (!STORE && blockIdx.x == 0 && tid == 0) *a.scale_out = scale_d;
   if (tid == 0) {
     __threadfence();
     if (atomicAdd(a.counter + 1, 1) == (int)gridDim.x - 1) {
       a.counter[0] = 0;
       a.counter[1] = 0;
-      *a.smax = 0u;  // every CTA read it before this, the next source kernel sets it
+      if constexpr (!STORE) *a.smax = 0u;  // every CTA read it before this, the next source kernel sets it
       __threadfence();
     }
   }
@@ -225,9 +246,129 @@ __global__ void k_disp3_reduce(long N, int n, int op, unsigned long long *__rest
   }
 }
 
+// ---- the dense operator from the stored pair weights (the 3D form of
+// k_expand_pairs): K_jk = A_jk sigma_s,k (j != k) and K_jj = d_j sigma_s,j,
+// row-major N x ldk, FP32 or BF16 hi + lo (lo = bf16(v - hi)), each stored
+// weight read once.  Grid lines (y, z) play the part of the 2D grid rows: an
+// item is a line displacement (dy, dz) (dz > 0, or dz = 0 and dy >= 0) and a
+// target line (yj, zj); the stored rows "D = (dx, dy, dz), targets (., yj,
+// zj)" of every dx go to shared memory (T[dx + n - 1][xj]), then
+//   K[j][k] = T sigma_s,k  for j = (xj, yj, zj), k = (xk, yj + dy, zj + dz),
+//   K[k][j] = T sigma_s,j  for the same pairs seen from k,
+// each written as whole row segments of n columns.  Every ordered pair is
+// written once: from its own line displacement when that is in the half
+// plane, else from the opposite one.  For (dy, dz) = (0, 0) the line of j
+// gets its columns k > j from the first part and k < j from the second, and
+// the diagonal.
+constexpr int kExpF32 = 0, kExpBF16 = 1;
+// small CTAs, several per SM: an item is small (2 n^2 entries), and one CTA's
+// barriers then leave the SM to the others
+constexpr int kExpThreads = 256, kExpWarps = kExpThreads / 32;
+constexpr int kExpRows = (2 * kMaxN3 - 1 + kExpWarps - 1) / kExpWarps;  // T rows per warp
+
+template <int OUT>
+__device__ __forceinline__ void put_k(long idx, float v, float *k32, unsigned short *khi, unsigned short *klo) {
+  if constexpr (OUT == kExpBF16) {
+    const unsigned short hi = bf16_bits_rn(v);
+    khi[idx] = hi;
+    klo[idx] = bf16_bits_rn(v - __uint_as_float((unsigned)hi << 16));
+  } else {
+    k32[idx] = v;
+  }
+}
+
+// items: ioff[q] = first item of line displacement q (q < nq; ioff[nq] = the
+// total), iqd[q] = dy | dz << 16 (dy as a signed 16-bit value)
+template <int OUT>
+__global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const float *__restrict__ w,
+                                                           const long long *__restrict__ doff,
+                                                           const int *__restrict__ ioff, const int *__restrict__ iqd,
+                                                           int nq, const float *__restrict__ ss,
+                                                           const double *__restrict__ diag,
+                                                           const double *__restrict__ ss64, long ldk, float *k32,
+                                                           unsigned short *khi, unsigned short *klo) {
+  extern __shared__ float T[];  // [2n - 1][p]
+  const int p = n + 2;           // strides p and 1 - p: at most one is even (2-way conflicts)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // blockDim.x = kExpThreads
+  const int m2 = 2 * n - 1;
+  const int items = ioff[nq];
+  for (int t = blockIdx.x; t < items; t += gridDim.x) {
+    int lo = 0, hi = nq - 1;  // the last q with ioff[q] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ioff[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int qd = iqd[lo];
+    const int dy = (short)(qd & 0xffff), dz = qd >> 16;
+    const int ylo = dy < 0 ? -dy : 0, wyl = n - (dy < 0 ? -dy : dy);
+    const int local = t - ioff[lo];
+    const int yj = ylo + local % wyl, zj = local / wyl;
+    const int yk = yj + dy, zk = zj + dz;
+    const bool same = dy == 0 && dz == 0;
+    const long jrow = (long)n * (yj + (long)n * zj), krow = (long)n * (yk + (long)n * zk);
+    // this lane's sigma_s on both lines (n <= 32: one column per lane)
+    const float ssj_l = lane < n ? __ldg(ss + jrow + lane) : 0.f;
+    const float ssk_l = lane < n ? __ldg(ss + krow + lane) : 0.f;
+    {
+      // every row load of this warp in flight before the first shared store
+      float v[kExpRows];
+#pragma unroll
+      for (int i = 0; i < kExpRows; ++i) {
+        const int dx = -(n - 1) + warp + i * kExpWarps;
+        const int wx = n - (dx < 0 ? -dx : dx);
+        v[i] = 0.f;
+        if (dx < n && !(same && dx <= 0) && lane < wx)
+          v[i] = __ldcs(w + doff[((long)(dz + n - 1) * m2 + (dy + n - 1)) * m2 + (dx + n - 1)] +
+                        ((long)zj * wyl + (yj - ylo)) * wx + lane);
+      }
+#pragma unroll
+      for (int i = 0; i < kExpRows; ++i) {
+        const int dx = -(n - 1) + warp + i * kExpWarps;
+        const int xlo = dx < 0 ? -dx : 0, wx = n - (dx < 0 ? -dx : dx);
+        if (dx < n && !(same && dx <= 0) && lane < wx) T[(dx + n - 1) * p + xlo + lane] = v[i];
+      }
+    }
+    __syncthreads();
+    if (!same) {
+      for (int xj = warp; xj < n; xj += kExpWarps) {
+        const float *tb = T + (n - 1 - xj) * p + xj;  // T[(xk - xj + n - 1) p + xj]
+        const long rb = (jrow + xj) * ldk + krow;
+        if (lane < n) put_k<OUT>(rb + lane, tb[lane * p] * ssk_l, k32, khi, klo);
+      }
+      for (int xk = warp; xk < n; xk += kExpWarps) {
+        const float *tb = T + (xk + n - 1) * p;  // T[(xk - xj + n - 1) p + xj]
+        const long rb = (krow + xk) * ldk + jrow;
+        if (lane < n) put_k<OUT>(rb + lane, tb[lane * (1 - p)] * ssj_l, k32, khi, klo);
+      }
+    } else {
+      for (int r = warp; r < n; r += kExpWarps) {
+        const long rb = (jrow + r) * ldk + jrow;
+        const int x = lane;
+        if (x < n && x != r) {
+          const float v = x > r ? T[(x - r + n - 1) * p + r] : T[(r - x + n - 1) * p + x];
+          put_k<OUT>(rb + x, v * ssj_l, k32, khi, klo);
+        }
+      }
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const long j = jrow + r;
+        put_k<OUT>(j * ldk + j, (float)(diag[j] * ss64[j]), k32, khi, klo);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_to_f32_3(long N, const double *__restrict__ x, float *__restrict__ y) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 typedef void (*Disp3Kernel)(Disp3Args);
 
-Disp3Kernel pick_disp3(int n) { return n == 32 ? k_pairs_disp3<33, 1089> : k_pairs_disp3<0, 0>; }
+Disp3Kernel pick_disp3(int n, bool store = false) {
+  if (store) return n == 32 ? k_pairs_disp3<33, 1089, true> : k_pairs_disp3<0, 0, true>;
+  return n == 32 ? k_pairs_disp3<33, 1089, false> : k_pairs_disp3<0, 0, false>;
+}
 
 // ---- geometry (host): stencils, chunk records and work units, per (device, n)
 
@@ -562,6 +703,9 @@ vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int devi
 
 void disp3_release(DispPlan3 *dp) {
   if (dp->geometry) geometry3_release((Geometry3 *)dp->geometry);
+  if (dp->doff) vie_free(dp->doff);
+  if (dp->ioff) vie_free(dp->ioff);
+  if (dp->iqd) vie_free(dp->iqd);
   if (dp->counter) vie_free(dp->counter);
   if (dp->lattice) vie_free(dp->lattice);
   if (dp->smax) vie_free(dp->smax);
@@ -606,6 +750,131 @@ vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const
                                                                         sigma_s, g, y);
   VIE_CHECK_LAUNCH("k_disp3_reduce");
   return VIE_OK;
+}
+
+static size_t expand3_smem_bytes(int n) { return sizeof(float) * (size_t)(2 * n - 1) * (n + 2); }
+
+// the store kernel's launch shape, the offsets of the stored weights per D
+// and the expansion's items (once per plan)
+static vie_status disp3_store_setup(DispPlan3 *dp, int device) {
+  if (dp->kernel_store) return VIE_OK;
+  const int n = dp->n;
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
+  Disp3Kernel k = pick_disp3(n, true);
+  VIE_TRY(raise_smem_limit((const void *)k, (size_t)((int)dp->smem)));
+  int bps = 0;
+  VIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kThreads3, dp->smem));
+  if (bps < 1) {
+    set_error("vie_assemble: the 3D store kernel does not fit an SM");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  const long m2 = 2 * n - 1;
+  std::vector<long long> doff((size_t)(m2 * m2 * m2), 0);
+  long off = 0;
+  for (int dz = 0; dz < n; ++dz)
+    for (int dy = -(n - 1); dy < n; ++dy)
+      for (int dx = -(n - 1); dx < n; ++dx) {
+        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+        const long idx = ((long)(dz + n - 1) * m2 + (dy + n - 1)) * m2 + (dx + n - 1);
+        doff[idx] = off;
+        off += (long)(n - std::abs(dx)) * (n - std::abs(dy)) * (n - dz);
+      }
+  std::vector<int> ioff, iqd;
+  int items = 0;
+  for (int dz = 0; dz < n; ++dz)
+    for (int dy = dz == 0 ? 0 : -(n - 1); dy < n; ++dy) {
+      ioff.push_back(items);
+      iqd.push_back((dy & 0xffff) | (dz << 16));
+      items += (n - std::abs(dy)) * (n - dz);
+    }
+  ioff.push_back(items);
+  VIE_CUDA(vie_malloc(&dp->doff, sizeof(long long) * doff.size()));
+  VIE_CUDA(cudaMemcpy(dp->doff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(vie_malloc(&dp->ioff, sizeof(int) * ioff.size()));
+  VIE_CUDA(cudaMemcpy(dp->ioff, ioff.data(), sizeof(int) * ioff.size(), cudaMemcpyHostToDevice));
+  VIE_CUDA(vie_malloc(&dp->iqd, sizeof(int) * iqd.size()));
+  VIE_CUDA(cudaMemcpy(dp->iqd, iqd.data(), sizeof(int) * iqd.size(), cudaMemcpyHostToDevice));
+  dp->nq = (int)iqd.size();
+  dp->stored = off;
+  dp->grid_store = bps * prop.multiProcessorCount;
+  dp->kernel_store = (const void *)k;
+  return VIE_OK;
+}
+
+vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const double *sigma_s, const double *diag,
+                          long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st) {
+  if (!dp->usable) {
+    set_error("vie_assemble: no 3D displacement plan");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  VIE_TRY(disp3_store_setup(dp, device));
+  const int n = dp->n;
+  const long N = (long)n * n * n;
+  float *pairs = nullptr, *ss32 = nullptr;
+  VIE_CUDA(vie_malloc(&pairs, sizeof(float) * (size_t)dp->stored));
+  cudaError_t ce = vie_malloc(&ss32, sizeof(float) * (size_t)N);
+  if (ce != cudaSuccess) {
+    vie_free(pairs);
+    return cuda_fail(ce, "cudaMalloc");
+  }
+  vie_status s = VIE_OK;
+  {
+    Disp3Args a{};
+    a.lat = (const float *)dp->lattice;
+    a.stencil = (const float4 *)dp->stencil;
+    a.pairs = pairs;
+    a.doff = dp->doff;
+    a.units = (const int4 *)dp->units;
+    a.counter = dp->counter;
+    a.n_units = dp->n_units;
+    a.n = n;
+    a.ldp = n + 1;
+    a.plane = (n + 1) * (n + 1);
+    a.lat_elems = dp->lat_elems;
+    a.tau_scale2 = tau_scale2;
+    a.wcoef = wcoef;
+    void *args[] = {&a};
+    ce = cudaLaunchKernel(dp->kernel_store, dim3(dp->grid_store), dim3(kThreads3), args, dp->smem, st);
+    if (ce != cudaSuccess) s = cuda_fail(ce, "k_pairs_disp3 (store)");
+    else count_launch();
+  }
+  const size_t esz = k32 ? sizeof(float) : sizeof(unsigned short);
+  if (s == VIE_OK && ldk > N) {  // zero the padding columns [N, ldk) of every row
+    if (k32) ce = cudaMemset2DAsync(k32 + N, ldk * esz, 0, (ldk - N) * esz, N, st);
+    else {
+      ce = cudaMemset2DAsync((unsigned short *)khi + N, ldk * esz, 0, (ldk - N) * esz, N, st);
+      if (ce == cudaSuccess) ce = cudaMemset2DAsync((unsigned short *)klo + N, ldk * esz, 0, (ldk - N) * esz, N, st);
+    }
+    if (ce != cudaSuccess) s = cuda_fail(ce, "cudaMemset2DAsync");
+  }
+  if (s == VIE_OK) {
+    k_to_f32_3<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, sigma_s, ss32);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) s = cuda_fail(ce, "k_to_f32_3");
+  }
+  if (s == VIE_OK) {
+    const size_t smem = expand3_smem_bytes(n);
+    DevProps prop;
+    s = get_dev_props(device, &prop);
+    if (s == VIE_OK) {
+      const int grid = 4 * prop.multiProcessorCount;
+      if (k32)
+        k_expand_pairs3<kExpF32><<<grid, kExpThreads, smem, st>>>(n, pairs, dp->doff, dp->ioff, dp->iqd, dp->nq, ss32, diag,
+                                                          sigma_s, ldk, k32, nullptr, nullptr);
+      else
+        k_expand_pairs3<kExpBF16><<<grid, kExpThreads, smem, st>>>(n, pairs, dp->doff, dp->ioff, dp->iqd, dp->nq, ss32,
+                                                           diag, sigma_s, ldk, nullptr, (unsigned short *)khi,
+                                                           (unsigned short *)klo);
+      ce = cudaGetLastError();
+      if (ce != cudaSuccess) s = cuda_fail(ce, "k_expand_pairs3");
+      else count_launch();
+    }
+  }
+  // the frees wait for the device (the expansion reads both buffers)
+  vie_free(pairs);
+  vie_free(ss32);
+  return s;
 }
 
 }  // namespace vie

@@ -1170,11 +1170,14 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
   // has room for the grid, else from the tile-pair assembler (M-iii only)
   const bool disp2 =
       h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 2 && disp_expand_fits(h->n, h->device);
+  // 3D: the pair weights of the 3D displacement kernel, expanded along grid lines
+  const bool disp3 = h->use_kernel == VIE_KERNEL_DISPLACEMENT && h->dim == 3 && h->disp3.usable &&
+                     h->opts.disc == VIE_DISC_MIII;
   if (!disp2 && h->opts.disc == VIE_DISC_MII) {
     set_error("vie_assemble: dense K with VIE_DISC_MII needs the pair-weight expansion (n <= 169)");
     return VIE_ERR_UNSUPPORTED;
   }
-  if ((!h->sym.usable && !disp2) || h->opts.precision != VIE_PREC_FP32 ||
+  if ((!h->sym.usable && !disp2 && !disp3) || h->opts.precision != VIE_PREC_FP32 ||
       h->opts.tau_mode != VIE_TAU_MARCH || h->opts.steps != 64) {
     set_error("vie_assemble: needs FP32 tiles, the march, S = 64 and a grid whose sigma_t fits "
               "in shared memory");
@@ -1211,6 +1214,10 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
     if (s != VIE_OK) return s;
     s = disp_expand(h->disp, h->n, (const float *)h->pairs, h->sig_s, h->diag, h->ldk, k32, khi, h->kmat_lo,
                     h->device, st);
+  } else if (disp3) {
+    const double hh = 1.0 / h->n;
+    s = disp3_assemble(&h->disp3, (float)(hh / h->opts.steps * 1.4426950408889634), (float)(hh / (4.0 * kPi)),
+                       h->sig_s, h->diag, h->ldk, k32, khi, h->kmat_lo, h->device, st);
   } else {
     s = launch_assemble(h->sym, h->dim, h->n, N, h->sig_s, h->diag, k32, khi, h->kmat_lo, h->device, st);
   }

@@ -46,6 +46,15 @@ struct DeviceIdle {
   ~DeviceIdle();
 };
 
+#ifdef __CUDACC__
+// bf16 bits of v rounded to nearest even (finite v), in integer arithmetic (the
+// FP32 -> BF16 conversion instruction shares GB300's narrow FP64 pipe)
+__device__ __forceinline__ unsigned short bf16_bits_rn(float v) {
+  const unsigned u = __float_as_uint(v);
+  return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+#endif
+
 struct WaitLimits {
   long long limit, first;
 };
@@ -196,6 +205,12 @@ struct DispPlan3 {
   float *src_t = nullptr;
   unsigned long long *yacc = nullptr;
   const void *kernel = nullptr;
+  // dense assembly from the stored pair weights (built on first use)
+  const void *kernel_store = nullptr;
+  int grid_store = 0, nq = 0;
+  long stored = 0;             // unordered pairs N (N - 1) / 2
+  long long *doff = nullptr;   // per D of the half space: its first stored weight
+  int *ioff = nullptr, *iqd = nullptr;  // expansion items per line displacement
 };
 size_t disp3_smem_bytes(int n);
 vie_status disp3_prepare(DispPlan3 *dp, int n, const float *sig_padded, int device, cudaStream_t st);
@@ -203,6 +218,10 @@ void disp3_release(DispPlan3 *dp);
 vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const double *g, const double *diag,
                        float *src, float tau_scale2, float wcoef, double *y, cudaEvent_t mid0, cudaEvent_t mid1,
                        cudaStream_t st);
+// K (row-major N x ldk, FP32 k32 or BF16 khi + klo) from the 3D displacement
+// kernel's march: every unordered pair's weight stored once, then expanded
+vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const double *sigma_s, const double *diag,
+                          long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
 
 size_t disp_smem_bytes(int n, int R);  // shared lattice bytes at stack depth R
 bool disp_expand_fits(int n, int device);  // k_expand_pairs has room for the grid (n <= 169)
