@@ -279,6 +279,62 @@ __device__ __forceinline__ void put_k(long idx, float v, float *k32, unsigned sh
 
 // items: ioff[q] = first item of line displacement q (q < nq; ioff[nq] = the
 // total), iqd[q] = dy | dz << 16 (dy as a signed 16-bit value)
+struct ExpItem {
+  int dy, dz, yj, zj, ylo, wyl;
+  bool same;  // (dy, dz) = (0, 0): one grid line
+  long jrow, krow;
+};
+
+__device__ __forceinline__ ExpItem exp_decode(int t, int n, const int *__restrict__ ioff,
+                                              const int *__restrict__ iqd, int nq) {
+  int lo = 0, hi = nq - 1;  // the last q with ioff[q] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ioff[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int qd = iqd[lo];
+  ExpItem it;
+  it.dy = (short)(qd & 0xffff);
+  it.dz = qd >> 16;
+  it.ylo = it.dy < 0 ? -it.dy : 0;
+  it.wyl = n - (it.dy < 0 ? -it.dy : it.dy);
+  const int local = t - ioff[lo];
+  it.yj = it.ylo + local % it.wyl;
+  it.zj = local / it.wyl;
+  it.same = it.dy == 0 && it.dz == 0;
+  it.jrow = (long)n * (it.yj + (long)n * it.zj);
+  it.krow = (long)n * (it.yj + it.dy + (long)n * (it.zj + it.dz));
+  return it;
+}
+
+// row i of this warp holds dx = -(n - 1) + warp + i kExpWarps (lane = xj - xlo)
+__device__ __forceinline__ bool exp_row(const ExpItem &it, int n, int warp, int i, int lane, int &dx, int &xlo,
+                                        int &wx) {
+  dx = -(n - 1) + warp + i * kExpWarps;
+  xlo = dx < 0 ? -dx : 0;
+  wx = n - (dx < 0 ? -dx : dx);
+  return dx < n && !(it.same && dx <= 0) && lane < wx;
+}
+
+// this warp's stored rows of item it into v, and the lane's sigma_s on both lines
+__device__ __forceinline__ void exp_load(const ExpItem &it, int n, int warp, int lane, const float *__restrict__ w,
+                                         const long long *__restrict__ doff, const float *__restrict__ ss,
+                                         float (&v)[kExpRows], float &ssj, float &ssk) {
+  const int m2 = 2 * n - 1;
+#pragma unroll
+  for (int i = 0; i < kExpRows; ++i) {
+    int dx, xlo, wx;
+    v[i] = 0.f;
+    if (exp_row(it, n, warp, i, lane, dx, xlo, wx))
+      v[i] = __ldcs(w + doff[((long)(it.dz + n - 1) * m2 + (it.dy + n - 1)) * m2 + (dx + n - 1)] +
+                    ((long)it.zj * it.wyl + (it.yj - it.ylo)) * wx + lane);
+  }
+  ssj = lane < n ? __ldg(ss + it.jrow + lane) : 0.f;  // n <= 32: one column per lane
+  ssk = lane < n ? __ldg(ss + it.krow + lane) : 0.f;
+}
+
+// Software-pipelined: while a CTA writes the K entries of one item, the row
+// loads of its next item are in flight.
 template <int OUT>
 __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const float *__restrict__ w,
                                                            const long long *__restrict__ doff,
@@ -290,46 +346,28 @@ __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const f
   extern __shared__ float T[];  // [2n - 1][p]
   const int p = n + 2;           // strides p and 1 - p: at most one is even (2-way conflicts)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // blockDim.x = kExpThreads
-  const int m2 = 2 * n - 1;
   const int items = ioff[nq];
-  for (int t = blockIdx.x; t < items; t += gridDim.x) {
-    int lo = 0, hi = nq - 1;  // the last q with ioff[q] <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (ioff[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int qd = iqd[lo];
-    const int dy = (short)(qd & 0xffff), dz = qd >> 16;
-    const int ylo = dy < 0 ? -dy : 0, wyl = n - (dy < 0 ? -dy : dy);
-    const int local = t - ioff[lo];
-    const int yj = ylo + local % wyl, zj = local / wyl;
-    const int yk = yj + dy, zk = zj + dz;
-    const bool same = dy == 0 && dz == 0;
-    const long jrow = (long)n * (yj + (long)n * zj), krow = (long)n * (yk + (long)n * zk);
-    // this lane's sigma_s on both lines (n <= 32: one column per lane)
-    const float ssj_l = lane < n ? __ldg(ss + jrow + lane) : 0.f;
-    const float ssk_l = lane < n ? __ldg(ss + krow + lane) : 0.f;
-    {
-      // every row load of this warp in flight before the first shared store
-      float v[kExpRows];
+  int t = blockIdx.x;
+  if (t >= items) return;
+  ExpItem cur = exp_decode(t, n, ioff, iqd, nq);
+  float v[kExpRows], ssj_n, ssk_n;
+  exp_load(cur, n, warp, lane, w, doff, ss, v, ssj_n, ssk_n);
+  for (; t < items; t += gridDim.x) {
 #pragma unroll
-      for (int i = 0; i < kExpRows; ++i) {
-        const int dx = -(n - 1) + warp + i * kExpWarps;
-        const int wx = n - (dx < 0 ? -dx : dx);
-        v[i] = 0.f;
-        if (dx < n && !(same && dx <= 0) && lane < wx)
-          v[i] = __ldcs(w + doff[((long)(dz + n - 1) * m2 + (dy + n - 1)) * m2 + (dx + n - 1)] +
-                        ((long)zj * wyl + (yj - ylo)) * wx + lane);
-      }
-#pragma unroll
-      for (int i = 0; i < kExpRows; ++i) {
-        const int dx = -(n - 1) + warp + i * kExpWarps;
-        const int xlo = dx < 0 ? -dx : 0, wx = n - (dx < 0 ? -dx : dx);
-        if (dx < n && !(same && dx <= 0) && lane < wx) T[(dx + n - 1) * p + xlo + lane] = v[i];
-      }
+    for (int i = 0; i < kExpRows; ++i) {
+      int dx, xlo, wx;
+      if (exp_row(cur, n, warp, i, lane, dx, xlo, wx)) T[(dx + n - 1) * p + xlo + lane] = v[i];
     }
+    const float ssj_l = ssj_n, ssk_l = ssk_n;
     __syncthreads();
-    if (!same) {
+    ExpItem nxt = cur;
+    const int tn = t + gridDim.x;
+    if (tn < items) {
+      nxt = exp_decode(tn, n, ioff, iqd, nq);
+      exp_load(nxt, n, warp, lane, w, doff, ss, v, ssj_n, ssk_n);
+    }
+    const long jrow = cur.jrow, krow = cur.krow;
+    if (!cur.same) {
       for (int xj = warp; xj < n; xj += kExpWarps) {
         const float *tb = T + (n - 1 - xj) * p + xj;  // T[(xk - xj + n - 1) p + xj]
         const long rb = (jrow + xj) * ldk + krow;
@@ -345,8 +383,8 @@ __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const f
         const long rb = (jrow + r) * ldk + jrow;
         const int x = lane;
         if (x < n && x != r) {
-          const float v = x > r ? T[(x - r + n - 1) * p + r] : T[(r - x + n - 1) * p + x];
-          put_k<OUT>(rb + x, v * ssj_l, k32, khi, klo);
+          const float tv = x > r ? T[(x - r + n - 1) * p + r] : T[(r - x + n - 1) * p + x];
+          put_k<OUT>(rb + x, tv * ssj_l, k32, khi, klo);
         }
       }
       for (int r = threadIdx.x; r < n; r += blockDim.x) {
@@ -355,6 +393,7 @@ __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const f
       }
     }
     __syncthreads();
+    cur = nxt;
   }
 }
 
