@@ -152,8 +152,8 @@ enum {
                                     displacement-major (2D handles that use the
                                     displacement kernel): applies stream it */
   VIE_OPERATOR_SYM32 = 4,        /* A (symmetric) in FP32 blocks, one per pair of
-                                    grid rows yj <= yk (same handles): applies
-                                    read each block once, y = A (sigma_s g) */
+                                    grid rows yj <= yk (2D) or grid lines (3D):
+                                    applies read each block once, y = A (sigma_s g) */
   VIE_OPERATOR_FMM = 5           /* the interpolation-based FMM of Section 3.3
                                     with cached near-field and M2L blocks
                                     (vie_assemble_fmm; Chebyshev order 6 here) */
@@ -166,8 +166,13 @@ enum {
  * s = sigma_s g (or g for VIE_OP_A_RAW) in FP32, takes from every block its row
  * sums (for row yj) and column sums (for row yk) in FP32, and adds each
  * target's n block sums in a fixed order in FP64: deterministic, half the bytes
- * of the dense K per apply.  Same handles as VIE_OPERATOR_PAIRS32.
- *
+ * of the dense K per apply.  Same handles as VIE_OPERATOR_PAIRS32 (2D, n <= 160).
+ * 3D handles on the 3D displacement kernel (n <= 32): one n x n block per
+ * unordered pair of grid lines (y, z), targets on the first line (x the row)
+ * and sources on the second (x the column), 2.16 GB at 32^3; each target adds
+ * its ~n^2 row or column sums as an FP32 hi + lo pair (error-free additions) in a
+ * fixed order. */
+
 /* VIE_OPERATOR_PAIRS32: the weights A_jk = A_kj (Section 2, Eq. EQ:Kernel with
  * the M-iii collocation of Section 3.2) of the N (N - 1) / 2 unordered pairs,
  * each stored once in FP32 (537 MB at 128^2), grouped by displacement D = k - j:

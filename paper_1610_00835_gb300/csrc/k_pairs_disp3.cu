@@ -260,7 +260,7 @@ __global__ void k_disp3_reduce(long N, int n, int op, unsigned long long *__rest
 // plane, else from the opposite one.  For (dy, dz) = (0, 0) the line of j
 // gets its columns k > j from the first part and k < j from the second, and
 // the diagonal.
-constexpr int kExpF32 = 0, kExpBF16 = 1;
+constexpr int kExpF32 = 0, kExpBF16 = 1, kExpSym = 2;  // kExpSym: A in the n x n blocks of the items
 // small CTAs, several per SM: an item is small (2 n^2 entries), and one CTA's
 // barriers then leave the SM to the others
 constexpr int kExpThreads = 256, kExpWarps = kExpThreads / 32;
@@ -367,7 +367,25 @@ __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const f
       exp_load(nxt, n, warp, lane, w, doff, ss, v, ssj_n, ssk_n);
     }
     const long jrow = cur.jrow, krow = cur.krow;
-    if (!cur.same) {
+    if constexpr (OUT == kExpSym) {
+      // block t: A_jk for j on line (yj, zj) (row xj), k on line (yk, zk)
+      // (column xk); no sigma_s; the one-line blocks whole, with d_j
+      float *blk = k32 + (long)t * n * n;
+      for (int xj = warp; xj < n; xj += kExpWarps) {
+        const int xk = lane;
+        if (xk < n) {
+          const int dx = xk - xj;
+          float tv;
+          if (!cur.same || dx > 0)
+            tv = T[(dx + n - 1) * p + xj];
+          else if (dx < 0)
+            tv = T[(-dx + n - 1) * p + xk];  // A_jk = A_kj, stored under (-dx, 0, 0) for target xk
+          else
+            tv = (float)diag[jrow + xj];
+          blk[(long)xj * n + xk] = tv;
+        }
+      }
+    } else if (!cur.same) {
       for (int xj = warp; xj < n; xj += kExpWarps) {
         const float *tb = T + (n - 1 - xj) * p + xj;  // T[(xk - xj + n - 1) p + xj]
         const long rb = (jrow + xj) * ldk + krow;
@@ -395,6 +413,127 @@ __global__ void __launch_bounds__(kExpThreads, 4) k_expand_pairs3(int n, const f
     __syncthreads();
     cur = nxt;
   }
+}
+
+// ---- applies of A stored in the expansion's blocks (kExpSym)
+//
+// y = A s with s = sigma_s g (or g).  k_symv3_blocks: one warp per block t
+// (item (dy, dz) and target line Lj; Lk = Lj + (dy, dz)) stages the block in
+// shared memory and writes P[t][0, n) = its row sums against s on Lk and, for
+// (dy, dz) != 0, P[t][n, 2n) = its column sums against s on Lj (A_kj = A_jk);
+// all sums in a fixed order.  k_symv3_reduce: one CTA per grid line adds, for
+// each target, the partials of every block that touches its line.
+constexpr int kSymvWarps3 = 8;
+
+__global__ void __launch_bounds__(32 * kSymvWarps3, 4) k_symv3_blocks(int n, const float *__restrict__ A,
+                                                                   const float *__restrict__ s,
+                                                                   const int *__restrict__ ioff,
+                                                                   const int *__restrict__ iqd, int nq,
+                                                                   float *__restrict__ P) {
+  __shared__ float tile[kSymvWarps3][32][33];
+  __shared__ float sjs[kSymvWarps3][32], sks[kSymvWarps3][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = ioff[nq];
+  float(*tl)[33] = tile[warp];
+  for (int t = blockIdx.x * kSymvWarps3 + warp; t < items; t += gridDim.x * kSymvWarps3) {
+    const ExpItem it = exp_decode(t, n, ioff, iqd, nq);
+    const float *blk = A + (long)t * n * n;
+    float v[32];
+#pragma unroll
+    for (int xj = 0; xj < 32; ++xj) v[xj] = (xj < n && lane < n) ? __ldcs(blk + (long)xj * n + lane) : 0.f;
+    const float sj = lane < n ? s[it.jrow + lane] : 0.f, sk = lane < n ? s[it.krow + lane] : 0.f;
+    // every load of the block issued before the first shared store
+    asm volatile("" ::: "memory");
+    sjs[warp][lane] = sj;
+    sks[warp][lane] = sk;
+#pragma unroll
+    for (int xj = 0; xj < 32; ++xj) tl[xj][lane] = v[xj];
+    __syncwarp();
+    float r = 0.f, c = 0.f;
+    for (int x = 0; x < n; ++x) {
+      r = fmaf(tl[lane][x], sks[warp][x], r);  // row lane, column x
+      c = fmaf(tl[x][lane], sjs[warp][x], c);  // row x, column lane
+    }
+    float *pt = P + (long)t * 2 * n;
+    if (lane < n) {
+      pt[lane] = r;
+      if (!it.same) pt[n + lane] = c;
+    }
+    __syncwarp();
+  }
+}
+
+// hi + lo += v: Knuth's error-free TwoSum on hi, the rounding error into lo
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float v) {
+  const float s1 = __fadd_rn(hi, v);
+  const float bv = __fsub_rn(s1, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bv)), __fsub_rn(v, bv)));
+  hi = s1;
+}
+
+// Per grid line L = blockIdx.x (y = L % n, z = L / n): warp w adds, for
+// target x = lane, the partials of the line displacements q = w, w + 8, ...:
+// the row sums of block (q, L) and then the column sums of block (q, L - q),
+// as an FP32 hi + lo pair; the eight warps' pairs are then added in warp order.
+__global__ void __launch_bounds__(32 * kSymvWarps3, 4) k_symv3_reduce(int n, int op, const float *__restrict__ P,
+                                                                   const int *__restrict__ ioff,
+                                                                   const int *__restrict__ iqd, int nq,
+                                                                   const double *__restrict__ g,
+                                                                   double *__restrict__ y) {
+  __shared__ float hs[kSymvWarps3][32], ls[kSymvWarps3][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int L = blockIdx.x, yl = L % n, zl = L / n;
+  float hi = 0.f, lo = 0.f;
+  if (lane < n) {
+    // kBatch displacements per step, their loads issued before the first add
+    constexpr int kBatch = 8;
+    for (int q0 = warp; q0 < nq; q0 += kBatch * kSymvWarps3) {
+      float va[kBatch], vb[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int q = q0 + u * kSymvWarps3;
+        va[u] = vb[u] = 0.f;
+        if (q < nq) {
+          const int qd = iqd[q];
+          const int dy = (short)(qd & 0xffff), dz = qd >> 16;
+          const int ylo = dy < 0 ? -dy : 0, wyl = n - (dy < 0 ? -dy : dy);
+          // L as the target line of block q: L + (dy, dz) inside the grid
+          const int yk = yl + dy, zk = zl + dz;
+          if (yk >= 0 && yk < n && zk < n) va[u] = __ldcs(P + (ioff[q] + (long)zl * wyl + (yl - ylo)) * 2 * n + lane);
+          // L as the source line: L - (dy, dz) inside the grid, (dy, dz) != 0
+          const int yj = yl - dy, zj = zl - dz;
+          if ((dy != 0 || dz != 0) && yj >= 0 && yj < n && zj >= 0)
+            vb[u] = __ldcs(P + (ioff[q] + (long)zj * wyl + (yj - ylo)) * 2 * n + n + lane);
+        }
+      }
+      asm volatile("" ::: "memory");  // the batch's loads issued before its first add
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        pair_add(hi, lo, va[u]);  // a missing block adds an exact zero
+        pair_add(hi, lo, vb[u]);
+      }
+    }
+  }
+  hs[warp][lane] = hi;
+  ls[warp][lane] = lo;
+  __syncthreads();
+  if (warp == 0 && lane < n) {
+    hi = hs[0][lane];
+    lo = ls[0][lane];
+    for (int w = 1; w < kSymvWarps3; ++w) {
+      pair_add(hi, lo, hs[w][lane]);
+      lo = __fadd_rn(lo, ls[w][lane]);
+    }
+    const long j = (long)L * n + lane;
+    const double v = (double)hi + (double)lo;
+    y[j] = op == VIE_OP_I_MINUS_K ? g[j] - v : v;
+  }
+}
+
+__global__ void k_symv3_source(long N, int op, const double *__restrict__ ss, const double *__restrict__ g,
+                               float *__restrict__ s) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    s[i] = (float)(op == VIE_OP_A_RAW ? g[i] : ss[i] * g[i]);
 }
 
 __global__ void k_to_f32_3(long N, const double *__restrict__ x, float *__restrict__ y) {
@@ -835,6 +974,7 @@ static vie_status disp3_store_setup(DispPlan3 *dp, int device) {
   VIE_CUDA(vie_malloc(&dp->iqd, sizeof(int) * iqd.size()));
   VIE_CUDA(cudaMemcpy(dp->iqd, iqd.data(), sizeof(int) * iqd.size(), cudaMemcpyHostToDevice));
   dp->nq = (int)iqd.size();
+  dp->items = items;
   dp->stored = off;
   dp->grid_store = bps * prop.multiProcessorCount;
   dp->kernel_store = (const void *)k;
@@ -879,7 +1019,7 @@ vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const do
     else count_launch();
   }
   const size_t esz = k32 ? sizeof(float) : sizeof(unsigned short);
-  if (s == VIE_OK && ldk > N) {  // zero the padding columns [N, ldk) of every row
+  if (s == VIE_OK && ldk > N) {  // dense K: zero the padding columns [N, ldk) of every row
     if (k32) ce = cudaMemset2DAsync(k32 + N, ldk * esz, 0, (ldk - N) * esz, N, st);
     else {
       ce = cudaMemset2DAsync((unsigned short *)khi + N, ldk * esz, 0, (ldk - N) * esz, N, st);
@@ -898,7 +1038,10 @@ vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const do
     s = get_dev_props(device, &prop);
     if (s == VIE_OK) {
       const int grid = 4 * prop.multiProcessorCount;
-      if (k32)
+      if (ldk == 0)
+        k_expand_pairs3<kExpSym><<<grid, kExpThreads, smem, st>>>(n, pairs, dp->doff, dp->ioff, dp->iqd, dp->nq, ss32,
+                                                                 diag, sigma_s, 0, k32, nullptr, nullptr);
+      else if (k32)
         k_expand_pairs3<kExpF32><<<grid, kExpThreads, smem, st>>>(n, pairs, dp->doff, dp->ioff, dp->iqd, dp->nq, ss32, diag,
                                                           sigma_s, ldk, k32, nullptr, nullptr);
       else
@@ -914,6 +1057,33 @@ vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const do
   vie_free(pairs);
   vie_free(ss32);
   return s;
+}
+
+vie_status disp3_sym_sizes(DispPlan3 *dp, int device, long *block_floats, long *partial_floats) {
+  if (!dp->usable) {
+    set_error("vie_assemble: no 3D displacement plan");
+    return VIE_ERR_UNSUPPORTED;
+  }
+  VIE_TRY(disp3_store_setup(dp, device));
+  *block_floats = dp->items * (long)dp->n * dp->n;
+  *partial_floats = dp->items * 2L * dp->n;
+  return VIE_OK;
+}
+
+vie_status symv3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const double *g, const float *blocks,
+                       float *s, float *partial, double *y, int device, cudaStream_t st) {
+  const int n = dp.n;
+  const long N = (long)n * n * n;
+  DevProps prop;
+  VIE_TRY(get_dev_props(device, &prop));
+  k_symv3_source<<<(int)std::min((N + 255) / 256, 1024L), 256, 0, st>>>(N, op, sigma_s, g, s);
+  VIE_CHECK_LAUNCH("k_symv3_source");
+  const long ctas = std::min((dp.items + kSymvWarps3 - 1) / kSymvWarps3, 8L * prop.multiProcessorCount);
+  k_symv3_blocks<<<(int)ctas, 32 * kSymvWarps3, 0, st>>>(n, blocks, s, dp.ioff, dp.iqd, dp.nq, partial);
+  VIE_CHECK_LAUNCH("k_symv3_blocks");
+  k_symv3_reduce<<<n * n, 32 * kSymvWarps3, 0, st>>>(n, op, partial, dp.ioff, dp.iqd, dp.nq, g, y);
+  VIE_CHECK_LAUNCH("k_symv3_reduce");
+  return VIE_OK;
 }
 
 }  // namespace vie

@@ -367,8 +367,10 @@ vie_status apply_dev(vie_handle *h, int op, const double *g, double *y, cudaStre
   }
   if (h->asm_mode == VIE_OPERATOR_SYM32) {
     if (timed) VIE_CUDA(cudaEventRecord(ev->e[1], st));
-    vie_status s = symv_apply(h->n, op, h->sig_s, g, (const float *)h->kmat, (float *)h->src, h->sym_partial, y,
-                              h->device, st);
+    vie_status s = h->dim == 3 ? symv3_apply(h->disp3, op, h->sig_s, g, (const float *)h->kmat, (float *)h->src,
+                                             h->sym_partial, y, h->device, st)
+                               : symv_apply(h->n, op, h->sig_s, g, (const float *)h->kmat, (float *)h->src,
+                                            h->sym_partial, y, h->device, st);
     if (s != VIE_OK) return s;
     if (timed) {
       VIE_CUDA(cudaEventRecord(ev->e[2], st));
@@ -1125,6 +1127,25 @@ static vie_status assemble_impl(vie_handle *h, int mode, int order, void *stream
       fmm_release(&h->fmm);
       return s;
     }
+    h->asm_mode = mode;
+    return VIE_OK;
+  }
+  if (mode == VIE_OPERATOR_SYM32 && h->dim == 3) {
+    // A in the symmetric blocks of grid-line pairs: the 3D pair weights, expanded
+    if (h->use_kernel != VIE_KERNEL_DISPLACEMENT || !h->disp3.usable || h->opts.disc != VIE_DISC_MIII) {
+      set_error("vie_assemble: VIE_OPERATOR_SYM32 in 3D needs the 3D displacement kernel (FP32 tiles, S = 64, "
+                "n <= 32)");
+      return VIE_ERR_UNSUPPORTED;
+    }
+    long bf = 0, pf = 0;
+    vie_status s = disp3_sym_sizes(&h->disp3, h->device, &bf, &pf);
+    if (s != VIE_OK) return s;
+    if (!reuse) VIE_CUDA(vie_malloc(&h->kmat, sizeof(float) * (size_t)bf));
+    if (!h->sym_partial) VIE_CUDA(vie_malloc((void **)&h->sym_partial, sizeof(float) * (size_t)pf));
+    const double hh = 1.0 / h->n;
+    s = disp3_assemble(&h->disp3, (float)(hh / h->opts.steps * 1.4426950408889634), (float)(hh / (4.0 * kPi)),
+                       h->sig_s, h->diag, 0, (float *)h->kmat, nullptr, nullptr, h->device, st);
+    if (s != VIE_OK) return s;
     h->asm_mode = mode;
     return VIE_OK;
   }

@@ -208,6 +208,7 @@ struct DispPlan3 {
   // dense assembly from the stored pair weights (built on first use)
   const void *kernel_store = nullptr;
   int grid_store = 0, nq = 0;
+  long items = 0;              // expansion items: (line displacement, target line) pairs
   long stored = 0;             // unordered pairs N (N - 1) / 2
   long long *doff = nullptr;   // per D of the half space: its first stored weight
   int *ioff = nullptr, *iqd = nullptr;  // expansion items per line displacement
@@ -219,9 +220,15 @@ vie_status disp3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const
                        float *src, float tau_scale2, float wcoef, double *y, cudaEvent_t mid0, cudaEvent_t mid1,
                        cudaStream_t st);
 // K (row-major N x ldk, FP32 k32 or BF16 khi + klo) from the 3D displacement
-// kernel's march: every unordered pair's weight stored once, then expanded
+// kernel's march: every unordered pair's weight stored once, then expanded;
+// ldk = 0: A in the symmetric blocks of grid-line pairs instead (into k32)
 vie_status disp3_assemble(DispPlan3 *dp, float tau_scale2, float wcoef, const double *sigma_s, const double *diag,
                           long ldk, float *k32, void *khi, void *klo, int device, cudaStream_t st);
+// floats of the 3D symmetric blocks and of their row/column-sum partials
+vie_status disp3_sym_sizes(DispPlan3 *dp, int device, long *block_floats, long *partial_floats);
+// y = op(A s) from the 3D symmetric blocks (s: FP32 scratch of N floats)
+vie_status symv3_apply(const DispPlan3 &dp, int op, const double *sigma_s, const double *g, const float *blocks,
+                       float *s, float *partial, double *y, int device, cudaStream_t st);
 
 size_t disp_smem_bytes(int n, int R);  // shared lattice bytes at stack depth R
 bool disp_expand_fits(int n, int device);  // k_expand_pairs has room for the grid (n <= 169)

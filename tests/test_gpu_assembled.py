@@ -128,8 +128,11 @@ def test_pairs32_switches_with_other_modes():
 @pytest.mark.parametrize("case", ["3d", "symmetric", "too_large"])
 def test_pairs32_unsupported_without_the_displacement_kernel(case, mode):
     if case == "3d":
+        # the pair weights are 2D only; the 3D symmetric blocks come from the 3D
+        # displacement kernel, so a handle on the tile-pair kernel has none
         m = V.heterogeneous_3d(n=5)
-        h = P.vie_create(3, 5, m.sigma_t, m.sigma_s)
+        kernel = P.VIE_KERNEL_SYMMETRIC if mode == P.VIE_OPERATOR_SYM32 else P.VIE_KERNEL_AUTO
+        h = P.vie_create(3, 5, m.sigma_t, m.sigma_s, kernel=kernel)
     elif case == "symmetric":
         m = V.heterogeneous_2d(n=16)
         h = P.vie_create(2, 16, m.sigma_t, m.sigma_s, kernel=P.VIE_KERNEL_SYMMETRIC)

@@ -22,7 +22,7 @@ def _apply(h, op, G, nrhs):
     return host(y).reshape(nrhs, -1)
 
 
-@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3])
+@pytest.mark.parametrize("mode", [P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_SYM32])
 @pytest.mark.parametrize("n", [2, 3, 5, 8, 11])
 def test_3d_assembled_all_rows_against_oracle_k(mode, n):
     m = V.heterogeneous_3d(n=n, seed=300 + n)
@@ -60,6 +60,13 @@ def test_3d_displacement_assembly_matches_tile_pair_assembly(n):
     for r in range(2):
         assert rel_l2(yd[r], yt[r]) < TOL, r
         assert rel_l2(yd[r], otf[r]) < 2e-6, r   # the same weights, summed in another order
+    # the symmetric blocks of grid-line pairs: the same weights, half the storage
+    P.vie_assemble(hd, P.VIE_OPERATOR_SYM32)
+    ys = _apply(hd, P.VIE_OP_K_SIGMA_S, G, 2)
+    for r in range(2):
+        assert rel_l2(ys[r], yd[r]) < 2e-6, r
+    ys2 = _apply(hd, P.VIE_OP_K_SIGMA_S, G, 2)
+    np.testing.assert_array_equal(ys2, ys)  # fixed summation order
     P.vie_destroy(hd)
     P.vie_destroy(ht)
 
@@ -74,7 +81,7 @@ def test_config3_assembled_solve_sampled_oracle_residual():
     f = dev(m.f)
     U0 = torch.empty(m.N, dtype=torch.float64, device="cuda:0")
     P.vie_solve_gmres(h, f, U0, rtol=1e-6)
-    for mode in (P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3):
+    for mode in (P.VIE_OPERATOR_FP32, P.VIE_OPERATOR_BF16X3, P.VIE_OPERATOR_SYM32):
         P.vie_assemble(h, mode)
         U = torch.empty_like(U0)
         rep = P.vie_solve_gmres(h, f, U, rtol=1e-6)
